@@ -1,0 +1,98 @@
+"""Continuum closed forms for Gaussian densities (oracle tier O3).
+
+  3D Coulomb, rho = exp(-|x|^2/s^2):      Eq. (DensGaus) first line (erf form).
+  3D Coulomb, rho = exp(-sum x_a^2/a_a^2): generalisation of Eq. (DensGaus) second
+      line to three widths (substitute s = sigma^2 t there):
+      u = (a1 a2 a3 / 4) int_0^inf exp(-sum x_a^2/(a_a^2+s)) / sqrt(prod (a_a^2+s)) ds.
+  3D dipolar (axis n), reading U-hat = 3(n.k)^2/|k|^2 - 1:  u = -rho - 3 d_nn u_Cou,
+      d_nn taken under the integral sign.
+  2D Coulomb, rho = exp(-|x|^2/s^2):      Eq. (2.5D-clb-exact) first line (I0 form, via i0e).
+  2D Poisson, rho = exp(-|x|^2/s^2):      Eq. (eg-2d-Exact) (E1 form).
+Sums of shifted Gaussians follow by superposition.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import integrate, special
+
+EULER_GAMMA = 0.57721566490153286061
+
+
+def coulomb3d_iso(r, s):
+    """sigma^3 sqrt(pi) erf(r/sigma) / (4 r); value sigma^2/2 at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    nz = r > 0
+    out[nz] = s ** 3 * math.sqrt(math.pi) * special.erf(r[nz] / s) / (4.0 * r[nz])
+    out[~nz] = 0.5 * s * s
+    return out
+
+
+def _tri_integrand_t(t, X, a, aref, dn=None):
+    """Integrand of the triaxial formula after s = aref^2 (1/t^2 - 1), t in (0,1]:
+    ds / sqrt(prod(a^2+s)) = 2 aref^2 dt / prod sqrt(aref^2 + (a^2 - aref^2) t^2)."""
+    c = [(aref * aref + (ai * ai - aref * aref) * t * t) for ai in a]   # (a^2+s) t^2
+    q = sum(x * x * t * t / ci for x, ci in zip(X, c))
+    base = 2.0 * aref * aref / math.sqrt(c[0] * c[1] * c[2]) if np.isscalar(t) else \
+        2.0 * aref * aref / np.sqrt(c[0] * c[1] * c[2])
+    e = np.exp(-q)
+    if dn is None:
+        return base * e
+    # d_nn exp(-sum x^2/(a^2+s)) with a^2+s = c/t^2
+    g = sum(nv * 2.0 * x * t * t / ci for nv, x, ci in zip(dn, X, c))
+    lap = sum(nv * nv * 2.0 * t * t / ci for nv, ci in zip(dn, c))
+    return base * e * (g * g - lap)
+
+
+def coulomb3d_triaxial(X, Y, Z, a, nq=600, dn=None):
+    """Triaxial formula by Gauss-Legendre in t (vectorised over points).
+    With dn given, returns d_nn of the potential instead."""
+    aref = min(a)
+    t, wt = np.polynomial.legendre.leggauss(nq)
+    t = 0.5 * (t + 1.0)
+    wt = 0.5 * wt
+    X = np.asarray(X, dtype=np.float64)
+    out = np.zeros_like(X)
+    pre = a[0] * a[1] * a[2] / 4.0
+    for ti, wi in zip(t, wt):
+        out += wi * _tri_integrand_t(ti, (X, Y, Z), a, aref, dn)
+    return pre * out
+
+
+def coulomb3d_triaxial_quad(x, a, dn=None):
+    """Same integral at one point by adaptive quadrature (scipy.integrate.quad)."""
+    aref = min(a)
+    f = lambda t: _tri_integrand_t(t, x, a, aref, dn)
+    val, _ = integrate.quad(f, 0.0, 1.0, epsabs=1e-15, epsrel=1e-13, limit=400)
+    return a[0] * a[1] * a[2] / 4.0 * val
+
+
+def dipole3d_triaxial(X, Y, Z, a, axis=(0.0, 0.0, 1.0), nq=600):
+    """u_dip = -rho - 3 d_nn u_Cou for rho = exp(-sum x^2/a^2)."""
+    nv = np.asarray(axis, dtype=np.float64)
+    nv = nv / np.linalg.norm(nv)
+    rho = np.exp(-(X * X / a[0] ** 2 + Y * Y / a[1] ** 2 + Z * Z / a[2] ** 2))
+    return -rho - 3.0 * coulomb3d_triaxial(X, Y, Z, a, nq=nq, dn=tuple(nv))
+
+
+def coulomb2d_iso(r, s):
+    """(sqrt(pi) s / 2) I0(r^2/2s^2) exp(-r^2/2s^2)."""
+    r = np.asarray(r, dtype=np.float64)
+    return 0.5 * math.sqrt(math.pi) * s * special.i0e(r * r / (2.0 * s * s))
+
+
+def poisson2d_iso(r, s):
+    """-(s^2/4) [E1(r^2/s^2) + 2 ln r]; value (s^2/4)(gamma - 2 ln s) at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    nz = r > 0
+    out[nz] = -0.25 * s * s * (special.exp1(r[nz] ** 2 / (s * s)) + 2.0 * np.log(r[nz]))
+    out[~nz] = 0.25 * s * s * (EULER_GAMMA - 2.0 * math.log(s))
+    return out
+
+
+def rel_linf(u, ref):
+    """Relative L-infinity error e_h of Eq. (error_infty)."""
+    return float(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))

@@ -1,0 +1,91 @@
+"""Pins for the oracle's gradient flow (Sec. 3) and time splitting (Sec. 4) on the CPU."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import load_golden
+from oracle import gf, potential, quadrature, ts
+
+
+@pytest.fixture(scope="module")
+def gs_setup():
+    # Example 3.1 trap V = (x^2 + y^2 + 4 z^2)/2; box [-5,5]^3 (the ground state is
+    # below 1e-10 there), h = 1/3: spectrally converged to the printed digits
+    g = W.cube(30, 5.0)
+    gam = (1.0, 1.0, 2.0)
+    V = W.harmonic_trap(g, gam)
+    P = math.pi / g.h[0]
+    op = potential.ConvolutionOperator(g, "coulomb3d", P)
+    return g, gam, V, op
+
+
+def test_gs_energies_match_paper_table(gs_setup):
+    g, gam, V, op = gs_setup
+    rows = {float(r[0]): r[1:] for r in load_golden("paper_gs_energies_3d_coulomb.txt")}
+    beta = 1.0
+    G = gf.GradientFlow(g, V, beta, op, tau=1e-2)
+    phi, nsteps, change = G.solve(W.normalized_gaussian_start(g, gam), eps0=1e-8)
+    e = G.energies(phi)
+    # each printed value must agree to one unit in its last printed place
+    # (the table truncates: E_g = 2.035163 is printed 2.0351)
+    for key, txt in zip(("E", "mu", "Ekin", "Epot", "Eint"), rows[beta]):
+        mant, _, ex = txt.upper().partition("E")
+        ulp = 10.0 ** (-len(mant.split(".")[1]) + (int(ex) if ex else 0))
+        assert abs(e[key] - float(txt)) < ulp, (key, e[key], txt)
+    # virial identity for 3D Coulomb: 2 E_kin - 2 E_pot + E_int = 0 (Sec. 3.2)
+    assert abs(2 * e["Ekin"] - 2 * e["Epot"] + e["Eint"]) < 1e-6
+    assert abs(float(np.prod(g.h)) * np.sum(phi ** 2) - 1.0) < 1e-13
+
+
+def test_gf_energy_decreases_and_evaluators_agree(gs_setup):
+    g, gam, V, op = gs_setup
+    P = math.pi / g.h[0]
+    direct = lambda rho: potential.eval_nufft(rho, g, "coulomb3d", P, tol=1e-13)
+    G1 = gf.GradientFlow(g, V, 5.0, op, tau=1e-2)
+    G2 = gf.GradientFlow(g, V, 5.0, direct, tau=1e-2)
+    phi = W.normalized_gaussian_start(g, (1.3, 0.8, 1.5))
+    p1, c1 = G1.step(phi)
+    p2, c2 = G2.step(phi)
+    assert np.max(np.abs(p1 - p2)) < 1e-11
+    E = [G1.energies(phi)["E"]]
+    for _ in range(5):
+        phi, _ = G1.step(phi)
+        E.append(G1.energies(phi)["E"])
+    assert all(b < a for a, b in zip(E, E[1:]))
+
+
+@pytest.fixture(scope="module")
+def ts_setup():
+    g = W.cube(32, 8.0, 2)
+    V = W.harmonic_trap(g, (1.0, 1.0))
+    op = potential.ConvolutionOperator(g, "coulomb2d", math.pi / g.h[0])
+    psi0 = W.gaussian(g, [math.sqrt(2.0)] * 2, center=(0.5, -0.3)).astype(np.complex128)
+    return g, V, op, psi0
+
+
+def _run(T, V, op, g, psi0, tau, order):
+    S = ts.TimeSplitting(g, V, 5.0, op)
+    psi = psi0.copy()
+    for _ in range(int(round(0.2 / tau))):
+        psi = S.step(psi, tau, order)
+    return S, psi
+
+
+def test_ts_mass_conserved(ts_setup):
+    g, V, op, psi0 = ts_setup
+    S, psi = _run(None, V, op, g, psi0, 0.02, 2)
+    assert abs(S.mass(psi) - S.mass(psi0)) < 1e-13 * S.mass(psi0)
+
+
+@pytest.mark.parametrize("order,ratio", [(2, 4.0), (4, 16.0)])
+def test_ts_temporal_order(ts_setup, order, ratio):
+    g, V, op, psi0 = ts_setup
+    _, ref = _run(None, V, op, g, psi0, 0.2 / 128, order)
+    errs = []
+    for tau in (0.2 / 4, 0.2 / 8, 0.2 / 16):
+        _, p = _run(None, V, op, g, psi0, tau, order)
+        errs.append(np.max(np.abs(p - ref)))
+    r = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(0.7 * ratio < x < 1.4 * ratio for x in r), (errs, r)
