@@ -1,0 +1,155 @@
+/*
+ * nlpot — NUFFT evaluation of nonlocal potentials phi = U * rho on one GB300 (sm_103a).
+ *
+ * Method: Bao, Jiang, Tang & Zhang, "Computing the ground state and dynamics of the
+ * nonlinear Schroedinger equation with nonlocal interactions via the nonuniform FFT"
+ * (arXiv:1410.3584).  Given rho on a uniform grid, phi = U * rho (Sec. 2, Eq. (nonlocal53))
+ * is evaluated in Fourier space on a spherical (3D) or polar (2D) quadrature grid whose
+ * Jacobian cancels the singularity of U-hat (Sec. 2.1, Eq. (ifft)): a type-2 NUFFT gives
+ * rho-hat at the nodes, each node is scaled by its weight times |k|^{d-1} U-hat(k), and a
+ * type-1 NUFFT returns phi to the grid.  The 2D Laplace kernel 1/|k|^2 uses the paper's
+ * Gaussian subtraction (Sec. 2.2, Algorithm 1).  The ground-state step is the backward-Euler
+ * normalized gradient flow (Sec. 3.1) and the dynamics step is time splitting (Sec. 4.1).
+ *
+ * Conventions for every entry point:
+ *  - Grid: per axis a, n[a] points on [-L[a], L[a]), h[a] = 2 L[a] / n[a],
+ *    x_m = -L + m h (m = 0..n-1; the origin is m = n/2).  Arrays are C order with the last
+ *    axis fastest: a[i][j][k] = f(x_i, y_j, z_k).
+ *  - Real arrays hold the plan precision (double for NLP_FP64, float for NLP_FP32); complex
+ *    arrays are interleaved (re, im) pairs of that type.
+ *  - Pointers named *_dev are device pointers owned by the caller; the plan owns every
+ *    workspace it allocates and frees it in nlp_plan_destroy.  *_host pointers are host
+ *    memory owned by the caller.
+ *  - All device work is enqueued on the plan's stream (the stream given at creation;
+ *    NULL = legacy default stream).  Calls return once the work is enqueued unless stated.
+ *  - Errors are return codes; nothing throws across this boundary.  Invalid arguments
+ *    are rejected with NLP_ERR_INVALID_ARG before any launch.  After NLP_ERR_CUDA the
+ *    plan should be destroyed.
+ *  - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef NLPOT_H
+#define NLPOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NLP_OK = 0,
+    NLP_ERR_INVALID_ARG = 1,
+    NLP_ERR_UNSUPPORTED = 2,
+    NLP_ERR_OOM = 3,
+    NLP_ERR_CUDA = 4,
+    NLP_ERR_TIMEOUT = 5,
+    NLP_ERR_DIVERGED = 6,
+    NLP_ERR_NOT_CONVERGED = 7
+} nlp_status;
+
+/* Interaction kernels (Sec. 1, Eqs. (Kernal), (Kernal21d)):
+ *   NLP_COULOMB_3D  U = 1/(4 pi |x|),      U-hat = 1/|k|^2
+ *   NLP_DIPOLE_3D   U-hat = 3 (n.k)^2/|k|^2 - 1 for dipole axis n (the paper names the
+ *                   dipolar kernel without writing it; this is the standard form)
+ *   NLP_COULOMB_2D  U = 1/(2 pi |x|),      U-hat = 1/|k|
+ *   NLP_POISSON_2D  U = -ln|x| / (2 pi),   U-hat = 1/|k|^2 (Algorithm 1)                  */
+typedef enum { NLP_COULOMB_3D = 0, NLP_DIPOLE_3D = 1, NLP_COULOMB_2D = 2, NLP_POISSON_2D = 3 } nlp_kernel;
+
+typedef enum { NLP_FP64 = 0, NLP_FP32 = 1 } nlp_precision;
+
+typedef struct {
+    int dim;        /* 2 or 3 (must match the kernel) */
+    int n[3];       /* points per axis: even, 8..1024, of the form 2^a 3^b 5^c; 3D: n <= 256 */
+    double L[3];    /* half-widths, > 0 */
+} nlp_grid;
+
+typedef struct {
+    double kmax;            /* truncation radius P of the Fourier ball (Sec. 2.1); 0 -> pi / max h */
+    int n_r, n_theta, n_phi;/* quadrature counts (radial GL, GL in cos(theta), trapezoid in phi);
+                               0 -> n_r = n_theta = roundup16(P R/2 + 16), n_phi = roundup16(P Rp + 32)
+                               with R, Rp the half-diagonals of the box and of its first two axes.
+                               n_theta and n_phi must be even (k -> -k symmetry). */
+    double dipole_axis[3];  /* NLP_DIPOLE_3D: unit vector (normalised here; zero vector -> z) */
+    double nufft_tol;       /* NUFFT tolerance, 1e-14..1e-2; 0 -> 1e-12 (FP64) / 1e-6 (FP32) */
+    int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 4, 8 or 16 */
+    int reserved[7];        /* must be zero */
+} nlp_opts;
+
+typedef struct nlp_plan_s *nlp_plan;
+
+/* Plan facts for tests and roofline accounting. */
+typedef struct {
+    int dim, kernel, precision;
+    int n[3], nf[3];        /* grid and oversampled (2n) fine grid */
+    int width;              /* spreading-function width w (fine cells) */
+    double beta_es;         /* shape parameter of the exp-of-semicircle function */
+    double kmax;            /* P */
+    int n_r, n_theta, n_phi;
+    int64_t nodes_total;    /* full symmetric node count M */
+    int64_t nodes_half;     /* nodes processed (k -> -k half) */
+    int64_t tiles, chunks;  /* non-empty tiles; work items of the interp/spread kernel */
+    int tile;
+    size_t workspace_bytes; /* device memory owned by the plan */
+    double sigma_poisson;   /* NLP_POISSON_2D: width of the auxiliary Gaussian */
+} nlp_plan_info;
+
+/* Create a plan: quadrature nodes and weights (FP64), their binning by fine-grid tile,
+ * the spreading-function tables, FFT twiddles and all workspace.  Synchronous.
+ * stream: a cudaStream_t (NULL = legacy default stream).  opts may be NULL (defaults). */
+nlp_status nlp_plan_create(const nlp_grid *grid, nlp_kernel kernel, nlp_precision prec,
+                           const nlp_opts *opts, void *stream, nlp_plan *out);
+
+void nlp_plan_destroy(nlp_plan plan);
+
+nlp_status nlp_plan_get_info(nlp_plan plan, nlp_plan_info *out);
+
+/* phi = U * rho (Sec. 2.1 Eq. (ifft); Sec. 2.2 Algorithm 1 for NLP_POISSON_2D).
+ * rho_dev, phi_dev: device arrays of prod(n) reals in the plan precision (may not alias).
+ * Steps: deconvolve + zero-pad + forward FFT (type 2), interpolate at the nodes, scale by
+ * the weights and |k|^{d-1} U-hat, spread (type 1), inverse FFT, deconvolve + crop. */
+nlp_status nlp_eval_potential(nlp_plan plan, const void *rho_dev, void *phi_dev);
+
+/* Same operation on HOST arrays: copies rho to plan-owned device memory, evaluates, copies
+ * phi back and synchronizes the plan stream before returning. */
+nlp_status nlp_eval_potential_host(nlp_plan plan, const void *rho_host, void *phi_host);
+
+/* One step of the backward-Euler normalized gradient flow (Sec. 3.1, Eqs. (gf-eq2)-(gffg33)):
+ *   b = V + g |phi^n|^2 + beta (U * |phi^n|^2),
+ *   solve (1/tau - Delta/2 + b) phi^(1) = phi^n / tau, phi^{n+1} = phi^(1)/||phi^(1)||.
+ * The linear solve (omitted in the paper) is the stabilised Fourier fixed point
+ *   (1/tau + alpha + |mu|^2/2) phi^(m+1) = F[phi^n/tau + (alpha - b) phi^(m)],
+ *   alpha = (max b + min b)/2, iterated until max|phi^(m+1) - phi^(m)| <= inner_tol or
+ *   max_inner iterations (NLP_ERR_NOT_CONVERGED if the cap is hit).
+ * phi_dev: real, normalised (h^d sum phi^2 = 1), updated in place; V_dev: real trap.
+ * Norms, min/max and energies are reduced in FP64 for both precisions.
+ * Outputs (host, may be NULL): *max_change = max|phi^{n+1} - phi^n| / tau (stopping rule of
+ * Sec. 3.2), *inner_iters, energies[5] = {E, E_kin, E_pot, E_int, mu} of phi^{n+1}.
+ * Synchronizes the plan stream.  NLP_ERR_DIVERGED if a non-finite value appears.
+ * Not available for NLP_POISSON_2D plans (NLP_ERR_UNSUPPORTED). */
+nlp_status nlp_gf_step(nlp_plan plan, void *phi_dev, const void *V_dev, double beta, double g,
+                       double tau, double inner_tol, int max_inner, double *max_change,
+                       int *inner_iters, double *energies);
+
+/* Energies {E, E_kin, E_pot, E_int, mu} of a real phi (Sec. 3.2), FP64 reductions.
+ * Synchronizes the plan stream. */
+nlp_status nlp_energies(nlp_plan plan, const void *phi_dev, const void *V_dev, double beta,
+                        double g, double *energies);
+
+/* One time step of the time-splitting Fourier pseudospectral method (Sec. 4.1):
+ * order 2: K(tau/2) P(tau) K(tau/2) with the kinetic flow K solved exactly in Fourier space
+ * and P(s): psi <- exp(-i (V + g|psi|^2 + beta U*|psi|^2) s) psi (Eq. (sps-eq68));
+ * order 4: Yoshida's composition of three order-2 steps.  psi_dev: complex, in place. */
+nlp_status nlp_ts_step(nlp_plan plan, void *psi_dev, const void *V_dev, double beta, double g,
+                       double tau, int order);
+
+const char *nlp_status_string(nlp_status s);
+
+/* Library version string. */
+const char *nlp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLPOT_H */

@@ -1,0 +1,222 @@
+"""ctypes binding of libnlpot (include/nlpot.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  The functions carry the C-ABI names;
+tensors are torch CUDA tensors (device memory and streams only) or numpy arrays for
+the *_host entry point.  If the library is missing the import of this module fails
+with an error that says how to build it: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libnlpot.so")
+
+NLP_OK, NLP_ERR_INVALID_ARG, NLP_ERR_UNSUPPORTED, NLP_ERR_OOM = 0, 1, 2, 3
+NLP_ERR_CUDA, NLP_ERR_TIMEOUT, NLP_ERR_DIVERGED, NLP_ERR_NOT_CONVERGED = 4, 5, 6, 7
+KERNELS = {"coulomb3d": 0, "dipole3d": 1, "coulomb2d": 2, "poisson2d": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+
+class nlp_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3)]
+
+
+class nlp_opts(ctypes.Structure):
+    _fields_ = [("kmax", ctypes.c_double), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
+                ("n_phi", ctypes.c_int), ("dipole_axis", ctypes.c_double * 3), ("nufft_tol", ctypes.c_double),
+                ("tile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class nlp_plan_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n", ctypes.c_int * 3), ("nf", ctypes.c_int * 3), ("width", ctypes.c_int),
+                ("beta_es", ctypes.c_double), ("kmax", ctypes.c_double), ("n_r", ctypes.c_int),
+                ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int), ("nodes_total", ctypes.c_int64),
+                ("nodes_half", ctypes.c_int64), ("tiles", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                ("tile", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t), ("sigma_poisson", ctypes.c_double)]
+
+
+class NlpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, nlp_status_string(status), status))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libnlpot.so not built (%s); run __graft_entry__.build() or "
+                          "python paper_1410_3584_gb300/build.py" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    sig = {
+        "nlp_plan_create": ([ctypes.POINTER(nlp_grid), I, I, ctypes.POINTER(nlp_opts), P, ctypes.POINTER(P)], I),
+        "nlp_plan_destroy": ([P], None),
+        "nlp_plan_get_info": ([P, ctypes.POINTER(nlp_plan_info)], I),
+        "nlp_eval_potential": ([P, P, P], I),
+        "nlp_eval_potential_host": ([P, P, P], I),
+        "nlp_gf_step": ([P, P, P, D, D, D, D, I, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
+        "nlp_energies": ([P, P, P, D, D, ctypes.POINTER(D)], I),
+        "nlp_ts_step": ([P, P, P, D, D, D, I], I),
+        "nlp_status_string": ([I], ctypes.c_char_p),
+        "nlp_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def nlp_status_string(status: int) -> str:
+    return _lib.nlp_status_string(int(status)).decode()
+
+
+def nlp_version() -> str:
+    return _lib.nlp_version().decode()
+
+
+def _check(st: int, where: str):
+    if st != NLP_OK:
+        raise NlpError(st, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.0, counts=None,
+                    dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, stream=None):
+    """Create a plan; returns an opaque handle (ctypes.c_void_p).  See nlpot.h."""
+    g = nlp_grid()
+    g.dim = len(n)
+    for a in range(len(n)):
+        g.n[a] = int(n[a])
+        g.L[a] = float(L[a])
+    o = nlp_opts()
+    o.kmax = float(kmax)
+    if counts is not None:
+        if len(counts) == 3:
+            o.n_r, o.n_theta, o.n_phi = (int(c) for c in counts)
+        else:
+            o.n_r, o.n_phi = (int(c) for c in counts)
+    for a in range(3):
+        o.dipole_axis[a] = float(dipole_axis[a])
+    o.nufft_tol = float(tol)
+    o.tile = int(tile)
+    h = ctypes.c_void_p()
+    _check(_lib.nlp_plan_create(ctypes.byref(g), KERNELS[kernel], PRECISIONS[precision], ctypes.byref(o),
+                                _stream_handle(stream), ctypes.byref(h)), "nlp_plan_create")
+    return h
+
+
+def nlp_plan_destroy(plan):
+    _lib.nlp_plan_destroy(plan)
+
+
+def nlp_plan_get_info(plan) -> dict:
+    info = nlp_plan_info()
+    _check(_lib.nlp_plan_get_info(plan, ctypes.byref(info)), "nlp_plan_get_info")
+    out = {}
+    for name, _ in nlp_plan_info._fields_:
+        v = getattr(info, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, dtype, numel, name):
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype or t.numel() != numel:
+        raise ValueError("%s: need a contiguous CUDA tensor of %d %s" % (name, numel, dtype))
+
+
+def nlp_eval_potential(plan, rho, phi):
+    """phi <- U * rho (device tensors of the plan precision)."""
+    _check(_lib.nlp_eval_potential(plan, _ptr(rho), _ptr(phi)), "nlp_eval_potential")
+
+
+def nlp_eval_potential_host(plan, rho: np.ndarray, phi: np.ndarray):
+    """Host arrays (C-contiguous, plan precision); copies in and out inside the call."""
+    assert rho.flags["C_CONTIGUOUS"] and phi.flags["C_CONTIGUOUS"]
+    _check(_lib.nlp_eval_potential_host(plan, rho.ctypes.data_as(ctypes.c_void_p),
+                                        phi.ctypes.data_as(ctypes.c_void_p)), "nlp_eval_potential_host")
+
+
+def nlp_gf_step(plan, phi, V, beta: float, g: float = 0.0, tau: float = 1e-2, inner_tol: float = 1e-12,
+                max_inner: int = 1000, energies: bool = False, raise_on_nonconv: bool = True):
+    """One gradient-flow step in place; returns (max_change, inner_iters, energies or None, status)."""
+    ch = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    E = (ctypes.c_double * 5)()
+    st = _lib.nlp_gf_step(plan, _ptr(phi), _ptr(V), float(beta), float(g), float(tau), float(inner_tol),
+                          int(max_inner), ctypes.byref(ch), ctypes.byref(it), E if energies else None)
+    if st != NLP_OK and not (st == NLP_ERR_NOT_CONVERGED and not raise_on_nonconv):
+        raise NlpError(st, "nlp_gf_step")
+    en = None
+    if energies:
+        en = dict(zip(("E", "Ekin", "Epot", "Eint", "mu"), list(E)))
+    return ch.value, it.value, en, st
+
+
+def nlp_energies(plan, phi, V, beta: float, g: float = 0.0) -> dict:
+    E = (ctypes.c_double * 5)()
+    _check(_lib.nlp_energies(plan, _ptr(phi), _ptr(V), float(beta), float(g), E), "nlp_energies")
+    return dict(zip(("E", "Ekin", "Epot", "Eint", "mu"), list(E)))
+
+
+def nlp_ts_step(plan, psi, V, beta: float, g: float = 0.0, tau: float = 1e-3, order: int = 2):
+    """One time-splitting step in place on complex psi (torch complex tensor or interleaved view)."""
+    _check(_lib.nlp_ts_step(plan, _ptr(psi), _ptr(V), float(beta), float(g), float(tau), int(order)),
+           "nlp_ts_step")
+
+
+class Plan:
+    """Owning wrapper: Plan(n, L, kernel, precision, ...) ... .close()."""
+
+    def __init__(self, n, L, kernel, precision="fp64", **kw):
+        self.n, self.L, self.kernel, self.precision = tuple(n), tuple(L), kernel, precision
+        self.handle = nlp_plan_create(n, L, kernel, precision, **kw)
+        self.info = nlp_plan_get_info(self.handle)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def eval(self, rho, phi=None):
+        import torch
+        if phi is None:
+            phi = torch.empty_like(rho)
+        _check_tensor(rho, self.torch_dtype, int(np.prod(self.n)), "rho")
+        _check_tensor(phi, self.torch_dtype, int(np.prod(self.n)), "phi")
+        nlp_eval_potential(self.handle, rho, phi)
+        return phi
+
+    def close(self):
+        if self.handle:
+            nlp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

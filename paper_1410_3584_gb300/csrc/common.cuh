@@ -1,0 +1,81 @@
+// Shared definitions of the nlpot CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/nlpot.h"
+
+namespace nlp {
+
+// ---------------------------------------------------------------- complex arithmetic
+template <typename T> struct cpx;
+template <> struct __align__(8) cpx<float> { float x, y; };
+template <> struct __align__(16) cpx<double> { double x, y; };
+
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> conj(cpx<T> a) { return mk<T>(a.x, -a.y); }
+// multiply by +i (s = +1) or -i (s = -1)
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mul_i(cpx<T> a, int s) {
+    return s > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxRadices = 16;     // FFT stages per length (N <= 2048 = 4^5 * 2)
+constexpr int kMaxFftLen = 2048;
+constexpr int kMaxWidth = 16;       // spreading-function width
+
+// One FFT length: its radix sequence and a twiddle table exp(-2 pi i k / N), k < N.
+template <typename T> struct FftLen {
+    int N;
+    int nrad;
+    int rad[kMaxRadices];
+    const cpx<T> *tw;   // device
+};
+
+// Interp/spread work item: one chunk of the nodes of one tile.
+struct Chunk {
+    int bx, by, bz;     // unwrapped fine-grid cell of the tile origin
+    int j0, j1;         // node range in the sorted node arrays
+};
+
+// Device pointers and sizes of one plan, in the plan precision T.
+template <typename T> struct DevPlan {
+    int dim;
+    int n[3];           // grid (dim 2: n[2] = 1, last axis is axis 1)
+    int nf[3];          // fine grid
+    int nh;             // half spectrum length along the last axis (nf_last/2 + 1)
+    int w;              // spreading width
+    T beta;             // ES shape
+    int T_tile[3];      // tile edge per axis (2D: T_tile[2] = 1)
+    FftLen<T> len[3];   // FFT lengths of the fine axes
+    const T *deconv[3]; // 1/psi-hat(i 2pi/nf) per axis, i = 0..n-1 (grid index order)
+    cpx<T> *F;          // forward spectrum, [nf0][nf1][nh] (3D) or [nf0][nh] (2D)
+    cpx<T> *G;          // spread target, same layout
+    // nodes, sorted by chunk: (delta_x, delta_y, delta_z, omega) and packed tile offsets
+    const T *nd;        // 4 per node
+    const uint32_t *no; // o_x | o_y << 8 | o_z << 16
+    const Chunk *chunks;
+    int64_t nchunks;
+    // 2D Poisson (Algorithm 1): per-node FP64 (kx, ky, |k|) in node order, device FP64
+    // moments {C0, M1x, M1y}, cell area and the auxiliary Gaussian width
+    const double *pois;
+    const double *mom;
+    double hvol;
+    double sigma;
+};
+
+}  // namespace nlp
+
+#define NLP_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return NLP_ERR_CUDA;        \
+    } while (0)

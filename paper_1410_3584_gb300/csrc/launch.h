@@ -1,0 +1,38 @@
+// Host-side launchers of the device kernels (one per kernel family).
+#pragma once
+#include "common.cuh"
+
+namespace nlp {
+
+// One strided C2C FFT pass (see k_fft_strided).
+struct StridedDesc {
+    int n_in, n_out;      // input / output windows (>= N means the whole line)
+    int64_t es;           // element stride along the transformed axis (complex units)
+    int ncol;             // contiguous columns per outer line
+    int nouter;           // outer lines
+    int64_t os;           // stride between outer lines
+    int outer_map_n;      // > 0: outer index o addresses line (o - outer_map_n/2) mod outer_map_N
+    int outer_map_N;
+};
+
+template <typename T> cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st);
+template <typename T> cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, int sign, T post, cudaStream_t st);
+
+// Fused interpolate -> scale -> spread over all node chunks (see spread.cu).
+template <typename T> cudaError_t launch_interp_spread(const DevPlan<T> &P, cudaStream_t st);
+template <typename T> size_t interp_spread_smem(const DevPlan<T> &P);
+
+// 2D Poisson (Algorithm 1) FP64 parts (see poisson2d.cu).  L, h: collapsed 3D view.
+template <typename T>
+cudaError_t launch_poisson_moments(const T *rho, const DevPlan<T> &P, const double *L, const double *h,
+                                   double *part, int nblocks, double *mom, cudaStream_t st);
+template <typename T> cudaError_t launch_poisson_origin(const DevPlan<T> &P, double *mom, cudaStream_t st);
+template <typename T>
+cudaError_t launch_poisson_u1(T *phi, const DevPlan<T> &P, const double *L, const double *h, cudaStream_t st);
+
+}  // namespace nlp

@@ -1,0 +1,430 @@
+// Plan construction (host): quadrature of Eq. (ifft) (Sec. 2.1), spreading-function
+// tables, node binning by fine-grid tile, FFT tables and workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "plan.h"
+
+namespace nlp {
+
+// ------------------------------------------------------------------ Gauss-Legendre
+// Nodes are the roots of the Legendre polynomial P_n, found by Newton's method from the
+// asymptotic guess cos(pi (i + 3/4)/(n + 1/2)); P_n and P_n' come from the three-term
+// recurrence (j P_j = (2j-1) x P_{j-1} - (j-1) P_{j-2}).  Weights 2 / ((1-x^2) P_n'(x)^2).
+static void legendre_pd(int n, double z, double *pn, double *dp) {
+    double pc = z, pm = 1.0;
+    for (int j = 2; j <= n; ++j) {
+        const double pj = ((2.0 * j - 1.0) * z * pc - (j - 1.0) * pm) / j;
+        pm = pc;
+        pc = pj;
+    }
+    *pn = (n == 0) ? 1.0 : pc;
+    *dp = n * (z * pc - pm) / (z * z - 1.0);
+}
+
+void gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double pn, dp;
+        for (int it = 0; it < 100; ++it) {
+            legendre_pd(n, z, &pn, &dp);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) <= 1e-16) break;
+        }
+        legendre_pd(n, z, &pn, &dp);
+        const double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = mid - half * z;      // roots come in +- pairs; ascending order
+        x[n - 1 - i] = mid + half * z;
+        w[i] = w[n - 1 - i] = half * wt;
+    }
+}
+
+// ------------------------------------------------------------------ spreading function
+// "Exponential of semicircle" (Barnett, Magland & af Klinteberg 2019), upsampling 2:
+// phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), w = ceil(log10(1/tol)) + 1, beta = 2.30 w.
+void es_params(double tol, int *w, double *beta) {
+    int ww = (int)std::ceil(std::log10(1.0 / tol)) + 1;
+    ww = std::max(2, std::min(ww, kMaxWidth));
+    *w = ww;
+    *beta = 2.30 * ww;
+}
+
+// psi-hat(xi) = int phi(z) cos(xi z) dz over |z| < w/2; with z = (w/2) sin(theta) the
+// integrand exp(beta (cos theta - 1)) cos(xi w/2 sin theta) cos theta is smooth on
+// [0, pi/2] and a 100-point Gauss-Legendre rule resolves it.
+double es_fourier(double xi, int w, double beta) {
+    static thread_local std::vector<double> gx, gw;
+    if (gx.empty()) gauss_legendre(100, 0.0, 0.5 * M_PI, gx, gw);
+    double s = 0.0;
+    for (size_t i = 0; i < gx.size(); ++i) {
+        const double th = gx[i];
+        s += gw[i] * std::exp(beta * (std::cos(th) - 1.0)) * std::cos(xi * 0.5 * w * std::sin(th)) * std::cos(th);
+    }
+    return w * s;
+}
+
+nlp_status alloc_dev(nlp_plan_s *p, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return NLP_OK;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return NLP_ERR_OOM;
+    }
+    p->allocs.push_back(*ptr);
+    p->bytes += bytes;
+    return NLP_OK;
+}
+
+static bool factor_radices(int N, int *rad, int *nrad) {
+    int k = 0;
+    while (N % 4 == 0 && k < kMaxRadices) { rad[k++] = 4; N /= 4; }
+    while (N % 2 == 0 && k < kMaxRadices) { rad[k++] = 2; N /= 2; }
+    while (N % 3 == 0 && k < kMaxRadices) { rad[k++] = 3; N /= 3; }
+    while (N % 5 == 0 && k < kMaxRadices) { rad[k++] = 5; N /= 5; }
+    *nrad = k;
+    return N == 1;
+}
+
+template <typename T> nlp_status make_fft_len(nlp_plan_s *p, int N, FftLen<T> *out) {
+    memset(out, 0, sizeof(*out));
+    out->N = N;
+    if (N == 1) return NLP_OK;
+    if (!factor_radices(N, out->rad, &out->nrad)) return NLP_ERR_UNSUPPORTED;
+    std::vector<cpx<T>> tw(N);
+    for (int k = 0; k < N; ++k) {
+        const double a = 2.0 * M_PI * (double)k / (double)N;
+        tw[k].x = (T)std::cos(a);
+        tw[k].y = (T)(-std::sin(a));
+    }
+    void *d = nullptr;
+    nlp_status s = alloc_dev(p, &d, sizeof(cpx<T>) * N);
+    if (s) return s;
+    if (cudaMemcpy(d, tw.data(), sizeof(cpx<T>) * N, cudaMemcpyHostToDevice) != cudaSuccess) return NLP_ERR_CUDA;
+    out->tw = (const cpx<T> *)d;
+    return NLP_OK;
+}
+template nlp_status make_fft_len<float>(nlp_plan_s *, int, FftLen<float> *);
+template nlp_status make_fft_len<double>(nlp_plan_s *, int, FftLen<double> *);
+
+static bool good_len(int n) {
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    while (n % 5 == 0) n /= 5;
+    return n == 1;
+}
+
+static int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Node record before conversion to the plan precision.
+struct HostNode {
+    double z[3];     // fine-grid coordinates (cells); axis 0 = 0 in 2D
+    double omega;    // h^d (2pi)^-d * quadrature weight * |k|^{d-1} U-hat
+    double k[2], r;  // 2D Poisson: k and |k|
+};
+
+template <typename T>
+static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes, DevPlan<T> &D) {
+    D.dim = p->grid.dim;
+    for (int a = 0; a < 3; ++a) {
+        D.n[a] = p->n3[a];
+        D.nf[a] = p->n3[a] == 1 ? 1 : 2 * p->n3[a];
+    }
+    D.nh = D.nf[2] / 2 + 1;
+    D.w = p->info.width;
+    D.beta = (T)p->info.beta_es;
+    int Tt = p->opts.tile;
+    if (Tt == 0) Tt = (p->grid.dim == 2) ? 16 : (sizeof(T) == 8 ? 4 : 8);
+    D.T_tile[0] = p->grid.dim == 3 ? Tt : 1;
+    D.T_tile[1] = Tt;
+    D.T_tile[2] = Tt;
+    p->info.tile = Tt;
+    if (interp_spread_smem(D) > 227 * 1024) return NLP_ERR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a) {
+        nlp_status s = make_fft_len<T>(p, D.nf[a], &D.len[a]);
+        if (s) return s;
+    }
+    // deconvolution tables 1/psi-hat(2 pi (i - n/2)/nf)
+    for (int a = 0; a < 3; ++a) {
+        std::vector<T> dc(D.n[a]);
+        for (int i = 0; i < D.n[a]; ++i) {
+            if (D.n[a] == 1) { dc[i] = (T)1; continue; }
+            const double xi = 2.0 * M_PI * (double)(i - D.n[a] / 2) / (double)D.nf[a];
+            dc[i] = (T)(1.0 / es_fourier(xi, D.w, p->info.beta_es));
+        }
+        void *d;
+        nlp_status s = alloc_dev(p, &d, sizeof(T) * dc.size());
+        if (s) return s;
+        cudaMemcpy(d, dc.data(), sizeof(T) * dc.size(), cudaMemcpyHostToDevice);
+        D.deconv[a] = (const T *)d;
+    }
+    const size_t spec = (size_t)D.nf[0] * D.nf[1] * D.nh;
+    void *dF, *dG;
+    nlp_status s = alloc_dev(p, &dF, sizeof(cpx<T>) * spec);
+    if (s) return s;
+    s = alloc_dev(p, &dG, sizeof(cpx<T>) * spec);
+    if (s) return s;
+    D.F = (cpx<T> *)dF;
+    D.G = (cpx<T> *)dG;
+
+    // ---- bin nodes by tile of their first tap
+    const int64_t M = (int64_t)nodes.size();
+    const int wa[3] = {p->grid.dim == 3 ? D.w : 1, D.w, D.w};
+    std::vector<int64_t> s0(M * 3), tb(M * 3);
+    int64_t tmin[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, tmax[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
+    for (int64_t j = 0; j < M; ++j)
+        for (int a = 0; a < 3; ++a) {
+            const int64_t sj = (int64_t)std::ceil(nodes[j].z[a] - 0.5 * wa[a]);
+            s0[3 * j + a] = sj;
+            tb[3 * j + a] = floordiv(sj, D.T_tile[a]);
+            tmin[a] = std::min(tmin[a], tb[3 * j + a]);
+            tmax[a] = std::max(tmax[a], tb[3 * j + a]);
+        }
+    int64_t K[3] = {1, 1, 1};
+    if (M > 0)
+        for (int a = 0; a < 3; ++a) K[a] = tmax[a] - tmin[a] + 1;
+    const int64_t ntile = K[0] * K[1] * K[2];
+    std::vector<int64_t> cnt(M > 0 ? ntile + 1 : 1, 0);
+    std::vector<int64_t> key(M);
+    for (int64_t j = 0; j < M; ++j) {
+        key[j] = ((tb[3 * j] - tmin[0]) * K[1] + (tb[3 * j + 1] - tmin[1])) * K[2] + (tb[3 * j + 2] - tmin[2]);
+        cnt[key[j] + 1]++;
+    }
+    for (int64_t t = 0; t < (M > 0 ? ntile : 0); ++t) cnt[t + 1] += cnt[t];
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - (M > 0 ? 1 : 0));
+    std::vector<int64_t> order(M);
+    for (int64_t j = 0; j < M; ++j) order[pos[key[j]]++] = j;
+    // chunks
+    const int CH = sizeof(T) == 8 ? 256 : 1024;
+    std::vector<Chunk> chunks;
+    int64_t ntiles_used = 0;
+    for (int64_t t = 0; t < (M > 0 ? ntile : 0); ++t) {
+        const int64_t c0 = cnt[t], c1 = cnt[t + 1];
+        if (c1 == c0) continue;
+        ++ntiles_used;
+        const int64_t k2 = t % K[2], k1 = (t / K[2]) % K[1], k0 = t / (K[1] * K[2]);
+        const int64_t nch = (c1 - c0 + CH - 1) / CH;
+        for (int64_t c = 0; c < nch; ++c) {
+            Chunk ch;
+            ch.bx = (int)((k0 + tmin[0]) * D.T_tile[0]);
+            ch.by = (int)((k1 + tmin[1]) * D.T_tile[1]);
+            ch.bz = (int)((k2 + tmin[2]) * D.T_tile[2]);
+            ch.j0 = (int)(c0 + (c1 - c0) * c / nch);
+            ch.j1 = (int)(c0 + (c1 - c0) * (c + 1) / nch);
+            chunks.push_back(ch);
+        }
+    }
+    std::stable_sort(chunks.begin(), chunks.end(),
+                     [](const Chunk &a, const Chunk &b) { return (a.j1 - a.j0) > (b.j1 - b.j0); });
+    std::vector<T> nd(4 * (size_t)M);
+    std::vector<uint32_t> no(M);
+    std::vector<double> pois;
+    if (p->kernel == NLP_POISSON_2D) pois.resize(3 * (size_t)M);
+    for (int64_t q = 0; q < M; ++q) {
+        const int64_t j = order[q];
+        uint32_t packed = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t sj = s0[3 * j + a];
+            const int64_t o = sj - tb[3 * j + a] * D.T_tile[a];
+            nd[4 * q + a] = (T)(nodes[j].z[a] - (double)sj);
+            packed |= (uint32_t)o << (8 * a);
+        }
+        nd[4 * q + 3] = (T)nodes[j].omega;
+        no[q] = packed;
+        if (!pois.empty()) {
+            pois[3 * q] = nodes[j].k[0];
+            pois[3 * q + 1] = nodes[j].k[1];
+            pois[3 * q + 2] = nodes[j].r;
+        }
+    }
+    void *dnd = nullptr, *dno = nullptr, *dch = nullptr;
+    if ((s = alloc_dev(p, &dnd, sizeof(T) * nd.size()))) return s;
+    if ((s = alloc_dev(p, &dno, sizeof(uint32_t) * no.size()))) return s;
+    if ((s = alloc_dev(p, &dch, sizeof(Chunk) * chunks.size()))) return s;
+    if (M) {
+        cudaMemcpy(dnd, nd.data(), sizeof(T) * nd.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dno, no.data(), sizeof(uint32_t) * no.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dch, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice);
+    }
+    D.pois = nullptr;
+    D.mom = nullptr;
+    D.hvol = p->h[1] * p->h[2] * (p->grid.dim == 3 ? p->h[0] : 1.0);
+    D.sigma = p->sigma;
+    if (!pois.empty()) {
+        void *dp, *dm, *dr;
+        if ((s = alloc_dev(p, &dp, sizeof(double) * pois.size()))) return s;
+        cudaMemcpy(dp, pois.data(), sizeof(double) * pois.size(), cudaMemcpyHostToDevice);
+        p->d_pois = (double *)dp;
+        p->red_blocks = 256;
+        if ((s = alloc_dev(p, &dr, sizeof(double) * 3 * (p->red_blocks + 1)))) return s;
+        p->d_red = (double *)dr;
+        if ((s = alloc_dev(p, &dm, sizeof(double) * 4))) return s;
+        cudaMemset(dm, 0, sizeof(double) * 4);
+        D.pois = p->d_pois;
+        D.mom = (const double *)dm;
+    }
+    D.nd = (const T *)dnd;
+    D.no = (const uint32_t *)dno;
+    D.chunks = (const Chunk *)dch;
+    D.nchunks = (int64_t)chunks.size();
+    p->info.tiles = ntiles_used;
+    p->info.chunks = D.nchunks;
+    if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
+    return NLP_OK;
+}
+
+static int roundup16(double x) { return (int)(16.0 * std::ceil(x / 16.0)); }
+
+nlp_status plan_build(nlp_plan_s *p) {
+    const nlp_grid &g = p->grid;
+    const int d = g.dim;
+    // collapsed 3D view
+    if (d == 3) {
+        for (int a = 0; a < 3; ++a) { p->n3[a] = g.n[a]; p->L3[a] = g.L[a]; }
+    } else {
+        p->n3[0] = 1; p->L3[0] = 1.0;
+        p->n3[1] = g.n[0]; p->L3[1] = g.L[0];
+        p->n3[2] = g.n[1]; p->L3[2] = g.L[1];
+    }
+    double hmax = 0, R2 = 0, Rp2 = 0;
+    for (int a = 0; a < 3; ++a) {
+        p->h[a] = (p->n3[a] == 1) ? 1.0 : 2.0 * p->L3[a] / p->n3[a];
+        if (p->n3[a] > 1) hmax = std::max(hmax, p->h[a]);
+    }
+    for (int a = 0; a < d; ++a) R2 += g.L[a] * g.L[a];
+    Rp2 = g.L[0] * g.L[0] + g.L[1] * g.L[1];
+    const double P = p->opts.kmax > 0 ? p->opts.kmax : M_PI / hmax;
+    int nr = p->opts.n_r, nth = p->opts.n_theta, nph = p->opts.n_phi;
+    if (nr <= 0) nr = roundup16(P * std::sqrt(R2) / 2.0 + 16.0);
+    if (d == 3 && nth <= 0) nth = nr;
+    if (nph <= 0) nph = roundup16(P * (d == 3 ? std::sqrt(Rp2) : std::sqrt(R2)) + 32.0);
+    if (d == 2) nth = 1;
+    if ((d == 3 && (nth % 2)) || (nph % 2)) return NLP_ERR_INVALID_ARG;
+    double tol = p->opts.nufft_tol > 0 ? p->opts.nufft_tol : (p->prec == NLP_FP64 ? 1e-12 : 1e-6);
+    p->opts.nufft_tol = tol;
+    int w;
+    double beta;
+    es_params(tol, &w, &beta);
+    p->info.dim = d;
+    p->info.kernel = p->kernel;
+    p->info.precision = p->prec;
+    for (int a = 0; a < 3; ++a) {
+        p->info.n[a] = p->n3[a];
+        p->info.nf[a] = p->n3[a] == 1 ? 1 : 2 * p->n3[a];
+    }
+    p->info.width = w;
+    p->info.beta_es = beta;
+    p->info.kmax = P;
+    p->info.n_r = nr;
+    p->info.n_theta = nth;
+    p->info.n_phi = nph;
+
+    // ---- quadrature nodes of the k -> -k half (Eq. (ifft)); weights carry h^d (2pi)^-d and
+    //      the Jacobian-weighted symbol |k|^{d-1} U-hat (Eq. (Kernal)); see nlpot.h
+    std::vector<double> r, wr, u, wu;
+    gauss_legendre(nr, 0.0, P, r, wr);
+    std::vector<HostNode> nodes;
+    const double twopi = 2.0 * M_PI;
+    const double wph = twopi / nph;
+    double hvol = 1.0;
+    for (int a = 0; a < 3; ++a) if (p->n3[a] > 1) hvol *= p->h[a];
+    const double pref = hvol / std::pow(twopi, d);
+    double nax[3] = {0, 0, 1};
+    if (p->kernel == NLP_DIPOLE_3D) {
+        const double *da = p->opts.dipole_axis;
+        const double nn = std::sqrt(da[0] * da[0] + da[1] * da[1] + da[2] * da[2]);
+        if (nn > 0) for (int a = 0; a < 3; ++a) nax[a] = da[a] / nn;
+    }
+    std::vector<double> cph(nph), sph(nph);
+    for (int c = 0; c < nph; ++c) {
+        cph[c] = std::cos(twopi * c / nph);
+        sph[c] = std::sin(twopi * c / nph);
+    }
+    if (d == 3) {
+        gauss_legendre(nth, -1.0, 1.0, u, wu);
+        nodes.reserve((size_t)nr * (nth / 2) * nph);
+        for (int ia = 0; ia < nr; ++ia)
+            for (int ib = nth / 2; ib < nth; ++ib) {   // u > 0 half (ascending GL nodes)
+                const double st = std::sqrt(std::max(0.0, 1.0 - u[ib] * u[ib]));
+                for (int ic = 0; ic < nph; ++ic) {
+                    HostNode hn{};
+                    const double k[3] = {r[ia] * st * cph[ic], r[ia] * st * sph[ic], r[ia] * u[ib]};
+                    double J = 1.0;
+                    if (p->kernel == NLP_DIPOLE_3D) {
+                        const double nk = nax[0] * k[0] + nax[1] * k[1] + nax[2] * k[2];
+                        J = 3.0 * nk * nk - r[ia] * r[ia];
+                    }
+                    hn.omega = pref * wr[ia] * wu[ib] * wph * J;
+                    for (int a = 0; a < 3; ++a) hn.z[a] = k[a] * p->h[a] * (2.0 * p->n3[a]) / twopi;
+                    nodes.push_back(hn);
+                }
+            }
+        p->info.nodes_total = (int64_t)nr * nth * nph;
+    } else {
+        nodes.reserve((size_t)nr * (nph / 2));
+        for (int ia = 0; ia < nr; ++ia)
+            for (int ic = 0; ic < nph / 2; ++ic) {     // phi in [0, pi): k_y >= 0 half
+                HostNode hn{};
+                const double k[2] = {r[ia] * cph[ic], r[ia] * sph[ic]};
+                if (p->kernel == NLP_POISSON_2D)       // W(k) form of Algorithm 1; h^2 applied in-kernel
+                    hn.omega = wr[ia] * wph / (twopi * twopi * r[ia]);
+                else
+                    hn.omega = pref * wr[ia] * wph;    // Coulomb 2D: |k| U-hat = 1
+                hn.z[0] = 0.0;
+                hn.z[1] = k[0] * p->h[1] * (2.0 * p->n3[1]) / twopi;
+                hn.z[2] = k[1] * p->h[2] * (2.0 * p->n3[2]) / twopi;
+                hn.k[0] = k[0];
+                hn.k[1] = k[1];
+                hn.r = r[ia];
+                nodes.push_back(hn);
+            }
+        p->info.nodes_total = (int64_t)nr * nph;
+    }
+    p->info.nodes_half = (int64_t)nodes.size();
+    if (p->kernel == NLP_POISSON_2D) p->sigma = 6.0 * std::sqrt(2.0) / P;
+    p->info.sigma_poisson = p->sigma;
+
+    nlp_status s = (p->prec == NLP_FP64) ? build_device<double>(p, nodes, p->pd) : build_device<float>(p, nodes, p->pf);
+    if (s) return s;
+    p->info.workspace_bytes = p->bytes;
+    return NLP_OK;
+}
+
+nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, const nlp_opts *o) {
+    if (!g) return NLP_ERR_INVALID_ARG;
+    if (g->dim != 2 && g->dim != 3) return NLP_ERR_INVALID_ARG;
+    if ((kernel == NLP_COULOMB_3D || kernel == NLP_DIPOLE_3D) && g->dim != 3) return NLP_ERR_INVALID_ARG;
+    if ((kernel == NLP_COULOMB_2D || kernel == NLP_POISSON_2D) && g->dim != 2) return NLP_ERR_INVALID_ARG;
+    if ((int)kernel < 0 || (int)kernel > 3) return NLP_ERR_INVALID_ARG;
+    if (prec != NLP_FP64 && prec != NLP_FP32) return NLP_ERR_INVALID_ARG;
+    for (int a = 0; a < g->dim; ++a) {
+        const int n = g->n[a];
+        if (n < 8 || n % 2 || !good_len(n) || n > (g->dim == 3 ? 256 : 1024)) return NLP_ERR_INVALID_ARG;
+        if (!(g->L[a] > 0.0) || !std::isfinite(g->L[a])) return NLP_ERR_INVALID_ARG;
+    }
+    if (o) {
+        if (o->nufft_tol != 0.0 && !(o->nufft_tol >= 1e-14 && o->nufft_tol <= 1e-2)) return NLP_ERR_INVALID_ARG;
+        if (o->kmax < 0.0 || !std::isfinite(o->kmax)) return NLP_ERR_INVALID_ARG;
+        if (o->n_r < 0 || o->n_theta < 0 || o->n_phi < 0) return NLP_ERR_INVALID_ARG;
+        if (o->n_r > 4096 || o->n_theta > 4096 || o->n_phi > 8192) return NLP_ERR_INVALID_ARG;
+        if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
+        if (o->tile != 0 && o->tile != 4 && o->tile != 8 && o->tile != 16 && o->tile != 32) return NLP_ERR_INVALID_ARG;
+        for (int i = 0; i < 7; ++i)
+            if (o->reserved[i]) return NLP_ERR_INVALID_ARG;
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(o->dipole_axis[a])) return NLP_ERR_INVALID_ARG;
+    }
+    return NLP_OK;
+}
+
+}  // namespace nlp

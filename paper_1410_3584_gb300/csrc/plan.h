@@ -1,0 +1,45 @@
+// Plan object behind the opaque nlp_plan handle.
+#pragma once
+#include <vector>
+#include <string>
+
+#include "common.cuh"
+
+struct nlp_plan_s {
+    nlp_grid grid{};          // as given (dim 2 or 3)
+    nlp_kernel kernel{};
+    nlp_precision prec{};
+    nlp_opts opts{};
+    cudaStream_t stream = nullptr;
+    nlp_plan_info info{};
+    double h[3] = {1, 1, 1};  // collapsed 3D view (2D: axis 0 is a dummy of size 1)
+    int n3[3] = {1, 1, 1};
+    double L3[3] = {1, 1, 1};
+    nlp::DevPlan<float> pf{};
+    nlp::DevPlan<double> pd{};
+    std::vector<void *> allocs;         // every device allocation of the plan
+    size_t bytes = 0;
+    // 2D Poisson (Algorithm 1) extras
+    double sigma = 0;
+    double *d_pois = nullptr;           // per-node FP64 data: kx, ky, r (hemisphere order)
+    double *d_red = nullptr;            // FP64 reduction scratch
+    int red_blocks = 0;
+    // gradient flow / time splitting workspace (plain grid FFTs), allocated on first use
+    void *d_work = nullptr;             // host struct describing the work buffers
+    void (*work_free)(void *) = nullptr;
+    size_t work_bytes = 0;
+    void *d_host_io = nullptr;          // device buffers for nlp_eval_potential_host
+    // FFT lengths of the plain (non-oversampled) grid for GF / TS
+    nlp::FftLen<float> plain_f[3]{};
+    nlp::FftLen<double> plain_d[3]{};
+    bool plain_ready = false;
+};
+
+namespace nlp {
+// host utilities shared by the plan and the tests' debug exports
+void gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w);
+void es_params(double tol, int *w, double *beta);
+double es_fourier(double xi, int w, double beta);
+nlp_status alloc_dev(nlp_plan_s *p, void **ptr, size_t bytes);
+template <typename T> nlp_status make_fft_len(nlp_plan_s *p, int N, FftLen<T> *out);
+}  // namespace nlp

@@ -1,0 +1,151 @@
+"""GPU parity of nlp_eval_potential against the FP64 oracle (through the C-ABI).
+
+Bars: relative L-infinity (Eq. (error_infty)) against the oracle <= 1e-10 for FP64 plans
+and <= 1e-5 for FP32 plans.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import potential, quadrature
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def nl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1410_3584_gb300 as m
+    return m
+
+
+def gpu_eval(nl, g, rho, kernel, prec, **kw):
+    import torch
+    plan = nl.Plan(g.n, g.L, kernel, prec, **kw)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    r = torch.from_numpy(rho).to("cuda", dt)
+    phi = plan.eval(r)
+    torch.cuda.synchronize()
+    out = phi.double().cpu().numpy()
+    info = plan.info
+    plan.close()
+    return out, info
+
+
+# ragged shapes: several tiles plus partial tiles, unequal axes, radix 2/3/5 fine sizes
+CASES_3D = [
+    ((24, 20, 16), (6.0, 5.0, 4.5)),
+    ((30, 32, 18), (7.0, 7.0, 5.0)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", ["coulomb3d", "dipole3d"])
+@pytest.mark.parametrize("shape", CASES_3D, ids=["24x20x16", "30x32x18"])
+def test_3d_parity_vs_oracle(nl, prec, kernel, shape):
+    g = W.Grid(*shape)
+    rho = W.gaussian(g, [1.0, 1.3, 0.8], center=(0.3, -0.2, 0.1))
+    P = math.pi / max(g.h)
+    counts = (32, 32, 64)
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, counts=counts)
+    ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+    err = cf.rel_linf(phi, ref)
+    assert err < TOL[prec], (err, info)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
+@pytest.mark.parametrize("shape", [((64, 48), (8.0, 6.0)), ((80, 90), (8.0, 9.0))], ids=["64x48", "80x90"])
+def test_2d_parity_vs_oracle(nl, prec, kernel, shape):
+    g = W.Grid(*shape)
+    cs, ws = W.three_gaussians_2d(11)
+    rho = W.gaussian_sum(g, [(0.4 * c[0], 0.4 * c[1]) for c in cs], ws)
+    P = math.pi / max(g.h)
+    counts = (64, 128)
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, counts=counts)
+    ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+    err = cf.rel_linf(phi, ref)
+    assert err < TOL[prec], (err, info)
+
+
+def test_config1_vs_direct_sum_and_erf(nl):
+    """32^3 over [-8,8)^3, rho = exp(-|x|^2), 32x32x64 nodes, tol 1e-12, P = 2 pi:
+    FP64 GPU vs the exact discrete definition (O1 direct sums); closed-form error recorded."""
+    g = W.cube(32, 8.0)
+    rho = W.gaussian(g, [1.0] * 3)
+    P = 2.0 * math.pi
+    counts = (32, 32, 64)
+    phi, info = gpu_eval(nl, g, rho, "coulomb3d", "fp64", kmax=P, counts=counts, tol=1e-12)
+    ref = potential.eval_direct(rho, g, "coulomb3d", P, counts)
+    assert cf.rel_linf(phi, ref) < 1e-10
+    X = g.mesh()
+    r = np.sqrt(sum(x * x for x in X))
+    err_cf = cf.rel_linf(phi, cf.coulomb3d_iso(r, 1.0))
+    # quadrature-limited at these counts (reading of the default rule); recorded, loosely bounded
+    assert err_cf < 1e-2
+    print("config1 closed-form error %.3e" % err_cf)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_linearity_and_repeatability(nl, prec):
+    import torch
+    g = W.Grid((24, 24, 24), (6.0, 6.0, 6.0))
+    a, b = W.random_density(g, 1), W.random_density(g, 2)
+    plan = nl.Plan(g.n, g.L, "coulomb3d", prec, counts=(32, 32, 64))
+    dt = plan.torch_dtype
+    ta, tb = torch.from_numpy(a).to("cuda", dt), torch.from_numpy(b).to("cuda", dt)
+    pa, pb = plan.eval(ta).double(), plan.eval(tb).double()
+    pab = plan.eval((2.0 * ta - 0.5 * tb).contiguous()).double()
+    pa2 = plan.eval(ta).double()
+    torch.cuda.synchronize()
+    plan.close()
+    scale = float(pab.abs().max())
+    assert float((pab - (2 * pa - 0.5 * pb)).abs().max()) / scale < (1e-13 if prec == "fp64" else 3e-6)
+    assert float((pa2 - pa).abs().max()) / float(pa.abs().max()) < (1e-14 if prec == "fp64" else 1e-6)
+
+
+def test_host_entry_point_matches_device(nl):
+    import torch
+    g = W.cube(24, 6.0)
+    rho = W.gaussian(g, [1.0, 1.0, 1.0])
+    plan = nl.Plan(g.n, g.L, "coulomb3d", "fp64", counts=(32, 32, 64))
+    d = plan.eval(torch.from_numpy(rho).cuda()).cpu().numpy()
+    h = np.empty_like(rho)
+    nl.nlp_eval_potential_host(plan.handle, rho, h)
+    plan.close()
+    assert np.max(np.abs(h - d)) <= 1e-14 * np.max(np.abs(d))
+
+
+def test_zero_density_gives_zero(nl):
+    import torch
+    g = W.cube(16, 4.0)
+    plan = nl.Plan(g.n, g.L, "coulomb3d", "fp64", counts=(16, 16, 32))
+    phi = plan.eval(torch.zeros(g.n, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    plan.close()
+    assert float(phi.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_metric_config(nl, prec):
+    """128^3 over [-12,12)^3, rho = exp(-(x^2 + y^2/2 + z^2/4)), density-informed P and the
+    default quadrature counts, tol 1e-12 (FP64) / 1e-6 (FP32): the launch configuration of
+    the benchmark, against the plain FP64 NUFFT oracle at full size."""
+    g = W.cube(128, 12.0)
+    a = (1.0, math.sqrt(2.0), 2.0)
+    rho = W.gaussian(g, a)
+    P = quadrature.density_P(min(a), g.h[0])
+    counts = quadrature.default_counts(g.L, P)
+    phi, info = gpu_eval(nl, g, rho, "coulomb3d", prec, kmax=P, counts=counts,
+                         tol=1e-12 if prec == "fp64" else 1e-6)
+    ref = potential.eval_nufft(rho, g, "coulomb3d", P, counts, tol=1e-13)
+    err = cf.rel_linf(phi, ref)
+    print("128^3 %s rel L-inf vs oracle %.3e  nodes %d" % (prec, err, info["nodes_total"]))
+    assert err < TOL[prec]
