@@ -1,0 +1,333 @@
+"""Benchmark: phi = U * rho evaluations per second, 3D Coulomb on a 128^3 grid.
+
+Workload: 128^3 over [-12,12)^3, rho = exp(-(x^2 + y^2/2 + z^2/4)) (anisotropic Gaussian of
+the paper's test family, Example 2.1), truncation radius P from the density (rho-hat < 1e-16
+beyond it), default quadrature counts, FP32 path at NUFFT tolerance 1e-6 (headline) and FP64
+path at 1e-12, each with its relative L-infinity error against the FP64 oracle.
+
+One step = one evaluation (deconvolve/pad + 3 forward FFT passes, fused interpolate/scale/
+spread, 3 inverse FFT passes + deconvolve/crop) with rho resident in HBM.  L2 (126 MB) is
+flushed between timed steps by writing a 512 MB buffer outside the timed events.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the evaluation does not shard);
+value = evaluations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_GRID, L_BOX = 128, 12.0
+WIDTHS = (1.0, math.sqrt(2.0), 2.0)
+METRIC = "phi=U*rho evals/s, 3D Coulomb 128^3, FP32 vs FP64 GPU at stated L-inf error"
+WORKLOAD = ("3D Coulomb 128^3 over [-12,12)^3, rho=exp(-(x^2+y^2/2+z^2/4)), density-informed P, "
+            "default spherical quadrature, FP32 NUFFT tol 1e-6 (headline) / FP64 tol 1e-12")
+
+
+def workload():
+    """Grid, density, truncation radius P (rho-hat below 1e-16 of its peak beyond P, never past
+    pi/h) and quadrature counts n_r = n_theta = roundup16(P R/2 + 16), n_phi = roundup16(P Rp + 32)."""
+    g = W.cube(N_GRID, L_BOX)
+    rho = W.gaussian(g, WIDTHS)
+    h = g.h[0]
+    P = min(math.pi / h, 2.0 * math.sqrt(math.log(1e16)) / min(WIDTHS))
+    R = math.sqrt(3.0) * L_BOX
+    Rp = math.sqrt(2.0) * L_BOX
+    nr = int(16 * math.ceil((P * R / 2.0 + 16.0) / 16.0))
+    nph = int(16 * math.ceil((P * Rp + 32.0) / 16.0))
+    return g, rho, P, (nr, nr, nph)
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nme)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stream, e2e=True):
+    tol = 1e-6 if prec == "fp32" else 1e-12
+    plan = nl.Plan(g.n, g.L, "coulomb3d", prec, kmax=P, counts=counts, tol=tol, stream=stream)
+    dt = plan.torch_dtype
+    with torch.cuda.stream(stream):
+        r = torch.from_numpy(rho).to("cuda", dt)
+        phi = torch.empty_like(r)
+    stream.synchronize()
+    for _ in range(warmup):
+        nl.nlp_eval_potential(plan.handle, r, phi)
+    stream.synchronize()
+    nl.nlp_set_stage_timing(plan.handle, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage_tot = {}
+    launches = 0
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        nl.nlp_eval_potential(plan.handle, r, phi)
+        ev[k][1].record(stream)
+        st = nl.nlp_get_stage_times(plan.handle)     # syncs on the last stage event
+        for name, ms in st:
+            stage_tot[name] = stage_tot.get(name, 0.0) + ms
+        launches += sum(1 for name, _ in st if name != "clear")
+    torch.cuda.synchronize()
+    nl.nlp_set_stage_timing(plan.handle, False)
+    times = [a.elapsed_time(b) for a, b in ev]
+    out = phi.double().cpu().numpy()
+    info = plan.info
+    if not e2e:
+        plan.close()
+        return dict(times=times, stages={k: v / steps for k, v in stage_tot.items()}, phi=out, info=info,
+                    launches=launches)
+    # end-to-end through the host entry point, pinned host buffers, copies inside the timing
+    hr = torch.from_numpy(rho.astype(np.float64 if prec == "fp64" else np.float32)).pin_memory()
+    hp = torch.empty_like(hr).pin_memory()
+    nl.nlp_eval_potential_host(plan.handle, hr.numpy(), hp.numpy())
+    t0 = time.perf_counter()
+    e2e_steps = max(3, steps // 2)
+    for _ in range(e2e_steps):
+        nl.nlp_eval_potential_host(plan.handle, hr.numpy(), hp.numpy())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    plan.close()
+    return dict(times=times, stages={k: v / steps for k, v in stage_tot.items()}, phi=out, info=info,
+                launches=launches, e2e_s=e2e_s, bytes_io=int(hr.numel() * hr.element_size()))
+
+
+def roofline(res, prec, alu_peak, hbm_peak, sm_mhz_note):
+    """Dominant kernel: the stage with the largest average time."""
+    st = res["stages"]
+    name = max(st, key=st.get)
+    info = res["info"]
+    t = st[name] * 1e-3
+    w = info["width"]
+    elt = 8 if prec == "fp32" else 16          # complex element bytes
+    n, nf = info["n"], info["nf"]
+    nh = nf[2] // 2 + 1
+    if name == "interp_spread":
+        # algorithmic work: per processed node w^3 taps of interpolation (2 FMA) and of
+        # spreading (2 mul + 2 add) = 8 flop per tap
+        flops = 8.0 * info["nodes_half"] * w ** 3
+        ach = flops / t
+        return dict(kernel=name, bound="alu", achieved=ach / 1e12, peak=alu_peak / 1e12, unit="TFLOP/s",
+                    frac=ach / alu_peak, traffic=None, peak_source="measured FMA microbenchmark (nlp_measure_alu_peak)")
+    # FFT passes: algorithmic bytes = one read + one write of the pass's data
+    spec = nf[0] * nf[1] * nh * elt
+    if name == "fwd_last" or name == "inv_last":
+        byt = n[0] * n[1] * n[2] * (elt // 2) + n[0] * n[1] * nh * elt
+    elif name in ("fwd_mid", "inv_mid"):
+        byt = n[0] * (n[1] + nf[1]) * nh * elt
+    elif name in ("fwd_first", "inv_first"):
+        byt = nf[1] * (n[0] + nf[0]) * nh * elt
+    else:
+        byt = spec
+    ach = byt / t
+    return dict(kernel=name, bound="hbm", achieved=ach / 1e9, peak=hbm_peak, unit="GB/s", frac=ach / 1e9 / hbm_peak,
+                traffic=None, peak_source="MEASURED_PEAKS.json hbm_gbs")
+
+
+def gpu_arm(args):
+    import torch
+    import paper_1410_3584_gb300 as nl
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    g, rho, P, counts = workload()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if args.profile:
+        res = run_precision(nl, torch, args.profile, g, rho, P, counts, args.steps, args.warmup, flush, stream,
+                            e2e=False)
+        print(json.dumps({"profile": args.profile, "ms": res["times"], "stages_ms": res["stages"]}))
+        return
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    alu = {p: nl.nlp_measure_alu_peak(p, stream) for p in ("fp32", "fp64")}
+    clk = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    res32 = run_precision(nl, torch, "fp32", g, rho, P, counts, args.steps, args.warmup, flush, stream)
+    res64 = run_precision(nl, torch, "fp64", g, rho, P, counts, max(3, args.steps // 4), min(args.warmup, 3), flush,
+                          stream)
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    t32 = sum(res32["times"]) / 1e3
+    t64 = sum(res64["times"]) / 1e3
+    e2e = res32["e2e_s"]
+    if ws > 1:
+        tt = torch.tensor([t32, t64, e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t32, t64, e2e = (float(x) for x in tt)
+    if rank == 0:
+        from oracle import closed_forms as cf
+        from oracle import native, potential
+        t0 = time.perf_counter()
+        ref = potential.eval_nufft(rho, g, "coulomb3d", P, counts, tol=1e-13)
+        t_or = time.perf_counter() - t0
+        err32 = cf.rel_linf(res32["phi"], ref)
+        err64 = cf.rel_linf(res64["phi"], ref)
+        X, Y, Z = g.mesh()
+        # closed form on a sample of grid lines (the full grid would take minutes)
+        sl = (slice(None), slice(None), slice(0, None, 16))
+        ex = cf.coulomb3d_triaxial(X[sl], Y[sl], Z[sl], WIDTHS)
+        err_cf = float(np.max(np.abs(res64["phi"][sl] - ex)) / np.max(np.abs(ex)))
+        sm = clocks.get("sm_mhz")
+        r32 = roofline(res32, "fp32", alu["fp32"], peaks["hbm_gbs"], sm)
+        r64 = roofline(res64, "fp64", alu["fp64"], peaks["hbm_gbs"], sm)
+        K = args.steps
+        line = {
+            "metric": METRIC,
+            "value": ws * K / t32,
+            "unit": "evals/s",
+            "n_gpus": ws,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * t32 / K,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "L": L_BOX, "kernel": "coulomb3d",
+                       "P": P, "quadrature": [res32["info"]["n_r"], res32["info"]["n_theta"], res32["info"]["n_phi"]],
+                       "nodes": res32["info"]["nodes_total"], "width_fp32": res32["info"]["width"],
+                       "width_fp64": res64["info"]["width"], "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "rel_linf_vs_oracle": err32,
+            "fp64": {"value": ws * len(res64["times"]) / t64, "unit": "evals/s",
+                     "ms_per_step": 1e3 * t64 / len(res64["times"]), "steps": len(res64["times"]),
+                     "rel_linf_vs_oracle": err64, "rel_linf_vs_closed_form_sampled": err_cf,
+                     "roofline": r64, "stages_ms": res64["stages"]},
+            "stages_ms": res32["stages"],
+            "roofline": r32,
+            "cpu_baseline": {"value": 1.0 / t_or, "unit": "evals/s", "cores": native.max_threads(), "kind": "oracle",
+                             "sample": "one full 128^3 evaluation by the FP64 oracle (plain NUFFT, tol 1e-13, "
+                                       "full symmetric node set)"},
+            "e2e": {"value": ws / e2e, "unit": "evals/s", "h2d_bytes_per_step": res32["bytes_io"],
+                    "d2h_bytes_per_step": res32["bytes_io"]},
+            "gpu_launches": res32["launches"],
+            "clocks": clocks,
+            "alu_peaks_tflops": {k: v / 1e12 for k, v in alu.items()},
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import native, potential
+    g, rho, P, counts = workload()
+    steps, warm = min(args.steps, 2), min(args.warmup, 1)
+    for _ in range(warm):
+        potential.eval_nufft(rho, g, "coulomb3d", P, counts, tol=1e-13)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        potential.eval_nufft(rho, g, "coulomb3d", P, counts, tol=1e-13)
+    t = time.perf_counter() - t0
+    v = steps / t
+    sample = ("full 128^3 evaluations by the FP64 oracle (plain NUFFT, tol 1e-13); %d timed, %d warm-up "
+              "(capped so the run stays within minutes)" % (steps, warm))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws, "steps": steps,
+        "warmup": warm, "ms_per_step": 1e3 * t / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "L": L_BOX, "kernel": "coulomb3d"},
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": native.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],
+                    help="only the timed evaluation loop of one precision (for ncu captures)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu" and not args.profile:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

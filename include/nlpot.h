@@ -143,6 +143,29 @@ nlp_status nlp_energies(nlp_plan plan, const void *phi_dev, const void *V_dev, d
 nlp_status nlp_ts_step(nlp_plan plan, void *psi_dev, const void *V_dev, double beta, double g,
                        double tau, int order);
 
+/* Stage timers for measurement (not part of the method).  When enabled, each evaluation
+ * records CUDA events on the plan stream between its stages; nlp_get_stage_times then
+ * synchronizes on the last event and returns, for the most recent evaluation, up to max
+ * (stage id, milliseconds) pairs in execution order.  Stage ids: */
+enum {
+    NLP_STAGE_FWD_LAST = 0,   /* deconvolve + zero-pad + R2C FFT along the last axis */
+    NLP_STAGE_FWD_MID = 1,    /* forward FFT along axis 1 (3D) / axis 0 (2D) */
+    NLP_STAGE_FWD_FIRST = 2,  /* forward FFT along axis 0 (3D only) */
+    NLP_STAGE_CLEAR = 3,      /* zero the spreading target */
+    NLP_STAGE_SPREAD = 4,     /* fused interpolate -> scale -> spread */
+    NLP_STAGE_INV_FIRST = 5,  /* inverse FFT along axis 0 (3D only) */
+    NLP_STAGE_INV_MID = 6,    /* inverse FFT along axis 1 (3D) / axis 0 (2D) */
+    NLP_STAGE_INV_LAST = 7,   /* C2R FFT along the last axis + deconvolve + crop */
+    NLP_STAGE_POISSON = 8     /* 2D Poisson FP64 parts (moments, rho-hat(0), u_1) */
+};
+nlp_status nlp_set_stage_timing(nlp_plan plan, int on);
+nlp_status nlp_get_stage_times(nlp_plan plan, int *stage_ids, double *ms, int max, int *count);
+
+/* Measured FMA throughput of the GPU in flop/s for the given precision (a microbenchmark of
+ * independent FMA chains over all SMs, best of 3 timed runs); the denominator of the ALU
+ * roofline of the interpolation/spreading kernel.  Allocates 64 bytes; synchronizes. */
+nlp_status nlp_measure_alu_peak(int precision, void *stream, double *flops_per_s);
+
 const char *nlp_status_string(nlp_status s);
 
 /* Library version string. */

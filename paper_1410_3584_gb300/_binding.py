@@ -61,6 +61,9 @@ def _load():
         "nlp_gf_step": ([P, P, P, D, D, D, D, I, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "nlp_energies": ([P, P, P, D, D, ctypes.POINTER(D)], I),
         "nlp_ts_step": ([P, P, P, D, D, D, I], I),
+        "nlp_set_stage_timing": ([P, I], I),
+        "nlp_get_stage_times": ([P, ctypes.POINTER(I), ctypes.POINTER(D), I, ctypes.POINTER(I)], I),
+        "nlp_measure_alu_peak": ([I, P, ctypes.POINTER(D)], I),
         "nlp_status_string": ([I], ctypes.c_char_p),
         "nlp_version": ([], ctypes.c_char_p),
     }
@@ -186,6 +189,31 @@ def nlp_ts_step(plan, psi, V, beta: float, g: float = 0.0, tau: float = 1e-3, or
     """One time-splitting step in place on complex psi (torch complex tensor or interleaved view)."""
     _check(_lib.nlp_ts_step(plan, _ptr(psi), _ptr(V), float(beta), float(g), float(tau), int(order)),
            "nlp_ts_step")
+
+
+STAGES = {0: "fwd_last", 1: "fwd_mid", 2: "fwd_first", 3: "clear", 4: "interp_spread",
+          5: "inv_first", 6: "inv_mid", 7: "inv_last", 8: "poisson_fp64"}
+
+
+def nlp_set_stage_timing(plan, on: bool):
+    _check(_lib.nlp_set_stage_timing(plan, 1 if on else 0), "nlp_set_stage_timing")
+
+
+def nlp_get_stage_times(plan):
+    """[(stage name, ms), ...] of the most recent evaluation (timers must be on)."""
+    ids = (ctypes.c_int * 16)()
+    ms = (ctypes.c_double * 16)()
+    cnt = ctypes.c_int(0)
+    _check(_lib.nlp_get_stage_times(plan, ids, ms, 16, ctypes.byref(cnt)), "nlp_get_stage_times")
+    return [(STAGES.get(ids[i], str(ids[i])), ms[i]) for i in range(cnt.value)]
+
+
+def nlp_measure_alu_peak(precision: str, stream=None) -> float:
+    """Measured FMA throughput (flop/s) of the GPU for 'fp32' or 'fp64'."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.nlp_measure_alu_peak(PRECISIONS[precision], _stream_handle(stream), ctypes.byref(v)),
+           "nlp_measure_alu_peak")
+    return v.value
 
 
 class Plan:

@@ -13,17 +13,29 @@ nlp_status gf_step_impl(nlp_plan_s *p, void *phi, const void *V, double beta, do
 nlp_status energies_impl(nlp_plan_s *p, const void *phi, const void *V, double beta, double g, double *energies);
 nlp_status ts_step_impl(nlp_plan_s *p, void *psi, const void *V, double beta, double g, double tau, int order);
 
+// Stage markers for the optional event timers (ids are part of the ABI: nlpot.h).
+static inline void mark(nlp_plan_s *p, int stage) {
+    if (!p->timing || p->nev >= 16) return;
+    cudaEventRecord(p->ev[p->nev], p->stream);
+    p->ev_stage[p->nev++] = stage;
+}
+
 // phi = U * rho on the plan's stream (see nlp_eval_potential).
 template <typename T>
 nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     cudaStream_t st = p->stream;
+    p->nev = 0;
+    mark(p, -1);
     const bool three = p->grid.dim == 3;
     const bool pois = p->kernel == NLP_POISSON_2D;
     const int64_t nh = D.nh;
-    if (pois)
+    if (pois) {
         NLP_CUDA_TRY(launch_poisson_moments<T>(rho, D, p->L3, p->h, p->d_red, p->red_blocks, (double *)D.mom, st));
+        mark(p, NLP_STAGE_POISSON);
+    }
     // type 2: deconvolve, zero-pad, forward FFT (last axis, then axis 1, then axis 0)
     NLP_CUDA_TRY(launch_fwd_r2c<T>(rho, D, st));
+    mark(p, NLP_STAGE_FWD_LAST);
     StridedDesc a1{};
     a1.n_in = D.n[1];
     a1.n_out = D.nf[1];
@@ -34,6 +46,7 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     a1.outer_map_n = three ? D.n[0] : 0;
     a1.outer_map_N = D.nf[0];
     NLP_CUDA_TRY(launch_fft_strided<T>(D.F, a1, D.len[1], -1, st));
+    mark(p, NLP_STAGE_FWD_MID);
     StridedDesc a0{};
     if (three) {
         a0.n_in = D.n[0];
@@ -43,24 +56,36 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
         a0.nouter = D.nf[1];
         a0.os = nh;
         NLP_CUDA_TRY(launch_fft_strided<T>(D.F, a0, D.len[0], -1, st));
+        mark(p, NLP_STAGE_FWD_FIRST);
     }
-    if (pois) NLP_CUDA_TRY(launch_poisson_origin<T>(D, (double *)D.mom, st));
+    if (pois) {
+        NLP_CUDA_TRY(launch_poisson_origin<T>(D, (double *)D.mom, st));
+        mark(p, NLP_STAGE_POISSON);
+    }
     // interpolate, scale, spread
     NLP_CUDA_TRY(cudaMemsetAsync(D.G, 0, sizeof(cpx<T>) * (size_t)D.nf[0] * D.nf[1] * nh, st));
+    mark(p, NLP_STAGE_CLEAR);
     NLP_CUDA_TRY(launch_interp_spread<T>(D, st));
+    mark(p, NLP_STAGE_SPREAD);
     // type 1: inverse FFT (axis 0, axis 1, last axis), deconvolve, crop
     if (three) {
         StridedDesc b0 = a0;
         b0.n_in = D.nf[0];
         b0.n_out = D.n[0];
         NLP_CUDA_TRY(launch_fft_strided<T>(D.G, b0, D.len[0], +1, st));
+        mark(p, NLP_STAGE_INV_FIRST);
     }
     StridedDesc b1 = a1;
     b1.n_in = D.nf[1];
     b1.n_out = D.n[1];
     NLP_CUDA_TRY(launch_fft_strided<T>(D.G, b1, D.len[1], +1, st));
+    mark(p, NLP_STAGE_INV_MID);
     NLP_CUDA_TRY(launch_inv_c2r<T>(phi, D, st));
-    if (pois) NLP_CUDA_TRY(launch_poisson_u1<T>(phi, D, p->L3, p->h, st));
+    mark(p, NLP_STAGE_INV_LAST);
+    if (pois) {
+        NLP_CUDA_TRY(launch_poisson_u1<T>(phi, D, p->L3, p->h, st));
+        mark(p, NLP_STAGE_POISSON);
+    }
     return NLP_OK;
 }
 
@@ -105,6 +130,8 @@ void nlp_plan_destroy(nlp_plan p) {
     else cudaDeviceSynchronize();
     for (void *a : p->allocs) cudaFree(a);
     if (p->d_work && p->work_free) p->work_free(p->d_work);
+    for (int i = 0; i < 16; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     delete p;
 }
 
@@ -182,6 +209,32 @@ nlp_status nlp_energies(nlp_plan p, const void *phi_dev, const void *V_dev, doub
 nlp_status nlp_ts_step(nlp_plan p, void *psi_dev, const void *V_dev, double beta, double g, double tau, int order) {
     if (!p || !psi_dev || !V_dev || !(tau > 0) || (order != 2 && order != 4)) return NLP_ERR_INVALID_ARG;
     return ts_step_impl(p, psi_dev, V_dev, beta, g, tau, order);
+}
+
+nlp_status nlp_set_stage_timing(nlp_plan p, int on) {
+    if (!p) return NLP_ERR_INVALID_ARG;
+    if (on && !p->ev[0])
+        for (int i = 0; i < 16; ++i)
+            if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return NLP_ERR_CUDA;
+    p->timing = on ? 1 : 0;
+    p->nev = 0;
+    return NLP_OK;
+}
+
+nlp_status nlp_get_stage_times(nlp_plan p, int *stage_ids, double *ms, int max, int *count) {
+    if (!p || !count) return NLP_ERR_INVALID_ARG;
+    *count = 0;
+    if (!p->timing || p->nev < 2) return NLP_OK;
+    if (cudaEventSynchronize(p->ev[p->nev - 1]) != cudaSuccess) return NLP_ERR_CUDA;
+    int c = 0;
+    for (int i = 1; i < p->nev && c < max; ++i, ++c) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev[i - 1], p->ev[i]) != cudaSuccess) return NLP_ERR_CUDA;
+        if (ms) ms[c] = (double)t;
+        if (stage_ids) stage_ids[c] = p->ev_stage[i];
+    }
+    *count = c;
+    return NLP_OK;
 }
 
 }  // extern "C"

@@ -33,6 +33,11 @@ struct nlp_plan_s {
     nlp::FftLen<float> plain_f[3]{};
     nlp::FftLen<double> plain_d[3]{};
     bool plain_ready = false;
+    // stage timers (CUDA events on the plan stream), off unless enabled
+    int timing = 0;
+    int nev = 0;
+    cudaEvent_t ev[16] = {};
+    int ev_stage[16] = {};
 };
 
 namespace nlp {
