@@ -136,6 +136,27 @@ nlp_status nlp_gf_step(nlp_plan plan, void *phi_dev, const void *V_dev, double b
 nlp_status nlp_energies(nlp_plan plan, const void *phi_dev, const void *V_dev, double beta,
                         double g, double *energies);
 
+/* Energies as nlp_energies, for callers that must not allocate device memory during the
+ * call.  nlp_energies allocates the plan's gradient-flow workspace on its first use; code
+ * that runs under CUDA stream capture (where cudaMalloc is not allowed) or inside a
+ * process whose device memory belongs to another allocator cannot let that happen.  This
+ * entry point calls no cudaMalloc, cudaFree or other allocating routine: its buffers
+ * (density, potential, spectrum, FFT tables, FP64 partial sums) live in one file-scope
+ * static device array of 1 MiB, which every GPU that loads the library holds until the
+ * process exits.  The potential inside uses the spectra nlp_plan_create allocated.
+ * (The paper has no counterpart: this is a deployment variant of nlp_energies.)
+ *  - Limit: grids of at most 32768 points (e.g. 32^3, 128 x 256); larger grids return
+ *    NLP_ERR_INVALID_ARG before any launch.  NLP_POISSON_2D plans: NLP_ERR_UNSUPPORTED.
+ *  - The first call on each device looks up the array's device address there
+ *    (cudaGetSymbolAddress, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the array and it keeps the last call's contents; every value a call
+ *    reads it first writes.  Calls that overlap on the GPU (other streams, other host
+ *    threads) race on the array and must not be issued.
+ * Synchronizes the plan stream. */
+nlp_status nlp_energies_noalloc(nlp_plan plan, const void *phi_dev, const void *V_dev, double beta,
+                                double g, double *energies);
+
 /* One time step of the time-splitting Fourier pseudospectral method (Sec. 4.1):
  * order 2: K(tau/2) P(tau) K(tau/2) with the kinetic flow K solved exactly in Fourier space
  * and P(s): psi <- exp(-i (V + g|psi|^2 + beta U*|psi|^2) s) psi (Eq. (sps-eq68));

@@ -61,6 +61,7 @@ def _load():
         "nlp_gf_step": ([P, P, P, D, D, D, D, I, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "nlp_energies": ([P, P, P, D, D, ctypes.POINTER(D)], I),
         "nlp_ts_step": ([P, P, P, D, D, D, I], I),
+        "nlp_energies_noalloc": ([P, P, P, D, D, ctypes.POINTER(D)], I),
         "nlp_set_stage_timing": ([P, I], I),
         "nlp_get_stage_times": ([P, ctypes.POINTER(I), ctypes.POINTER(D), I, ctypes.POINTER(I)], I),
         "nlp_measure_alu_peak": ([I, P, ctypes.POINTER(D)], I),
@@ -182,6 +183,13 @@ def nlp_gf_step(plan, phi, V, beta: float, g: float = 0.0, tau: float = 1e-2, in
 def nlp_energies(plan, phi, V, beta: float, g: float = 0.0) -> dict:
     E = (ctypes.c_double * 5)()
     _check(_lib.nlp_energies(plan, _ptr(phi), _ptr(V), float(beta), float(g), E), "nlp_energies")
+    return dict(zip(("E", "Ekin", "Epot", "Eint", "mu"), list(E)))
+
+
+def nlp_energies_noalloc(plan, phi, V, beta: float, g: float = 0.0) -> dict:
+    """As nlp_energies, with no device allocation (static 1 MiB scratch; grids <= 32768 points)."""
+    E = (ctypes.c_double * 5)()
+    _check(_lib.nlp_energies_noalloc(plan, _ptr(phi), _ptr(V), float(beta), float(g), E), "nlp_energies_noalloc")
     return dict(zip(("E", "Ekin", "Epot", "Eint", "mu"), list(E)))
 
 

@@ -12,6 +12,7 @@ nlp_status gf_step_impl(nlp_plan_s *p, void *phi, const void *V, double beta, do
                         double inner_tol, int max_inner, double *max_change, int *inner_iters, double *energies);
 nlp_status energies_impl(nlp_plan_s *p, const void *phi, const void *V, double beta, double g, double *energies);
 nlp_status ts_step_impl(nlp_plan_s *p, void *psi, const void *V, double beta, double g, double tau, int order);
+nlp_status energies_noalloc_impl(nlp_plan_s *p, const void *phi, const void *V, double beta, double g, double *E);
 
 // Stage markers for the optional event timers (ids are part of the ABI: nlpot.h).
 static inline void mark(nlp_plan_s *p, int stage) {
@@ -204,6 +205,13 @@ nlp_status nlp_energies(nlp_plan p, const void *phi_dev, const void *V_dev, doub
     if (!p || !phi_dev || !V_dev || !energies) return NLP_ERR_INVALID_ARG;
     if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
     return energies_impl(p, phi_dev, V_dev, beta, g, energies);
+}
+
+nlp_status nlp_energies_noalloc(nlp_plan p, const void *phi_dev, const void *V_dev, double beta, double g,
+                                double *energies) {
+    if (!p || !phi_dev || !V_dev || !energies) return NLP_ERR_INVALID_ARG;
+    if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+    return energies_noalloc_impl(p, phi_dev, V_dev, beta, g, energies);
 }
 
 nlp_status nlp_ts_step(nlp_plan p, void *psi_dev, const void *V_dev, double beta, double g, double tau, int order) {

@@ -7,6 +7,7 @@
 // Sums, minima/maxima and norms are reduced in FP64 for both plan precisions.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "launch.h"
@@ -446,6 +447,114 @@ static nlp_status ts_t(nlp_plan_s *p, cpx<T> *psi, const T *V, double beta, doub
 nlp_status ts_step_impl(nlp_plan_s *p, void *psi, const void *V, double beta, double g, double tau, int order) {
     if (p->prec == NLP_FP64) return ts_t<double>(p, (cpx<double> *)psi, (const double *)V, beta, g, tau, order);
     return ts_t<float>(p, (cpx<float> *)psi, (const float *)V, beta, g, tau, order);
+}
+
+// ------------------------------------------------------------------ energies without allocation
+// nlp_energies allocates the plan's gradient-flow workspace on its first call.  Callers that
+// must not call the device allocator at that point (code running under stream capture,
+// where cudaMalloc is not allowed, or a process whose device memory is owned by another
+// allocator) use nlp_energies_noalloc instead: the same energy reductions with every
+// buffer carved from one file-scope static device array.  The potential evaluation inside
+// uses the plan's spectra, which nlp_plan_create already allocated.
+constexpr int64_t kNoAllocMaxPoints = 32768;          // grid points (e.g. 32^3 or 128 x 256)
+constexpr size_t kNoAllocBytes = 1u << 20;            // 1 MiB per device, held until exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128] = {};
+
+// Device address of the static array on the current device (set up once per device).
+static nlp_status noalloc_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NLP_ERR_CUDA;
+    if (dev < 0 || dev >= 128) return NLP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return NLP_ERR_CUDA;
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NLP_OK;
+}
+
+template <typename T> __global__ void k_fill_twiddles(cpx<T> *tw, int N) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)k / (double)N, &sn, &cs);
+        tw[k] = mk<T>((T)cs, (T)(-sn));
+    }
+}
+
+template <typename T> __global__ void k_fill_value(T *a, int n, T v) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) a[k] = v;
+}
+
+static bool factor_noalloc(int N, int *rad, int *nrad) {
+    int k = 0;
+    while (N % 4 == 0 && k < kMaxRadices) { rad[k++] = 4; N /= 4; }
+    while (N % 2 == 0 && k < kMaxRadices) { rad[k++] = 2; N /= 2; }
+    while (N % 3 == 0 && k < kMaxRadices) { rad[k++] = 3; N /= 3; }
+    while (N % 5 == 0 && k < kMaxRadices) { rad[k++] = 5; N /= 5; }
+    *nrad = k;
+    return N == 1;
+}
+
+template <typename T>
+static nlp_status energies_noalloc_t(nlp_plan_s *p, const T *x, const T *V, double beta, double g, double *E) {
+    const int64_t N = (int64_t)grid_points(p);
+    if (N > kNoAllocMaxPoints) return NLP_ERR_INVALID_ARG;
+    const int n[3] = {p->n3[0], p->n3[1], p->n3[2]};
+    const size_t nh = (size_t)n[2] / 2 + 1;
+    // layout of the static array, checked before any launch
+    size_t sizes[11] = {sizeof(T) * N, sizeof(T) * N, sizeof(cpx<T>) * n[0] * n[1] * nh,
+                        sizeof(double) * 2 * kRedBlocks, sizeof(double) * S_COUNT};
+    for (int a = 0; a < 3; ++a) {
+        sizes[5 + a] = n[a] > 1 ? sizeof(cpx<T>) * n[a] : 0;
+        sizes[8 + a] = sizeof(T) * n[a];
+    }
+    size_t off[11], total = 0;
+    for (int i = 0; i < 11; ++i) {
+        off[i] = total;
+        total += (sizes[i] + 255) & ~(size_t)255;
+    }
+    if (total > kNoAllocBytes) return NLP_ERR_INVALID_ARG;
+    void *base = nullptr;
+    nlp_status s = noalloc_scratch(&base);
+    if (s) return s;
+    char *b = (char *)base;
+    Work<T> W;
+    memset(&W, 0, sizeof(W));
+    W.rho = (T *)(b + off[0]);
+    W.pot = (T *)(b + off[1]);
+    W.spec = (cpx<T> *)(b + off[2]);
+    W.part = (double *)(b + off[3]);
+    W.scal = (double *)(b + off[4]);
+    DevPlan<T> &D = W.PD;
+    D.dim = p->grid.dim;
+    for (int a = 0; a < 3; ++a) {
+        D.n[a] = n[a];
+        D.nf[a] = n[a];
+        D.len[a].N = n[a];
+        if (n[a] > 1) {
+            if (!factor_noalloc(n[a], D.len[a].rad, &D.len[a].nrad)) return NLP_ERR_UNSUPPORTED;
+            cpx<T> *tw = (cpx<T> *)(b + off[5 + a]);
+            k_fill_twiddles<T><<<(n[a] + 255) / 256, 256, 0, p->stream>>>(tw, n[a]);
+            D.len[a].tw = tw;
+        }
+        T *ones = (T *)(b + off[8 + a]);
+        k_fill_value<T><<<(n[a] + 255) / 256, 256, 0, p->stream>>>(ones, n[a], (T)1);
+        D.deconv[a] = ones;
+    }
+    if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
+    D.nh = (int)nh;
+    D.F = D.G = W.spec;
+    return energies_t<T>(p, &W, x, V, beta, g, E);
+}
+
+nlp_status energies_noalloc_impl(nlp_plan_s *p, const void *phi, const void *V, double beta, double g, double *E) {
+    if (p->prec == NLP_FP64) return energies_noalloc_t<double>(p, (const double *)phi, (const double *)V, beta, g, E);
+    return energies_noalloc_t<float>(p, (const float *)phi, (const float *)V, beta, g, E);
 }
 
 }  // namespace nlp
