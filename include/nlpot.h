@@ -72,8 +72,10 @@ typedef struct {
                                n_theta and n_phi must be even (k -> -k symmetry). */
     double dipole_axis[3];  /* NLP_DIPOLE_3D: unit vector (normalised here; zero vector -> z) */
     double nufft_tol;       /* NUFFT tolerance, 1e-14..1e-2; 0 -> 1e-12 (FP64) / 1e-6 (FP32) */
-    int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 4, 8 or 16 */
-    int reserved[7];        /* must be zero */
+    int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 4, 8, 16 or 32 */
+    int spread_variant;     /* 0 = default (3D: register-column kernel where the width is supported),
+                               1 = shared-memory-atomics kernel everywhere */
+    int reserved[6];        /* must be zero */
 } nlp_opts;
 
 typedef struct nlp_plan_s *nlp_plan;
@@ -92,6 +94,8 @@ typedef struct {
     int tile;
     size_t workspace_bytes; /* device memory owned by the plan */
     double sigma_poisson;   /* NLP_POISSON_2D: width of the auxiliary Gaussian */
+    int sub_tile;           /* register kernel sub-tile edge (0: shared-memory-atomics kernel) */
+    int64_t segments;       /* register kernel work units (node runs of one sub-tile) */
 } nlp_plan_info;
 
 /* Create a plan: quadrature nodes and weights (FP64), their binning by fine-grid tile,

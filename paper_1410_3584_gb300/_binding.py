@@ -28,7 +28,7 @@ class nlp_grid(ctypes.Structure):
 class nlp_opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_double), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
                 ("n_phi", ctypes.c_int), ("dipole_axis", ctypes.c_double * 3), ("nufft_tol", ctypes.c_double),
-                ("tile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("tile", ctypes.c_int), ("spread_variant", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class nlp_plan_info(ctypes.Structure):
@@ -37,7 +37,8 @@ class nlp_plan_info(ctypes.Structure):
                 ("beta_es", ctypes.c_double), ("kmax", ctypes.c_double), ("n_r", ctypes.c_int),
                 ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int), ("nodes_total", ctypes.c_int64),
                 ("nodes_half", ctypes.c_int64), ("tiles", ctypes.c_int64), ("chunks", ctypes.c_int64),
-                ("tile", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t), ("sigma_poisson", ctypes.c_double)]
+                ("tile", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t), ("sigma_poisson", ctypes.c_double),
+                ("sub_tile", ctypes.c_int), ("segments", ctypes.c_int64)]
 
 
 class NlpError(RuntimeError):
@@ -105,7 +106,8 @@ def _stream_handle(stream):
 
 
 def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.0, counts=None,
-                    dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, stream=None):
+                    dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, spread_variant: int = 0,
+                    stream=None):
     """Create a plan; returns an opaque handle (ctypes.c_void_p).  See nlpot.h."""
     g = nlp_grid()
     g.dim = len(n)
@@ -123,6 +125,7 @@ def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.
         o.dipole_axis[a] = float(dipole_axis[a])
     o.nufft_tol = float(tol)
     o.tile = int(tile)
+    o.spread_variant = int(spread_variant)
     h = ctypes.c_void_p()
     _check(_lib.nlp_plan_create(ctypes.byref(g), KERNELS[kernel], PRECISIONS[precision], ctypes.byref(o),
                                 _stream_handle(stream), ctypes.byref(h)), "nlp_plan_create")

@@ -70,6 +70,15 @@ template <typename T> struct DevPlan {
     const double *mom;
     double hvol;
     double sigma;
+    // register kernel (3D): sub-tile edge (0 = generic kernel only), segments = pieces of
+    // runs of nodes of one sub-tile ([start, end) node pairs, packed sub-tile origin),
+    // chunks = ranges of segments of one tile
+    int sub_T;
+    const int *seg_node;
+    const uint32_t *seg_sub;
+    const Chunk *rchunks;
+    int64_t nrchunks;
+    const T *psi_tab;   // per node: kernel values [3][W] in sub-window coordinates (register kernels)
 };
 
 }  // namespace nlp

@@ -26,6 +26,10 @@ cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, 
 // Fused interpolate -> scale -> spread over all node chunks (see spread.cu).
 template <typename T> cudaError_t launch_interp_spread(const DevPlan<T> &P, cudaStream_t st);
 template <typename T> size_t interp_spread_smem(const DevPlan<T> &P);
+// Register-column variant for 3D (see spread_reg.cu); W = sub-tile edge + w - 1.
+template <typename T> bool reg_kernel_supported(int W);
+template <typename T> size_t interp_spread_reg_smem(const DevPlan<T> &P);
+template <typename T> cudaError_t launch_interp_spread_reg(const DevPlan<T> &P, cudaStream_t st);
 
 // 2D Poisson (Algorithm 1) FP64 parts (see poisson2d.cu).  L, h: collapsed 3D view.
 template <typename T>

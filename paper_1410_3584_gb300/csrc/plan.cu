@@ -143,13 +143,25 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.nh = D.nf[2] / 2 + 1;
     D.w = p->info.width;
     D.beta = (T)p->info.beta_es;
+    // register kernel (3D): sub-tile edge Ts with column length W = Ts + w - 1 (see spread_reg.cu)
+    D.sub_T = 0;
     int Tt = p->opts.tile;
+    if (p->grid.dim == 3 && p->opts.spread_variant == 0) {
+        const int Ts = 2;
+        if (reg_kernel_supported<T>(Ts + D.w - 1)) {
+            D.sub_T = Ts;
+            if (Tt == 0) Tt = sizeof(T) == 8 ? 4 : 8;
+            if (Tt % Ts) Tt = (Tt / Ts + 1) * Ts;
+        }
+    }
     if (Tt == 0) Tt = (p->grid.dim == 2) ? 16 : (sizeof(T) == 8 ? 4 : 8);
     D.T_tile[0] = p->grid.dim == 3 ? Tt : 1;
     D.T_tile[1] = Tt;
     D.T_tile[2] = Tt;
     p->info.tile = Tt;
+    p->info.sub_tile = D.sub_T;
     if (interp_spread_smem(D) > 227 * 1024) return NLP_ERR_UNSUPPORTED;
+    if (D.sub_T > 0 && interp_spread_reg_smem(D) > 227 * 1024) return NLP_ERR_UNSUPPORTED;
     for (int a = 0; a < 3; ++a) {
         nlp_status s = make_fft_len<T>(p, D.nf[a], &D.len[a]);
         if (s) return s;
@@ -177,9 +189,12 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.F = (cpx<T> *)dF;
     D.G = (cpx<T> *)dG;
 
-    // ---- bin nodes by tile of their first tap
+    // ---- bin nodes by tile of their first tap, then by sub-tile inside the tile
     const int64_t M = (int64_t)nodes.size();
     const int wa[3] = {p->grid.dim == 3 ? D.w : 1, D.w, D.w};
+    const int Ts = D.sub_T;
+    const int nsub = (Ts > 0) ? D.T_tile[2] / Ts : 1;            // sub-tiles per tile edge (3D)
+    const int64_t nsub3 = (int64_t)nsub * nsub * nsub;
     std::vector<int64_t> s0(M * 3), tb(M * 3);
     int64_t tmin[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, tmax[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
     for (int64_t j = 0; j < M; ++j)
@@ -194,40 +209,113 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     if (M > 0)
         for (int a = 0; a < 3; ++a) K[a] = tmax[a] - tmin[a] + 1;
     const int64_t ntile = K[0] * K[1] * K[2];
-    std::vector<int64_t> cnt(M > 0 ? ntile + 1 : 1, 0);
+    const int64_t nkey = ntile * nsub3;
+    std::vector<int64_t> cnt(M > 0 ? nkey + 1 : 1, 0);
     std::vector<int64_t> key(M);
     for (int64_t j = 0; j < M; ++j) {
-        key[j] = ((tb[3 * j] - tmin[0]) * K[1] + (tb[3 * j + 1] - tmin[1])) * K[2] + (tb[3 * j + 2] - tmin[2]);
+        const int64_t tk = ((tb[3 * j] - tmin[0]) * K[1] + (tb[3 * j + 1] - tmin[1])) * K[2] + (tb[3 * j + 2] - tmin[2]);
+        int64_t sk = 0;
+        if (Ts > 0)
+            for (int a = 0; a < 3; ++a) sk = sk * nsub + (s0[3 * j + a] - tb[3 * j + a] * D.T_tile[a]) / Ts;
+        key[j] = tk * nsub3 + sk;
         cnt[key[j] + 1]++;
     }
-    for (int64_t t = 0; t < (M > 0 ? ntile : 0); ++t) cnt[t + 1] += cnt[t];
+    for (int64_t t = 0; t < (M > 0 ? nkey : 0); ++t) cnt[t + 1] += cnt[t];
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - (M > 0 ? 1 : 0));
     std::vector<int64_t> order(M);
     for (int64_t j = 0; j < M; ++j) order[pos[key[j]]++] = j;
-    // chunks
+    // chunks (generic kernel: node ranges of one tile) and segments (register kernel:
+    // runs of one sub-tile, chunked at segment boundaries)
     const int CH = sizeof(T) == 8 ? 256 : 1024;
-    std::vector<Chunk> chunks;
+    std::vector<Chunk> chunks, rchunks;
+    std::vector<int> seg_node;
+    std::vector<uint32_t> seg_sub;
     int64_t ntiles_used = 0;
     for (int64_t t = 0; t < (M > 0 ? ntile : 0); ++t) {
-        const int64_t c0 = cnt[t], c1 = cnt[t + 1];
+        const int64_t c0 = cnt[t * nsub3], c1 = cnt[(t + 1) * nsub3];
         if (c1 == c0) continue;
         ++ntiles_used;
         const int64_t k2 = t % K[2], k1 = (t / K[2]) % K[1], k0 = t / (K[1] * K[2]);
+        Chunk ch;
+        ch.bx = (int)((k0 + tmin[0]) * D.T_tile[0]);
+        ch.by = (int)((k1 + tmin[1]) * D.T_tile[1]);
+        ch.bz = (int)((k2 + tmin[2]) * D.T_tile[2]);
         const int64_t nch = (c1 - c0 + CH - 1) / CH;
         for (int64_t c = 0; c < nch; ++c) {
-            Chunk ch;
-            ch.bx = (int)((k0 + tmin[0]) * D.T_tile[0]);
-            ch.by = (int)((k1 + tmin[1]) * D.T_tile[1]);
-            ch.bz = (int)((k2 + tmin[2]) * D.T_tile[2]);
             ch.j0 = (int)(c0 + (c1 - c0) * c / nch);
             ch.j1 = (int)(c0 + (c1 - c0) * (c + 1) / nch);
             chunks.push_back(ch);
         }
+        if (Ts > 0) {
+            // pieces of at most SEGMAX nodes of one sub-tile (dense sub-tiles spread over all
+            // warps of a CTA); a chunk closes at a piece boundary once it holds CH nodes
+            const int SEGMAX = sizeof(T) == 8 ? 32 : 64;
+            int64_t acc = 0;
+            Chunk rc = ch;
+            rc.j0 = (int)seg_sub.size();
+            auto close = [&]() {
+                rc.j1 = (int)seg_sub.size();
+                if (rc.j1 > rc.j0) {
+                    // heaviest pieces first inside the chunk (dynamic assignment to warps)
+                    std::vector<int> idx(rc.j1 - rc.j0);
+                    std::iota(idx.begin(), idx.end(), rc.j0);
+                    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+                        return seg_node[2 * a + 1] - seg_node[2 * a] > seg_node[2 * b + 1] - seg_node[2 * b];
+                    });
+                    std::vector<int> sn(2 * idx.size());
+                    std::vector<uint32_t> ss(idx.size());
+                    for (size_t i = 0; i < idx.size(); ++i) {
+                        sn[2 * i] = seg_node[2 * idx[i]];
+                        sn[2 * i + 1] = seg_node[2 * idx[i] + 1];
+                        ss[i] = seg_sub[idx[i]];
+                    }
+                    std::copy(sn.begin(), sn.end(), seg_node.begin() + 2 * rc.j0);
+                    std::copy(ss.begin(), ss.end(), seg_sub.begin() + rc.j0);
+                    rchunks.push_back(rc);
+                }
+                rc.j0 = (int)seg_sub.size();
+                acc = 0;
+            };
+            for (int64_t u = 0; u < nsub3; ++u) {
+                int64_t a0 = cnt[t * nsub3 + u];
+                const int64_t a1 = cnt[t * nsub3 + u + 1];
+                const uint32_t so = (uint32_t)((u / (nsub * nsub)) * Ts) | (uint32_t)(((u / nsub) % nsub) * Ts) << 8 |
+                                    (uint32_t)((u % nsub) * Ts) << 16;
+                while (a0 < a1) {
+                    const int64_t take = std::min<int64_t>(a1 - a0, SEGMAX);
+                    if (acc > 0 && acc + take > CH) close();
+                    seg_node.push_back((int)a0);
+                    seg_node.push_back((int)(a0 + take));
+                    seg_sub.push_back(so);
+                    acc += take;
+                    a0 += take;
+                }
+            }
+            close();
+        }
     }
-    std::stable_sort(chunks.begin(), chunks.end(),
-                     [](const Chunk &a, const Chunk &b) { return (a.j1 - a.j0) > (b.j1 - b.j0); });
+    auto by_size = [](const Chunk &a, const Chunk &b) { return (a.j1 - a.j0) > (b.j1 - b.j0); };
+    std::stable_sort(chunks.begin(), chunks.end(), by_size);
+    if (Ts > 0) {   // heaviest chunks (most nodes) first
+        auto nodes_of = [&](const Chunk &c) {
+            int64_t n = 0;
+            for (int i = c.j0; i < c.j1; ++i) n += seg_node[2 * i + 1] - seg_node[2 * i];
+            return n;
+        };
+        std::vector<std::pair<int64_t, int>> w(rchunks.size());
+        for (size_t i = 0; i < rchunks.size(); ++i) w[i] = {nodes_of(rchunks[i]), (int)i};
+        std::stable_sort(w.begin(), w.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+        std::vector<Chunk> sorted(rchunks.size());
+        for (size_t i = 0; i < w.size(); ++i) sorted[i] = rchunks[w[i].second];
+        rchunks.swap(sorted);
+    }
     std::vector<T> nd(4 * (size_t)M);
     std::vector<uint32_t> no(M);
+    // kernel values of every node (the nodes are fixed per plan), already placed in the
+    // sub-window of its segment: psi[j][axis][i], i = 0..W-1, tap t = i - (o mod Ts), zero
+    // outside 0 <= t < w
+    const int Wsub = Ts + D.w - 1;
+    std::vector<T> ptab(Ts > 0 ? (size_t)M * 3 * Wsub : 0);
     std::vector<double> pois;
     if (p->kernel == NLP_POISSON_2D) pois.resize(3 * (size_t)M);
     for (int64_t q = 0; q < M; ++q) {
@@ -241,6 +329,20 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         }
         nd[4 * q + 3] = (T)nodes[j].omega;
         no[q] = packed;
+        if (!ptab.empty())
+            for (int a = 0; a < 3; ++a) {
+                const int r = (int)((s0[3 * j + a] - tb[3 * j + a] * D.T_tile[a]) % Ts);
+                for (int i = 0; i < Wsub; ++i) {
+                    const int t = i - r;
+                    double v = 0.0;
+                    if (t >= 0 && t < D.w) {
+                        const double x = 2.0 * ((double)t - (nodes[j].z[a] - (double)s0[3 * j + a])) / D.w;
+                        const double sv = 1.0 - x * x;
+                        v = sv > 0 ? std::exp(p->info.beta_es * (std::sqrt(sv) - 1.0)) : 0.0;
+                    }
+                    ptab[((size_t)q * 3 + a) * Wsub + i] = (T)v;
+                }
+            }
         if (!pois.empty()) {
             pois[3 * q] = nodes[j].k[0];
             pois[3 * q + 1] = nodes[j].k[1];
@@ -255,6 +357,27 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         cudaMemcpy(dnd, nd.data(), sizeof(T) * nd.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(dno, no.data(), sizeof(uint32_t) * no.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(dch, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice);
+    }
+    D.rchunks = nullptr;
+    D.nrchunks = 0;
+    D.psi_tab = nullptr;
+    if (Ts > 0 && M) {
+        void *dpt;
+        if ((s = alloc_dev(p, &dpt, sizeof(T) * ptab.size()))) return s;
+        cudaMemcpy(dpt, ptab.data(), sizeof(T) * ptab.size(), cudaMemcpyHostToDevice);
+        D.psi_tab = (const T *)dpt;
+        void *dsn, *dss, *drc;
+        if ((s = alloc_dev(p, &dsn, sizeof(int) * seg_node.size()))) return s;
+        if ((s = alloc_dev(p, &dss, sizeof(uint32_t) * seg_sub.size()))) return s;
+        if ((s = alloc_dev(p, &drc, sizeof(Chunk) * rchunks.size()))) return s;
+        cudaMemcpy(dsn, seg_node.data(), sizeof(int) * seg_node.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dss, seg_sub.data(), sizeof(uint32_t) * seg_sub.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(drc, rchunks.data(), sizeof(Chunk) * rchunks.size(), cudaMemcpyHostToDevice);
+        D.seg_node = (const int *)dsn;
+        D.seg_sub = (const uint32_t *)dss;
+        D.rchunks = (const Chunk *)drc;
+        D.nrchunks = (int64_t)rchunks.size();
+        p->info.segments = (int64_t)seg_sub.size();
     }
     D.pois = nullptr;
     D.mom = nullptr;
@@ -419,7 +542,8 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if (o->n_r > 4096 || o->n_theta > 4096 || o->n_phi > 8192) return NLP_ERR_INVALID_ARG;
         if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
         if (o->tile != 0 && o->tile != 4 && o->tile != 8 && o->tile != 16 && o->tile != 32) return NLP_ERR_INVALID_ARG;
-        for (int i = 0; i < 7; ++i)
+        if (o->spread_variant != 0 && o->spread_variant != 1) return NLP_ERR_INVALID_ARG;
+        for (int i = 0; i < 6; ++i)
             if (o->reserved[i]) return NLP_ERR_INVALID_ARG;
         for (int a = 0; a < 3; ++a)
             if (!std::isfinite(o->dipole_axis[a])) return NLP_ERR_INVALID_ARG;

@@ -1,0 +1,396 @@
+// Fused interpolate -> scale -> spread for 3D with register-resident columns.
+//
+// Same operation as k_interp_spread (spread.cu); different work decomposition.  The tile
+// window of the forward spectrum F and of the spreading target G stays in shared memory,
+// but per-tap shared-memory traffic is removed:
+//   - nodes of a tile are sorted by sub-tile (edge Ts) at plan time; a run of nodes of one
+//     sub-tile is a segment.  All nodes of a segment share the sub-window of W = Ts + w - 1
+//     cells per axis.
+//   - a team of warps owns one segment at a time: lane (cx, cy) holds the z-column
+//     F[cx, cy, 0..W) of the sub-window and a G accumulator column in registers.
+//   - nodes are processed in batches of NB.  The w kernel values per axis are written to
+//     shared memory shifted to sub-window coordinates (zeros outside the support), so
+//     interpolation is, per lane, W complex-real multiply-adds on registers; the partial
+//     sums of the NB nodes are reduced across the team with one multi-value transpose
+//     reduction (log2(32) shuffle steps for all 2 NB values together) and a short
+//     cross-warp pass; scaled values come back through shared memory and spreading is W
+//     more multiply-adds into the register accumulators.
+//   - at the end of a segment the G columns are added to the shared window (one shared
+//     atomic per cell and segment, not per tap), and at the end of the chunk the window
+//     is added to global G with the Hermitian fold.
+#include "common.cuh"
+#include "launch.h"
+#include "spread_common.cuh"
+
+namespace nlp {
+
+template <int W> struct RegCfg {
+    static constexpr int TT = ((W * W + 31) / 32) * 32;       // threads per team
+    static constexpr int NT = (256 / TT) > 0 ? (256 / TT) : 1; // teams per CTA
+    static constexpr int TW = TT / 32;                         // warps per team
+};
+
+__device__ __forceinline__ void team_sync(int team, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(nthreads) : "memory");
+}
+
+// Reduce V values across the 32 lanes of a warp (V a power of two <= 32).  Recursive
+// halving: at the step with offset s each lane keeps the half of its values selected by
+// its lane bit s and adds the other half received from lane ^ s.  On return v[0] of lane
+// L is the warp sum of value index (L >> (5 - log2 V)) & (V - 1).
+template <typename T, int V>
+__device__ __forceinline__ void warp_reduce_multi(T (&v)[V], int lane) {
+    int off = 16;
+#pragma unroll
+    for (int half = V / 2; half >= 1; half /= 2) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const T send = up ? v[i] : v[i + half];
+            const T keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+        off >>= 1;
+    }
+    for (; off >= 1; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+}
+
+template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
+template <> struct Log2<1> { static constexpr int value = 0; };
+
+template <typename T, int W, int NB>
+__global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_reg(DevPlan<T> P) {
+    constexpr int TT = RegCfg<W>::TT, TW = RegCfg<W>::TW;
+    constexpr int NT = RegCfg<W>::NT;
+    constexpr int V = 2 * NB;
+    constexpr int SH = 5 - Log2<V>::value;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int w = P.w;
+    const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
+    const int WW = Wt0 * Wt1 * Wt2;
+    cpx<T> *sF = (cpx<T> *)smraw;
+    cpx<T> *sG = sF + WW;
+    const int team = threadIdx.x / TT, tl = threadIdx.x % TT;
+    T *psi = (T *)(sG + WW) + team * (NB * 3 * W + TW * V + V);
+    T *red = psi + NB * 3 * W;
+    T *cbuf = red + TW * V;
+    const Chunk ch = P.rchunks[blockIdx.x];
+
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
+        sF[q] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
+        sG[q] = mk<T>(0, 0);
+    }
+    __syncthreads();
+
+    const bool active = tl < W * W;
+    const int cx = active ? tl / W : 0, cy = active ? tl % W : 0;
+    const int lane = threadIdx.x & 31, wt = tl >> 5;
+    for (int sg = ch.j0 + team; sg < ch.j1; sg += NT) {
+        const uint32_t so = P.seg_sub[sg];
+        const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
+        const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
+        const int colbase = ((so0 + cx) * Wt1 + (so1 + cy)) * Wt2 + so2;
+        T fx[W], fy[W], gx[W], gy[W];
+#pragma unroll
+        for (int z = 0; z < W; ++z) {
+            const cpx<T> f = active ? sF[colbase + z] : mk<T>(0, 0);
+            fx[z] = f.x;
+            fy[z] = f.y;
+            gx[z] = (T)0;
+            gy[z] = (T)0;
+        }
+        for (int jb = j0; jb < j1; jb += NB) {
+            const int nb = min(NB, j1 - jb);
+            // kernel values of the batch: a contiguous block of the plan-time table
+            {
+                const T *src = P.psi_tab + (int64_t)jb * 3 * W;
+                for (int q = tl; q < nb * 3 * W; q += TT) psi[q] = src[q];
+            }
+            team_sync(team, TT);
+            // interpolation partials of the NB nodes
+            T v[V];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                v[2 * k] = (T)0;
+                v[2 * k + 1] = (T)0;
+                if (k < nb) {   // uniform across the team: empty batch slots cost nothing
+                    const T *pk = psi + k * 3 * W;
+                    const T wxy = pk[cx] * pk[W + cy];
+                    T sx = (T)0, sy = (T)0;
+#pragma unroll
+                    for (int z = 0; z < W; ++z) {
+                        const T pz = pk[2 * W + z];
+                        sx += fx[z] * pz;
+                        sy += fy[z] * pz;
+                    }
+                    if (active) {
+                        v[2 * k] = wxy * sx;
+                        v[2 * k + 1] = wxy * sy;
+                    }
+                }
+            }
+            warp_reduce_multi<T, V>(v, lane);
+            if ((lane & ((1 << SH) - 1)) == 0) red[wt * V + ((lane >> SH) & (V - 1))] = v[0];
+            team_sync(team, TT);
+            if (tl < V) {
+                T s = (T)0;
+#pragma unroll
+                for (int u = 0; u < TW; ++u) s += red[u * V + tl];
+                const int k = tl >> 1;
+                cbuf[tl] = (k < nb) ? s * P.nd[4 * ((int64_t)jb + k) + 3] : (T)0;
+            }
+            team_sync(team, TT);
+            // spreading into the register columns
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                if (k < nb) {
+                    const T *pk = psi + k * 3 * W;
+                    const T wxy = active ? pk[cx] * pk[W + cy] : (T)0;
+                    const T cr = cbuf[2 * k] * wxy, ci = cbuf[2 * k + 1] * wxy;
+#pragma unroll
+                    for (int z = 0; z < W; ++z) {
+                        const T pz = pk[2 * W + z];
+                        gx[z] += cr * pz;
+                        gy[z] += ci * pz;
+                    }
+                }
+            }
+            team_sync(team, TT);
+        }
+        if (active) {
+#pragma unroll
+            for (int z = 0; z < W; ++z) {
+                if (gx[z] != (T)0) atomicAdd(&sG[colbase + z].x, gx[z]);
+                if (gy[z] != (T)0) atomicAdd(&sG[colbase + z].y, gy[z]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        const cpx<T> v = sG[q];
+        if (v.x == (T)0 && v.y == (T)0) continue;
+        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
+        store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
+    }
+}
+
+// One warp per segment (W*W <= 64): lane L owns the z-columns L and L + 32 of the sub-window,
+// so interpolation sums reduce inside the warp and the node loop needs no block barrier.
+template <typename T, int W, int NB>
+__global__ void __launch_bounds__(256) k_interp_spread_warp(DevPlan<T> P) {
+    static_assert(W * W <= 64, "two columns per lane");
+    constexpr int V = 2 * NB;
+    constexpr int SH = 5 - Log2<V>::value;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int w = P.w;
+    const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
+    const int WW = Wt0 * Wt1 * Wt2;
+    cpx<T> *sF = (cpx<T> *)smraw;
+    cpx<T> *sG = sF + WW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    T *psi = (T *)(sG + WW) + warp * (NB * 3 * W + V);
+    T *cb = psi + NB * 3 * W;
+    const Chunk ch = P.rchunks[blockIdx.x];
+    __shared__ int next_seg;
+    if (threadIdx.x == 0) next_seg = ch.j0 + nwarps;
+
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
+        sF[q] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
+        sG[q] = mk<T>(0, 0);
+    }
+    __syncthreads();
+
+    const int ca = lane, cbc = lane + 32;
+    const bool act_b = cbc < W * W;
+    const int xa = ca / W, ya = ca % W;                 // W*W > 32 for W >= 6: column a always active
+    const int xb = act_b ? cbc / W : 0, yb = act_b ? cbc % W : 0;
+    const bool act_a = ca < W * W;
+    // pieces are sorted heaviest first; each warp takes the next free one
+    for (int sg = ch.j0 + warp; sg < ch.j1;) {
+        const uint32_t so = P.seg_sub[sg];
+        const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
+        const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
+        const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * Wt2 + so2;
+        const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * Wt2 + so2;
+        T fax[W], fay[W], fbx[W], fby[W], gax[W], gay[W], gbx[W], gby[W];
+#pragma unroll
+        for (int z = 0; z < W; ++z) {
+            const cpx<T> fa = act_a ? sF[basea + z] : mk<T>(0, 0);
+            const cpx<T> fb = act_b ? sF[baseb + z] : mk<T>(0, 0);
+            fax[z] = fa.x; fay[z] = fa.y; fbx[z] = fb.x; fby[z] = fb.y;
+            gax[z] = gay[z] = gbx[z] = gby[z] = (T)0;
+        }
+        // the batch's kernel values are a contiguous block of the plan-time table; the next
+        // block is fetched into registers while the current batch computes
+        constexpr int PQ = (NB * 3 * W + 31) / 32;
+        T pf[PQ];
+        auto fetch = [&](int jbn, int nbn) {
+            const T *src = P.psi_tab + (int64_t)jbn * 3 * W;
+#pragma unroll
+            for (int u = 0; u < PQ; ++u) {
+                const int q = lane + 32 * u;
+                pf[u] = (q < nbn * 3 * W) ? __ldg(src + q) : (T)0;
+            }
+        };
+        fetch(j0, min(NB, j1 - j0));
+        for (int jb = j0; jb < j1; jb += NB) {
+            const int nb = min(NB, j1 - jb);
+#pragma unroll
+            for (int u = 0; u < PQ; ++u) {
+                const int q = lane + 32 * u;
+                if (q < NB * 3 * W) psi[q] = pf[u];
+            }
+            __syncwarp();
+            if (jb + NB < j1) fetch(jb + NB, min(NB, j1 - jb - NB));
+            T v[V], wa[NB], wb[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                v[2 * k] = v[2 * k + 1] = (T)0;
+                wa[k] = wb[k] = (T)0;
+                if (k < nb) {
+                    const T *pk = psi + k * 3 * W;
+                    wa[k] = act_a ? pk[xa] * pk[W + ya] : (T)0;
+                    wb[k] = act_b ? pk[xb] * pk[W + yb] : (T)0;
+                    T sax = 0, say = 0, sbx = 0, sby = 0;
+#pragma unroll
+                    for (int z = 0; z < W; ++z) {
+                        const T pz = pk[2 * W + z];
+                        sax += fax[z] * pz;
+                        say += fay[z] * pz;
+                        sbx += fbx[z] * pz;
+                        sby += fby[z] * pz;
+                    }
+                    v[2 * k] = wa[k] * sax + wb[k] * sbx;
+                    v[2 * k + 1] = wa[k] * say + wb[k] * sby;
+                }
+            }
+            warp_reduce_multi<T, V>(v, lane);
+            if ((lane & ((1 << SH) - 1)) == 0) {
+                const int idx = (lane >> SH) & (V - 1);
+                const int k = idx >> 1;
+                cb[idx] = (k < nb) ? v[0] * P.nd[4 * ((int64_t)jb + k) + 3] : (T)0;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                if (k < nb) {
+                    const T *pk = psi + k * 3 * W;
+                    const T cr = cb[2 * k], ci = cb[2 * k + 1];
+                    const T ar = cr * wa[k], ai = ci * wa[k], br = cr * wb[k], bi = ci * wb[k];
+#pragma unroll
+                    for (int z = 0; z < W; ++z) {
+                        const T pz = pk[2 * W + z];
+                        gax[z] += ar * pz;
+                        gay[z] += ai * pz;
+                        gbx[z] += br * pz;
+                        gby[z] += bi * pz;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int z = 0; z < W; ++z) {
+            if (act_a) {
+                if (gax[z] != (T)0) atomicAdd(&sG[basea + z].x, gax[z]);
+                if (gay[z] != (T)0) atomicAdd(&sG[basea + z].y, gay[z]);
+            }
+            if (act_b) {
+                if (gbx[z] != (T)0) atomicAdd(&sG[baseb + z].x, gbx[z]);
+                if (gby[z] != (T)0) atomicAdd(&sG[baseb + z].y, gby[z]);
+            }
+        }
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&next_seg, 1);
+        sg = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        const cpx<T> v = sG[q];
+        if (v.x == (T)0 && v.y == (T)0) continue;
+        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
+        store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
+    }
+}
+
+// supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
+template <typename T> bool reg_kernel_supported(int W) {
+    return sizeof(T) == 8 ? (W >= 9 && W <= 16) : (W >= 5 && W <= 11);
+}
+
+template <typename T> static constexpr int nb_of() { return 4; }   // nodes per batch (register budget)
+
+template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
+    const size_t WW = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
+    constexpr int NB = nb_of<T>();
+    if constexpr (W * W <= 64) return 2 * WW * sizeof(cpx<T>) + 8 * (NB * 3 * W + 2 * NB) * sizeof(T);
+    return 2 * WW * sizeof(cpx<T>) +
+           (size_t)RegCfg<W>::NT * (NB * 3 * W + RegCfg<W>::TW * 2 * NB + 2 * NB) * sizeof(T);
+}
+
+template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cudaStream_t st) {
+    constexpr int NB = nb_of<T>();
+    const size_t sm = reg_smem<T, W>(P);
+    if constexpr (W * W <= 64) {
+        cudaError_t e = cudaFuncSetAttribute(k_interp_spread_warp<T, W, NB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_interp_spread_warp<T, W, NB><<<(unsigned)P.nrchunks, 256, sm, st>>>(P);
+        return cudaGetLastError();
+    }
+    cudaError_t e =
+        cudaFuncSetAttribute(k_interp_spread_reg<T, W, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_interp_spread_reg<T, W, NB><<<(unsigned)P.nrchunks, RegCfg<W>::TT * RegCfg<W>::NT, sm, st>>>(P);
+    return cudaGetLastError();
+}
+
+#define NLP_REG_SWITCH(T, W, CALL)                       \
+    switch (W) {                                         \
+        case 5: CALL(T, 5); case 6: CALL(T, 6);          \
+        case 7: CALL(T, 7); case 8: CALL(T, 8);          \
+        case 9: CALL(T, 9); case 10: CALL(T, 10);        \
+        case 11: CALL(T, 11); case 12: CALL(T, 12);      \
+        case 13: CALL(T, 13); case 14: CALL(T, 14);      \
+        case 15: CALL(T, 15); case 16: CALL(T, 16);      \
+        default: break;                                  \
+    }
+
+template <> size_t interp_spread_reg_smem<float>(const DevPlan<float> &P) {
+    const int W = P.sub_T + P.w - 1;
+#define SM_F(T, X) if constexpr (X >= 5 && X <= 11) return reg_smem<T, X>(P); break;
+    NLP_REG_SWITCH(float, W, SM_F)
+#undef SM_F
+    return 0;
+}
+template <> size_t interp_spread_reg_smem<double>(const DevPlan<double> &P) {
+    const int W = P.sub_T + P.w - 1;
+#define SM_D(T, X) if constexpr (X >= 9 && X <= 16) return reg_smem<T, X>(P); break;
+    NLP_REG_SWITCH(double, W, SM_D)
+#undef SM_D
+    return 0;
+}
+
+template <> cudaError_t launch_interp_spread_reg<float>(const DevPlan<float> &P, cudaStream_t st) {
+    if (P.nrchunks == 0) return cudaSuccess;
+    const int W = P.sub_T + P.w - 1;
+#define L_F(T, X) if constexpr (X >= 5 && X <= 11) return launch_w<T, X>(P, st); break;
+    NLP_REG_SWITCH(float, W, L_F)
+#undef L_F
+    return cudaErrorInvalidValue;
+}
+template <> cudaError_t launch_interp_spread_reg<double>(const DevPlan<double> &P, cudaStream_t st) {
+    if (P.nrchunks == 0) return cudaSuccess;
+    const int W = P.sub_T + P.w - 1;
+#define L_D(T, X) if constexpr (X >= 9 && X <= 16) return launch_w<T, X>(P, st); break;
+    NLP_REG_SWITCH(double, W, L_D)
+#undef L_D
+    return cudaErrorInvalidValue;
+}
+
+template bool reg_kernel_supported<float>(int);
+template bool reg_kernel_supported<double>(int);
+
+}  // namespace nlp

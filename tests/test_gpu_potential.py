@@ -149,3 +149,20 @@ def test_full_size_metric_config(nl, prec):
     err = cf.rel_linf(phi, ref)
     print("128^3 %s rel L-inf vs oracle %.3e  nodes %d" % (prec, err, info["nodes_total"]))
     assert err < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,tol,variant", [
+    ("fp32", 1e-6, 1), ("fp64", 1e-12, 1),                  # shared-memory-atomics kernel
+    ("fp32", 1e-4, 0), ("fp32", 1e-8, 0), ("fp32", 1e-9, 0),  # register kernel, w = 5, 9, 10
+    ("fp64", 1e-10, 0), ("fp64", 1e-13, 0), ("fp64", 1e-14, 0)])
+def test_3d_spread_variants_and_widths(nl, prec, tol, variant):
+    g = W.Grid((30, 24, 20), (7.0, 6.0, 5.0))
+    rho = W.random_density(g, 9)
+    P = math.pi / max(g.h)
+    counts = (32, 32, 64)
+    phi, info = gpu_eval(nl, g, rho, "coulomb3d", prec, kmax=P, counts=counts, tol=tol, spread_variant=variant)
+    ref = potential.eval_nufft(rho, g, "coulomb3d", P, counts, tol=1e-13)
+    err = cf.rel_linf(phi, ref)
+    bound = max(TOL[prec] if tol <= (1e-6 if prec == "fp32" else 1e-12) else 0.0, 50 * tol, 1e-13)
+    assert (info["sub_tile"] > 0) == (variant == 0)
+    assert err < bound, (err, bound, info["width"], info["sub_tile"])
