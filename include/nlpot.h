@@ -72,7 +72,7 @@ typedef struct {
                                n_theta and n_phi must be even (k -> -k symmetry). */
     double dipole_axis[3];  /* NLP_DIPOLE_3D: unit vector (normalised here; zero vector -> z) */
     double nufft_tol;       /* NUFFT tolerance, 1e-14..1e-2; 0 -> 1e-12 (FP64) / 1e-6 (FP32) */
-    int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 4, 8, 16 or 32 */
+    int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 2..32 */
     int spread_variant;     /* 0 = default (3D: register-column kernel where the width is supported),
                                1 = shared-memory-atomics kernel everywhere */
     int reserved[6];        /* must be zero */
@@ -167,6 +167,48 @@ nlp_status nlp_energies_noalloc(nlp_plan plan, const void *phi_dev, const void *
  * order 4: Yoshida's composition of three order-2 steps.  psi_dev: complex, in place. */
 nlp_status nlp_ts_step(nlp_plan plan, void *psi_dev, const void *V_dev, double beta, double g,
                        double tau, int order);
+
+/* ---------------------------------------------------------------- batched evaluation
+ * Many FP32 plans (any mix of grids and of the NLP_COULOMB_3D / NLP_DIPOLE_3D /
+ * NLP_COULOMB_2D kernels) evaluated by ONE persistent kernel launch, replayed from a CUDA
+ * graph captured at creation.  Work items are (plan, stage, block) tasks taken in
+ * stage-major order from a device ticket counter; a stage of one plan starts when the
+ * previous stage of the same plan has completed, which the device checks with a bounded
+ * number of polls (NLP_ERR_TIMEOUT if a limit runs out; the batch stays usable).
+ * The batch uses the plans' own workspaces: the plans must outlive the batch and must not
+ * be evaluated while a batch evaluation is in flight.  Not thread-safe. */
+typedef struct nlp_batch_s *nlp_batch;
+
+/* plans: count FP32 plans (no NLP_POISSON_2D: NLP_ERR_UNSUPPORTED).  stream: cudaStream_t
+ * for all batch work (must not be the legacy NULL stream: graph capture). */
+nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_batch *out);
+
+/* phi_i = U_i * rho_i for every plan i: rho_dev[i], phi_dev[i] device arrays as for
+ * nlp_eval_potential.  Asynchronous (one graph launch); call nlp_batch_sync for the result
+ * status.  The pointer arrays are copied before return. */
+nlp_status nlp_batch_eval(nlp_batch batch, const void *const *rho_dev, void *const *phi_dev);
+
+/* Waits for the last nlp_batch_eval; NLP_ERR_TIMEOUT if a dependency poll ran out. */
+nlp_status nlp_batch_sync(nlp_batch batch);
+
+nlp_status nlp_batch_get_info(nlp_batch batch, int *tasks, int *grid_ctas, size_t *smem_bytes);
+
+/* Test hook: set the poll limit of the dependency waits and, if block_item and block_stage
+ * are >= 0, make that stage of that item never count as complete, so the stages after it
+ * run out of polls (failure injection on the host; the device only sees an unreachable
+ * count).  Pass -1, -1 to restore normal operation.  Re-captures the graph. */
+nlp_status nlp_batch_set_wait_limit(nlp_batch batch, long long polls, int block_item, int block_stage);
+
+void nlp_batch_destroy(nlp_batch batch);
+
+/* Spread-tile autotuner: times complete evaluations of plans built with each candidate
+ * tile edge (FP32 3D: 4, 8, 16; FP64 3D: 2, 4, 6; 2D: 8, 16, 32) on zero input (the work is
+ * data independent) and returns the fastest in *best_tile with its time.  If cache_path
+ * is not NULL the choice is looked up in / appended to that text file (one line per
+ * configuration).  Allocates plan workspaces temporarily; synchronous. */
+nlp_status nlp_autotune_tile(const nlp_grid *grid, nlp_kernel kernel, nlp_precision prec,
+                             const nlp_opts *base, void *stream, const char *cache_path,
+                             int *best_tile, double *best_ms);
 
 /* Stage timers for measurement (not part of the method).  When enabled, each evaluation
  * records CUDA events on the plan stream between its stages; nlp_get_stage_times then

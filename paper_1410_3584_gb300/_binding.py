@@ -66,6 +66,14 @@ def _load():
         "nlp_set_stage_timing": ([P, I], I),
         "nlp_get_stage_times": ([P, ctypes.POINTER(I), ctypes.POINTER(D), I, ctypes.POINTER(I)], I),
         "nlp_measure_alu_peak": ([I, P, ctypes.POINTER(D)], I),
+        "nlp_batch_create": ([ctypes.POINTER(P), I, P, ctypes.POINTER(P)], I),
+        "nlp_batch_eval": ([P, ctypes.POINTER(P), ctypes.POINTER(P)], I),
+        "nlp_batch_sync": ([P], I),
+        "nlp_batch_get_info": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t)], I),
+        "nlp_batch_set_wait_limit": ([P, ctypes.c_longlong, I, I], I),
+        "nlp_batch_destroy": ([P], None),
+        "nlp_autotune_tile": ([ctypes.POINTER(nlp_grid), I, I, ctypes.POINTER(nlp_opts), P, ctypes.c_char_p,
+                               ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "nlp_status_string": ([I], ctypes.c_char_p),
         "nlp_version": ([], ctypes.c_char_p),
     }
@@ -105,10 +113,7 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.0, counts=None,
-                    dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, spread_variant: int = 0,
-                    stream=None):
-    """Create a plan; returns an opaque handle (ctypes.c_void_p).  See nlpot.h."""
+def _grid_opts(n, L, kmax=0.0, counts=None, dipole_axis=(0.0, 0.0, 0.0), tol=0.0, tile=0, spread_variant=0):
     g = nlp_grid()
     g.dim = len(n)
     for a in range(len(n)):
@@ -126,6 +131,14 @@ def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.
     o.nufft_tol = float(tol)
     o.tile = int(tile)
     o.spread_variant = int(spread_variant)
+    return g, o
+
+
+def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.0, counts=None,
+                    dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, spread_variant: int = 0,
+                    stream=None):
+    """Create a plan; returns an opaque handle (ctypes.c_void_p).  See nlpot.h."""
+    g, o = _grid_opts(n, L, kmax, counts, dipole_axis, tol, tile, spread_variant)
     h = ctypes.c_void_p()
     _check(_lib.nlp_plan_create(ctypes.byref(g), KERNELS[kernel], PRECISIONS[precision], ctypes.byref(o),
                                 _stream_handle(stream), ctypes.byref(h)), "nlp_plan_create")
@@ -227,11 +240,60 @@ def nlp_measure_alu_peak(precision: str, stream=None) -> float:
     return v.value
 
 
+def nlp_autotune_tile(n, L, kernel: str, precision: str = "fp32", cache_path=None, stream=None, **opts):
+    """Fastest spread tile edge for this configuration: (tile, ms)."""
+    g, o = _grid_opts(n, L, **opts)
+    t = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(_lib.nlp_autotune_tile(ctypes.byref(g), KERNELS[kernel], PRECISIONS[precision], ctypes.byref(o),
+                                  _stream_handle(stream), cache_path.encode() if cache_path else None,
+                                  ctypes.byref(t), ctypes.byref(ms)), "nlp_autotune_tile")
+    return t.value, ms.value
+
+
+def nlp_batch_create(plans, stream=None):
+    """Batch of FP32 plan handles -> batch handle (the plans must outlive it)."""
+    arr = (ctypes.c_void_p * len(plans))(*[ctypes.cast(p, ctypes.c_void_p) for p in plans])
+    h = ctypes.c_void_p()
+    _check(_lib.nlp_batch_create(arr, len(plans), _stream_handle(stream), ctypes.byref(h)), "nlp_batch_create")
+    return h
+
+
+def nlp_batch_eval(batch, rhos, phis):
+    """One graph-replayed persistent launch over all plans (asynchronous)."""
+    r = (ctypes.c_void_p * len(rhos))(*[t.data_ptr() for t in rhos])
+    f = (ctypes.c_void_p * len(phis))(*[t.data_ptr() for t in phis])
+    _check(_lib.nlp_batch_eval(batch, r, f), "nlp_batch_eval")
+
+
+def nlp_batch_sync(batch, raise_on_error: bool = True) -> int:
+    st = _lib.nlp_batch_sync(batch)
+    if raise_on_error:
+        _check(st, "nlp_batch_sync")
+    return st
+
+
+def nlp_batch_get_info(batch) -> dict:
+    t, g, sm = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
+    _check(_lib.nlp_batch_get_info(batch, ctypes.byref(t), ctypes.byref(g), ctypes.byref(sm)), "nlp_batch_get_info")
+    return {"tasks": t.value, "grid": g.value, "smem": sm.value}
+
+
+def nlp_batch_set_wait_limit(batch, polls: int, block_item: int = -1, block_stage: int = -1):
+    _check(_lib.nlp_batch_set_wait_limit(batch, int(polls), int(block_item), int(block_stage)),
+           "nlp_batch_set_wait_limit")
+
+
+def nlp_batch_destroy(batch):
+    _lib.nlp_batch_destroy(batch)
+
+
 class Plan:
     """Owning wrapper: Plan(n, L, kernel, precision, ...) ... .close()."""
 
     def __init__(self, n, L, kernel, precision="fp64", **kw):
         self.n, self.L, self.kernel, self.precision = tuple(n), tuple(L), kernel, precision
+        self.stream = kw.get("stream")
         self.handle = nlp_plan_create(n, L, kernel, precision, **kw)
         self.info = nlp_plan_get_info(self.handle)
 
@@ -248,6 +310,11 @@ class Plan:
         _check_tensor(phi, self.torch_dtype, int(np.prod(self.n)), "phi")
         nlp_eval_potential(self.handle, rho, phi)
         return phi
+
+    def sync(self):
+        """Wait for the work enqueued on the plan's stream (the current stream if none was given)."""
+        import torch
+        (self.stream or torch.cuda.current_stream()).synchronize()
 
     def close(self):
         if self.handle:

@@ -1,0 +1,451 @@
+// Batched evaluation of many FP32 plans (different grids and kernels) in one persistent
+// launch, replayed from a captured CUDA graph, and the spread-tile autotuner.
+//
+// Work is a list of tasks (plan p, stage k, block i) in stage-major order; each CTA of the
+// persistent grid takes the next ticket from a global counter.  Stage k of plan p may run
+// once the last non-empty earlier stage of p has completed all its blocks: the CTA's first
+// thread polls that stage's completion counter (acquire) with a bounded number of tries.
+// Every ticket a task can wait on is smaller than its own, so the CTAs that hold them are
+// already running: progress needs no co-residency guarantee.  A poll that runs out sets the
+// device error word; every CTA then drains the remaining tickets without work and the host
+// reports NLP_ERR_TIMEOUT.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fft_dev.cuh"
+#include "launch.h"
+#include "plan.h"
+#include "spread_dev.cuh"
+
+namespace nlp {
+
+enum { ST_R2C = 0, ST_A1, ST_A0, ST_CLEAR, ST_SPREAD, ST_B0, ST_B1, ST_C2R, kStages };
+constexpr int kClearChunk = 1 << 16;   // complex elements of G zeroed per clear task
+
+struct BatchItem {
+    DevPlan<float> P;
+    StridedDesc a1, a0, b0, b1;
+    int nb_r2c, nb_a1, nb_a0, nb_c2r;
+    int ntask[kStages];
+    int dep[kStages];        // stage this stage waits for (-1: none)
+    int spread_warp;         // 1: register kernel (W = 8), 0: shared-atomics kernel
+    int64_t gsize;           // complex elements of G
+};
+
+struct BatchArgs {
+    const BatchItem *items;
+    int nitems;
+    const int *off;          // kStages * nitems + 1 ticket offsets (stage-major)
+    int total;
+    int *ticket;             // [0] ticket counter, [1] error word
+    int *done;               // nitems * kStages completion counters
+    long long spin_limit;    // polls before giving up
+    const float *const *rho; // per item (pointer table)
+    float *const *phi;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(256, 1) k_batch_persistent(BatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_task, s_ok;
+    for (;;) {
+        __syncthreads();   // the previous task's shared memory is no longer in use
+        if (threadIdx.x == 0) s_task = atomicAdd(A.ticket, 1);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= A.total) break;
+        // decode (stage, item): last offset <= t
+        int lo = 0, hi = kStages * A.nitems;   // off[lo] <= t < off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (A.off[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int k = lo / A.nitems, p = lo % A.nitems, i = t - A.off[lo];
+        const BatchItem &B = A.items[p];
+        if (threadIdx.x == 0) {
+            int ok = ld_acquire(A.ticket + 1) == 0;
+            const int d = B.dep[k];
+            if (ok && d >= 0) {
+                const int *cnt = A.done + p * kStages + d;
+                const int need = B.ntask[d];
+                long long n = 0;
+                while (ld_acquire(cnt) < need) {
+                    if (++n > A.spin_limit || ld_acquire(A.ticket + 1) != 0) {
+                        ok = 0;
+                        atomicExch(A.ticket + 1, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();   // as a grid barrier: the stage's writes are visible to this CTA
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) continue;   // drain: tickets are still taken so every CTA reaches the end
+        switch (k) {
+            case ST_R2C: fwd_r2c_block<float>(A.rho[p], B.P, B.nb_r2c, i, smraw); break;
+            case ST_A1: fft_strided_block<float, -1>(B.P.F, B.a1, B.P.len[1], B.nb_a1, i, smraw); break;
+            case ST_A0: fft_strided_block<float, -1>(B.P.F, B.a0, B.P.len[0], B.nb_a0, i, smraw); break;
+            case ST_CLEAR: {
+                const int64_t e0 = (int64_t)i * kClearChunk, e1 = min(e0 + kClearChunk, B.gsize);
+                for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) B.P.G[e] = mk<float>(0.f, 0.f);
+                break;
+            }
+            case ST_SPREAD:
+                if (B.spread_warp) spread_warp_block<float, 8, 4>(B.P, i, smraw);
+                else spread_generic_block<float>(B.P, i, smraw);
+                break;
+            case ST_B0: fft_strided_block<float, +1>(B.P.G, B.b0, B.P.len[0], B.nb_a0, i, smraw); break;
+            case ST_B1: fft_strided_block<float, +1>(B.P.G, B.b1, B.P.len[1], B.nb_a1, i, smraw); break;
+            case ST_C2R: inv_c2r_block<float>(A.phi[p], B.P, B.nb_c2r, i, smraw); break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(A.done + p * kStages + k, 1);
+        }
+    }
+}
+
+// lines per block of one FFT pass, as the single-plan launchers choose it
+static int lpb(int N) {
+    const int budget = 160 * 1024 / (int)sizeof(cpx<float>);
+    int nb = 16;
+    while (nb > 1 && 2 * N * (nb + 1) + N > budget) nb >>= 1;
+    return nb;
+}
+static size_t fft_bytes(int N, int nb) { return sizeof(cpx<float>) * ((size_t)N + 2 * (size_t)N * (nb + 1)); }
+
+}  // namespace nlp
+
+using namespace nlp;
+
+struct nlp_batch_s {
+    cudaStream_t stream = nullptr;
+    int count = 0;
+    std::vector<nlp_plan> plans;
+    std::vector<void *> allocs;
+    BatchItem *d_items = nullptr;
+    int *d_off = nullptr, *d_ctr = nullptr;   // ctr: [ticket, err] + done counters
+    const float **d_rho = nullptr;
+    float **d_phi = nullptr;
+    void **h_ptrs = nullptr;                  // pinned: rho[count], phi[count]
+    int *h_err = nullptr;                     // pinned copy of the error word
+    size_t ctr_bytes = 0;
+    int total = 0, grid = 0;
+    size_t smem = 0;
+    long long spin_limit = 1 << 24;
+    std::vector<BatchItem> items;
+    std::vector<int> off;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+
+static nlp_status batch_graph(nlp_batch_s *b) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    BatchArgs A;
+    A.items = b->d_items;
+    A.nitems = b->count;
+    A.off = b->d_off;
+    A.total = b->total;
+    A.ticket = b->d_ctr;
+    A.done = b->d_ctr + 2;
+    A.spin_limit = b->spin_limit;
+    A.rho = b->d_rho;
+    A.phi = b->d_phi;
+    cudaStream_t st = b->stream;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NLP_ERR_CUDA;
+    cudaMemcpyAsync(b->d_rho, b->h_ptrs, sizeof(void *) * 2 * b->count, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
+    k_batch_persistent<<<b->grid, 256, b->smem, st>>>(A);
+    cudaMemcpyAsync(b->h_err, b->d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamEndCapture(st, &b->graph) != cudaSuccess) return NLP_ERR_CUDA;
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return NLP_ERR_CUDA;
+    return NLP_OK;
+}
+
+extern "C" {
+
+void nlp_batch_destroy(nlp_batch b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev) cudaEventDestroy(b->ev);
+    for (void *a : b->allocs) cudaFree(a);
+    if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    delete b;
+}
+
+nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_batch *out) {
+    if (!out || !plans || count < 1 || count > 4096) return NLP_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int p = 0; p < count; ++p) {
+        if (!plans[p]) return NLP_ERR_INVALID_ARG;
+        if (plans[p]->prec != NLP_FP32 || plans[p]->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+    }
+    nlp_batch_s *b = new (std::nothrow) nlp_batch_s();
+    if (!b) return NLP_ERR_OOM;
+    b->stream = (cudaStream_t)stream;
+    b->count = count;
+    b->plans.assign(plans, plans + count);
+    b->items.resize(count);
+    size_t smem = 0;
+    for (int p = 0; p < count; ++p) {
+        nlp_plan_s *pl = plans[p];
+        const DevPlan<float> &D = pl->pf;
+        BatchItem &B = b->items[p];
+        memset(&B, 0, sizeof(B));
+        B.P = D;
+        const bool three = pl->grid.dim == 3;
+        const int64_t nh = D.nh;
+        B.a1.n_in = D.n[1]; B.a1.n_out = D.nf[1]; B.a1.es = nh; B.a1.ncol = (int)nh;
+        B.a1.nouter = three ? D.n[0] : 1; B.a1.os = (int64_t)D.nf[1] * nh;
+        B.a1.outer_map_n = three ? D.n[0] : 0; B.a1.outer_map_N = D.nf[0];
+        B.b1 = B.a1; B.b1.n_in = D.nf[1]; B.b1.n_out = D.n[1];
+        if (three) {
+            B.a0.n_in = D.n[0]; B.a0.n_out = D.nf[0]; B.a0.es = (int64_t)D.nf[1] * nh; B.a0.ncol = (int)nh;
+            B.a0.nouter = D.nf[1]; B.a0.os = nh;
+            B.b0 = B.a0; B.b0.n_in = D.nf[0]; B.b0.n_out = D.n[0];
+        }
+        B.nb_r2c = B.nb_c2r = lpb(D.len[2].N);
+        B.nb_a1 = nh >= 16 ? lpb(D.len[1].N) : (int)nh;
+        B.nb_a0 = three ? (nh >= 16 ? lpb(D.len[0].N) : (int)nh) : 1;
+        const int64_t npairs = (int64_t)D.n[0] * D.n[1] / 2;
+        B.ntask[ST_R2C] = (int)((npairs + B.nb_r2c - 1) / B.nb_r2c);
+        B.ntask[ST_A1] = B.a1.nouter * (int)((nh + B.nb_a1 - 1) / B.nb_a1);
+        B.ntask[ST_A0] = three ? B.a0.nouter * (int)((nh + B.nb_a0 - 1) / B.nb_a0) : 0;
+        B.gsize = (int64_t)D.nf[0] * D.nf[1] * nh;
+        B.ntask[ST_CLEAR] = (int)((B.gsize + kClearChunk - 1) / kClearChunk);
+        B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
+        B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);
+        B.ntask[ST_B0] = B.ntask[ST_A0];
+        B.ntask[ST_B1] = B.ntask[ST_A1];
+        B.ntask[ST_C2R] = B.ntask[ST_R2C];
+        // stage dependencies: spreading needs the forward spectrum and the cleared G
+        int last = -1;
+        for (int k = 0; k < kStages; ++k) {
+            B.dep[k] = last;
+            if (B.ntask[k] > 0) last = k;
+        }
+        // fixed-size sums of the FFT and spreading shared memory
+        smem = std::max(smem, fft_bytes(D.len[2].N, B.nb_r2c));
+        smem = std::max(smem, fft_bytes(D.len[1].N, B.nb_a1));
+        if (three) smem = std::max(smem, fft_bytes(D.len[0].N, B.nb_a0));
+        smem = std::max(smem, B.spread_warp ? interp_spread_reg_smem<float>(D) : interp_spread_smem<float>(D));
+    }
+    b->smem = smem;
+    // CLEAR of G only needs nothing before it, but must finish before SPREAD: SPREAD depends
+    // on CLEAR, which depends on the forward passes (stage order), so G is never cleared
+    // while a previous evaluation still reads it.
+    b->off.assign((size_t)kStages * count + 1, 0);
+    int t = 0;
+    for (int k = 0; k < kStages; ++k)
+        for (int p = 0; p < count; ++p) {
+            b->off[(size_t)k * count + p] = t;
+            t += b->items[p].ntask[k];
+        }
+    b->off[(size_t)kStages * count] = t;
+    b->total = t;
+    auto dalloc = [&](void **ptr, size_t bytes) -> nlp_status {
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) { cudaGetLastError(); return NLP_ERR_OOM; }
+        b->allocs.push_back(*ptr);
+        return NLP_OK;
+    };
+    nlp_status s;
+    void *d;
+    if ((s = dalloc(&d, sizeof(BatchItem) * count))) { nlp_batch_destroy(b); return s; }
+    b->d_items = (BatchItem *)d;
+    if ((s = dalloc(&d, sizeof(int) * b->off.size()))) { nlp_batch_destroy(b); return s; }
+    b->d_off = (int *)d;
+    b->ctr_bytes = sizeof(int) * (2 + (size_t)kStages * count);
+    if ((s = dalloc(&d, b->ctr_bytes))) { nlp_batch_destroy(b); return s; }
+    b->d_ctr = (int *)d;
+    if ((s = dalloc(&d, sizeof(void *) * 2 * count))) { nlp_batch_destroy(b); return s; }
+    b->d_rho = (const float **)d;
+    b->d_phi = (float **)d + count;
+    if (cudaMallocHost((void **)&b->h_ptrs, sizeof(void *) * 2 * count) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_err, sizeof(int)) != cudaSuccess) {
+        nlp_batch_destroy(b);
+        return NLP_ERR_OOM;
+    }
+    memset(b->h_ptrs, 0, sizeof(void *) * 2 * count);
+    *b->h_err = 0;
+    cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_off, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
+    if (cudaFuncSetAttribute(k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
+        cudaSuccess) {
+        nlp_batch_destroy(b);
+        return NLP_ERR_UNSUPPORTED;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent, 256, b->smem);
+    b->grid = std::max(1, sms * std::max(1, per));
+    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess || (s = batch_graph(b))) {
+        nlp_batch_destroy(b);
+        return s ? s : NLP_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) { nlp_batch_destroy(b); return NLP_ERR_CUDA; }
+    *out = b;
+    return NLP_OK;
+}
+
+nlp_status nlp_batch_eval(nlp_batch b, const void *const *rho_dev, void *const *phi_dev) {
+    if (!b || !rho_dev || !phi_dev) return NLP_ERR_INVALID_ARG;
+    for (int p = 0; p < b->count; ++p)
+        if (!rho_dev[p] || !phi_dev[p]) return NLP_ERR_INVALID_ARG;
+    if (b->pending) {   // the pinned pointer table may still be read by the previous replay
+        if (cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;
+        b->pending = false;
+    }
+    for (int p = 0; p < b->count; ++p) {
+        b->h_ptrs[p] = (void *)rho_dev[p];
+        b->h_ptrs[b->count + p] = phi_dev[p];
+    }
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return NLP_ERR_CUDA;
+    if (cudaEventRecord(b->ev, b->stream) != cudaSuccess) return NLP_ERR_CUDA;
+    b->pending = true;
+    return NLP_OK;
+}
+
+nlp_status nlp_batch_sync(nlp_batch b) {
+    if (!b) return NLP_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return NLP_ERR_CUDA;
+    b->pending = false;
+    return *b->h_err ? NLP_ERR_TIMEOUT : NLP_OK;
+}
+
+nlp_status nlp_batch_get_info(nlp_batch b, int *tasks, int *grid, size_t *smem_bytes) {
+    if (!b) return NLP_ERR_INVALID_ARG;
+    if (tasks) *tasks = b->total;
+    if (grid) *grid = b->grid;
+    if (smem_bytes) *smem_bytes = b->smem;
+    return NLP_OK;
+}
+
+nlp_status nlp_batch_set_wait_limit(nlp_batch b, long long polls, int block_item, int block_stage) {
+    if (!b || polls < 1 || block_item >= b->count || block_stage >= kStages) return NLP_ERR_INVALID_ARG;
+    if (b->pending && cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;
+    b->pending = false;
+    b->spin_limit = polls;
+    // fault injection for tests: one stage's completion target is made unreachable, so the
+    // stages after it poll until the limit runs out and the batch reports NLP_ERR_TIMEOUT
+    std::vector<BatchItem> items = b->items;
+    if (block_item >= 0 && block_stage >= 0) items[block_item].ntask[block_stage] += 1;
+    cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * b->count, cudaMemcpyHostToDevice);
+    return batch_graph(b);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- spread-tile autotuner
+static std::string tune_key(const nlp_grid *g, nlp_kernel k, nlp_precision pr, const nlp_opts &o) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%d %d %d %d %.9g %.9g %.9g %d %d %.3g %.9g %d %d %d %d", g->dim, g->n[0], g->n[1],
+             g->dim == 3 ? g->n[2] : 1, g->L[0], g->L[1], g->dim == 3 ? g->L[2] : 0.0, (int)k, (int)pr, o.nufft_tol,
+             o.kmax, o.n_r, o.n_theta, o.n_phi, o.spread_variant);
+    return std::string(buf);
+}
+
+extern "C" nlp_status nlp_autotune_tile(const nlp_grid *grid, nlp_kernel kernel, nlp_precision prec,
+                                        const nlp_opts *base, void *stream, const char *cache_path, int *best_tile,
+                                        double *best_ms) {
+    if (!grid || !best_tile) return NLP_ERR_INVALID_ARG;
+    nlp_opts o;
+    if (base) o = *base;
+    else memset(&o, 0, sizeof(o));
+    const std::string key = tune_key(grid, kernel, prec, o);
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "r")) {
+            char line[640];
+            int found = 0;
+            while (fgets(line, sizeof(line), f)) {
+                const std::string l(line);
+                const size_t bar = l.find('|');
+                if (bar == std::string::npos) continue;
+                if (l.substr(0, bar) == key) {
+                    int t = 0;
+                    double ms = 0;
+                    if (sscanf(l.c_str() + bar + 1, "%d %lf", &t, &ms) == 2) {
+                        *best_tile = t;
+                        if (best_ms) *best_ms = ms;
+                        found = 1;
+                    }
+                }
+            }
+            fclose(f);
+            if (found) return NLP_OK;
+        }
+    }
+    std::vector<int> cands;
+    if (grid->dim == 2) cands = {8, 16, 32};
+    else if (prec == NLP_FP32) cands = {4, 8, 16};
+    else cands = {2, 4, 6};
+    size_t N = 1;
+    for (int a = 0; a < grid->dim; ++a) N *= (size_t)grid->n[a];
+    const size_t rb = N * (prec == NLP_FP64 ? 8 : 4);
+    void *rho = nullptr, *phi = nullptr;
+    if (cudaMalloc(&rho, rb) != cudaSuccess || cudaMalloc(&phi, rb) != cudaSuccess) {
+        cudaGetLastError();
+        if (rho) cudaFree(rho);
+        return NLP_ERR_OOM;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(rho, 0, rb, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    double bms = 1e300;
+    nlp_status last = NLP_OK;
+    for (int c : cands) {
+        o.tile = c;
+        nlp_plan p = nullptr;
+        nlp_status s = nlp_plan_create(grid, kernel, prec, &o, stream, &p);
+        if (s) { last = s; continue; }
+        double tmin = 1e300;
+        for (int rep = 0; rep < 5; ++rep) {
+            cudaEventRecord(e0, st);
+            s = nlp_eval_potential(p, rho, phi);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < tmin) tmin = ms;   // first evaluation is a warm-up
+        }
+        nlp_plan_destroy(p);
+        if (s) { last = s; continue; }
+        if (tmin < bms) { bms = tmin; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(rho);
+    cudaFree(phi);
+    if (!best) return last ? last : NLP_ERR_UNSUPPORTED;
+    *best_tile = best;
+    if (best_ms) *best_ms = bms;
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "a")) {
+            fprintf(f, "%s|%d %.6f\n", key.c_str(), best, bms);
+            fclose(f);
+        }
+    }
+    return NLP_OK;
+}

@@ -1,0 +1,291 @@
+// FFT device code shared by the single-plan kernels (fft.cu) and the batched persistent
+// kernel (batch.cu): small DFTs, the shared-memory Stockham engine and the per-block bodies
+// of the R2C / C2R / strided passes (block index passed explicitly).
+#pragma once
+#include "common.cuh"
+#include "launch.h"
+
+namespace nlp {
+
+// ------------------------------------------------------------------ small DFTs
+template <typename T, int SGN>
+__device__ __forceinline__ void dft2(cpx<T> *v) {
+    cpx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+}
+template <typename T, int SGN>
+__device__ __forceinline__ void dft4(cpx<T> *v) {
+    cpx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = mul_i(v[1] - v[3], SGN);
+    v[0] = t0 + t2;
+    v[2] = t0 - t2;
+    v[1] = t1 + t3;
+    v[3] = t1 - t3;
+}
+template <typename T, int SGN>
+__device__ __forceinline__ void dft3(cpx<T> *v) {
+    const T s = (T)(SGN * 0.86602540378443864676);   // sign * sin(2 pi / 3)
+    cpx<T> t = v[1] + v[2], u = v[1] - v[2];
+    cpx<T> m = v[0] - scale(t, (T)0.5);
+    cpx<T> iu = mul_i(scale(u, s), 1);
+    v[0] = v[0] + t;
+    v[1] = m + iu;
+    v[2] = m - iu;
+}
+template <typename T, int SGN>
+__device__ __forceinline__ void dft5(cpx<T> *v) {
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
+    const T s1 = (T)(SGN * 0.95105651629515357212), s2 = (T)(SGN * 0.58778525229247312917);
+    cpx<T> a = v[1] + v[4], b = v[2] + v[3], c = v[1] - v[4], d = v[2] - v[3];
+    cpx<T> p1 = v[0] + scale(a, c1) + scale(b, c2);
+    cpx<T> p2 = v[0] + scale(a, c2) + scale(b, c1);
+    cpx<T> q1 = mul_i(scale(c, s1) + scale(d, s2), 1);
+    cpx<T> q2 = mul_i(scale(c, s2) - scale(d, s1), 1);
+    v[0] = v[0] + a + b;
+    v[1] = p1 + q1;
+    v[4] = p1 - q1;
+    v[2] = p2 + q2;
+    v[3] = p2 - q2;
+}
+
+// Batched Stockham FFT of nb lines of length N held as src[i * ldb + b]; ping-pong with
+// dst.  Returns the buffer holding the result.  All threads of the block participate.
+template <typename T, int SGN>
+__device__ cpx<T> *fft_smem(cpx<T> *src, cpx<T> *dst, const FftLen<T> &L, const cpx<T> *tw, int nb,
+                            int ldb) {
+    const int N = L.N;
+    int Ns = 1;
+    for (int s = 0; s < L.nrad; ++s) {
+        const int R = L.rad[s];
+        const int nbf = N / R;
+        const int tws = N / (Ns * R);
+        for (int q = threadIdx.x; q < nbf * nb; q += blockDim.x) {
+            const int b = q % nb;
+            const int j = q / nb;
+            const int k = j % Ns;
+            cpx<T> v[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) v[r] = src[(j + r * nbf) * ldb + b];
+            if (k) {
+#pragma unroll
+                for (int r = 1; r < 5; ++r)
+                    if (r < R) {
+                        cpx<T> t = tw[k * r * tws];
+                        if (SGN > 0) t = conj(t);
+                        v[r] = v[r] * t;
+                    }
+            }
+            if (R == 4) dft4<T, SGN>(v);
+            else if (R == 2) dft2<T, SGN>(v);
+            else if (R == 3) dft3<T, SGN>(v);
+            else dft5<T, SGN>(v);
+            const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) dst[(base + r * Ns) * ldb + b] = v[r];
+        }
+        __syncthreads();
+        cpx<T> *t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T> *s_tw, const FftLen<T> &L) {
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) s_tw[i] = L.tw[i];
+}
+
+__device__ __forceinline__ int wrapi(int l, int N) {
+    int r = l % N;
+    return r < 0 ? r + N : r;
+}
+
+// ------------------------------------------------------------------ forward R2C lines
+// Real grid lines along the last axis (grid index order, n2 points) are multiplied by the
+// deconvolution factors, zero-padded to N2 = nf2 (point i goes to (i - n2/2) mod N2),
+// transformed (e^{-}), and written as half spectra into F[l0][l1][0..nh), where
+// (l0, l1) are the wrapped fine positions of the line.  Two real lines travel as one
+// complex line (x1 + i x2) and are separated after the transform.
+template <typename T>
+__device__ __forceinline__ void fwd_r2c_block(const T *__restrict__ rho, const DevPlan<T> &P, int nb, int bid, unsigned char *smraw) {
+    const FftLen<T> &L = P.len[2];
+    const int N = L.N, n2 = P.n[2], ldb = nb + 1;
+    cpx<T> *s_tw = (cpx<T> *)smraw;
+    cpx<T> *A = s_tw + N;
+    cpx<T> *B = A + N * ldb;
+    load_twiddles(s_tw, L);
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const int64_t p0 = (int64_t)bid * nb;
+    // zero padded positions, load window
+    for (int q = threadIdx.x; q < N * nb; q += blockDim.x) {
+        const int b = q / N, l = q % N;
+        // l is the fine position; window point i with (i - n2/2) mod N == l
+        int i = l < n2 / 2 ? l + n2 / 2 : l - N + n2 / 2;
+        cpx<T> v = mk<T>(0, 0);
+        const int64_t p = p0 + b;
+        if (p < npairs && i >= 0 && i < n2) {
+            const int64_t line0 = 2 * p, line1 = 2 * p + 1;
+            const int i0a = (int)(line0 / P.n[1]), i1a = (int)(line0 % P.n[1]);
+            const int i0b = (int)(line1 / P.n[1]), i1b = (int)(line1 % P.n[1]);
+            const T d2 = P.deconv[2][i];
+            v.x = rho[line0 * n2 + i] * (P.deconv[0][i0a] * P.deconv[1][i1a] * d2);
+            v.y = rho[line1 * n2 + i] * (P.deconv[0][i0b] * P.deconv[1][i1b] * d2);
+        }
+        A[l * ldb + b] = v;
+    }
+    __syncthreads();
+    cpx<T> *R = fft_smem<T, -1>(A, B, L, s_tw, nb, ldb);
+    const int nh = P.nh;
+    for (int q = threadIdx.x; q < nh * nb * 2; q += blockDim.x) {
+        const int k = q % nh;
+        const int t = q / nh;
+        const int b = t >> 1, which = t & 1;
+        const int64_t p = p0 + b;
+        if (p >= npairs) continue;
+        cpx<T> z = R[k * ldb + b];
+        cpx<T> zc = conj(R[((N - k) % N) * ldb + b]);
+        cpx<T> x = which == 0 ? scale(z + zc, (T)0.5) : mul_i(scale(z - zc, (T)0.5), -1);
+        const int64_t line = 2 * p + which;
+        const int i0 = (int)(line / P.n[1]), i1 = (int)(line % P.n[1]);
+        const int l0 = wrapi(i0 - P.n[0] / 2, P.nf[0]), l1 = wrapi(i1 - P.n[1] / 2, P.nf[1]);
+        P.F[((int64_t)l0 * P.nf[1] + l1) * nh + k] = x;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_r2c(const T *__restrict__ rho, DevPlan<T> P, int nb) {
+    extern __shared__ unsigned char smraw[];
+    fwd_r2c_block<T>(rho, P, nb, blockIdx.x, smraw);
+}
+
+// ------------------------------------------------------------------ inverse C2R lines
+// Half spectra G[l0][l1][0..nh) of the wrapped fine positions of each output grid line
+// are transformed back (e^{+}); the output window point i of the line is fine position
+// (i - n2/2) mod N2 and is multiplied by the deconvolution factors.
+template <typename T>
+__device__ __forceinline__ void inv_c2r_block(T *__restrict__ phi, const DevPlan<T> &P, int nb, int bid, unsigned char *smraw) {
+    const FftLen<T> &L = P.len[2];
+    const int N = L.N, n2 = P.n[2], ldb = nb + 1, nh = P.nh;
+    cpx<T> *s_tw = (cpx<T> *)smraw;
+    cpx<T> *A = s_tw + N;
+    cpx<T> *B = A + N * ldb;
+    load_twiddles(s_tw, L);
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const int64_t p0 = (int64_t)bid * nb;
+    for (int q = threadIdx.x; q < nh * nb; q += blockDim.x) {
+        const int k = q % nh, b = q / nh;
+        const int64_t p = p0 + b;
+        cpx<T> x1 = mk<T>(0, 0), x2 = mk<T>(0, 0);
+        if (p < npairs) {
+            const int64_t la = 2 * p, lb = 2 * p + 1;
+            const int l0a = wrapi((int)(la / P.n[1]) - P.n[0] / 2, P.nf[0]);
+            const int l1a = wrapi((int)(la % P.n[1]) - P.n[1] / 2, P.nf[1]);
+            const int l0b = wrapi((int)(lb / P.n[1]) - P.n[0] / 2, P.nf[0]);
+            const int l1b = wrapi((int)(lb % P.n[1]) - P.n[1] / 2, P.nf[1]);
+            x1 = P.G[((int64_t)l0a * P.nf[1] + l1a) * nh + k];
+            x2 = P.G[((int64_t)l0b * P.nf[1] + l1b) * nh + k];
+            if (k == 0 || 2 * k == N) {   // half-spectrum ends of a real line are real
+                x1.y = 0;
+                x2.y = 0;
+            }
+        }
+        // Z[k] = X1[k] + i X2[k];  Z[N-k] = conj(X1[k]) + i conj(X2[k])
+        A[k * ldb + b] = x1 + mul_i(x2, 1);
+        if (k != 0 && 2 * k != N) A[(N - k) * ldb + b] = conj(x1) + mul_i(conj(x2), 1);
+    }
+    __syncthreads();
+    cpx<T> *R = fft_smem<T, +1>(A, B, L, s_tw, nb, ldb);
+    for (int q = threadIdx.x; q < n2 * nb * 2; q += blockDim.x) {
+        const int i = q % n2;
+        const int t = q / n2;
+        const int b = t >> 1, which = t & 1;
+        const int64_t p = p0 + b;
+        if (p >= npairs) continue;
+        const int l = wrapi(i - n2 / 2, N);
+        const cpx<T> z = R[l * ldb + b];
+        const int64_t line = 2 * p + which;
+        const int i0 = (int)(line / P.n[1]), i1 = (int)(line % P.n[1]);
+        const T v = which == 0 ? z.x : z.y;
+        phi[line * n2 + i] = v * (P.deconv[0][i0] * P.deconv[1][i1] * P.deconv[2][i]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_c2r(T *__restrict__ phi, DevPlan<T> P, int nb) {
+    extern __shared__ unsigned char smraw[];
+    inv_c2r_block<T>(phi, P, nb, blockIdx.x, smraw);
+}
+
+// ------------------------------------------------------------------ strided C2C pass
+// Transforms lines along one non-contiguous axis.  Block = (outer line, tile of nb
+// contiguous columns).  Input window: n_in points (fine positions (i - n_in/2) mod N, the
+// rest treated as zero) or the whole line; output window likewise.
+template <typename T, int SGN>
+__device__ __forceinline__ void fft_strided_block(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int nb, int bid, unsigned char *smraw) {
+    const int N = L.N, ldb = nb + 1;
+    cpx<T> *s_tw = (cpx<T> *)smraw;
+    cpx<T> *A = s_tw + N;
+    cpx<T> *B = A + N * ldb;
+    load_twiddles(s_tw, L);
+    const int ctiles = (d.ncol + nb - 1) / nb;
+    const int o = bid / ctiles;
+    const int c0 = (bid % ctiles) * nb;
+    const int oo = d.outer_map_n > 0 ? wrapi(o - d.outer_map_n / 2, d.outer_map_N) : o;
+    cpx<T> *base = data + (int64_t)oo * d.os + c0;
+    const int ncl = min(nb, d.ncol - c0);
+    if (d.n_in < N) {
+        for (int q = threadIdx.x; q < N * nb; q += blockDim.x) A[(q / nb) * ldb + (q % nb)] = mk<T>(0, 0);
+        __syncthreads();
+    }
+    const int nin = d.n_in < N ? d.n_in : N;
+    for (int q = threadIdx.x; q < nin * nb; q += blockDim.x) {
+        const int b = q % nb, i = q / nb;
+        const int l = d.n_in < N ? wrapi(i - d.n_in / 2, N) : i;
+        A[l * ldb + b] = b < ncl ? base[(int64_t)l * d.es + b] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    cpx<T> *R = fft_smem<T, SGN>(A, B, L, s_tw, nb, ldb);
+    const int nout = d.n_out < N ? d.n_out : N;
+    for (int q = threadIdx.x; q < nout * nb; q += blockDim.x) {
+        const int b = q % nb, i = q / nb;
+        if (b >= ncl) continue;
+        const int l = d.n_out < N ? wrapi(i - d.n_out / 2, N) : i;
+        base[(int64_t)l * d.es + b] = R[l * ldb + b];
+    }
+}
+
+template <typename T, int SGN>
+__global__ void __launch_bounds__(256) k_fft_strided(cpx<T> *data, StridedDesc d, FftLen<T> L, int nb) {
+    extern __shared__ unsigned char smraw[];
+    fft_strided_block<T, SGN>(data, d, L, nb, blockIdx.x, smraw);
+}
+
+// ------------------------------------------------------------------ contiguous C2C pass
+// In-place transform of nlines contiguous complex lines of length N, scaled by post.
+template <typename T, int SGN>
+__global__ void __launch_bounds__(256) k_fft_contig(cpx<T> *data, int64_t nlines, FftLen<T> L, int nb, T post) {
+    extern __shared__ unsigned char smraw[];
+    const int N = L.N, ldb = nb + 1;
+    cpx<T> *s_tw = (cpx<T> *)smraw;
+    cpx<T> *A = s_tw + N;
+    cpx<T> *B = A + N * ldb;
+    load_twiddles(s_tw, L);
+    const int64_t l0 = (int64_t)blockIdx.x * nb;
+    for (int q = threadIdx.x; q < N * nb; q += blockDim.x) {
+        const int b = q / N, i = q % N;
+        A[i * ldb + b] = (l0 + b < nlines) ? data[(l0 + b) * N + i] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    cpx<T> *R = fft_smem<T, SGN>(A, B, L, s_tw, nb, ldb);
+    for (int q = threadIdx.x; q < N * nb; q += blockDim.x) {
+        const int b = q / N, i = q % N;
+        if (l0 + b < nlines) data[(l0 + b) * N + i] = scale(R[i * ldb + b], post);
+    }
+}
+
+
+}  // namespace nlp

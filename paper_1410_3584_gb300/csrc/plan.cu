@@ -124,6 +124,33 @@ static bool good_len(int n) {
     return n == 1;
 }
 
+// psi[j][a][i] = phi(2 (i - r_a - delta_a) / w), r_a = (tile offset of node j) mod Ts, zero
+// outside the w taps: the kernel values of node j on the sub-window of its segment (FP64).
+template <typename T>
+__global__ void k_psi_table(T *tab, const T *nd, const uint32_t *no, int64_t M, int w, int Wsub, int Ts, double beta) {
+    const int64_t total = M * 3 * Wsub;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / (3 * Wsub);
+        const int r3 = (int)(e - j * 3 * Wsub), a = r3 / Wsub, i = r3 - a * Wsub;
+        const int r = (int)((no[j] >> (8 * a)) & 0xff) % Ts;
+        const int t = i - r;
+        double v = 0.0;
+        if (t >= 0 && t < w) {
+            const double x = 2.0 * ((double)t - (double)nd[4 * j + a]) / w;
+            const double sv = 1.0 - x * x;
+            v = sv > 0 ? exp(beta * (sqrt(sv) - 1.0)) : 0.0;
+        }
+        tab[e] = (T)v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_psi_table(T *tab, const T *nd, const uint32_t *no, int64_t M, int w, int Wsub, int Ts, double beta,
+                             cudaStream_t st) {
+    k_psi_table<T><<<152 * 16, 256, 0, st>>>(tab, nd, no, M, w, Wsub, Ts, beta);
+    return cudaGetLastError();
+}
+
 static int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Node record before conversion to the plan precision.
@@ -197,11 +224,15 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     const int64_t nsub3 = (int64_t)nsub * nsub * nsub;
     std::vector<int64_t> s0(M * 3), tb(M * 3);
     int64_t tmin[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, tmax[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < M; ++j)
         for (int a = 0; a < 3; ++a) {
             const int64_t sj = (int64_t)std::ceil(nodes[j].z[a] - 0.5 * wa[a]);
             s0[3 * j + a] = sj;
             tb[3 * j + a] = floordiv(sj, D.T_tile[a]);
+        }
+    for (int64_t j = 0; j < M; ++j)
+        for (int a = 0; a < 3; ++a) {
             tmin[a] = std::min(tmin[a], tb[3 * j + a]);
             tmax[a] = std::max(tmax[a], tb[3 * j + a]);
         }
@@ -311,11 +342,7 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     }
     std::vector<T> nd(4 * (size_t)M);
     std::vector<uint32_t> no(M);
-    // kernel values of every node (the nodes are fixed per plan), already placed in the
-    // sub-window of its segment: psi[j][axis][i], i = 0..W-1, tap t = i - (o mod Ts), zero
-    // outside 0 <= t < w
     const int Wsub = Ts + D.w - 1;
-    std::vector<T> ptab(Ts > 0 ? (size_t)M * 3 * Wsub : 0);
     std::vector<double> pois;
     if (p->kernel == NLP_POISSON_2D) pois.resize(3 * (size_t)M);
     for (int64_t q = 0; q < M; ++q) {
@@ -329,20 +356,7 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         }
         nd[4 * q + 3] = (T)nodes[j].omega;
         no[q] = packed;
-        if (!ptab.empty())
-            for (int a = 0; a < 3; ++a) {
-                const int r = (int)((s0[3 * j + a] - tb[3 * j + a] * D.T_tile[a]) % Ts);
-                for (int i = 0; i < Wsub; ++i) {
-                    const int t = i - r;
-                    double v = 0.0;
-                    if (t >= 0 && t < D.w) {
-                        const double x = 2.0 * ((double)t - (nodes[j].z[a] - (double)s0[3 * j + a])) / D.w;
-                        const double sv = 1.0 - x * x;
-                        v = sv > 0 ? std::exp(p->info.beta_es * (std::sqrt(sv) - 1.0)) : 0.0;
-                    }
-                    ptab[((size_t)q * 3 + a) * Wsub + i] = (T)v;
-                }
-            }
+
         if (!pois.empty()) {
             pois[3 * q] = nodes[j].k[0];
             pois[3 * q + 1] = nodes[j].k[1];
@@ -362,9 +376,13 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.nrchunks = 0;
     D.psi_tab = nullptr;
     if (Ts > 0 && M) {
+        // kernel values of every node (the nodes are fixed per plan), placed in the
+        // sub-window of its segment; computed on the device from (delta, offsets)
         void *dpt;
-        if ((s = alloc_dev(p, &dpt, sizeof(T) * ptab.size()))) return s;
-        cudaMemcpy(dpt, ptab.data(), sizeof(T) * ptab.size(), cudaMemcpyHostToDevice);
+        if ((s = alloc_dev(p, &dpt, sizeof(T) * (size_t)M * 3 * Wsub))) return s;
+        if (launch_psi_table<T>((T *)dpt, (const T *)dnd, (const uint32_t *)dno, M, D.w, Wsub, Ts, p->info.beta_es,
+                                p->stream) != cudaSuccess)
+            return NLP_ERR_CUDA;
         D.psi_tab = (const T *)dpt;
         void *dsn, *dss, *drc;
         if ((s = alloc_dev(p, &dsn, sizeof(int) * seg_node.size()))) return s;
@@ -475,12 +493,14 @@ nlp_status plan_build(nlp_plan_s *p) {
     }
     if (d == 3) {
         gauss_legendre(nth, -1.0, 1.0, u, wu);
-        nodes.reserve((size_t)nr * (nth / 2) * nph);
+        nodes.resize((size_t)nr * (nth / 2) * nph);
+#pragma omp parallel for collapse(2) schedule(static)
         for (int ia = 0; ia < nr; ++ia)
             for (int ib = nth / 2; ib < nth; ++ib) {   // u > 0 half (ascending GL nodes)
                 const double st = std::sqrt(std::max(0.0, 1.0 - u[ib] * u[ib]));
                 for (int ic = 0; ic < nph; ++ic) {
-                    HostNode hn{};
+                    HostNode &hn = nodes[((size_t)ia * (nth / 2) + (ib - nth / 2)) * nph + ic];
+                    hn = HostNode{};
                     const double k[3] = {r[ia] * st * cph[ic], r[ia] * st * sph[ic], r[ia] * u[ib]};
                     double J = 1.0;
                     if (p->kernel == NLP_DIPOLE_3D) {
@@ -489,7 +509,6 @@ nlp_status plan_build(nlp_plan_s *p) {
                     }
                     hn.omega = pref * wr[ia] * wu[ib] * wph * J;
                     for (int a = 0; a < 3; ++a) hn.z[a] = k[a] * p->h[a] * (2.0 * p->n3[a]) / twopi;
-                    nodes.push_back(hn);
                 }
             }
         p->info.nodes_total = (int64_t)nr * nth * nph;
@@ -541,7 +560,7 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if (o->n_r < 0 || o->n_theta < 0 || o->n_phi < 0) return NLP_ERR_INVALID_ARG;
         if (o->n_r > 4096 || o->n_theta > 4096 || o->n_phi > 8192) return NLP_ERR_INVALID_ARG;
         if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
-        if (o->tile != 0 && o->tile != 4 && o->tile != 8 && o->tile != 16 && o->tile != 32) return NLP_ERR_INVALID_ARG;
+        if (o->tile != 0 && (o->tile < 2 || o->tile > 32)) return NLP_ERR_INVALID_ARG;
         if (o->spread_variant != 0 && o->spread_variant != 1) return NLP_ERR_INVALID_ARG;
         for (int i = 0; i < 6; ++i)
             if (o->reserved[i]) return NLP_ERR_INVALID_ARG;

@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "spread_common.cuh"
+#include "spread_dev.cuh"
 
 namespace nlp {
 
@@ -33,30 +34,6 @@ template <int W> struct RegCfg {
 __device__ __forceinline__ void team_sync(int team, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(nthreads) : "memory");
 }
-
-// Reduce V values across the 32 lanes of a warp (V a power of two <= 32).  Recursive
-// halving: at the step with offset s each lane keeps the half of its values selected by
-// its lane bit s and adds the other half received from lane ^ s.  On return v[0] of lane
-// L is the warp sum of value index (L >> (5 - log2 V)) & (V - 1).
-template <typename T, int V>
-__device__ __forceinline__ void warp_reduce_multi(T (&v)[V], int lane) {
-    int off = 16;
-#pragma unroll
-    for (int half = V / 2; half >= 1; half /= 2) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const T send = up ? v[i] : v[i + half];
-            const T keep = up ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-        off >>= 1;
-    }
-    for (; off >= 1; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
-}
-
-template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
-template <> struct Log2<1> { static constexpr int value = 0; };
 
 template <typename T, int W, int NB>
 __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_reg(DevPlan<T> P) {
@@ -175,145 +152,12 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
     }
 }
 
-// One warp per segment (W*W <= 64): lane L owns the z-columns L and L + 32 of the sub-window,
-// so interpolation sums reduce inside the warp and the node loop needs no block barrier.
 template <typename T, int W, int NB>
 __global__ void __launch_bounds__(256) k_interp_spread_warp(DevPlan<T> P) {
-    static_assert(W * W <= 64, "two columns per lane");
-    constexpr int V = 2 * NB;
-    constexpr int SH = 5 - Log2<V>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int w = P.w;
-    const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
-    const int WW = Wt0 * Wt1 * Wt2;
-    cpx<T> *sF = (cpx<T> *)smraw;
-    cpx<T> *sG = sF + WW;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    T *psi = (T *)(sG + WW) + warp * (NB * 3 * W + V);
-    T *cb = psi + NB * 3 * W;
-    const Chunk ch = P.rchunks[blockIdx.x];
-    __shared__ int next_seg;
-    if (threadIdx.x == 0) next_seg = ch.j0 + nwarps;
-
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        sF[q] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
-        sG[q] = mk<T>(0, 0);
-    }
-    __syncthreads();
-
-    const int ca = lane, cbc = lane + 32;
-    const bool act_b = cbc < W * W;
-    const int xa = ca / W, ya = ca % W;                 // W*W > 32 for W >= 6: column a always active
-    const int xb = act_b ? cbc / W : 0, yb = act_b ? cbc % W : 0;
-    const bool act_a = ca < W * W;
-    // pieces are sorted heaviest first; each warp takes the next free one
-    for (int sg = ch.j0 + warp; sg < ch.j1;) {
-        const uint32_t so = P.seg_sub[sg];
-        const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
-        const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
-        const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * Wt2 + so2;
-        const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * Wt2 + so2;
-        T fax[W], fay[W], fbx[W], fby[W], gax[W], gay[W], gbx[W], gby[W];
-#pragma unroll
-        for (int z = 0; z < W; ++z) {
-            const cpx<T> fa = act_a ? sF[basea + z] : mk<T>(0, 0);
-            const cpx<T> fb = act_b ? sF[baseb + z] : mk<T>(0, 0);
-            fax[z] = fa.x; fay[z] = fa.y; fbx[z] = fb.x; fby[z] = fb.y;
-            gax[z] = gay[z] = gbx[z] = gby[z] = (T)0;
-        }
-        // the batch's kernel values are a contiguous block of the plan-time table; the next
-        // block is fetched into registers while the current batch computes
-        constexpr int PQ = (NB * 3 * W + 31) / 32;
-        T pf[PQ];
-        auto fetch = [&](int jbn, int nbn) {
-            const T *src = P.psi_tab + (int64_t)jbn * 3 * W;
-#pragma unroll
-            for (int u = 0; u < PQ; ++u) {
-                const int q = lane + 32 * u;
-                pf[u] = (q < nbn * 3 * W) ? __ldg(src + q) : (T)0;
-            }
-        };
-        fetch(j0, min(NB, j1 - j0));
-        for (int jb = j0; jb < j1; jb += NB) {
-            const int nb = min(NB, j1 - jb);
-#pragma unroll
-            for (int u = 0; u < PQ; ++u) {
-                const int q = lane + 32 * u;
-                if (q < NB * 3 * W) psi[q] = pf[u];
-            }
-            __syncwarp();
-            if (jb + NB < j1) fetch(jb + NB, min(NB, j1 - jb - NB));
-            T v[V], wa[NB], wb[NB];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                v[2 * k] = v[2 * k + 1] = (T)0;
-                wa[k] = wb[k] = (T)0;
-                if (k < nb) {
-                    const T *pk = psi + k * 3 * W;
-                    wa[k] = act_a ? pk[xa] * pk[W + ya] : (T)0;
-                    wb[k] = act_b ? pk[xb] * pk[W + yb] : (T)0;
-                    T sax = 0, say = 0, sbx = 0, sby = 0;
-#pragma unroll
-                    for (int z = 0; z < W; ++z) {
-                        const T pz = pk[2 * W + z];
-                        sax += fax[z] * pz;
-                        say += fay[z] * pz;
-                        sbx += fbx[z] * pz;
-                        sby += fby[z] * pz;
-                    }
-                    v[2 * k] = wa[k] * sax + wb[k] * sbx;
-                    v[2 * k + 1] = wa[k] * say + wb[k] * sby;
-                }
-            }
-            warp_reduce_multi<T, V>(v, lane);
-            if ((lane & ((1 << SH) - 1)) == 0) {
-                const int idx = (lane >> SH) & (V - 1);
-                const int k = idx >> 1;
-                cb[idx] = (k < nb) ? v[0] * P.nd[4 * ((int64_t)jb + k) + 3] : (T)0;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (k < nb) {
-                    const T *pk = psi + k * 3 * W;
-                    const T cr = cb[2 * k], ci = cb[2 * k + 1];
-                    const T ar = cr * wa[k], ai = ci * wa[k], br = cr * wb[k], bi = ci * wb[k];
-#pragma unroll
-                    for (int z = 0; z < W; ++z) {
-                        const T pz = pk[2 * W + z];
-                        gax[z] += ar * pz;
-                        gay[z] += ai * pz;
-                        gbx[z] += br * pz;
-                        gby[z] += bi * pz;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int z = 0; z < W; ++z) {
-            if (act_a) {
-                if (gax[z] != (T)0) atomicAdd(&sG[basea + z].x, gax[z]);
-                if (gay[z] != (T)0) atomicAdd(&sG[basea + z].y, gay[z]);
-            }
-            if (act_b) {
-                if (gbx[z] != (T)0) atomicAdd(&sG[baseb + z].x, gbx[z]);
-                if (gby[z] != (T)0) atomicAdd(&sG[baseb + z].y, gby[z]);
-            }
-        }
-        int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(&next_seg, 1);
-        sg = __shfl_sync(0xffffffffu, nxt, 0);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const cpx<T> v = sG[q];
-        if (v.x == (T)0 && v.y == (T)0) continue;
-        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
-    }
+    spread_warp_block<T, W, NB>(P, blockIdx.x, smraw);
 }
+
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
 template <typename T> bool reg_kernel_supported(int W) {

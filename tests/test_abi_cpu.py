@@ -46,7 +46,8 @@ def test_status_strings_and_version(nl):
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"tol": 1e-20}),
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"counts": (32, 31, 64)}),   # odd n_theta
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"counts": (32, 32, 63)}),   # odd n_phi
-    ((32, 32, 32), (8, 8, 8), "coulomb3d", {"tile": 5}),
+    ((32, 32, 32), (8, 8, 8), "coulomb3d", {"tile": 64}),
+    ((32, 32, 32), (8, 8, 8), "coulomb3d", {"spread_variant": 2}),
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"kmax": -1.0}),
 ])
 def test_invalid_arguments_rejected_before_launch(nl, n, L, kernel, kw):
@@ -61,3 +62,7 @@ def test_null_handles_rejected(nl):
     assert lib.nlp_plan_get_info(None, None) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_ts_step(None, None, None, 1.0, 0.0, 0.1, 2) == nl.NLP_ERR_INVALID_ARG
     lib.nlp_plan_destroy(None)   # no-op
+    assert lib.nlp_batch_create(None, 0, None, None) == nl.NLP_ERR_INVALID_ARG
+    assert lib.nlp_batch_eval(None, None, None) == nl.NLP_ERR_INVALID_ARG
+    assert lib.nlp_batch_sync(None) == nl.NLP_ERR_INVALID_ARG
+    lib.nlp_batch_destroy(None)

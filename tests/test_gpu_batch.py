@@ -1,0 +1,115 @@
+"""Batched persistent evaluation (one graph-replayed launch over many FP32 plans)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import potential
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1410_3584_gb300 as m
+    return m
+
+
+SPECS = [  # (n, L, kernel, widths) -- mixed grids, kernels and dimensions
+    ((24, 20, 16), (6.0, 5.0, 4.5), "coulomb3d", (1.0, 1.3, 0.8)),
+    ((32, 32, 32), (7.0, 7.0, 7.0), "dipole3d", (1.0, 1.6, 2.2)),
+    ((30, 24, 20), (7.0, 6.0, 5.0), "coulomb3d", (1.2, 1.0, 1.5)),
+    ((64, 48), (8.0, 6.0), "coulomb2d", (1.0, 1.4)),
+    ((20, 20, 20), (5.0, 5.0, 5.0), "dipole3d", (0.9, 0.9, 1.8)),
+]
+
+
+def _build(nl, torch, stream):
+    plans, rhos, phis, refs, grids = [], [], [], [], []
+    for n, L, kern, a in SPECS:
+        g = W.Grid(n, L)
+        rho = W.gaussian(g, a)
+        P = math.pi / max(g.h)
+        counts = (32, 32, 64) if g.dim == 3 else (64, 128)
+        pl = nl.Plan(n, L, kern, "fp32", kmax=P, counts=counts, stream=stream)
+        r = torch.from_numpy(rho).to("cuda", torch.float32)
+        out = pl.eval(r)
+        pl.sync()      # the plan works on its own stream
+        single = out.double().cpu().numpy()
+        plans.append(pl)
+        rhos.append(r)
+        phis.append(torch.zeros_like(r))
+        refs.append(single)
+        grids.append((g, rho, kern, P, counts))
+    return plans, rhos, phis, refs, grids
+
+
+def test_batch_matches_single_plans_and_oracle(nl):
+    import torch
+    stream = torch.cuda.Stream()
+    plans, rhos, phis, refs, grids = _build(nl, torch, stream)
+    b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
+    info = nl.nlp_batch_get_info(b)
+    assert info["tasks"] > 0 and info["grid"] >= 152
+    for rep in range(2):   # replays of the same graph
+        for ph in phis:
+            ph.zero_()
+        torch.cuda.synchronize()
+        nl.nlp_batch_eval(b, rhos, phis)
+        nl.nlp_batch_sync(b)
+        for ph, ref in zip(phis, refs):
+            out = ph.double().cpu().numpy()
+            assert np.max(np.abs(out - ref)) <= 1e-6 * np.max(np.abs(ref))
+    for i in (0, 1, 3):
+        g, rho, kern, P, counts = grids[i]
+        o = potential.eval_nufft(rho, g, kern, P, counts, tol=1e-13)
+        assert cf.rel_linf(phis[i].double().cpu().numpy(), o) < 1e-5
+    # new inputs through the same graph: scaled densities give scaled potentials
+    scaled = [2.5 * r for r in rhos]
+    nl.nlp_batch_eval(b, scaled, phis)
+    nl.nlp_batch_sync(b)
+    for ph, ref in zip(phis, refs):
+        assert np.max(np.abs(ph.double().cpu().numpy() - 2.5 * ref)) <= 3e-6 * np.max(np.abs(2.5 * ref))
+    nl.nlp_batch_destroy(b)
+    for p in plans:
+        p.close()
+
+
+def test_batch_wait_timeout_is_reported_and_recoverable(nl):
+    import torch
+    stream = torch.cuda.Stream()
+    plans, rhos, phis, refs, grids = _build(nl, torch, stream)
+    b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
+    # item 1, stage 2 (forward FFT along axis 0) never counts as complete: the stages after
+    # it poll 2000 times and give up
+    nl.nlp_batch_set_wait_limit(b, 2000, 1, 2)
+    nl.nlp_batch_eval(b, rhos, phis)
+    st = nl.nlp_batch_sync(b, raise_on_error=False)
+    assert st == nl.NLP_ERR_TIMEOUT
+    nl.nlp_batch_set_wait_limit(b, 1 << 24, -1, -1)
+    nl.nlp_batch_eval(b, rhos, phis)
+    nl.nlp_batch_sync(b)
+    for ph, ref in zip(phis, refs):
+        assert np.max(np.abs(ph.double().cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
+    nl.nlp_batch_destroy(b)
+    for p in plans:
+        p.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches(nl, tmp_path):
+    cache = str(tmp_path / "tune.txt")
+    t1, ms1 = nl.nlp_autotune_tile((32, 32, 32), (7.0, 7.0, 7.0), "coulomb3d", "fp32", cache_path=cache,
+                                   counts=(32, 32, 64))
+    assert t1 in (4, 8, 16) and ms1 > 0
+    assert os.path.exists(cache)
+    t2, ms2 = nl.nlp_autotune_tile((32, 32, 32), (7.0, 7.0, 7.0), "coulomb3d", "fp32", cache_path=cache,
+                                   counts=(32, 32, 64))
+    assert (t2, ms2) == (t1, pytest.approx(ms1, rel=1e-5))
+    t3, _ = nl.nlp_autotune_tile((64, 48), (8.0, 6.0), "coulomb2d", "fp32", counts=(64, 128))
+    assert t3 in (8, 16, 32)
