@@ -75,7 +75,14 @@ typedef struct {
     int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 2..32 */
     int spread_variant;     /* 0 = default (3D: register-column kernel where the width is supported),
                                1 = shared-memory-atomics kernel everywhere */
-    int reserved[6];        /* must be zero */
+    int method;             /* 0 = NUFFT per evaluation (default).  1 = precomputed discrete kernel:
+                               the quadrature sum of Eq. (ifft) equals sum_i' K(i - i') rho_i' with
+                               K(m) = sum_j w_j |k_j|^{d-1} U-hat(k_j) cos(k_j . m h) h^d / (2 pi)^d;
+                               the plan computes K once (type-1 NUFFT of the weights onto the doubled
+                               grid) and each evaluation is an aperiodic convolution by FFT on the
+                               2n grid.  Not for NLP_POISSON_2D (its operator is not translation
+                               invariant): NLP_ERR_UNSUPPORTED. */
+    int reserved[5];        /* must be zero */
 } nlp_opts;
 
 typedef struct nlp_plan_s *nlp_plan;

@@ -28,7 +28,7 @@ class nlp_grid(ctypes.Structure):
 class nlp_opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_double), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
                 ("n_phi", ctypes.c_int), ("dipole_axis", ctypes.c_double * 3), ("nufft_tol", ctypes.c_double),
-                ("tile", ctypes.c_int), ("spread_variant", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("tile", ctypes.c_int), ("spread_variant", ctypes.c_int), ("method", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class nlp_plan_info(ctypes.Structure):
@@ -113,7 +113,8 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _grid_opts(n, L, kmax=0.0, counts=None, dipole_axis=(0.0, 0.0, 0.0), tol=0.0, tile=0, spread_variant=0):
+def _grid_opts(n, L, kmax=0.0, counts=None, dipole_axis=(0.0, 0.0, 0.0), tol=0.0, tile=0, spread_variant=0,
+               method=0):
     g = nlp_grid()
     g.dim = len(n)
     for a in range(len(n)):
@@ -131,14 +132,15 @@ def _grid_opts(n, L, kmax=0.0, counts=None, dipole_axis=(0.0, 0.0, 0.0), tol=0.0
     o.nufft_tol = float(tol)
     o.tile = int(tile)
     o.spread_variant = int(spread_variant)
+    o.method = int(method)
     return g, o
 
 
 def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.0, counts=None,
                     dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, spread_variant: int = 0,
-                    stream=None):
+                    method: int = 0, stream=None):
     """Create a plan; returns an opaque handle (ctypes.c_void_p).  See nlpot.h."""
-    g, o = _grid_opts(n, L, kmax, counts, dipole_axis, tol, tile, spread_variant)
+    g, o = _grid_opts(n, L, kmax, counts, dipole_axis, tol, tile, spread_variant, method)
     h = ctypes.c_void_p()
     _check(_lib.nlp_plan_create(ctypes.byref(g), KERNELS[kernel], PRECISIONS[precision], ctypes.byref(o),
                                 _stream_handle(stream), ctypes.byref(h)), "nlp_plan_create")

@@ -63,12 +63,18 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
         NLP_CUDA_TRY(launch_poisson_origin<T>(D, (double *)D.mom, st));
         mark(p, NLP_STAGE_POISSON);
     }
-    // interpolate, scale, spread
-    NLP_CUDA_TRY(cudaMemsetAsync(D.G, 0, sizeof(cpx<T>) * (size_t)D.nf[0] * D.nf[1] * nh, st));
-    mark(p, NLP_STAGE_CLEAR);
-    if (D.sub_T > 0) NLP_CUDA_TRY(launch_interp_spread_reg<T>(D, st));
-    else NLP_CUDA_TRY(launch_interp_spread<T>(D, st));
-    mark(p, NLP_STAGE_SPREAD);
+    if (D.Khat) {
+        // precomputed discrete kernel: pointwise product with its spectrum (in place)
+        NLP_CUDA_TRY(launch_mul_spec<T>(D.F, D.Khat, (int64_t)D.nf[0] * D.nf[1] * nh, st));
+        mark(p, NLP_STAGE_SPREAD);
+    } else {
+        // interpolate, scale, spread
+        NLP_CUDA_TRY(cudaMemsetAsync(D.G, 0, sizeof(cpx<T>) * (size_t)D.nf[0] * D.nf[1] * nh, st));
+        mark(p, NLP_STAGE_CLEAR);
+        if (D.sub_T > 0) NLP_CUDA_TRY(launch_interp_spread_reg<T>(D, st));
+        else NLP_CUDA_TRY(launch_interp_spread<T>(D, st));
+        mark(p, NLP_STAGE_SPREAD);
+    }
     // type 1: inverse FFT (axis 0, axis 1, last axis), deconvolve, crop
     if (three) {
         StridedDesc b0 = a0;

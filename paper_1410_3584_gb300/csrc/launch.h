@@ -39,6 +39,9 @@ template <typename T> cudaError_t launch_poisson_origin(const DevPlan<T> &P, dou
 template <typename T>
 cudaError_t launch_poisson_u1(T *phi, const DevPlan<T> &P, const double *L, const double *h, cudaStream_t st);
 
+// precomputed-kernel method: F *= K-hat (toeplitz.cu)
+template <typename T> cudaError_t launch_mul_spec(cpx<T> *F, const cpx<T> *K, int64_t M, cudaStream_t st);
+
 // plan-time per-node kernel-value table of the register kernels (plan.cu)
 template <typename T>
 cudaError_t launch_psi_table(T *tab, const T *nd, const uint32_t *no, int64_t M, int w, int Wsub, int Ts, double beta,

@@ -424,6 +424,8 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     return NLP_OK;
 }
 
+nlp_status build_toeplitz(nlp_plan_s *p);
+
 static int roundup16(double x) { return (int)(16.0 * std::ceil(x / 16.0)); }
 
 nlp_status plan_build(nlp_plan_s *p) {
@@ -538,6 +540,10 @@ nlp_status plan_build(nlp_plan_s *p) {
 
     nlp_status s = (p->prec == NLP_FP64) ? build_device<double>(p, nodes, p->pd) : build_device<float>(p, nodes, p->pf);
     if (s) return s;
+    if (p->opts.method == 1) {
+        std::vector<HostNode>().swap(nodes);
+        if ((s = build_toeplitz(p))) return s;
+    }
     p->info.workspace_bytes = p->bytes;
     return NLP_OK;
 }
@@ -562,7 +568,12 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
         if (o->tile != 0 && (o->tile < 2 || o->tile > 32)) return NLP_ERR_INVALID_ARG;
         if (o->spread_variant != 0 && o->spread_variant != 1) return NLP_ERR_INVALID_ARG;
-        for (int i = 0; i < 6; ++i)
+        if (o->method != 0 && o->method != 1) return NLP_ERR_INVALID_ARG;
+        if (o->method == 1 && kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+        if (o->method == 1)   // the kernel is built on a 4n-point fine grid
+            for (int a = 0; a < g->dim; ++a)
+                if (4 * g->n[a] > kMaxFftLen) return NLP_ERR_UNSUPPORTED;
+        for (int i = 0; i < 5; ++i)
             if (o->reserved[i]) return NLP_ERR_INVALID_ARG;
         for (int a = 0; a < 3; ++a)
             if (!std::isfinite(o->dipole_axis[a])) return NLP_ERR_INVALID_ARG;

@@ -44,7 +44,7 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
 
     for (int q = threadIdx.x; q < WW; q += blockDim.x) {
         const int c = q % W2, t = q / W2, b = t % W1, a = t / W1;
-        sF[q] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
+        sF[q] = P.ones_mode ? mk<T>(0, 0) : load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
         sG[q] = mk<T>(0, 0);
     }
     __syncthreads();
@@ -88,7 +88,9 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
         }
         cpx<T> cj;
-        if (P.pois == nullptr) {
+        if (P.ones_mode) {
+            cj = mk<T>(om, (T)0);
+        } else if (P.pois == nullptr) {
             cj = scale(acc, om);
         } else {
             // Algorithm 1: W(k) = (rho-hat(k) - (C0 - i k.M1) e^{-sigma^2 |k|^2/2}) / |k| in FP64

@@ -48,12 +48,19 @@ def test_status_strings_and_version(nl):
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"counts": (32, 32, 63)}),   # odd n_phi
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"tile": 64}),
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"spread_variant": 2}),
+    ((32, 32, 32), (8, 8, 8), "coulomb3d", {"method": 3}),
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"kmax": -1.0}),
 ])
 def test_invalid_arguments_rejected_before_launch(nl, n, L, kernel, kw):
     with pytest.raises(nl.NlpError) as e:
         nl.nlp_plan_create(n, L, kernel, "fp64", stream=0, **kw)
     assert e.value.status == nl.NLP_ERR_INVALID_ARG
+
+
+def test_precomputed_kernel_rejects_poisson(nl):
+    with pytest.raises(nl.NlpError) as e:
+        nl.nlp_plan_create((64, 64), (8, 8), "poisson2d", "fp64", method=1, stream=0)
+    assert e.value.status == nl.NLP_ERR_UNSUPPORTED
 
 
 def test_null_handles_rejected(nl):

@@ -166,3 +166,21 @@ def test_3d_spread_variants_and_widths(nl, prec, tol, variant):
     bound = max(TOL[prec] if tol <= (1e-6 if prec == "fp32" else 1e-12) else 0.0, 50 * tol, 1e-13)
     assert (info["sub_tile"] > 0) == (variant == 0)
     assert err < bound, (err, bound, info["width"], info["sub_tile"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel,shape", [("coulomb3d", ((24, 20, 16), (6.0, 5.0, 4.5))),
+                                          ("dipole3d", ((30, 32, 18), (7.0, 7.0, 5.0))),
+                                          ("coulomb2d", ((64, 48), (8.0, 6.0)))])
+def test_precomputed_kernel_method(nl, prec, kernel, shape):
+    """method = 1: the same discrete operator through its precomputed Toeplitz kernel."""
+    g = W.Grid(*shape)
+    rho = W.random_density(g, 21)
+    P = math.pi / max(g.h)
+    counts = (32, 32, 64) if g.dim == 3 else (64, 128)
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, counts=counts, method=1)
+    ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+    assert cf.rel_linf(phi, ref) < TOL[prec]
+    # and the oracle's own Toeplitz form of the operator
+    op = potential.ConvolutionOperator(g, kernel, P, counts)
+    assert cf.rel_linf(phi, op(rho)) < TOL[prec]
