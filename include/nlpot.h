@@ -142,6 +142,16 @@ nlp_status nlp_gf_step(nlp_plan plan, void *phi_dev, const void *V_dev, double b
                        double tau, double inner_tol, int max_inner, double *max_change,
                        int *inner_iters, double *energies);
 
+/* The gradient flow run to convergence: nlp_gf_step repeated until
+ * max|phi^{n+1} - phi^n| / tau <= stop_tol (the stopping rule of Sec. 3.2, epsilon_0 = 1e-10
+ * there) or max_steps steps.  A step whose inner solve hits max_inner is kept (the iterate is
+ * normalised) and the flow continues.  Outputs (host, may be NULL): *steps taken,
+ * *max_change of the last step, energies[5] of the final phi.  NLP_ERR_NOT_CONVERGED if
+ * max_steps ran out.  Synchronizes the plan stream. */
+nlp_status nlp_gf_solve(nlp_plan plan, void *phi_dev, const void *V_dev, double beta, double g,
+                        double tau, double stop_tol, int max_steps, double inner_tol, int max_inner,
+                        int *steps, double *max_change, double *energies);
+
 /* Energies {E, E_kin, E_pot, E_int, mu} of a real phi (Sec. 3.2), FP64 reductions.
  * Synchronizes the plan stream. */
 nlp_status nlp_energies(nlp_plan plan, const void *phi_dev, const void *V_dev, double beta,
@@ -234,6 +244,76 @@ enum {
 };
 nlp_status nlp_set_stage_timing(nlp_plan plan, int on);
 nlp_status nlp_get_stage_times(nlp_plan plan, int *stage_ids, double *ms, int max, int *count);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned initial guess for the gradient flow (the paper has no counterpart; the flow it
+ * starts is unchanged and still decides the ground state).  A network maps the features
+ *   f = [log10(beta)/3, (gamma - 1)/3, kernel == NLP_COULOMB_3D, kernel == NLP_DIPOLE_3D]
+ * (beta: interaction strength, gamma: trap anisotropy of V = (x^2 + y^2 + gamma^2 z^2)/2) to
+ * a ground-state amplitude on a 48^3 grid over [-box_L, box_L)^3 (point j at
+ * -box_L + j * 2 box_L / 48):
+ *   MLP 64 -> 512 -> 512 -> 512 -> 512 (SiLU; f zero-padded to 64) -> 1792 (linear; the
+ *   first 1728 outputs are 8 channels of 6^3), then [nearest x2, 3^3 conv 8->8, SiLU] at 12^3
+ *   and 24^3, nearest x2 and a 3^3 conv 8->1 at 48^3 (zero padding).
+ * Parameters are one FP32 vector, in this order: for l = 0..4, W_l [out][in] row-major then
+ * b_l [out] (sizes 512x64, 512x512 (3x), 1792x512); then for each conv layer w [co][ci][27]
+ * (tap d = 9 dz + 3 dy + dx for offsets (dz, dy, dx) - 1 in {-1, 0, 1}, input position
+ * p + offset) then bias [co].  Padding entries (W_0 columns >= 4, W_4 rows >= 1728, b_4
+ * entries >= 1728) start at zero and receive zero gradient.
+ * mode 0: dense layers as BF16 tensor-core GEMMs (tcgen05, FP32 accumulation) on BF16
+ * copies of the weights; mode 1: the same on FP32 CUDA cores (gradient checks).
+ * Batches hold 1..128 samples: features [B][4] and targets [B][48^3] FP32 on the device.
+ * All calls run on the given stream and are not thread-safe per object. */
+typedef struct nlp_surrogate_s *nlp_surrogate;
+
+/* Feature vector for (beta, gamma, kernel) as defined above (host). */
+void nlp_surrogate_features(double beta, double gamma, nlp_kernel kernel, float *feat4);
+
+/* Allocates the network (about 1.7 GB of device memory for batches up to 128) and
+ * initialises W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from seed, biases zero.  Synchronous. */
+nlp_status nlp_surrogate_create(double box_L, unsigned long long seed, int mode, void *stream,
+                                nlp_surrogate *out);
+int64_t nlp_surrogate_num_params(nlp_surrogate s);
+nlp_status nlp_surrogate_get_params(nlp_surrogate s, float *params_host);
+nlp_status nlp_surrogate_set_params(nlp_surrogate s, const float *params_host);
+
+/* out_dev [B][48^3] = network(feat_dev [B][4]).  Synchronizes; NLP_ERR_TIMEOUT if a
+ * tensor-core wait ran out. */
+nlp_status nlp_surrogate_forward(nlp_surrogate s, const float *feat_dev, int B, float *out_dev);
+
+/* Loss = mean over B x 48^3 of (out - target)^2 and its gradient with respect to every
+ * parameter, copied to grads_host (may be NULL) in the parameter layout.  Synchronizes. */
+nlp_status nlp_surrogate_gradients(nlp_surrogate s, const float *feat_dev, const float *target_dev,
+                                   int B, double *loss, float *grads_host);
+
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, decoupled weight
+ * decay) on that loss.  Synchronizes only when loss is not NULL. */
+nlp_status nlp_surrogate_train_step(nlp_surrogate s, const float *feat_dev, const float *target_dev,
+                                    int B, float lr, float weight_decay, double *loss);
+
+/* The network learns the correction to the beta = 0 ground state of the trap,
+ *   b(x) = gamma^{1/4} pi^{-3/4} exp(-(x^2 + y^2 + gamma z^2)/2):
+ * training targets are (ground state - b) on the 48^3 cube.  out_dev [B][48^3] = b on the
+ * cube for gamma_dev [B] (device FP32).  Asynchronous. */
+nlp_status nlp_surrogate_base(nlp_surrogate s, const float *gamma_dev, int B, float *out_dev);
+
+/* Initial guess for nlp_gf_step / nlp_gf_solve on a 3D grid:
+ *   phi = S[max(0, b(x) + c(x))] normalised to h^3 sum phi^2 = 1 (FP64 reductions),
+ * c = the network output for (beta, gamma, kernel) sampled trilinearly at the grid points
+ * (zero outside the 48^3 cube), S = the average over the 8 reflections x_a -> -x_a of the
+ * grid (index i -> (n - i) mod n on each axis): the trap and both kernels are even under
+ * each reflection, and so is the ground state.  Written in the given precision.
+ * kernel: NLP_COULOMB_3D or NLP_DIPOLE_3D.  Synchronizes. */
+nlp_status nlp_surrogate_initial_guess(nlp_surrogate s, double beta, double gamma, nlp_kernel kernel,
+                                       const nlp_grid *grid, nlp_precision prec, void *phi_dev);
+
+void nlp_surrogate_destroy(nlp_surrogate s);
+
+/* Test hook for the tensor-core GEMM of the network: C[M x N] (FP32) = A[M x K] B[N x K]^T,
+ * A and B BF16 row-major device arrays; M % 128 == 0, K % 64 == 0, N % 64 == 0.
+ * Synchronizes; NLP_ERR_TIMEOUT if a tensor-core wait ran out. */
+nlp_status nlp_gemm_bf16(const void *A_dev, const void *B_dev, float *C_dev, int M, int N, int K,
+                         void *stream);
 
 /* Measured FMA throughput of the GPU in flop/s for the given precision (a microbenchmark of
  * independent FMA chains over all SMs, best of 3 timed runs); the denominator of the ALU

@@ -7,4 +7,4 @@ subtraction for the 2D Laplace kernel (Algorithm 1), the normalized gradient flo
 include/nlpot.h); this package is its thin binding.
 """
 from ._binding import *  # noqa: F401,F403
-from ._binding import Plan, NlpError, LIB_PATH  # noqa: F401
+from ._binding import Plan, Surrogate, NlpError, LIB_PATH  # noqa: F401

@@ -74,6 +74,19 @@ def _load():
         "nlp_batch_destroy": ([P], None),
         "nlp_autotune_tile": ([ctypes.POINTER(nlp_grid), I, I, ctypes.POINTER(nlp_opts), P, ctypes.c_char_p,
                                ctypes.POINTER(I), ctypes.POINTER(D)], I),
+        "nlp_gf_solve": ([P, P, P, D, D, D, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "nlp_surrogate_features": ([D, D, I, ctypes.POINTER(ctypes.c_float)], None),
+        "nlp_surrogate_create": ([D, ctypes.c_ulonglong, I, P, ctypes.POINTER(P)], I),
+        "nlp_surrogate_num_params": ([P], ctypes.c_int64),
+        "nlp_surrogate_get_params": ([P, P], I),
+        "nlp_surrogate_set_params": ([P, P], I),
+        "nlp_surrogate_forward": ([P, P, I, P], I),
+        "nlp_surrogate_gradients": ([P, P, P, I, ctypes.POINTER(D), P], I),
+        "nlp_surrogate_train_step": ([P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.POINTER(D)], I),
+        "nlp_surrogate_initial_guess": ([P, D, D, I, ctypes.POINTER(nlp_grid), I, P], I),
+        "nlp_surrogate_base": ([P, P, I, P], I),
+        "nlp_surrogate_destroy": ([P], None),
+        "nlp_gemm_bf16": ([P, P, P, I, I, I, P], I),
         "nlp_status_string": ([I], ctypes.c_char_p),
         "nlp_version": ([], ctypes.c_char_p),
     }
@@ -196,6 +209,21 @@ def nlp_gf_step(plan, phi, V, beta: float, g: float = 0.0, tau: float = 1e-2, in
     if energies:
         en = dict(zip(("E", "Ekin", "Epot", "Eint", "mu"), list(E)))
     return ch.value, it.value, en, st
+
+
+def nlp_gf_solve(plan, phi, V, beta: float, g: float = 0.0, tau: float = 1e-2, stop_tol: float = 1e-10,
+                 max_steps: int = 100000, inner_tol: float = 1e-12, max_inner: int = 1000,
+                 raise_on_nonconv: bool = True):
+    """Gradient flow to max|phi^{n+1}-phi^n|/tau <= stop_tol, in place.
+    Returns (steps, max_change, energies dict, status)."""
+    n = ctypes.c_int(0)
+    ch = ctypes.c_double(0.0)
+    E = (ctypes.c_double * 5)()
+    st = _lib.nlp_gf_solve(plan, _ptr(phi), _ptr(V), float(beta), float(g), float(tau), float(stop_tol),
+                           int(max_steps), float(inner_tol), int(max_inner), ctypes.byref(n), ctypes.byref(ch), E)
+    if st != NLP_OK and not (st == NLP_ERR_NOT_CONVERGED and not raise_on_nonconv):
+        raise NlpError(st, "nlp_gf_solve")
+    return n.value, ch.value, dict(zip(("E", "Ekin", "Epot", "Eint", "mu"), list(E))), st
 
 
 def nlp_energies(plan, phi, V, beta: float, g: float = 0.0) -> dict:
@@ -321,6 +349,101 @@ class Plan:
     def close(self):
         if self.handle:
             nlp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SURROGATE_GRID = 48
+SURROGATE_MAX_BATCH = 128
+
+
+def nlp_surrogate_features(beta: float, gamma: float, kernel: str) -> np.ndarray:
+    f = (ctypes.c_float * 4)()
+    _lib.nlp_surrogate_features(float(beta), float(gamma), KERNELS[kernel], f)
+    return np.array(list(f), dtype=np.float32)
+
+
+def nlp_gemm_bf16(A, B, C, stream=None):
+    """C (fp32 [M,N]) = A (bf16 [M,K]) @ B (bf16 [N,K])^T on the tensor cores (test hook)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(_lib.nlp_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), M, N, K, _stream_handle(stream)), "nlp_gemm_bf16")
+
+
+class Surrogate:
+    """Learned gradient-flow initial guess (see nlpot.h): Surrogate(box_L, seed, mode)."""
+
+    def __init__(self, box_L: float = 10.0, seed: int = 0, mode: int = 0, stream=None):
+        self.box_L = float(box_L)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(_lib.nlp_surrogate_create(self.box_L, int(seed), int(mode), _stream_handle(stream),
+                                         ctypes.byref(h)), "nlp_surrogate_create")
+        self.handle = h
+        self.num_params = int(_lib.nlp_surrogate_num_params(h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(_lib.nlp_surrogate_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        _check(_lib.nlp_surrogate_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)), "set_params")
+
+    def forward(self, feat, out=None):
+        import torch
+        B = feat.shape[0]
+        _check_tensor(feat, torch.float32, B * 4, "feat")
+        if out is None:
+            out = torch.empty((B, SURROGATE_GRID, SURROGATE_GRID, SURROGATE_GRID), dtype=torch.float32,
+                              device=feat.device)
+        _check(_lib.nlp_surrogate_forward(self.handle, _ptr(feat), B, _ptr(out)), "nlp_surrogate_forward")
+        return out
+
+    def gradients(self, feat, target):
+        B = feat.shape[0]
+        loss = ctypes.c_double(0.0)
+        g = np.empty(self.num_params, dtype=np.float32)
+        _check(_lib.nlp_surrogate_gradients(self.handle, _ptr(feat), _ptr(target), B, ctypes.byref(loss),
+                                            g.ctypes.data_as(ctypes.c_void_p)), "nlp_surrogate_gradients")
+        return loss.value, g
+
+    def train_step(self, feat, target, lr: float, weight_decay: float = 0.0, want_loss: bool = True):
+        B = feat.shape[0]
+        loss = ctypes.c_double(0.0)
+        _check(_lib.nlp_surrogate_train_step(self.handle, _ptr(feat), _ptr(target), B, float(lr),
+                                             float(weight_decay), ctypes.byref(loss) if want_loss else None),
+               "nlp_surrogate_train_step")
+        return loss.value if want_loss else None
+
+    def base(self, gamma, out=None):
+        """The beta = 0 amplitude on the 48^3 cube for each gamma (device FP32 [B])."""
+        import torch
+        B = gamma.shape[0]
+        _check_tensor(gamma, torch.float32, B, "gamma")
+        if out is None:
+            out = torch.empty((B, SURROGATE_GRID, SURROGATE_GRID, SURROGATE_GRID), dtype=torch.float32,
+                              device=gamma.device)
+        _check(_lib.nlp_surrogate_base(self.handle, _ptr(gamma), B, _ptr(out)), "nlp_surrogate_base")
+        return out
+
+    def initial_guess(self, beta: float, gamma: float, kernel: str, n, L, phi, precision: str = "fp64"):
+        g, _ = _grid_opts(n, L)
+        _check(_lib.nlp_surrogate_initial_guess(self.handle, float(beta), float(gamma), KERNELS[kernel],
+                                                ctypes.byref(g), PRECISIONS[precision], _ptr(phi)),
+               "nlp_surrogate_initial_guess")
+        return phi
+
+    def close(self):
+        if self.handle:
+            _lib.nlp_surrogate_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,4 +1,5 @@
 // C-ABI entry points of libnlpot (declared in include/nlpot.h).
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -206,6 +207,31 @@ nlp_status nlp_gf_step(nlp_plan p, void *phi_dev, const void *V_dev, double beta
     if (!p || !phi_dev || !V_dev || !(tau > 0) || !(inner_tol > 0) || max_inner < 1) return NLP_ERR_INVALID_ARG;
     if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
     return gf_step_impl(p, phi_dev, V_dev, beta, g, tau, inner_tol, max_inner, max_change, inner_iters, energies);
+}
+
+nlp_status nlp_gf_solve(nlp_plan p, void *phi_dev, const void *V_dev, double beta, double g, double tau,
+                        double stop_tol, int max_steps, double inner_tol, int max_inner, int *steps,
+                        double *max_change, double *energies) {
+    if (!p || !phi_dev || !V_dev || !(tau > 0) || !(stop_tol > 0) || max_steps < 1 || !(inner_tol > 0) ||
+        max_inner < 1)
+        return NLP_ERR_INVALID_ARG;
+    if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+    double ch = INFINITY;
+    int n = 0;
+    nlp_status s = NLP_OK;
+    while (n < max_steps) {
+        s = gf_step_impl(p, phi_dev, V_dev, beta, g, tau, inner_tol, max_inner, &ch, nullptr, nullptr);
+        ++n;
+        // an inner solve that hit its cap still leaves a normalised iterate; keep going
+        if (s != NLP_OK && s != NLP_ERR_NOT_CONVERGED) break;
+        s = NLP_OK;
+        if (ch <= stop_tol) break;
+    }
+    if (steps) *steps = n;
+    if (max_change) *max_change = ch;
+    if (s) return s;
+    if (energies && (s = energies_impl(p, phi_dev, V_dev, beta, g, energies))) return s;
+    return ch <= stop_tol ? NLP_OK : NLP_ERR_NOT_CONVERGED;
 }
 
 nlp_status nlp_energies(nlp_plan p, const void *phi_dev, const void *V_dev, double beta, double g, double *energies) {

@@ -288,8 +288,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
     *b->h_err = 0;
     cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_off, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
-    if (cudaFuncSetAttribute(k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
-        cudaSuccess) {
+    if ((int)b->smem > max_dyn_smem() || allow_smem<k_batch_persistent>() != cudaSuccess) {
         nlp_batch_destroy(b);
         return NLP_ERR_UNSUPPORTED;
     }

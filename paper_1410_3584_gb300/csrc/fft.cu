@@ -30,7 +30,7 @@ cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     const int nb = lines_per_block<T>(N);
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = fft_smem_bytes<T>(N, nb);
-    cudaFuncSetAttribute(k_fwd_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_smem<k_fwd_r2c<T>>();
     k_fwd_r2c<T><<<(unsigned)((npairs + nb - 1) / nb), 256, sm, st>>>(rho, P, nb);
     return cudaGetLastError();
 }
@@ -41,7 +41,7 @@ cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st) {
     const int nb = lines_per_block<T>(N);
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = fft_smem_bytes<T>(N, nb);
-    cudaFuncSetAttribute(k_inv_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_smem<k_inv_c2r<T>>();
     k_inv_c2r<T><<<(unsigned)((npairs + nb - 1) / nb), 256, sm, st>>>(phi, P, nb);
     return cudaGetLastError();
 }
@@ -54,10 +54,10 @@ cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<
     const int ctiles = (d.ncol + nb - 1) / nb;
     const unsigned grid = (unsigned)((int64_t)d.nouter * ctiles);
     if (sign < 0) {
-        cudaFuncSetAttribute(k_fft_strided<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem<k_fft_strided<T, -1>>();
         k_fft_strided<T, -1><<<grid, 256, sm, st>>>(data, d, L, nb);
     } else {
-        cudaFuncSetAttribute(k_fft_strided<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem<k_fft_strided<T, +1>>();
         k_fft_strided<T, +1><<<grid, 256, sm, st>>>(data, d, L, nb);
     }
     return cudaGetLastError();
@@ -69,10 +69,10 @@ cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, 
     const size_t sm = fft_smem_bytes<T>(L.N, nb);
     const unsigned grid = (unsigned)((nlines + nb - 1) / nb);
     if (sign < 0) {
-        cudaFuncSetAttribute(k_fft_contig<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem<k_fft_contig<T, -1>>();
         k_fft_contig<T, -1><<<grid, 256, sm, st>>>(data, nlines, L, nb, post);
     } else {
-        cudaFuncSetAttribute(k_fft_contig<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem<k_fft_contig<T, +1>>();
         k_fft_contig<T, +1><<<grid, 256, sm, st>>>(data, nlines, L, nb, post);
     }
     return cudaGetLastError();

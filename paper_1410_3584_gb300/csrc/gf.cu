@@ -22,7 +22,8 @@ constexpr int kRedBlocks = 608;   // 152 SMs x 4
 enum { S_MIN = 0, S_MAX, S_DIFF, S_NORM, S_CHANGE, S_EPOT, S_EINT, S_EKIN, S_COUNT = 16 };
 
 template <typename T> struct Work {
-    T *rho, *pot, *b, *x, *xn, *r;
+    T *rho, *pot, *b, *x, *xn, *r, *xf;   // xf: inner iterate captured at convergence
+    int *iflag;                           // [0] first converged inner iteration, [1] first non-finite one
     cpx<T> *spec;       // plain-grid spectrum (R2C half for GF)
     double *part;       // kRedBlocks x 2 partials
     double *scal;       // S_COUNT scalars
@@ -40,12 +41,15 @@ template <typename T> static nlp_status ensure_work(nlp_plan_s *p, Work<T> *&W) 
     const size_t nh = (size_t)n2 / 2 + 1;
     void *d;
     nlp_status s;
-    T *bufs[6];
-    for (int i = 0; i < 6; ++i) {
+    T *bufs[7];
+    for (int i = 0; i < 7; ++i) {
         if ((s = alloc_dev(p, &d, sizeof(T) * N))) return s;
         bufs[i] = (T *)d;
     }
     W->rho = bufs[0]; W->pot = bufs[1]; W->b = bufs[2]; W->x = bufs[3]; W->xn = bufs[4]; W->r = bufs[5];
+    W->xf = bufs[6];
+    if ((s = alloc_dev(p, &d, sizeof(int) * 2))) return s;
+    W->iflag = (int *)d;
     if ((s = alloc_dev(p, &d, sizeof(cpx<T>) * (size_t)n0 * n1 * nh))) return s;
     W->spec = (cpx<T> *)d;
     if ((s = alloc_dev(p, &d, sizeof(double) * 2 * kRedBlocks))) return s;
@@ -170,6 +174,21 @@ template <typename T> __global__ void k_maxdiff(const T *a, const T *c, int64_t 
     GRID_STRIDE(q, N) m = fmax(m, fabs((double)a[q] - (double)c[q]));
     m = block_reduce(m, 1);
     if (threadIdx.x == 0) part[2 * blockIdx.x] = m;
+}
+
+// inner-iteration bookkeeping on the device: records the first iteration whose update
+// max|x^(m+1) - x^(m)| is <= tol (flag[0]) or non-finite (flag[1])
+__global__ void k_inner_check(const double *scal, double tol, int it, int *flag) {
+    if (flag[0] || flag[1]) return;
+    const double d = scal[S_DIFF];
+    if (!isfinite(d)) flag[1] = it;
+    else if (d <= tol) flag[0] = it;
+}
+
+// dst = src on the iteration that converged (later iterations leave dst alone)
+template <typename T> __global__ void k_capture(const int *flag, int it, const T *src, T *dst, int64_t N) {
+    if (flag[0] != it) return;
+    GRID_STRIDE(q, N) dst[q] = src[q];
 }
 
 // partial sum x^2
@@ -322,10 +341,14 @@ static nlp_status gf_step_t(nlp_plan_s *p, T *phi, const T *V, double beta, doub
     k_make_b<T><<<eg(), 256, 0, st>>>(V, W->rho, W->pot, (T)g, (T)beta, W->b, N, W->part);
     if ((s = reduce_to(p, W, 0, 2, 1.0, S_MIN)) || (s = reduce_to(p, W, 1, 1, 1.0, S_MAX))) return s;
     if (cudaMemcpyAsync(W->x, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st)) return NLP_ERR_CUDA;
-    int it = 0;
-    bool conv = false;
-    double hs[S_COUNT];
-    for (it = 1; it <= max_inner; ++it) {
+    // Inner fixed point.  The convergence test runs on the device every iteration; the host
+    // reads its verdict every kCheckEvery iterations, so up to kCheckEvery - 1 iterations may
+    // run past convergence.  Their results are not used: the iterate of the first converged
+    // iteration is captured in xf, so the step equals one that stopped exactly there.
+    constexpr int kCheckEvery = 4;
+    if (cudaMemsetAsync(W->iflag, 0, sizeof(int) * 2, st)) return NLP_ERR_CUDA;
+    int flags[2] = {0, 0};
+    for (int it = 1; it <= max_inner; ++it) {
         k_rhs<T><<<eg(), 256, 0, st>>>(phi, W->b, W->x, (T)(1.0 / tau), W->scal, W->r, N);
         if (r2c_plain<T>(W->r, D, st)) return NLP_ERR_CUDA;
         k_diag<T><<<eg(), 256, 0, st>>>(D.F, D.n[0], D.n[1], D.n[2], D.nh, p->L3[0], p->L3[1], p->L3[2], 1.0 / tau,
@@ -333,18 +356,27 @@ static nlp_status gf_step_t(nlp_plan_s *p, T *phi, const T *V, double beta, doub
         if (c2r_plain<T>(W->xn, D, st)) return NLP_ERR_CUDA;
         k_maxdiff<T><<<eg(), 256, 0, st>>>(W->xn, W->x, N, W->part);
         if ((s = reduce_to(p, W, 0, 1, 1.0, S_DIFF))) return s;
+        k_inner_check<<<1, 1, 0, st>>>(W->scal, inner_tol, it, W->iflag);
+        k_capture<T><<<eg(), 256, 0, st>>>(W->iflag, it, W->xn, W->xf, N);
         T *tmp = W->x;
         W->x = W->xn;
         W->xn = tmp;
-        if ((s = read_scal(p, W, hs))) return s;
-        if (!std::isfinite(hs[S_DIFF])) return NLP_ERR_DIVERGED;
-        if (hs[S_DIFF] <= inner_tol) { conv = true; break; }
+        if (it % kCheckEvery == 0 || it == max_inner) {
+            if (cudaMemcpyAsync(flags, W->iflag, sizeof(flags), cudaMemcpyDeviceToHost, st) ||
+                cudaStreamSynchronize(st))
+                return NLP_ERR_CUDA;
+            if (flags[0] || flags[1]) break;
+        }
     }
-    if (inner_iters) *inner_iters = conv ? it : max_inner;
+    if (flags[1] && (!flags[0] || flags[1] < flags[0])) return NLP_ERR_DIVERGED;
+    const bool conv = flags[0] != 0;
+    if (inner_iters) *inner_iters = conv ? flags[0] : max_inner;
+    const T *res = conv ? W->xf : W->x;
+    double hs[S_COUNT];
     // normalise, change
-    k_sumsq<T><<<eg(), 256, 0, st>>>(W->x, N, W->part);
+    k_sumsq<T><<<eg(), 256, 0, st>>>(res, N, W->part);
     if ((s = reduce_to(p, W, 0, 0, hvol_of(p), S_NORM))) return s;
-    k_finish<T><<<eg(), 256, 0, st>>>(W->x, phi, W->scal, N, W->part);
+    k_finish<T><<<eg(), 256, 0, st>>>(res, phi, W->scal, N, W->part);
     if ((s = reduce_to(p, W, 0, 1, 1.0, S_CHANGE))) return s;
     if ((s = read_scal(p, W, hs))) return s;
     if (!std::isfinite(hs[S_CHANGE]) || !std::isfinite(hs[S_NORM])) return NLP_ERR_DIVERGED;

@@ -4,6 +4,23 @@
 
 namespace nlp {
 
+// Dynamic shared-memory opt-in limit of the current device.  Every kernel that may take more
+// than the default 48 KB is given, once, the whole opt-in limit minus its static shared
+// memory (not the size of the launch at hand), so launches of different sizes from several
+// host threads never change a limit that another thread's launch relies on.  The setup runs
+// on the device current at the first call.
+int max_dyn_smem();
+template <auto Kernel> inline cudaError_t allow_smem() {
+    static const cudaError_t status = [] {
+        cudaFuncAttributes a{};
+        cudaError_t e = cudaFuncGetAttributes(&a, Kernel);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    max_dyn_smem() - (int)a.sharedSizeBytes);
+    }();
+    return status;
+}
+
 // One strided C2C FFT pass (see k_fft_strided).
 struct StridedDesc {
     int n_in, n_out;      // input / output windows (>= N means the whole line)

@@ -1,5 +1,6 @@
 // Plan construction (host): quadrature of Eq. (ifft) (Sec. 2.1), spreading-function
 // tables, node binning by fine-grid tile, FFT tables and workspace.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -11,6 +12,18 @@
 #include "plan.h"
 
 namespace nlp {
+
+int max_dyn_smem() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    int v = cache[dev & 63].load();
+    if (v) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+        return 48 * 1024;
+    cache[dev & 63].store(v);
+    return v;
+}
 
 // ------------------------------------------------------------------ Gauss-Legendre
 // Nodes are the roots of the Legendre polynomial P_n, found by Newton's method from the

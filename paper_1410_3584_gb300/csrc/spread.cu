@@ -36,7 +36,7 @@ template <typename T> size_t interp_spread_smem(const DevPlan<T> &P) {
 template <typename T> cudaError_t launch_interp_spread(const DevPlan<T> &P, cudaStream_t st) {
     if (P.nchunks == 0) return cudaSuccess;
     const size_t sm = interp_spread_smem(P);
-    cudaError_t e = cudaFuncSetAttribute(k_interp_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_smem<k_interp_spread<T>>();
     if (e != cudaSuccess) return e;
     k_interp_spread<T><<<(unsigned)P.nchunks, 256, sm, st>>>(P);
     return cudaGetLastError();

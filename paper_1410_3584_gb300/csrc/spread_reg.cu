@@ -178,14 +178,13 @@ template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cu
     constexpr int NB = nb_of<T>();
     const size_t sm = reg_smem<T, W>(P);
     if constexpr (W * W <= 64) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp_spread_warp<T, W, NB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = allow_smem<k_interp_spread_warp<T, W, NB>>();
         if (e != cudaSuccess) return e;
         k_interp_spread_warp<T, W, NB><<<(unsigned)P.nrchunks, 256, sm, st>>>(P);
         return cudaGetLastError();
     }
     cudaError_t e =
-        cudaFuncSetAttribute(k_interp_spread_reg<T, W, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem<k_interp_spread_reg<T, W, NB>>();
     if (e != cudaSuccess) return e;
     k_interp_spread_reg<T, W, NB><<<(unsigned)P.nrchunks, RegCfg<W>::TT * RegCfg<W>::NT, sm, st>>>(P);
     return cudaGetLastError();

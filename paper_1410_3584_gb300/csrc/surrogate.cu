@@ -1,0 +1,800 @@
+// Learned initial guess for the normalized gradient flow of Sec. 3.1 (not part of the paper):
+// a small network maps (beta, trap anisotropy gamma, kernel type) to a ground-state
+// amplitude sampled on a 48^3 grid; the gradient flow started from it finishes the solve.
+//
+//   features : [log10(beta)/3, (gamma-1)/3, is Coulomb, is dipolar]        (padded to 64)
+//   MLP      : 64 -> 512 -> 512 -> 512 -> 512, SiLU; dense layers as BF16 tcgen05 GEMMs with
+//              FP32 accumulation (FP32 master weights, BF16 copies refreshed after updates)
+//   head     : 512 -> 1728 (padded to 1792), linear, read as 8 channels x 6^3
+//   decoder  : [nearest x2 -> 3^3 conv 8->8 -> SiLU] at 12^3 and 24^3, nearest x2 -> 3^3 conv
+//              8->1 at 48^3 (zero padding)
+//   loss     : mean squared error against the target amplitude; AdamW.
+// Every forward and backward step is a kernel of this file; the decoder and elementwise
+// work run on CUDA cores in FP32.  Mode 1 runs the dense layers on an FP32 CUDA-core GEMM
+// instead (used to check the gradients against an FP64 host computation).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <random>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm_tc.cuh"
+#include "launch.h"
+
+namespace nlp {
+
+constexpr int kFeat = 4, kFeatPad = 64, kHid = 512, kHeadOut = 8 * 216, kHeadPad = 1792;
+constexpr int kC = 8;
+constexpr int kGout = 48;
+constexpr int64_t kOut = (int64_t)kGout * kGout * kGout;
+constexpr int kBP = 128;   // padded batch = GEMM M of the forward layers
+constexpr int kConv = 3;   // conv layers: (8->8 @ 12^3), (8->8 @ 24^3), (8->1 @ 48^3)
+constexpr int kConvCi[kConv] = {kC, kC, kC}, kConvCo[kConv] = {kC, kC, 1}, kConvG[kConv] = {12, 24, 48};
+
+// flat FP32 parameter vector: W_l [out][in] row-major then b_l, for l = 0..4; then for each
+// conv layer w [co][ci][27] (tap d = 9 dz + 3 dy + dx, offsets -1..1) then bias [co]
+struct Layout {
+    size_t W[5], b[5], cw[kConv], cb[kConv], total;
+    int nin[5], nout[5];
+    Layout() {
+        const int ins[5] = {kFeatPad, kHid, kHid, kHid, kHid}, outs[5] = {kHid, kHid, kHid, kHid, kHeadPad};
+        size_t o = 0;
+        for (int l = 0; l < 5; ++l) {
+            nin[l] = ins[l];
+            nout[l] = outs[l];
+            W[l] = o;
+            o += (size_t)ins[l] * outs[l];
+            b[l] = o;
+            o += outs[l];
+        }
+        for (int c = 0; c < kConv; ++c) {
+            cw[c] = o;
+            o += (size_t)kConvCo[c] * kConvCi[c] * 27;
+            cb[c] = o;
+            o += kConvCo[c];
+        }
+        total = o;
+    }
+};
+
+#define GS(q, N) \
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)(N); q += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ float sig(float x) { return 1.f / (1.f + expf(-x)); }
+
+// Y = act(C + b) on rows < B (rows >= B stay zero); keeps the pre-activation; BF16 copies of Y
+// and of its transpose for the GEMMs that read it
+__global__ void k_bias_act(const float *C, const float *b, float *pre, float *Y, __nv_bfloat16 *Ybf,
+                           __nv_bfloat16 *Ytbf, int B, int N, int act) {
+    GS(q, (int64_t)kBP * N) {
+        const int r = (int)(q / N), c = (int)(q % N);
+        float v = 0.f, y = 0.f;
+        if (r < B) {
+            v = C[q] + b[c];
+            y = act ? v * sig(v) : v;
+        }
+        pre[q] = v;
+        Y[q] = y;
+        const __nv_bfloat16 yb = __float2bfloat16(y);
+        if (Ybf) Ybf[q] = yb;
+        if (Ytbf) Ytbf[(size_t)c * kBP + r] = yb;
+    }
+}
+
+// dPre = dY * act'(pre) on rows < B; BF16 copies of dPre and of its transpose
+__global__ void k_act_back(const float *dY, const float *pre, float *dP, __nv_bfloat16 *dPbf, __nv_bfloat16 *dPtbf,
+                           int B, int N, int act) {
+    GS(q, (int64_t)kBP * N) {
+        const int r = (int)(q / N), c = (int)(q % N);
+        float g = 0.f;
+        if (r < B) {
+            const float v = pre[q], s = sig(v);
+            g = act ? dY[q] * (s * (1.f + v * (1.f - s))) : dY[q];
+        }
+        dP[q] = g;
+        const __nv_bfloat16 gb = __float2bfloat16(g);
+        dPbf[q] = gb;
+        dPtbf[(size_t)c * kBP + r] = gb;
+    }
+}
+
+// db[c] = sum over rows of dP (fixed order)
+__global__ void k_colsum(const float *dP, float *db, int N) {
+    GS(c, N) {
+        float s = 0.f;
+        for (int r = 0; r < kBP; ++r) s += dP[(size_t)r * N + c];
+        db[c] = s;
+    }
+}
+
+// BF16 copy and/or BF16 transpose and/or FP32 transpose of a row-major FP32 matrix [R x Cc]
+__global__ void k_convert(const float *X, __nv_bfloat16 *Xb, __nv_bfloat16 *Xtb, float *Xt, int R, int Cc) {
+    GS(q, (int64_t)R * Cc) {
+        const int r = (int)(q / Cc), c = (int)(q % Cc);
+        const float x = X[q];
+        const __nv_bfloat16 v = __float2bfloat16(x);
+        if (Xb) Xb[q] = v;
+        if (Xtb) Xtb[(size_t)c * R + r] = v;
+        if (Xt) Xt[(size_t)c * R + r] = x;
+    }
+}
+
+// features [B x 4] -> padded input rows [kBP x 64] (FP32, BF16, BF16 transposed)
+__global__ void k_input(const float *feat, int B, float *X, __nv_bfloat16 *Xbf, __nv_bfloat16 *Xtbf) {
+    GS(q, (int64_t)kBP * kFeatPad) {
+        const int r = (int)(q / kFeatPad), c = (int)(q % kFeatPad);
+        const float v = (r < B && c < kFeat) ? feat[r * kFeat + c] : 0.f;
+        X[q] = v;
+        Xbf[q] = __float2bfloat16(v);
+        Xtbf[(size_t)c * kBP + r] = __float2bfloat16(v);
+    }
+}
+
+// head rows [kBP x 1792] -> z0 [B][1728]; and the reverse for the gradient (zeros elsewhere)
+__global__ void k_head_unpack(const float *Y, float *z0, int B) {
+    GS(q, (int64_t)B * kHeadOut) z0[q] = Y[(q / kHeadOut) * kHeadPad + q % kHeadOut];
+}
+__global__ void k_head_pack(const float *dz0, float *dY, int B) {
+    GS(q, (int64_t)kBP * kHeadPad) {
+        const int64_t r = q / kHeadPad, c = q % kHeadPad;
+        dY[q] = (r < B && c < kHeadOut) ? dz0[r * kHeadOut + c] : 0.f;
+    }
+}
+
+// nearest x2: in [B*C][g^3] -> out [B*C][(2g)^3]; the backward sums the 8 children
+__global__ void k_up2(const float *in, float *out, int64_t BC, int g) {
+    const int G = 2 * g;
+    const int64_t G3 = (int64_t)G * G * G, g3 = (int64_t)g * g * g;
+    GS(q, BC * G3) {
+        const int64_t p = q % G3;
+        const int x = (int)(p % G), y = (int)((p / G) % G), z = (int)(p / ((int64_t)G * G));
+        out[q] = in[(q / G3) * g3 + ((z >> 1) * g + (y >> 1)) * g + (x >> 1)];
+    }
+}
+__global__ void k_up2_back(const float *dout, float *din, int64_t BC, int g) {
+    const int G = 2 * g;
+    const int64_t G3 = (int64_t)G * G * G, g3 = (int64_t)g * g * g;
+    GS(q, BC * g3) {
+        const int64_t p = q % g3;
+        const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
+        const float *src = dout + (q / g3) * G3;
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d)
+            s += src[((int64_t)(2 * z + (d >> 2)) * G + (2 * y + ((d >> 1) & 1))) * G + (2 * x + (d & 1))];
+        din[q] = s;
+    }
+}
+
+// 3^3 convolution, zero padding 1: out[b][co](p) = bias[co] + sum_ci sum_d w[co][ci][d] in[b][ci](p + d - 1)
+__global__ void k_conv_fwd(const float *in, const float *w, const float *bias, float *out, int B, int Ci, int Co,
+                           int g) {
+    const int64_t G3 = (int64_t)g * g * g;
+    GS(q, (int64_t)B * Co * G3) {
+        const int64_t p = q % G3;
+        const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
+        const int co = (int)((q / G3) % Co), b = (int)(q / (G3 * Co));
+        float s = bias[co];
+        for (int ci = 0; ci < Ci; ++ci) {
+            const float *src = in + ((int64_t)b * Ci + ci) * G3;
+            const float *wk = w + ((int64_t)co * Ci + ci) * 27;
+#pragma unroll
+            for (int d = 0; d < 27; ++d) {
+                const int zz = z + d / 9 - 1, yy = y + (d / 3) % 3 - 1, xx = x + d % 3 - 1;
+                if (zz >= 0 && zz < g && yy >= 0 && yy < g && xx >= 0 && xx < g)
+                    s += wk[d] * src[((int64_t)zz * g + yy) * g + xx];
+            }
+        }
+        out[q] = s;
+    }
+}
+
+// d in[b][ci](p) = sum_co sum_d w[co][ci][d] dout[b][co](p - d + 1)
+__global__ void k_conv_bwd_in(const float *dout, const float *w, float *din, int B, int Ci, int Co, int g) {
+    const int64_t G3 = (int64_t)g * g * g;
+    GS(q, (int64_t)B * Ci * G3) {
+        const int64_t p = q % G3;
+        const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
+        const int ci = (int)((q / G3) % Ci), b = (int)(q / (G3 * Ci));
+        float s = 0.f;
+        for (int co = 0; co < Co; ++co) {
+            const float *src = dout + ((int64_t)b * Co + co) * G3;
+            const float *wk = w + ((int64_t)co * Ci + ci) * 27;
+#pragma unroll
+            for (int d = 0; d < 27; ++d) {
+                const int zz = z - (d / 9 - 1), yy = y - ((d / 3) % 3 - 1), xx = x - (d % 3 - 1);
+                if (zz >= 0 && zz < g && yy >= 0 && yy < g && xx >= 0 && xx < g)
+                    s += wk[d] * src[((int64_t)zz * g + yy) * g + xx];
+            }
+        }
+        din[q] = s;
+    }
+}
+
+// weight gradient, stage 1: block (job, slice), job = co * (Ci + 1) + ci; ci < Ci accumulates
+// the 27 taps dw[co][ci][d] = sum_{b,p} dout[b][co](p) in[b][ci](p + d - 1) over one slice of
+// the (b, p) range; ci == Ci accumulates the bias sum.  Partials land in part[(job*27+d)*S+slice].
+__global__ void __launch_bounds__(256) k_conv_bwd_w_part(const float *dout, const float *in, float *part, int B,
+                                                         int Ci, int Co, int g, int S) {
+    const int job = blockIdx.x, co = job / (Ci + 1), ci = job % (Ci + 1);
+    const int64_t G3 = (int64_t)g * g * g, total = (int64_t)B * G3;
+    const int64_t per = (total + S - 1) / S, beg = (int64_t)blockIdx.y * per, end = min(total, beg + per);
+    float acc[27];
+#pragma unroll
+    for (int d = 0; d < 27; ++d) acc[d] = 0.f;
+    for (int64_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
+        const int b = (int)(q / G3);
+        const int64_t p = q % G3;
+        const float go = dout[((int64_t)b * Co + co) * G3 + p];
+        if (ci == Ci) {
+            acc[0] += go;
+        } else {
+            const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
+            const float *src = in + ((int64_t)b * Ci + ci) * G3;
+#pragma unroll
+            for (int d = 0; d < 27; ++d) {
+                const int zz = z + d / 9 - 1, yy = y + (d / 3) % 3 - 1, xx = x + d % 3 - 1;
+                if (zz >= 0 && zz < g && yy >= 0 && yy < g && xx >= 0 && xx < g)
+                    acc[d] += go * src[((int64_t)zz * g + yy) * g + xx];
+            }
+        }
+    }
+    __shared__ float red[8][27];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        float v = acc[d];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][d] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 27) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        part[((int64_t)job * 27 + threadIdx.x) * S + blockIdx.y] = s;
+    }
+}
+
+// stage 2: sum the slices in order into dw [co][ci][27] and db [co]
+__global__ void k_conv_bwd_w_final(const float *part, float *dw, float *db, int Ci, int Co, int S) {
+    GS(q, (int64_t)Co * (Ci + 1) * 27) {
+        const int job = (int)(q / 27), d = (int)(q % 27), co = job / (Ci + 1), ci = job % (Ci + 1);
+        float s = 0.f;
+        for (int i = 0; i < S; ++i) s += part[q * S + i];
+        if (ci < Ci) dw[((int64_t)co * Ci + ci) * 27 + d] = s;
+        else if (d == 0) db[co] = s;
+    }
+}
+
+__global__ void k_silu(const float *pre, float *y, int64_t n) {
+    GS(q, n) {
+        const float v = pre[q];
+        y[q] = v * sig(v);
+    }
+}
+__global__ void k_silu_back(const float *dy, const float *pre, float *dp, int64_t n) {
+    GS(q, n) {
+        const float v = pre[q], s = sig(v);
+        dp[q] = dy[q] * (s * (1.f + v * (1.f - s)));
+    }
+}
+
+// squared-error partial sums per block and d out = 2 (out - t) / n
+__global__ void k_mse(const float *out, const float *t, float *dout, int64_t n, double *part) {
+    double s = 0.0;
+    GS(q, n) {
+        const float d = out[q] - t[q];
+        s += (double)d * d;
+        dout[q] = 2.f * d / (float)n;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// AdamW with bias-corrected moments and decoupled weight decay
+__global__ void k_adamw(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, float wd, float c1, float c2) {
+    GS(q, n) {
+        const float gq = g[q];
+        const float mq = b1 * m[q] + (1.f - b1) * gq;
+        const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+        m[q] = mq;
+        v[q] = vq;
+        p[q] -= lr * ((mq / c1) / (sqrtf(vq / c2) + eps) + wd * p[q]);
+    }
+}
+
+// beta = 0 ground state of the trap V = (x^2 + y^2 + gamma^2 z^2)/2, normalised in the continuum:
+// b(x) = gamma^{1/4} pi^{-3/4} exp(-(x^2 + y^2 + gamma z^2)/2).  The network learns the
+// correction to it.
+__device__ __forceinline__ double base_amp(double x, double y, double z, double gamma) {
+    return pow(gamma, 0.25) * pow(M_PI, -0.75) * exp(-0.5 * (x * x + y * y + gamma * z * z));
+}
+
+// guess at the target grid points: b(x) + trilinear sample of the 48^3 network output (point j
+// at -Ls + j hs; zero correction outside the sampled cube), clamped at zero
+template <typename T>
+__global__ void k_resample(const float *src, double Ls, double gamma, T *dst, int n0, int n1, int n2, double L0,
+                           double L1, double L2) {
+    const double hs = 2.0 * Ls / kGout;
+    const int nn[3] = {n0, n1, n2};
+    const double LL[3] = {L0, L1, L2};
+    GS(q, (int64_t)n0 * n1 * n2) {
+        const int64_t idx[3] = {q / ((int64_t)n1 * n2), (q / n2) % n1, q % n2};
+        int lo[3];
+        double f[3], x[3];
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+            x[a] = -LL[a] + idx[a] * (2.0 * LL[a] / nn[a]);
+            const double u = (x[a] + Ls) / hs;
+            if (!(u >= 0.0 && u <= kGout - 1)) inside = false;
+            lo[a] = min(max((int)floor(u), 0), kGout - 2);
+            f[a] = u - lo[a];
+        }
+        double v = base_amp(x[0], x[1], x[2], gamma);
+        if (inside) {
+            for (int d = 0; d < 8; ++d) {
+                const int dz = d >> 2, dy = (d >> 1) & 1, dx = d & 1;
+                const double wgt = (dz ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dx ? f[2] : 1 - f[2]);
+                v += wgt * src[((int64_t)(lo[0] + dz) * kGout + (lo[1] + dy)) * kGout + (lo[2] + dx)];
+            }
+        }
+        dst[q] = (T)fmax(v, 0.0);
+    }
+}
+
+// average over the 8 reflections x_a -> -x_a of the grid (index i -> (n - i) mod n on each axis),
+// in place: one thread per orbit, representative indices 0..n/2 on every axis
+template <typename T> __global__ void k_symmetrize(T *x, int n0, int n1, int n2) {
+    const int h0 = n0 / 2 + 1, h1 = n1 / 2 + 1, h2 = n2 / 2 + 1;
+    GS(q, (int64_t)h0 * h1 * h2) {
+        const int i2 = (int)(q % h2), i1 = (int)((q / h2) % h1), i0 = (int)(q / ((int64_t)h1 * h2));
+        const int a0[2] = {i0, (n0 - i0) % n0}, a1[2] = {i1, (n1 - i1) % n1}, a2[2] = {i2, (n2 - i2) % n2};
+        double s = 0.0;
+        for (int d = 0; d < 8; ++d)
+            s += (double)x[((int64_t)a0[d >> 2] * n1 + a1[(d >> 1) & 1]) * n2 + a2[d & 1]];
+        const T m = (T)(0.125 * s);
+        for (int d = 0; d < 8; ++d) x[((int64_t)a0[d >> 2] * n1 + a1[(d >> 1) & 1]) * n2 + a2[d & 1]] = m;
+    }
+}
+
+// FP64 partial sums of x^2 per block
+template <typename T> __global__ void k_sumsq_part(const T *x, int64_t n, double *part) {
+    double acc = 0.0;
+    GS(q, n) {
+        const double v = (double)x[q];
+        acc += v * v;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// phi *= 1 / sqrt(hvol sum phi^2) (partials summed in order by every block)
+template <typename T> __global__ void k_normalize(T *x, int64_t n, const double *part, int np, double hvol) {
+    __shared__ double s;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < np; ++i) t += part[i];
+        s = t > 0.0 ? 1.0 / sqrt(hvol * t) : 0.0;
+    }
+    __syncthreads();
+    GS(q, n) x[q] = (T)((double)x[q] * s);
+}
+
+// the beta = 0 amplitude on the 48^3 cube (training targets are ground state minus this)
+__global__ void k_base_cube(double Ls, const float *gamma, int B, float *out) {
+    const double hs = 2.0 * Ls / kGout;
+    GS(q, (int64_t)B * kOut) {
+        const int64_t p = q % kOut;
+        const int b = (int)(q / kOut);
+        const int k = (int)(p % kGout), j = (int)((p / kGout) % kGout), i = (int)(p / ((int64_t)kGout * kGout));
+        out[q] = (float)base_amp(-Ls + i * hs, -Ls + j * hs, -Ls + k * hs, (double)gamma[b]);
+    }
+}
+
+static dim3 grid_for(int64_t n) {
+    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
+}
+
+constexpr int kRedBlocks = 512;
+
+}  // namespace nlp
+
+using namespace nlp;
+
+struct nlp_surrogate_s {
+    Layout lay;
+    cudaStream_t stream = nullptr;
+    int mode = 0;          // 0: BF16 tensor-core GEMMs, 1: FP32 CUDA-core GEMMs
+    double box_L = 10.0;   // output point j sits at -box_L + j * 2 box_L / 48 on each axis
+    std::vector<void *> allocs;
+    float *P = nullptr, *Gr = nullptr, *Mm = nullptr, *Vv = nullptr;   // params, grads, AdamW moments
+    __nv_bfloat16 *Wbf[5] = {}, *Wtbf[5] = {};                         // W [out x in], W^T [in x out]
+    float *Wt32[5] = {};                                               // W^T in FP32 (mode 1)
+    float *X[6] = {}, *pre[5] = {}, *Cbuf = nullptr;                   // layer inputs/outputs [kBP x width]
+    __nv_bfloat16 *Xbf[6] = {}, *Xtbf[6] = {};
+    float *Xt32 = nullptr, *dPt32 = nullptr;                           // FP32 transposes (mode 1)
+    float *dY = nullptr, *dP = nullptr;
+    __nv_bfloat16 *dPbf = nullptr, *dPtbf = nullptr;
+    // decoder: z0 -> [up -> conv -> (SiLU)] x 3 ; cin[c] is conv c's input, cpre[c] its output
+    float *z0 = nullptr, *cin[kConv] = {}, *cpre[kConv] = {}, *cact[kConv] = {};
+    float *dz0 = nullptr, *dcin[kConv] = {}, *dcpre[kConv] = {}, *dcact[kConv] = {};
+    float *wpart = nullptr, *dout = nullptr, *feat1 = nullptr;
+    double *part = nullptr;
+    int *err = nullptr;
+    long long step = 0;
+};
+
+static nlp_status sg_alloc(nlp_surrogate_s *s, void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return NLP_ERR_OOM;
+    }
+    s->allocs.push_back(*p);
+    return NLP_OK;
+}
+
+static cudaError_t launch_gemm_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K,
+                                  int *err, cudaStream_t st) {
+    if (M % 128 || K % 64 || N % 64) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem<k_gemm_bf16_tc<128>>();
+    if (e == cudaSuccess) e = allow_smem<k_gemm_bf16_tc<64>>();
+    if (e != cudaSuccess) return e;
+    if (N % 128 == 0)
+        k_gemm_bf16_tc<128><<<dim3(N / 128, M / 128), 128, kGemmSmemBytes, st>>>(A, B, C, M, N, K, err, 1ll << 22);
+    else
+        k_gemm_bf16_tc<64><<<dim3(N / 64, M / 128), 128, kGemmSmemBytes, st>>>(A, B, C, M, N, K, err, 1ll << 22);
+    return cudaGetLastError();
+}
+
+// C[M x N] = A[M x K] B[N x K]^T, BF16 operands (mode 0) or FP32 operands (mode 1)
+static nlp_status gemm(nlp_surrogate_s *s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *A32,
+                       const float *B32, float *C, int M, int N, int K) {
+    if (s->mode) {
+        k_gemm_f32_simt<<<dim3((N + 15) / 16, (M + 15) / 16), 256, 0, s->stream>>>(A32, B32, C, M, N, K);
+        return cudaGetLastError() == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+    }
+    return launch_gemm_tc(A, B, C, M, N, K, s->err, s->stream) == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+}
+
+static void refresh_weights(nlp_surrogate_s *s) {
+    for (int l = 0; l < 5; ++l) {
+        const int ni = s->lay.nin[l], no = s->lay.nout[l];
+        k_convert<<<grid_for((int64_t)ni * no), 256, 0, s->stream>>>(s->P + s->lay.W[l], s->Wbf[l], s->Wtbf[l],
+                                                                     s->mode ? s->Wt32[l] : nullptr, no, ni);
+    }
+}
+
+static nlp_status forward(nlp_surrogate_s *s, const float *feat, int B) {
+    cudaStream_t st = s->stream;
+    const Layout &L = s->lay;
+    nlp_status r;
+    k_input<<<grid_for((int64_t)kBP * kFeatPad), 256, 0, st>>>(feat, B, s->X[0], s->Xbf[0], s->Xtbf[0]);
+    for (int l = 0; l < 5; ++l) {
+        const int ni = L.nin[l], no = L.nout[l];
+        if ((r = gemm(s, s->Xbf[l], s->Wbf[l], s->X[l], s->P + L.W[l], s->Cbuf, kBP, no, ni))) return r;
+        k_bias_act<<<grid_for((int64_t)kBP * no), 256, 0, st>>>(s->Cbuf, s->P + L.b[l], s->pre[l], s->X[l + 1],
+                                                                s->Xbf[l + 1], s->Xtbf[l + 1], B, no, l < 4);
+    }
+    k_head_unpack<<<grid_for((int64_t)B * kHeadOut), 256, 0, st>>>(s->X[5], s->z0, B);
+    const float *prev = s->z0;
+    int g = 6;
+    for (int c = 0; c < kConv; ++c) {
+        const int64_t BC = (int64_t)B * kConvCi[c], G3 = (int64_t)kConvG[c] * kConvG[c] * kConvG[c];
+        k_up2<<<grid_for(BC * G3), 256, 0, st>>>(prev, s->cin[c], BC, g);
+        g = kConvG[c];
+        k_conv_fwd<<<grid_for((int64_t)B * kConvCo[c] * G3), 256, 0, st>>>(s->cin[c], s->P + L.cw[c], s->P + L.cb[c],
+                                                                          s->cpre[c], B, kConvCi[c], kConvCo[c], g);
+        if (c + 1 < kConv) {
+            k_silu<<<grid_for((int64_t)B * kConvCo[c] * G3), 256, 0, st>>>(s->cpre[c], s->cact[c],
+                                                                          (int64_t)B * kConvCo[c] * G3);
+            prev = s->cact[c];
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+}
+
+static nlp_status check_err(nlp_surrogate_s *s) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return NLP_ERR_CUDA;
+    return h ? NLP_ERR_TIMEOUT : NLP_OK;
+}
+
+// loss and every parameter gradient into s->Gr (flat layout)
+static nlp_status backward(nlp_surrogate_s *s, const float *target, int B, double *loss) {
+    cudaStream_t st = s->stream;
+    const Layout &L = s->lay;
+    const int64_t nout = (int64_t)B * kOut;
+    k_mse<<<kRedBlocks, 256, 0, st>>>(s->cpre[kConv - 1], target, s->dout, nout, s->part);
+    const float *dnext = s->dout;   // gradient w.r.t. the current conv output (pre-activation)
+    for (int c = kConv - 1; c >= 0; --c) {
+        const int Ci = kConvCi[c], Co = kConvCo[c], g = kConvG[c];
+        const int64_t G3 = (int64_t)g * g * g, total = (int64_t)B * G3;
+        const int S = (int)std::max<int64_t>(1, std::min<int64_t>(64, total / (256 * 32)));
+        k_conv_bwd_w_part<<<dim3(Co * (Ci + 1), S), 256, 0, st>>>(dnext, s->cin[c], s->wpart, B, Ci, Co, g, S);
+        k_conv_bwd_w_final<<<grid_for((int64_t)Co * (Ci + 1) * 27), 256, 0, st>>>(s->wpart, s->Gr + L.cw[c],
+                                                                                   s->Gr + L.cb[c], Ci, Co, S);
+        k_conv_bwd_in<<<grid_for((int64_t)B * Ci * G3), 256, 0, st>>>(dnext, s->P + L.cw[c], s->dcin[c], B, Ci, Co, g);
+        const int gp = g / 2;
+        const int64_t BC = (int64_t)B * Ci, gp3 = (int64_t)gp * gp * gp;
+        if (c > 0) {
+            k_up2_back<<<grid_for(BC * gp3), 256, 0, st>>>(s->dcin[c], s->dcact[c - 1], BC, gp);
+            k_silu_back<<<grid_for(BC * gp3), 256, 0, st>>>(s->dcact[c - 1], s->cpre[c - 1], s->dcpre[c - 1], BC * gp3);
+            dnext = s->dcpre[c - 1];
+        } else {
+            k_up2_back<<<grid_for(BC * gp3), 256, 0, st>>>(s->dcin[c], s->dz0, BC, gp);
+        }
+    }
+    k_head_pack<<<grid_for((int64_t)kBP * kHeadPad), 256, 0, st>>>(s->dz0, s->dY, B);
+    nlp_status r;
+    for (int l = 4; l >= 0; --l) {
+        const int ni = L.nin[l], no = L.nout[l];
+        k_act_back<<<grid_for((int64_t)kBP * no), 256, 0, st>>>(s->dY, s->pre[l], s->dP, s->dPbf, s->dPtbf, B, no,
+                                                                l < 4);
+        k_colsum<<<grid_for(no), 256, 0, st>>>(s->dP, s->Gr + L.b[l], no);
+        // dW [no x ni] = dPre^T X : A = dPre^T [no x kBP], B = X^T [ni x kBP]
+        if (s->mode) {
+            k_convert<<<grid_for((int64_t)kBP * no), 256, 0, st>>>(s->dP, nullptr, nullptr, s->dPt32, kBP, no);
+            k_convert<<<grid_for((int64_t)kBP * ni), 256, 0, st>>>(s->X[l], nullptr, nullptr, s->Xt32, kBP, ni);
+        }
+        if ((r = gemm(s, s->dPtbf, s->Xtbf[l], s->dPt32, s->Xt32, s->Gr + L.W[l], no, ni, kBP))) return r;
+        // dX [kBP x ni] = dPre W : A = dPre [kBP x no], B = W^T [ni x no]; the next layer's dY
+        if (l > 0 && (r = gemm(s, s->dPbf, s->Wtbf[l], s->dP, s->Wt32[l], s->dY, kBP, ni, no))) return r;
+    }
+    if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
+    if (loss) {
+        double h[kRedBlocks];
+        if (cudaMemcpyAsync(h, s->part, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return NLP_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return NLP_ERR_CUDA;
+        double t = 0;
+        for (double x : h) t += x;
+        *loss = t / (double)nout;
+    }
+    return NLP_OK;
+}
+
+extern "C" {
+
+void nlp_surrogate_features(double beta, double gamma, nlp_kernel kernel, float *feat) {
+    if (!feat) return;
+    feat[0] = (float)(std::log10(beta > 0 ? beta : 1e-300) / 3.0);
+    feat[1] = (float)((gamma - 1.0) / 3.0);
+    feat[2] = kernel == NLP_COULOMB_3D ? 1.f : 0.f;
+    feat[3] = kernel == NLP_DIPOLE_3D ? 1.f : 0.f;
+}
+
+void nlp_surrogate_destroy(nlp_surrogate s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (void *p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+nlp_status nlp_surrogate_create(double box_L, unsigned long long seed, int mode, void *stream, nlp_surrogate *out) {
+    if (!out) return NLP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!(box_L > 0) || (mode != 0 && mode != 1)) return NLP_ERR_INVALID_ARG;
+    nlp_surrogate_s *s = new (std::nothrow) nlp_surrogate_s();
+    if (!s) return NLP_ERR_OOM;
+    s->stream = (cudaStream_t)stream;
+    s->mode = mode;
+    s->box_L = box_L;
+    const Layout &L = s->lay;
+    nlp_status r = NLP_OK;
+    auto A = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (r == NLP_OK) r = sg_alloc(s, &p, bytes);
+        return p;
+    };
+    s->P = (float *)A(4 * L.total);
+    s->Gr = (float *)A(4 * L.total);
+    s->Mm = (float *)A(4 * L.total);
+    s->Vv = (float *)A(4 * L.total);
+    for (int l = 0; l < 5; ++l) {
+        const size_t e = (size_t)L.nin[l] * L.nout[l];
+        s->Wbf[l] = (__nv_bfloat16 *)A(2 * e);
+        s->Wtbf[l] = (__nv_bfloat16 *)A(2 * e);
+        s->Wt32[l] = (float *)A(4 * e);
+    }
+    const int widths[6] = {kFeatPad, kHid, kHid, kHid, kHid, kHeadPad};
+    for (int l = 0; l < 6; ++l) {
+        s->X[l] = (float *)A(4 * (size_t)kBP * widths[l]);
+        s->Xbf[l] = (__nv_bfloat16 *)A(2 * (size_t)kBP * widths[l]);
+        s->Xtbf[l] = (__nv_bfloat16 *)A(2 * (size_t)kBP * widths[l]);
+        if (l < 5) s->pre[l] = (float *)A(4 * (size_t)kBP * widths[l + 1]);
+    }
+    const size_t wide = (size_t)kBP * kHeadPad;
+    s->Cbuf = (float *)A(4 * wide);
+    s->dY = (float *)A(4 * wide);
+    s->dP = (float *)A(4 * wide);
+    s->dPbf = (__nv_bfloat16 *)A(2 * wide);
+    s->dPtbf = (__nv_bfloat16 *)A(2 * wide);
+    s->Xt32 = (float *)A(4 * wide);
+    s->dPt32 = (float *)A(4 * wide);
+    s->z0 = (float *)A(4 * (size_t)kBP * kHeadOut);
+    s->dz0 = (float *)A(4 * (size_t)kBP * kHeadOut);
+    for (int c = 0; c < kConv; ++c) {
+        const size_t G3 = (size_t)kConvG[c] * kConvG[c] * kConvG[c];
+        s->cin[c] = (float *)A(4 * kBP * kConvCi[c] * G3);
+        s->dcin[c] = (float *)A(4 * kBP * kConvCi[c] * G3);
+        s->cpre[c] = (float *)A(4 * kBP * kConvCo[c] * G3);
+        if (c + 1 < kConv) {
+            s->cact[c] = (float *)A(4 * kBP * kConvCo[c] * G3);
+            s->dcact[c] = (float *)A(4 * kBP * kConvCo[c] * G3);
+            s->dcpre[c] = (float *)A(4 * kBP * kConvCo[c] * G3);
+        }
+    }
+    s->dout = (float *)A(4 * (size_t)kBP * kOut);
+    s->wpart = (float *)A(4 * (size_t)kC * (kC + 1) * 27 * 64);
+    s->feat1 = (float *)A(4 * kFeat);
+    s->part = (double *)A(8 * kRedBlocks);
+    s->err = (int *)A(sizeof(int));
+    if (r) {
+        nlp_surrogate_destroy(s);
+        return r;
+    }
+    // initialisation: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) over the real (unpadded) entries,
+    // padding entries and biases zero
+    std::vector<float> h(L.total, 0.f);
+    std::mt19937_64 rng(seed);
+    auto fill = [&](size_t off, int rows, int cols, int used_rows, int used_cols, double fan) {
+        std::uniform_real_distribution<double> U(-1.0 / std::sqrt(fan), 1.0 / std::sqrt(fan));
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j)
+                h[off + (size_t)i * cols + j] = (i < used_rows && j < used_cols) ? (float)U(rng) : 0.f;
+    };
+    fill(L.W[0], kHid, kFeatPad, kHid, kFeat, kFeat);
+    for (int l = 1; l < 4; ++l) fill(L.W[l], kHid, kHid, kHid, kHid, kHid);
+    fill(L.W[4], kHeadPad, kHid, kHeadOut, kHid, kHid);
+    for (int c = 0; c < kConv; ++c)
+        fill(L.cw[c], kConvCo[c] * kConvCi[c], 27, kConvCo[c] * kConvCi[c], 27, kConvCi[c] * 27.0);
+    bool ok = cudaMemcpy(s->P, h.data(), 4 * L.total, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(s->Mm, 0, 4 * L.total) == cudaSuccess && cudaMemset(s->Vv, 0, 4 * L.total) == cudaSuccess &&
+              cudaMemset(s->Gr, 0, 4 * L.total) == cudaSuccess && cudaMemset(s->err, 0, sizeof(int)) == cudaSuccess;
+    if (ok) {
+        refresh_weights(s);
+        ok = cudaStreamSynchronize(s->stream) == cudaSuccess;
+    }
+    if (!ok) {
+        nlp_surrogate_destroy(s);
+        return NLP_ERR_CUDA;
+    }
+    *out = s;
+    return NLP_OK;
+}
+
+int64_t nlp_surrogate_num_params(nlp_surrogate s) { return s ? (int64_t)s->lay.total : 0; }
+
+nlp_status nlp_surrogate_get_params(nlp_surrogate s, float *host) {
+    if (!s || !host) return NLP_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+        cudaMemcpy(host, s->P, 4 * s->lay.total, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NLP_ERR_CUDA;
+    return NLP_OK;
+}
+
+nlp_status nlp_surrogate_set_params(nlp_surrogate s, const float *host) {
+    if (!s || !host) return NLP_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+        cudaMemcpy(s->P, host, 4 * s->lay.total, cudaMemcpyHostToDevice) != cudaSuccess)
+        return NLP_ERR_CUDA;
+    refresh_weights(s);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+}
+
+nlp_status nlp_surrogate_forward(nlp_surrogate s, const float *feat_dev, int B, float *out_dev) {
+    if (!s || !feat_dev || !out_dev || B < 1 || B > kBP) return NLP_ERR_INVALID_ARG;
+    nlp_status r = forward(s, feat_dev, B);
+    if (r) return r;
+    if (cudaMemcpyAsync(out_dev, s->cpre[kConv - 1], 4 * (size_t)B * kOut, cudaMemcpyDeviceToDevice, s->stream) !=
+        cudaSuccess)
+        return NLP_ERR_CUDA;
+    return check_err(s);
+}
+
+nlp_status nlp_surrogate_gradients(nlp_surrogate s, const float *feat_dev, const float *target_dev, int B,
+                                   double *loss, float *grads_host) {
+    if (!s || !feat_dev || !target_dev || B < 1 || B > kBP) return NLP_ERR_INVALID_ARG;
+    nlp_status r = forward(s, feat_dev, B);
+    if (r || (r = backward(s, target_dev, B, loss)) || (r = check_err(s))) return r;
+    if (grads_host && cudaMemcpy(grads_host, s->Gr, 4 * s->lay.total, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NLP_ERR_CUDA;
+    return NLP_OK;
+}
+
+nlp_status nlp_surrogate_train_step(nlp_surrogate s, const float *feat_dev, const float *target_dev, int B, float lr,
+                                    float weight_decay, double *loss) {
+    if (!s || !feat_dev || !target_dev || B < 1 || B > kBP || !(lr > 0) || !(weight_decay >= 0))
+        return NLP_ERR_INVALID_ARG;
+    nlp_status r = forward(s, feat_dev, B);
+    if (r || (r = backward(s, target_dev, B, loss))) return r;
+    s->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)s->step));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)s->step));
+    k_adamw<<<grid_for((int64_t)s->lay.total), 256, 0, s->stream>>>(s->P, s->Gr, s->Mm, s->Vv, (int64_t)s->lay.total,
+                                                                     lr, b1, b2, 1e-8f, weight_decay, c1, c2);
+    refresh_weights(s);
+    if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
+    return loss ? check_err(s) : NLP_OK;
+}
+
+nlp_status nlp_surrogate_initial_guess(nlp_surrogate s, double beta, double gamma, nlp_kernel kernel,
+                                       const nlp_grid *grid, nlp_precision prec, void *phi_dev) {
+    if (!s || !grid || !phi_dev || grid->dim != 3 || !(beta > 0) || !(gamma > 0) ||
+        (kernel != NLP_COULOMB_3D && kernel != NLP_DIPOLE_3D) || (prec != NLP_FP64 && prec != NLP_FP32))
+        return NLP_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (grid->n[a] < 2 || !(grid->L[a] > 0)) return NLP_ERR_INVALID_ARG;
+    float f[kFeat];
+    nlp_surrogate_features(beta, gamma, kernel, f);
+    if (cudaMemcpyAsync(s->feat1, f, sizeof(f), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return NLP_ERR_CUDA;
+    nlp_status r = forward(s, s->feat1, 1);
+    if (r) return r;
+    const int n0 = grid->n[0], n1 = grid->n[1], n2 = grid->n[2];
+    const int64_t N = (int64_t)n0 * n1 * n2, H = (int64_t)(n0 / 2 + 1) * (n1 / 2 + 1) * (n2 / 2 + 1);
+    const double hvol = (2.0 * grid->L[0] / n0) * (2.0 * grid->L[1] / n1) * (2.0 * grid->L[2] / n2);
+    const float *src = s->cpre[kConv - 1];
+    cudaStream_t st = s->stream;
+    if (prec == NLP_FP64) {
+        double *phi = (double *)phi_dev;
+        k_resample<double><<<grid_for(N), 256, 0, st>>>(src, s->box_L, gamma, phi, n0, n1, n2, grid->L[0], grid->L[1],
+                                                        grid->L[2]);
+        k_symmetrize<double><<<grid_for(H), 256, 0, st>>>(phi, n0, n1, n2);
+        k_sumsq_part<double><<<kRedBlocks, 256, 0, st>>>(phi, N, s->part);
+        k_normalize<double><<<grid_for(N), 256, 0, st>>>(phi, N, s->part, kRedBlocks, hvol);
+    } else {
+        float *phi = (float *)phi_dev;
+        k_resample<float><<<grid_for(N), 256, 0, st>>>(src, s->box_L, gamma, phi, n0, n1, n2, grid->L[0], grid->L[1],
+                                                       grid->L[2]);
+        k_symmetrize<float><<<grid_for(H), 256, 0, st>>>(phi, n0, n1, n2);
+        k_sumsq_part<float><<<kRedBlocks, 256, 0, st>>>(phi, N, s->part);
+        k_normalize<float><<<grid_for(N), 256, 0, st>>>(phi, N, s->part, kRedBlocks, hvol);
+    }
+    if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
+    return check_err(s);
+}
+
+nlp_status nlp_surrogate_base(nlp_surrogate s, const float *gamma_dev, int B, float *out_dev) {
+    if (!s || !gamma_dev || !out_dev || B < 1) return NLP_ERR_INVALID_ARG;
+    k_base_cube<<<grid_for((int64_t)B * kOut), 256, 0, s->stream>>>(s->box_L, gamma_dev, B, out_dev);
+    return cudaGetLastError() == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+}
+
+nlp_status nlp_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, void *stream) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 64) return NLP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return NLP_ERR_OOM;
+    int h = 0;
+    const bool ok = cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess &&
+                    launch_gemm_tc((const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, C, M, N, K, err, st) ==
+                        cudaSuccess &&
+                    cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;
+    cudaFree(err);
+    if (!ok) return NLP_ERR_CUDA;
+    return h ? NLP_ERR_TIMEOUT : NLP_OK;
+}
+
+}  // extern "C"

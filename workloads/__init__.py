@@ -129,6 +129,14 @@ def gf_params(count: int, seed: int):
     return [(float(b), float(g)) for b, g in zip(beta, gam)]
 
 
+def gs_problems(count: int, seed: int):
+    """(beta, gamma, kernel) draws for the learned-initial-guess workload: the (beta, gamma)
+    of gf_params and the kernel drawn uniformly from Coulomb / dipolar."""
+    rng = np.random.default_rng(seed + 1)
+    kern = rng.integers(0, 2, size=count)
+    return [(b, g, "coulomb3d" if k == 0 else "dipole3d") for (b, g), k in zip(gf_params(count, seed), kern)]
+
+
 def random_density(grid: Grid, seed: int) -> np.ndarray:
     """Non-negative smooth random density (sum of 4 random Gaussians), for
     invariance and linearity tests."""
