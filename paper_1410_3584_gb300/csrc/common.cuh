@@ -36,8 +36,10 @@ constexpr int kMaxWidth = 16;       // spreading-function width
 template <typename T> struct FftLen {
     int N;
     int nrad;
-    int rad[kMaxRadices];
-    const cpx<T> *tw;   // device
+    int rad[kMaxRadices];     // radices 4, 2, 3, 5 (shared-memory Stockham engine)
+    int nrad_reg;
+    int rad_reg[8];           // radices 16, 8, 4, 2, 3, 5 (register engine of the column passes)
+    const cpx<T> *tw;         // device: e^{-2 pi i m / N}, m = 0..N-1
 };
 
 // Interp/spread work item: one chunk of the nodes of one tile.

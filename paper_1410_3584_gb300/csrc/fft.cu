@@ -24,8 +24,19 @@ template <typename T> static size_t fft_smem_bytes(int N, int nb) {
     return sizeof(cpx<T>) * ((size_t)N + 2 * (size_t)N * (nb + 1));
 }
 
+// line pairs per block of the register-engine R2C / C2R kernels
+template <typename T> constexpr int pairs_per_block() { return sizeof(T) == 4 ? 16 : 8; }
+
 template <typename T>
 cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
+    if (P.len[2].nrad_reg > 0) {
+        constexpr int NBC = pairs_per_block<T>();
+        const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+        const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+        allow_smem<k_fwd_r2c_reg<T, NBC>>();
+        k_fwd_r2c_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
+        return cudaGetLastError();
+    }
     const int N = P.len[2].N;
     const int nb = lines_per_block<T>(N);
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
@@ -37,6 +48,14 @@ cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st) {
+    if (P.len[2].nrad_reg > 0) {
+        constexpr int NBC = pairs_per_block<T>();
+        const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+        const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (P.len[2].nrad_reg > 2 ? 2 : 1);
+        allow_smem<k_inv_c2r_reg<T, NBC>>();
+        k_inv_c2r_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(phi, P);
+        return cudaGetLastError();
+    }
     const int N = P.len[2].N;
     const int nb = lines_per_block<T>(N);
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
@@ -46,9 +65,26 @@ cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// columns per block of the register engine: 16 x 8 B (FP32) or 8 x 16 B (FP64) = 128 B rows
+template <typename T> constexpr int cols_per_block() { return sizeof(T) == 4 ? 16 : 8; }
+
 template <typename T>
 cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign,
                                cudaStream_t st) {
+    if (L.nrad_reg > 0) {
+        constexpr int NBC = cols_per_block<T>();
+        const size_t sm = sizeof(cpx<T>) * (size_t)L.N * NBC * (L.nrad_reg > 2 ? 2 : 1);
+        const int ctiles = (d.ncol + NBC - 1) / NBC;
+        const unsigned grid = (unsigned)((int64_t)d.nouter * ctiles);
+        if (sign < 0) {
+            allow_smem<k_fft_cols<T, -1, NBC>>();
+            k_fft_cols<T, -1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);
+        } else {
+            allow_smem<k_fft_cols<T, +1, NBC>>();
+            k_fft_cols<T, +1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);
+        }
+        return cudaGetLastError();
+    }
     const int nb = d.ncol >= 16 ? lines_per_block<T>(L.N) : d.ncol;
     const size_t sm = fft_smem_bytes<T>(L.N, nb);
     const int ctiles = (d.ncol + nb - 1) / nb;

@@ -264,6 +264,259 @@ __global__ void __launch_bounds__(256) k_fft_strided(cpx<T> *data, StridedDesc d
     fft_strided_block<T, SGN>(data, d, L, nb, blockIdx.x, smraw);
 }
 
+// ------------------------------------------------------------------ register radix engine
+// e^{SGN 2 pi i m / 16} for a compile-time m (after unrolling)
+template <typename T, int SGN> __device__ __forceinline__ cpx<T> w16(int m) {
+    constexpr double C[16] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                              0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                              -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173,
+                              0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613};
+    const int q = m & 15;
+    // sin(2 pi q / 16) = cos(2 pi (q - 4) / 16)
+    return mk<T>((T)C[q], (T)(SGN * C[(q + 12) & 15]));
+}
+
+template <typename T, int SGN, int R> struct Dft;
+template <typename T, int SGN> struct Dft<T, SGN, 2> {
+    static __device__ __forceinline__ void run(cpx<T> *v) { dft2<T, SGN>(v); }
+};
+template <typename T, int SGN> struct Dft<T, SGN, 3> {
+    static __device__ __forceinline__ void run(cpx<T> *v) { dft3<T, SGN>(v); }
+};
+template <typename T, int SGN> struct Dft<T, SGN, 4> {
+    static __device__ __forceinline__ void run(cpx<T> *v) { dft4<T, SGN>(v); }
+};
+template <typename T, int SGN> struct Dft<T, SGN, 5> {
+    static __device__ __forceinline__ void run(cpx<T> *v) { dft5<T, SGN>(v); }
+};
+// DFT of size R1 R2 in registers by one Cooley-Tukey split: n = n1 + R1 n2, k = k2 + R2 k1
+template <typename T, int SGN, int R1, int R2> struct DftSplit {
+    static __device__ __forceinline__ void run(cpx<T> *v) {
+        constexpr int N = R1 * R2;
+        cpx<T> y[N];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            cpx<T> s[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) s[n2] = v[n1 + R1 * n2];
+            Dft<T, SGN, R2>::run(s);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2)
+                y[n1 * R2 + k2] = (n1 * k2 == 0) ? s[k2] : s[k2] * w16<T, SGN>(n1 * k2 * (16 / N));
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+            cpx<T> s[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) s[n1] = y[n1 * R2 + k2];
+            Dft<T, SGN, R1>::run(s);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) v[k2 + R2 * k1] = s[k1];
+        }
+    }
+};
+template <typename T, int SGN> struct Dft<T, SGN, 8> {
+    static __device__ __forceinline__ void run(cpx<T> *v) { DftSplit<T, SGN, 2, 4>::run(v); }
+};
+template <typename T, int SGN> struct Dft<T, SGN, 16> {
+    static __device__ __forceinline__ void run(cpx<T> *v) { DftSplit<T, SGN, 4, 4>::run(v); }
+};
+
+// One Stockham pass of radix R over the butterflies j = t, t + tpc, ... of one line:
+// inputs src(j + r N/R), twiddles e^{SGN 2 pi i k r / (Ns R)} with k = j mod Ns, outputs
+// dst((j / Ns) Ns R + k + r Ns).  src / dst address the line by position.
+template <typename T, int SGN, int R, class Src, class Dst>
+__device__ __forceinline__ void reg_pass(Src &src, Dst &dst, int N, int Ns, const cpx<T> *__restrict__ tw, int t,
+                                         int tpc) {
+    const int nbf = N / R, tws = N / (Ns * R);
+    const uint32_t mag = Ns > 1 ? 0xFFFFFFFFu / (uint32_t)Ns + 1u : 0u;   // j / Ns = umulhi(j, mag), j Ns < 2^32
+    for (int j = t; j < nbf; j += tpc) {
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src(j + r * nbf);
+        int jq = j, k = 0;
+        if (Ns > 1) {
+            jq = (int)__umulhi((uint32_t)j, mag);
+            k = j - jq * Ns;
+        }
+        if (k) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                cpx<T> w = tw[k * r * tws];
+                if (SGN > 0) w = conj(w);
+                v[r] = v[r] * w;
+            }
+        }
+        Dft<T, SGN, R>::run(v);
+        const int base = jq * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst(base + r * Ns, v[r]);
+    }
+}
+
+template <typename T, int SGN, class Src, class Dst>
+__device__ __forceinline__ void reg_pass_any(int R, Src &src, Dst &dst, int N, int Ns, const cpx<T> *tw, int t,
+                                             int tpc) {
+    switch (R) {
+        case 16: reg_pass<T, SGN, 16>(src, dst, N, Ns, tw, t, tpc); break;
+        case 8: reg_pass<T, SGN, 8>(src, dst, N, Ns, tw, t, tpc); break;
+        case 4: reg_pass<T, SGN, 4>(src, dst, N, Ns, tw, t, tpc); break;
+        case 2: reg_pass<T, SGN, 2>(src, dst, N, Ns, tw, t, tpc); break;
+        case 3: reg_pass<T, SGN, 3>(src, dst, N, Ns, tw, t, tpc); break;
+        default: reg_pass<T, SGN, 5>(src, dst, N, Ns, tw, t, tpc); break;
+    }
+}
+
+// FFT of the lines of a block, line (column) b of the block handled by the tpc threads with
+// the same b.  The first pass reads the line through gsrc(position), the last pass writes it
+// through gdst(position, value); intermediate results live in shared memory (position p of
+// line b at s[idx(p, b)]), ping-ponging between sA (after passes 0, 2, ...) and sB (after
+// passes 1, 3, ...).  All threads of the block must call it.
+template <typename T, int SGN, class GSrc, class GDst, class Idx>
+__device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cpx<T> *sB, const Idx &idx, int b, int t,
+                                              int tpc, GSrc &gsrc, GDst &gdst) {
+    const int N = L.N;
+    int Ns = 1;
+    for (int s = 0; s < L.nrad_reg; ++s) {
+        const int R = L.rad_reg[s];
+        const bool first = s == 0, last = s == L.nrad_reg - 1;
+        cpx<T> *in = (s & 1) ? sA : sB;
+        cpx<T> *out = (s & 1) ? sB : sA;
+        auto ssrc = [&](int l) { return in[idx(l, b)]; };
+        auto sdst = [&](int l, cpx<T> v) { out[idx(l, b)] = v; };
+        if (first && last) reg_pass_any<T, SGN>(R, gsrc, gdst, N, Ns, L.tw, t, tpc);
+        else if (first) reg_pass_any<T, SGN>(R, gsrc, sdst, N, Ns, L.tw, t, tpc);
+        else if (last) reg_pass_any<T, SGN>(R, ssrc, gdst, N, Ns, L.tw, t, tpc);
+        else reg_pass_any<T, SGN>(R, ssrc, sdst, N, Ns, L.tw, t, tpc);
+        __syncthreads();
+        Ns *= R;
+    }
+}
+
+// Strided C2C pass on the register engine: the same operation as k_fft_strided, NBC
+// contiguous columns per block, 16 threads per column.  Pruned input / output windows
+// are predicated loads / stores (positions outside the input window read as zero).
+template <typename T, int SGN, int NBC>
+__global__ void __launch_bounds__(NBC * 16) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = L.N;
+    cpx<T> *sA = (cpx<T> *)smraw;
+    cpx<T> *sB = sA + (size_t)N * NBC;
+    const int b = threadIdx.x % NBC, t = threadIdx.x / NBC;
+    const int ctiles = (d.ncol + NBC - 1) / NBC;
+    const int o = blockIdx.x / ctiles, c0 = (blockIdx.x % ctiles) * NBC;
+    const int oo = d.outer_map_n > 0 ? wrapi(o - d.outer_map_n / 2, d.outer_map_N) : o;
+    const bool colok = c0 + b < d.ncol;
+    cpx<T> *base = data + (int64_t)oo * d.os + c0 + b;
+    // window of n points: positions [0, n - n/2) and [N - n/2, N)
+    const int ilo = d.n_in < N ? d.n_in - d.n_in / 2 : N, ihi = d.n_in < N ? N - d.n_in / 2 : N;
+    const int olo = d.n_out < N ? d.n_out - d.n_out / 2 : N, ohi = d.n_out < N ? N - d.n_out / 2 : N;
+    auto gsrc = [&](int l) -> cpx<T> {
+        return (colok && (l < ilo || l >= ihi)) ? base[(int64_t)l * d.es] : mk<T>(0, 0);
+    };
+    auto gdst = [&](int l, cpx<T> v) {
+        if (colok && (l < olo || l >= ohi)) base[(int64_t)l * d.es] = v;
+    };
+    auto idx = [](int l, int c) { return l * NBC + c; };
+    fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+}
+
+// Padded line-major shared layout for the contiguous-axis kernels: position l of line b at
+// b * LDL + l + l / 16, so that unit-stride and stride-16 position accesses of 16 threads of
+// one line fall on distinct banks.
+__host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; }
+
+// Forward R2C along the last axis on the register engine: the same operation as
+// k_fwd_r2c.  NBC line pairs per block, 16 threads per pair (consecutive threads walk one
+// line, so the global loads and stores are contiguous).  The first pass reads rho,
+// deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
+// where the spectra of the two real lines are separated and written as half spectra.
+template <typename T, int NBC>
+__global__ void __launch_bounds__(NBC * 16) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const FftLen<T> &L = P.len[2];
+    const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
+    cpx<T> *sA = (cpx<T> *)smraw;
+    cpx<T> *sB = sA + (size_t)NBC * LDL;
+    const int t = threadIdx.x & 15, b = threadIdx.x >> 4;
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const int64_t p = (int64_t)blockIdx.x * NBC + b;
+    const bool ok = p < npairs;
+    const int64_t line0 = 2 * p, line1 = 2 * p + 1;
+    const int i0a = ok ? (int)(line0 / P.n[1]) : 0, i1a = ok ? (int)(line0 % P.n[1]) : 0;
+    const int i0b = ok ? (int)(line1 / P.n[1]) : 0, i1b = ok ? (int)(line1 % P.n[1]) : 0;
+    const T fa = P.deconv[0][i0a] * P.deconv[1][i1a], fb = P.deconv[0][i0b] * P.deconv[1][i1b];
+    auto gsrc = [&](int l) -> cpx<T> {
+        const int i = l < n2 / 2 ? l + n2 / 2 : l - N + n2 / 2;   // window point at fine position l
+        if (!ok || i < 0 || i >= n2) return mk<T>(0, 0);
+        const T d2 = P.deconv[2][i];
+        return mk<T>(rho[line0 * n2 + i] * (fa * d2), rho[line1 * n2 + i] * (fb * d2));
+    };
+    cpx<T> *res = ((L.nrad_reg - 1) & 1) ? sB : sA;
+    auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
+    auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
+    fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+    if (!ok) return;
+    const int l0a = wrapi(i0a - P.n[0] / 2, P.nf[0]), l1a = wrapi(i1a - P.n[1] / 2, P.nf[1]);
+    const int l0b = wrapi(i0b - P.n[0] / 2, P.nf[0]), l1b = wrapi(i1b - P.n[1] / 2, P.nf[1]);
+    cpx<T> *Fa = P.F + ((int64_t)l0a * P.nf[1] + l1a) * nh, *Fb = P.F + ((int64_t)l0b * P.nf[1] + l1b) * nh;
+    for (int k = t; k < nh; k += 16) {
+        const cpx<T> z = res[idx(k, b)];
+        const int kc = k == 0 ? 0 : N - k;
+        const cpx<T> zc = conj(res[idx(kc, b)]);
+        Fa[k] = scale(z + zc, (T)0.5);
+        Fb[k] = mul_i(scale(z - zc, (T)0.5), -1);
+    }
+}
+
+// Inverse C2R along the last axis on the register engine: the same operation as
+// k_inv_c2r.  The first pass reads the half spectra of a line pair from HBM and forms
+// Z = X1 + i X2 on the fly (Z[N - k] = conj(X1[k]) + i conj(X2[k])); the last pass writes
+// the output window, deconvolved, straight to HBM.
+template <typename T, int NBC>
+__global__ void __launch_bounds__(NBC * 16) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const FftLen<T> &L = P.len[2];
+    const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
+    cpx<T> *sA = (cpx<T> *)smraw;
+    cpx<T> *sB = sA + (size_t)NBC * LDL;
+    const int t = threadIdx.x & 15, b = threadIdx.x >> 4;
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const int64_t p = (int64_t)blockIdx.x * NBC + b;
+    const bool ok = p < npairs;
+    const int64_t line0 = 2 * p, line1 = 2 * p + 1;
+    const int i0a = ok ? (int)(line0 / P.n[1]) : 0, i1a = ok ? (int)(line0 % P.n[1]) : 0;
+    const int i0b = ok ? (int)(line1 / P.n[1]) : 0, i1b = ok ? (int)(line1 % P.n[1]) : 0;
+    const int l0a = wrapi(i0a - P.n[0] / 2, P.nf[0]), l1a = wrapi(i1a - P.n[1] / 2, P.nf[1]);
+    const int l0b = wrapi(i0b - P.n[0] / 2, P.nf[0]), l1b = wrapi(i1b - P.n[1] / 2, P.nf[1]);
+    const cpx<T> *Ga = P.G + ((int64_t)l0a * P.nf[1] + l1a) * nh, *Gb = P.G + ((int64_t)l0b * P.nf[1] + l1b) * nh;
+    auto gsrc = [&](int l) -> cpx<T> {
+        if (!ok) return mk<T>(0, 0);
+        const bool lo = 2 * l <= N;
+        const int k = lo ? l : N - l;
+        cpx<T> x1 = Ga[k], x2 = Gb[k];
+        if (k == 0 || 2 * k == N) {   // half-spectrum ends of a real line are real
+            x1.y = 0;
+            x2.y = 0;
+        }
+        return lo ? x1 + mul_i(x2, 1) : conj(x1) + mul_i(conj(x2), 1);
+    };
+    const T fa = P.deconv[0][i0a] * P.deconv[1][i1a], fb = P.deconv[0][i0b] * P.deconv[1][i1b];
+    const int hi0 = n2 - n2 / 2, lo1 = N - n2 / 2;
+    auto gdst = [&](int l, cpx<T> z) {
+        if (!ok) return;
+        int i;
+        if (l < hi0) i = l + n2 / 2;
+        else if (l >= lo1) i = l - lo1;
+        else return;
+        const T d2 = P.deconv[2][i];
+        phi[line0 * n2 + i] = z.x * (fa * d2);
+        phi[line1 * n2 + i] = z.y * (fb * d2);
+    };
+    auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
+    fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+}
+
 // ------------------------------------------------------------------ contiguous C2C pass
 // In-place transform of nlines contiguous complex lines of length N, scaled by post.
 template <typename T, int SGN>

@@ -108,11 +108,25 @@ static bool factor_radices(int N, int *rad, int *nrad) {
     return N == 1;
 }
 
+// radices of the register engine: as many 16s as the power of two allows, the rest of it as
+// one 8, 4 or 2, then 3s and 5s
+static bool factor_radices_reg(int N, int *rad, int *nrad) {
+    int k = 0, p2 = 0;
+    while (N % 2 == 0) { N /= 2; ++p2; }
+    while (p2 >= 4 && k < 8) { rad[k++] = 16; p2 -= 4; }
+    if (p2 > 0 && k < 8) rad[k++] = 1 << p2;
+    while (N % 3 == 0 && k < 8) { rad[k++] = 3; N /= 3; }
+    while (N % 5 == 0 && k < 8) { rad[k++] = 5; N /= 5; }
+    *nrad = k;
+    return N == 1;
+}
+
 template <typename T> nlp_status make_fft_len(nlp_plan_s *p, int N, FftLen<T> *out) {
     memset(out, 0, sizeof(*out));
     out->N = N;
     if (N == 1) return NLP_OK;
     if (!factor_radices(N, out->rad, &out->nrad)) return NLP_ERR_UNSUPPORTED;
+    if (!factor_radices_reg(N, out->rad_reg, &out->nrad_reg)) return NLP_ERR_UNSUPPORTED;
     std::vector<cpx<T>> tw(N);
     for (int k = 0; k < N; ++k) {
         const double a = 2.0 * M_PI * (double)k / (double)N;
