@@ -28,6 +28,38 @@ __device__ __forceinline__ void warp_reduce_multi(T (&v)[V], int lane) {
     for (; off >= 1; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
 }
 
+// the W kernel values of one axis of a node, from shared memory, in 16- or 8-byte loads where
+// the row is aligned for them (rows start at multiples of W elements of 16-byte aligned buffers)
+template <typename T, int W> __device__ __forceinline__ void load_row(const T *p, T (&out)[W]) {
+    if constexpr (sizeof(T) == 4 && W % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4 *>(p)[i];
+            out[4 * i] = v.x;
+            out[4 * i + 1] = v.y;
+            out[4 * i + 2] = v.z;
+            out[4 * i + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && W % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) {
+            const float2 v = reinterpret_cast<const float2 *>(p)[i];
+            out[2 * i] = v.x;
+            out[2 * i + 1] = v.y;
+        }
+    } else if constexpr (sizeof(T) == 8 && W % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) {
+            const double2 v = reinterpret_cast<const double2 *>(p)[i];
+            out[2 * i] = v.x;
+            out[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) out[i] = p[i];
+    }
+}
+
 template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
 template <> struct Log2<1> { static constexpr int value = 0; };
 
@@ -172,7 +204,8 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
         // the batch's kernel values are a contiguous block of the plan-time table; the next
         // block is fetched into registers while the current batch computes
         constexpr int PQ = (NB * 3 * W + 31) / 32;
-        T pf[PQ];
+        T pf[PQ], wf;
+        // the next batch's kernel values and node weights are fetched while this one computes
         auto fetch = [&](int jbn, int nbn) {
             const T *src = P.psi_tab + (int64_t)jbn * 3 * W;
 #pragma unroll
@@ -180,6 +213,7 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 const int q = lane + 32 * u;
                 pf[u] = (q < nbn * 3 * W) ? __ldg(src + q) : (T)0;
             }
+            wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : (T)0;
         };
         fetch(j0, min(NB, j1 - j0));
         for (int jb = j0; jb < j1; jb += NB) {
@@ -189,6 +223,7 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 const int q = lane + 32 * u;
                 if (q < NB * 3 * W) psi[q] = pf[u];
             }
+            const T wcur = wf;
             __syncwarp();
             if (jb + NB < j1) fetch(jb + NB, min(NB, j1 - jb - NB));
             T v[V], wa[NB], wb[NB];
@@ -201,9 +236,11 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                     wa[k] = act_a ? pk[xa] * pk[W + ya] : (T)0;
                     wb[k] = act_b ? pk[xb] * pk[W + yb] : (T)0;
                     T sax = 0, say = 0, sbx = 0, sby = 0;
+                    T pzv[W];
+                    load_row<T, W>(pk + 2 * W, pzv);
 #pragma unroll
                     for (int z = 0; z < W; ++z) {
-                        const T pz = pk[2 * W + z];
+                        const T pz = pzv[z];
                         sax += fax[z] * pz;
                         say += fay[z] * pz;
                         sbx += fbx[z] * pz;
@@ -214,10 +251,11 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 }
             }
             warp_reduce_multi<T, V>(v, lane);
-            if ((lane & ((1 << SH) - 1)) == 0) {
+            {
                 const int idx = (lane >> SH) & (V - 1);
                 const int k = idx >> 1;
-                cb[idx] = (k < nb) ? v[0] * P.nd[4 * ((int64_t)jb + k) + 3] : (T)0;
+                const T wk = __shfl_sync(0xffffffffu, wcur, k);   // weight of node k of the batch
+                if ((lane & ((1 << SH) - 1)) == 0) cb[idx] = (k < nb) ? v[0] * wk : (T)0;
             }
             __syncwarp();
 #pragma unroll
@@ -226,9 +264,11 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                     const T *pk = psi + k * 3 * W;
                     const T cr = cb[2 * k], ci = cb[2 * k + 1];
                     const T ar = cr * wa[k], ai = ci * wa[k], br = cr * wb[k], bi = ci * wb[k];
+                    T pzv[W];
+                    load_row<T, W>(pk + 2 * W, pzv);
 #pragma unroll
                     for (int z = 0; z < W; ++z) {
-                        const T pz = pk[2 * W + z];
+                        const T pz = pzv[z];
                         gax[z] += ar * pz;
                         gay[z] += ai * pz;
                         gbx[z] += br * pz;

@@ -95,11 +95,12 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
                     const T *pk = psi + k * 3 * W;
                     const T wxy = pk[cx] * pk[W + cy];
                     T sx = (T)0, sy = (T)0;
+                    T pzv[W];
+                    load_row<T, W>(pk + 2 * W, pzv);
 #pragma unroll
                     for (int z = 0; z < W; ++z) {
-                        const T pz = pk[2 * W + z];
-                        sx += fx[z] * pz;
-                        sy += fy[z] * pz;
+                        sx += fx[z] * pzv[z];
+                        sy += fy[z] * pzv[z];
                     }
                     if (active) {
                         v[2 * k] = wxy * sx;
@@ -125,11 +126,12 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
                     const T *pk = psi + k * 3 * W;
                     const T wxy = active ? pk[cx] * pk[W + cy] : (T)0;
                     const T cr = cbuf[2 * k] * wxy, ci = cbuf[2 * k + 1] * wxy;
+                    T pzv[W];
+                    load_row<T, W>(pk + 2 * W, pzv);
 #pragma unroll
                     for (int z = 0; z < W; ++z) {
-                        const T pz = pk[2 * W + z];
-                        gx[z] += cr * pz;
-                        gy[z] += ci * pz;
+                        gx[z] += cr * pzv[z];
+                        gy[z] += ci * pzv[z];
                     }
                 }
             }
