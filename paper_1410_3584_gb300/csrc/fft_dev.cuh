@@ -397,7 +397,7 @@ __device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cp
 // contiguous columns per block, 16 threads per column.  Pruned input / output windows
 // are predicated loads / stores (positions outside the input window read as zero).
 template <typename T, int SGN, int NBC>
-__global__ void __launch_bounds__(NBC * 16) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
+__global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = L.N;
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -432,7 +432,7 @@ __host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; 
 // deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
 // where the spectra of the two real lines are separated and written as half spectra.
 template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+__global__ void __launch_bounds__(NBC * 16, 3) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
