@@ -111,10 +111,11 @@ class ClockSampler:
         return out
 
 
-def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stream, e2e=True, method=0):
+def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stream, e2e=True, method=0,
+                  kernel="coulomb3d"):
     tol = 1e-6 if prec == "fp32" else 1e-12
     t_plan = time.perf_counter()
-    plan = nl.Plan(g.n, g.L, "coulomb3d", prec, kmax=P, counts=counts, tol=tol, stream=stream, method=method)
+    plan = nl.Plan(g.n, g.L, kernel, prec, kmax=P, counts=counts, tol=tol, stream=stream, method=method)
     t_plan = time.perf_counter() - t_plan
     dt = plan.torch_dtype
     with torch.cuda.stream(stream):
@@ -383,6 +384,101 @@ def batch_arm(args):
         "dtype": "f32", "data": "synthetic", "l2": "flushed between timed steps (512 MB write)"}))
 
 
+def twod_arm(args):
+    """2D workload: 1024^2 over [-16,16)^2, rho = three Gaussians (centres in [-4,4]^2, widths
+    in [0.5,2], seed 20141014); 2D Coulomb (U-hat = 1/|k|, cancelled by the polar Jacobian) and
+    the 2D Laplace kernel (U-hat = 1/|k|^2, Algorithm 1), FP64 tol 1e-12 and FP32 tol 1e-6,
+    each against the FP64 oracle on the same nodes and against the closed form."""
+    import torch
+    import paper_1410_3584_gb300 as nl
+    from oracle import closed_forms as cf
+    from oracle import potential, quadrature
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    g = W.cube(1024, 16.0, dim=2)
+    cs, ws = W.three_gaussians_2d(W.SEED_TRAIN)
+    rho = W.gaussian_sum(g, cs, ws)
+    P = quadrature.density_P(min(ws), g.h[0])
+    counts = quadrature.default_counts(g.L, P)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    X, Y = g.mesh()
+    out = {}
+    clk = ClockSampler(0)
+    clk.start()
+    for kernel in ("coulomb2d", "poisson2d"):
+        ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+        form = cf.coulomb2d_iso if kernel == "coulomb2d" else cf.poisson2d_iso
+        exact = np.zeros_like(ref)
+        for (cx, cy), s in zip(cs, ws):
+            exact += form(np.sqrt((X - cx) ** 2 + (Y - cy) ** 2), s)
+        for prec in ("fp32", "fp64"):
+            res = run_precision(nl, torch, prec, g, rho, P, counts, args.steps, args.warmup, flush, stream,
+                                e2e=False, kernel=kernel)
+            t = sum(res["times"]) / 1e3
+            out["%s_%s" % (kernel, prec)] = {
+                "value": len(res["times"]) / t, "unit": "evals/s", "ms_per_step": 1e3 * t / len(res["times"]),
+                "rel_linf_vs_oracle": cf.rel_linf(res["phi"], ref), "rel_linf_vs_closed_form": cf.rel_linf(res["phi"], exact),
+                "stages_ms": res["stages"], "nodes": res["info"]["nodes_total"], "width": res["info"]["width"]}
+    clocks = clk.stop()
+    print(json.dumps({"metric": "2D phi=U*rho evals/s, 1024^2, three Gaussians", "steps": args.steps,
+                      "warmup": args.warmup, "config": {"grid": [1024, 1024], "L": 16.0, "P": P,
+                      "quadrature": list(counts), "l2": "flushed between timed steps (512 MB write)"},
+                      "results": out, "clocks": clocks, "dtype": "f32/f64", "data": "synthetic"}))
+
+
+def groundstate_arm(args):
+    """Ground states with the learned initial guess: training states from the library's own
+    gradient flow on 48^3 over [-10,10)^3 (seed 20141014), the network trained by the library's
+    kernels, then held-out problems (seed 20141015) solved on 96^3 over [-10,10)^3 from the
+    plain Gaussian start and from the network's guess, each to the Sec. 3.2 stopping rule
+    max|phi^{n+1} - phi^n|/tau <= 1e-10 (tau = 1e-2, FP64); timing = device-seconds."""
+    import torch
+    import paper_1410_3584_gb300 as nl
+    from paper_1410_3584_gb300 import surrogate as SG
+    torch.cuda.set_device(0)
+    params = W.gs_problems(args.gs_train, W.SEED_TRAIN)
+    t0 = time.perf_counter()
+    targets, feats, info = SG.generate(params, workers=12)
+    t_gen = time.perf_counter() - t0
+    sur = nl.Surrogate(10.0, seed=W.SEED_TRAIN, mode=0)
+    resid = SG.residual_targets(sur, targets, params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = SG.train(sur, feats, resid, steps=args.gs_train_steps, batch=64, lr=3e-3, lr_final=7.5e-5, log_every=500)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del targets, resid
+    solver = SG.GroundStateSolver(96, 10.0)
+    cases = []
+    for beta, gamma, kernel in W.gs_problems(args.gs_heldout, W.SEED_HELDOUT):
+        _, n_p, t_p, E_p = solver.solve(beta, gamma, kernel, stop_tol=1e-10)
+        phi0 = torch.empty((96, 96, 96), dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sur.initial_guess(beta, gamma, kernel, (96,) * 3, (10.0,) * 3, phi0)
+        e1.record()
+        e1.synchronize()
+        t_g = e0.elapsed_time(e1) * 1e-3
+        _, n_s, t_s, E_s = solver.solve(beta, gamma, kernel, phi=phi0, stop_tol=1e-10)
+        cases.append({"beta": beta, "gamma": gamma, "kernel": kernel, "plain_steps": n_p, "plain_s": t_p,
+                      "surrogate_steps": n_s, "surrogate_s": t_s + t_g, "guess_s": t_g,
+                      "E_plain": E_p["E"], "dE": abs(E_s["E"] - E_p["E"]),
+                      "converged": bool(E_p["converged"] and E_s["converged"])})
+    solver.close()
+    sur.close()
+    tp = sum(c["plain_s"] for c in cases)
+    ts = sum(c["surrogate_s"] for c in cases)
+    print(json.dumps({
+        "metric": "gradient-flow device-seconds to the stopping rule, 96^3, plain start vs learned start",
+        "value": ts / max(1, len(cases)), "unit": "s per ground state (learned start)", "higher_is_better": False,
+        "plain_s_per_state": tp / max(1, len(cases)), "speedup": tp / ts if ts > 0 else None,
+        "max_dE": max(c["dE"] for c in cases), "cases": cases,
+        "training": {"states": len(params), "grid": [48, 48, 48], "generation_wall_s": t_gen,
+                     "generation_device_s": sum(i["seconds"] for i in info),
+                     "train_steps": args.gs_train_steps, "train_s": t_train, "loss": hist},
+        "dtype": "f64 flow / bf16+f32 network", "data": "synthetic"}))
+
+
 def batch_quadrature(g, widths):
     """FP32 batch items: P where rho-hat falls below 1e-8 (never past pi/h), default counts."""
     h = max(g.h)
@@ -427,7 +523,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="metric", choices=["metric", "batch"])
+    ap.add_argument("--workload", default="metric", choices=["metric", "batch", "2d", "groundstate"])
+    ap.add_argument("--gs-train", type=int, default=192, help="training ground states (groundstate workload)")
+    ap.add_argument("--gs-heldout", type=int, default=4, help="held-out problems timed at 96^3")
+    ap.add_argument("--gs-train-steps", type=int, default=4000)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],
                     help="only the timed evaluation loop of one precision (for ncu captures)")
@@ -438,6 +537,10 @@ def main():
         reference_arm(args)
     elif args.workload == "batch":
         batch_arm(args)
+    elif args.workload == "2d":
+        twod_arm(args)
+    elif args.workload == "groundstate":
+        groundstate_arm(args)
     else:
         gpu_arm(args)
 

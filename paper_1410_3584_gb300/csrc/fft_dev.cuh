@@ -1,4 +1,4 @@
-// FFT device code shared by the single-plan kernels (fft.cu) and the batched persistent
+// FFT device code shared by the single-plan kernels (fft_launch.cuh) and the batched persistent
 // kernel (batch.cu): small DFTs, the shared-memory Stockham engine and the per-block bodies
 // of the R2C / C2R / strided passes (block index passed explicitly).
 #pragma once

@@ -1,0 +1,154 @@
+// Launchers of the hand-written FFT passes (included once per precision by fft_f32.cu and
+// fft_f64.cu, which instantiate them).
+//
+// Hand-written FFT passes for the oversampled grids of the NUFFT (and the plain grids of
+// the gradient flow / time splitting).  Lengths with a register-engine factorisation run on
+// the register radix engine (k_fft_cols, k_fwd_r2c_reg, k_inv_c2r_reg); the mixed radix
+// 2/3/4/5 shared-memory Stockham kernels remain for descriptors built without it.  One CTA
+// transforms a batch of lines.  Twiddles are FP64-built tables rounded to the plan precision.
+//
+// Layout convention: a 3D array [n0][n1][n2] with the last axis contiguous; the real-to-
+// complex half spectrum along the last axis has nh = N2/2 + 1 entries.  2D arrays are
+// handled as 3D with n0 = 1.
+#pragma once
+#include "common.cuh"
+#include "launch.h"
+#include "fft_dev.cuh"
+
+namespace nlp {
+// ------------------------------------------------------------------ launchers
+template <typename T> static int lines_per_block(int N) {
+    // keep 2 * N * (nb+1) complex + twiddles within 160 KB
+    const int budget = 160 * 1024 / (int)sizeof(cpx<T>);
+    int nb = 16;
+    while (nb > 1 && 2 * N * (nb + 1) + N > budget) nb >>= 1;
+    return nb;
+}
+
+template <typename T> static size_t fft_smem_bytes(int N, int nb) {
+    return sizeof(cpx<T>) * ((size_t)N + 2 * (size_t)N * (nb + 1));
+}
+
+// Lines per block of the register-engine kernels: 16 (FP32) / 8 (FP64) so that one position of
+// a block's lines is a 128-byte row, halved while the shared memory of a block would exceed
+// kRegSmemBudget (long lines, e.g. N = 2048), down to one line (pair) per block.
+constexpr size_t kRegSmemBudget = 100 * 1024;
+template <typename T> constexpr int lines_max() { return sizeof(T) == 4 ? 16 : 8; }
+static int pick_lines(int nmax, size_t bytes_per_line) {
+    int nb = nmax;
+    while (nb > 1 && bytes_per_line * nb > kRegSmemBudget) nb >>= 1;
+    return nb;
+}
+
+template <typename T, int NBC> static cudaError_t r2c_reg(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+    allow_smem<k_fwd_r2c_reg<T, NBC>>();
+    k_fwd_r2c_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
+    return cudaGetLastError();
+}
+template <typename T, int NBC> static cudaError_t c2r_reg(T *phi, const DevPlan<T> &P, cudaStream_t st) {
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (P.len[2].nrad_reg > 2 ? 2 : 1);
+    allow_smem<k_inv_c2r_reg<T, NBC>>();
+    k_inv_c2r_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(phi, P);
+    return cudaGetLastError();
+}
+template <typename T, int NBC>
+static cudaError_t cols_reg(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign, cudaStream_t st) {
+    const size_t sm = sizeof(cpx<T>) * (size_t)L.N * NBC * (L.nrad_reg > 2 ? 2 : 1);
+    const int ctiles = (d.ncol + NBC - 1) / NBC;
+    const unsigned grid = (unsigned)((int64_t)d.nouter * ctiles);
+    if (sign < 0) {
+        allow_smem<k_fft_cols<T, -1, NBC>>();
+        k_fft_cols<T, -1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);
+    } else {
+        allow_smem<k_fft_cols<T, +1, NBC>>();
+        k_fft_cols<T, +1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);
+    }
+    return cudaGetLastError();
+}
+
+// calls F<NBC>() for the chosen power of two NBC <= lines_max<T>()
+#define NLP_LINES_SWITCH(T, nb, CALL)                          \
+    switch (nb) {                                              \
+        case 16: if constexpr (lines_max<T>() >= 16) return CALL(16); [[fallthrough]]; \
+        case 8: return CALL(8);                                \
+        case 4: return CALL(4);                                \
+        case 2: return CALL(2);                                \
+        default: return CALL(1);                               \
+    }
+
+template <typename T>
+cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
+    if (P.len[2].nrad_reg > 0) {
+        const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)line_ld(P.len[2].N) * 2);
+#define NLP_CALL(K) r2c_reg<T, K>(rho, P, st)
+        NLP_LINES_SWITCH(T, nb, NLP_CALL)
+#undef NLP_CALL
+    }
+    const int N = P.len[2].N;
+    const int nb = lines_per_block<T>(N);
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const size_t sm = fft_smem_bytes<T>(N, nb);
+    allow_smem<k_fwd_r2c<T>>();
+    k_fwd_r2c<T><<<(unsigned)((npairs + nb - 1) / nb), 256, sm, st>>>(rho, P, nb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st) {
+    if (P.len[2].nrad_reg > 0) {
+        const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)line_ld(P.len[2].N) *
+                                                      (P.len[2].nrad_reg > 2 ? 2 : 1));
+#define NLP_CALL(K) c2r_reg<T, K>(phi, P, st)
+        NLP_LINES_SWITCH(T, nb, NLP_CALL)
+#undef NLP_CALL
+    }
+    const int N = P.len[2].N;
+    const int nb = lines_per_block<T>(N);
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const size_t sm = fft_smem_bytes<T>(N, nb);
+    allow_smem<k_inv_c2r<T>>();
+    k_inv_c2r<T><<<(unsigned)((npairs + nb - 1) / nb), 256, sm, st>>>(phi, P, nb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign,
+                               cudaStream_t st) {
+    if (L.nrad_reg > 0) {
+        const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)L.N * (L.nrad_reg > 2 ? 2 : 1));
+#define NLP_CALL(K) cols_reg<T, K>(data, d, L, sign, st)
+        NLP_LINES_SWITCH(T, nb, NLP_CALL)
+#undef NLP_CALL
+    }
+    const int nb = d.ncol >= 16 ? lines_per_block<T>(L.N) : d.ncol;
+    const size_t sm = fft_smem_bytes<T>(L.N, nb);
+    const int ctiles = (d.ncol + nb - 1) / nb;
+    const unsigned grid = (unsigned)((int64_t)d.nouter * ctiles);
+    if (sign < 0) {
+        allow_smem<k_fft_strided<T, -1>>();
+        k_fft_strided<T, -1><<<grid, 256, sm, st>>>(data, d, L, nb);
+    } else {
+        allow_smem<k_fft_strided<T, +1>>();
+        k_fft_strided<T, +1><<<grid, 256, sm, st>>>(data, d, L, nb);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, int sign, T post, cudaStream_t st) {
+    const int nb = lines_per_block<T>(L.N);
+    const size_t sm = fft_smem_bytes<T>(L.N, nb);
+    const unsigned grid = (unsigned)((nlines + nb - 1) / nb);
+    if (sign < 0) {
+        allow_smem<k_fft_contig<T, -1>>();
+        k_fft_contig<T, -1><<<grid, 256, sm, st>>>(data, nlines, L, nb, post);
+    } else {
+        allow_smem<k_fft_contig<T, +1>>();
+        k_fft_contig<T, +1><<<grid, 256, sm, st>>>(data, nlines, L, nb, post);
+    }
+    return cudaGetLastError();
+}
+}  // namespace nlp

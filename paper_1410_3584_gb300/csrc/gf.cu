@@ -264,7 +264,7 @@ template <typename T> static StridedDesc plain_axis(const DevPlan<T> &D, int axi
     return d;
 }
 
-// real x -> half spectrum (shift-consistent placement, see fft.cu)
+// real x -> half spectrum (shift-consistent placement, see fft_dev.cuh)
 template <typename T> static cudaError_t r2c_plain(const T *x, DevPlan<T> &D, cudaStream_t st) {
     cudaError_t e = launch_fwd_r2c<T>(x, D, st);
     if (e) return e;
