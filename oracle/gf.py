@@ -8,10 +8,16 @@ One step, for phi^n with h^d sum |phi^n|^2 = 1:
     phi^{n+1} = phi^(1) / ||phi^(1)||                             (Eq. (gffg33))
 The paper omits how the linear system is solved.  Reading (stabilised
 fixed point, Fourier-diagonal preconditioner): with alpha = (max b + min b)/2,
-    (1/tau + alpha + |mu|^2/2) phi^(1),m+1 = F[ phi^n/tau + (alpha - b) phi^(1),m ]
-in Fourier space (periodic box, mu_p = pi p / L), from phi^(1),0 = phi^n, until
-max|phi^(1),m+1 - phi^(1),m| <= inner_tol.  It converges because
-|alpha - b| / (1/tau + alpha) < 1, and its fixed point is the backward-Euler solution.
+    G(x) = F^{-1}[ F[ phi^n/tau + (alpha - b) x ] / (1/tau + alpha + |mu|^2/2) ]
+(periodic box, mu_p = pi p / L); the fixed point of G is the backward-Euler solution, and
+G(x) - x is the residual preconditioned by M = 1/tau + alpha - Delta/2.  The eigenvalues of
+M^{-1} (1/tau - Delta/2 + b) lie in [1 - q, 1 + q], q = max|b - alpha| / (1/tau + alpha) < 1,
+so the iteration is accelerated by the Chebyshev semi-iteration on that interval (Saad,
+Iterative Methods for Sparse Linear Systems, Alg. 12.1, centre 1, half-width q):
+    x_1 = G(x_0),  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / q)(G(x_k) - x_k),
+    x_{k+1} = x_k + d_k,  rho_0 = q,  rho_k = 1/(2/q - rho_{k-1}),
+from x_0 = phi^n until max|x_{k+1} - x_k| <= inner_tol (plain x_{k+1} = G(x_k) if q is
+not in (0, 1)).
 g rho is an optional local (contact) term; the paper's examples have g = 0.
 Stopping rule of Sec. 3.2: max |phi^{n+1} - phi^n| / tau <= eps0.
 """
@@ -51,17 +57,28 @@ class GradientFlow:
         rho = phi * phi
         Phi = self.pot(rho)
         b = self.V + self.g * rho + self.beta * Phi
-        alpha = 0.5 * (float(np.max(b)) + float(np.min(b)))
+        bmax, bmin = float(np.max(b)), float(np.min(b))
+        alpha = 0.5 * (bmax + bmin)
+        q = 0.5 * (bmax - bmin) / (1.0 / tau + alpha)
+        cheb = 0.0 < q < 1.0
         denom = 1.0 / tau + alpha + 0.5 * self.mu2r
         rhs0 = phi / tau
         x = phi.copy()
+        d = np.zeros_like(x)
+        rho_prev, rho = 0.0, q
         it = 0
         n = self.grid.n
         for it in range(1, self.max_inner + 1):
-            xn = sfft.irfftn(sfft.rfftn(rhs0 + (alpha - b) * x, workers=WORKERS) / denom, s=n,
+            gx = sfft.irfftn(sfft.rfftn(rhs0 + (alpha - b) * x, workers=WORKERS) / denom, s=n,
                              workers=WORKERS)
-            diff = float(np.max(np.abs(xn - x)))
-            x = xn
+            if it == 1 or not cheb:
+                d = gx - x                                   # x_1 = G(x_0)
+            else:
+                d = rho * rho_prev * d + (2.0 * rho / q) * (gx - x)
+            x = x + d
+            if cheb:
+                rho_prev, rho = rho, 1.0 / (2.0 / q - rho)
+            diff = float(np.max(np.abs(d)))
             if diff <= self.inner_tol:
                 break
         self.last_inner = it

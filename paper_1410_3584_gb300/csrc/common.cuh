@@ -70,6 +70,7 @@ template <typename T> struct DevPlan {
     // moments {C0, M1x, M1y}, cell area and the auxiliary Gaussian width
     const double *pois;
     const double *mom;
+    const double *u1tab;   // per grid point {u_{1,1}, u_{1,2} x, u_{1,2} y} (built at plan time)
     double hvol;
     double sigma;
     // register kernel (3D): sub-tile edge (0 = generic kernel only), segments = pieces of

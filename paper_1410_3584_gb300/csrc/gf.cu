@@ -19,10 +19,12 @@ nlp_status eval_any(nlp_plan_s *p, const void *rho, void *phi);
 size_t grid_points(const nlp_plan_s *p);
 
 constexpr int kRedBlocks = 608;   // 152 SMs x 4
-enum { S_MIN = 0, S_MAX, S_DIFF, S_NORM, S_CHANGE, S_EPOT, S_EINT, S_EKIN, S_COUNT = 16 };
+enum { S_MIN = 0, S_MAX, S_DIFF, S_NORM, S_CHANGE, S_EPOT, S_EINT, S_EKIN,
+       S_CHEB_Q, S_CHEB_R0, S_CHEB_R1, S_COUNT = 16 };
 
 template <typename T> struct Work {
     T *rho, *pot, *b, *x, *xn, *r, *xf;   // xf: inner iterate captured at convergence
+    T *d;                                 // last inner update (Chebyshev recurrence)
     int *iflag;                           // [0] first converged inner iteration, [1] first non-finite one
     cpx<T> *spec;       // plain-grid spectrum (R2C half for GF)
     double *part;       // kRedBlocks x 2 partials
@@ -41,13 +43,14 @@ template <typename T> static nlp_status ensure_work(nlp_plan_s *p, Work<T> *&W) 
     const size_t nh = (size_t)n2 / 2 + 1;
     void *d;
     nlp_status s;
-    T *bufs[7];
-    for (int i = 0; i < 7; ++i) {
+    T *bufs[8];
+    for (int i = 0; i < 8; ++i) {
         if ((s = alloc_dev(p, &d, sizeof(T) * N))) return s;
         bufs[i] = (T *)d;
     }
     W->rho = bufs[0]; W->pot = bufs[1]; W->b = bufs[2]; W->x = bufs[3]; W->xn = bufs[4]; W->r = bufs[5];
     W->xf = bufs[6];
+    W->d = bufs[7];
     if ((s = alloc_dev(p, &d, sizeof(int) * 2))) return s;
     W->iflag = (int *)d;
     if ((s = alloc_dev(p, &d, sizeof(cpx<T>) * (size_t)n0 * n1 * nh))) return s;
@@ -168,17 +171,60 @@ __global__ void k_diag(cpx<T> *spec, int n0, int n1, int n2, int nh, double L0, 
     }
 }
 
-// partial max |a - c|
-template <typename T> __global__ void k_maxdiff(const T *a, const T *c, int64_t N, double *part) {
+
+// Chebyshev acceleration of the inner fixed point.  With G(x) = M^{-1}(phi^n/tau + (alpha - b) x),
+// M = 1/tau + alpha - Delta/2 and A = 1/tau - Delta/2 + b = M + (b - alpha), the preconditioned
+// residual is G(x) - x and the eigenvalues of M^{-1} A lie in [1 - q, 1 + q],
+// q = (max b - min b) / (2/tau + max b + min b).  The semi-iteration on that interval
+// (centre 1, half-width q; Chebyshev acceleration as in Saad, Iterative Methods for Sparse
+// Linear Systems, Alg. 12.1) takes x_1 = G(x_0) and then
+//   d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / q) (G(x_k) - x_k),  x_{k+1} = x_k + d_k,
+//   rho_0 = q,  rho_k = 1 / (2/q - rho_{k-1}),
+// with the same fixed point (the backward-Euler solution).  q outside (0, 1) falls back to
+// the plain iteration x_{k+1} = G(x_k).
+__global__ void k_cheb_init(double *scal, double inv_tau) {
+    const double bmin = scal[S_MIN], bmax = scal[S_MAX];
+    const double q = 0.5 * (bmax - bmin) / (inv_tau + 0.5 * (bmax + bmin));
+    scal[S_CHEB_Q] = q;
+    scal[S_CHEB_R0] = 0.0;
+    scal[S_CHEB_R1] = q;   // rho_0
+}
+
+__device__ __forceinline__ bool cheb_ok(double q) { return q > 1e-300 && q < 1.0; }
+
+// iteration it: d = c1 d + c2 (xn - x), x += d; partial max |d|
+template <typename T>
+__global__ void k_cheb_update(T *x, const T *xn, T *d, const double *scal, int it, int64_t N, double *part) {
+    const double q = scal[S_CHEB_Q];
+    double c1 = 0.0, c2 = 1.0;
+    if (it > 1 && cheb_ok(q)) {
+        c1 = scal[S_CHEB_R1] * scal[S_CHEB_R0];
+        c2 = 2.0 * scal[S_CHEB_R1] / q;
+    }
     double m = 0.0;
-    GRID_STRIDE(q, N) m = fmax(m, fabs((double)a[q] - (double)c[q]));
+    GRID_STRIDE(k, N) {
+        const T dn = (T)(c1 * (double)d[k] + c2 * ((double)xn[k] - (double)x[k]));
+        d[k] = dn;
+        x[k] = x[k] + dn;
+        m = fmax(m, fabs((double)dn));
+    }
     m = block_reduce(m, 1);
     if (threadIdx.x == 0) part[2 * blockIdx.x] = m;
 }
 
 // inner-iteration bookkeeping on the device: records the first iteration whose update
-// max|x^(m+1) - x^(m)| is <= tol (flag[0]) or non-finite (flag[1])
-__global__ void k_inner_check(const double *scal, double tol, int it, int *flag) {
+// max|x^(m+1) - x^(m)| is <= tol (flag[0]) or non-finite (flag[1]); advances the
+// Chebyshev coefficients (rho_{k-1}, rho_k) for the next iteration
+__global__ void k_inner_check(double *scal, double tol, int it, int *flag) {
+    const double q = scal[S_CHEB_Q];
+    if (it > 1 && cheb_ok(q)) {
+        const double r1 = scal[S_CHEB_R1];
+        scal[S_CHEB_R0] = r1;
+        scal[S_CHEB_R1] = 1.0 / (2.0 / q - r1);
+    } else if (it == 1 && cheb_ok(q)) {
+        scal[S_CHEB_R0] = q;                       // rho_0
+        scal[S_CHEB_R1] = 1.0 / (2.0 / q - q);     // rho_1
+    }
     if (flag[0] || flag[1]) return;
     const double d = scal[S_DIFF];
     if (!isfinite(d)) flag[1] = it;
@@ -341,12 +387,14 @@ static nlp_status gf_step_t(nlp_plan_s *p, T *phi, const T *V, double beta, doub
     k_make_b<T><<<eg(), 256, 0, st>>>(V, W->rho, W->pot, (T)g, (T)beta, W->b, N, W->part);
     if ((s = reduce_to(p, W, 0, 2, 1.0, S_MIN)) || (s = reduce_to(p, W, 1, 1, 1.0, S_MAX))) return s;
     if (cudaMemcpyAsync(W->x, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st)) return NLP_ERR_CUDA;
-    // Inner fixed point.  The convergence test runs on the device every iteration; the host
-    // reads its verdict every kCheckEvery iterations, so up to kCheckEvery - 1 iterations may
-    // run past convergence.  Their results are not used: the iterate of the first converged
-    // iteration is captured in xf, so the step equals one that stopped exactly there.
+    // Inner solve: the Chebyshev-accelerated fixed point (k_cheb_init).  The convergence test
+    // runs on the device every iteration; the host reads its verdict every kCheckEvery
+    // iterations, so up to kCheckEvery - 1 iterations may run past convergence.  Their results
+    // are not used: the iterate of the first converged iteration is captured in xf, so the
+    // step equals one that stopped exactly there.
     constexpr int kCheckEvery = 4;
     if (cudaMemsetAsync(W->iflag, 0, sizeof(int) * 2, st)) return NLP_ERR_CUDA;
+    k_cheb_init<<<1, 1, 0, st>>>(W->scal, 1.0 / tau);
     int flags[2] = {0, 0};
     for (int it = 1; it <= max_inner; ++it) {
         k_rhs<T><<<eg(), 256, 0, st>>>(phi, W->b, W->x, (T)(1.0 / tau), W->scal, W->r, N);
@@ -354,13 +402,10 @@ static nlp_status gf_step_t(nlp_plan_s *p, T *phi, const T *V, double beta, doub
         k_diag<T><<<eg(), 256, 0, st>>>(D.F, D.n[0], D.n[1], D.n[2], D.nh, p->L3[0], p->L3[1], p->L3[2], 1.0 / tau,
                                         W->scal, 1.0 / (double)N);
         if (c2r_plain<T>(W->xn, D, st)) return NLP_ERR_CUDA;
-        k_maxdiff<T><<<eg(), 256, 0, st>>>(W->xn, W->x, N, W->part);
+        k_cheb_update<T><<<eg(), 256, 0, st>>>(W->x, W->xn, W->d, W->scal, it, N, W->part);
         if ((s = reduce_to(p, W, 0, 1, 1.0, S_DIFF))) return s;
         k_inner_check<<<1, 1, 0, st>>>(W->scal, inner_tol, it, W->iflag);
-        k_capture<T><<<eg(), 256, 0, st>>>(W->iflag, it, W->xn, W->xf, N);
-        T *tmp = W->x;
-        W->x = W->xn;
-        W->xn = tmp;
+        k_capture<T><<<eg(), 256, 0, st>>>(W->iflag, it, W->x, W->xf, N);
         if (it % kCheckEvery == 0 || it == max_inner) {
             if (cudaMemcpyAsync(flags, W->iflag, sizeof(flags), cudaMemcpyDeviceToHost, st) ||
                 cudaStreamSynchronize(st))

@@ -55,6 +55,9 @@ cudaError_t launch_poisson_moments(const T *rho, const DevPlan<T> &P, const doub
 template <typename T> cudaError_t launch_poisson_origin(const DevPlan<T> &P, double *mom, cudaStream_t st);
 template <typename T>
 cudaError_t launch_poisson_u1(T *phi, const DevPlan<T> &P, const double *L, const double *h, cudaStream_t st);
+// plan time: the u_{1,1}, u_{1,2} table of the grid (3 doubles per point)
+cudaError_t launch_u1_table(double *tab, int nx, int ny, const double *L, const double *h, double sigma,
+                            cudaStream_t st);
 
 // precomputed-kernel method: F *= K-hat (toeplitz.cu)
 template <typename T> cudaError_t launch_mul_spec(cpx<T> *F, const cpx<T> *K, int64_t M, cudaStream_t st);

@@ -426,6 +426,7 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     }
     D.pois = nullptr;
     D.mom = nullptr;
+    D.u1tab = nullptr;
     D.hvol = p->h[1] * p->h[2] * (p->grid.dim == 3 ? p->h[0] : 1.0);
     D.sigma = p->sigma;
     if (!pois.empty()) {
@@ -440,6 +441,12 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         cudaMemset(dm, 0, sizeof(double) * 4);
         D.pois = p->d_pois;
         D.mom = (const double *)dm;
+        void *du;
+        const int64_t Ng = (int64_t)p->n3[1] * p->n3[2];
+        if ((s = alloc_dev(p, &du, sizeof(double) * 3 * (size_t)Ng))) return s;
+        if (launch_u1_table((double *)du, p->n3[1], p->n3[2], p->L3, p->h, p->sigma, p->stream) != cudaSuccess)
+            return NLP_ERR_CUDA;
+        D.u1tab = (const double *)du;
     }
     D.nd = (const T *)dnd;
     D.no = (const uint32_t *)dno;

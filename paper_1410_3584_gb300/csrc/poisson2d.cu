@@ -128,12 +128,11 @@ __global__ void k_interp_origin(DevPlan<T> P, double *mom) {
     }
 }
 
-// phi += C0 u_{1,1}(x) - M1 . u_{1,2}(x)   (FP64; Eqs. (phi1_exct), (phi12_ext))
-template <typename T>
-__global__ void k_u1_add(T *phi, int nx, int ny, double Lx, double Ly, double hx, double hy, double sigma,
-                         const double *mom) {
+// u_{1,1}(x) and u_{1,2}(x) of the auxiliary Gaussian at every grid point (FP64; Eqs.
+// (phi1_exct), (phi12_ext)): they depend only on the grid and sigma, so the plan tabulates
+// them once and every evaluation adds C0 u_{1,1} - M1 . u_{1,2}.
+__global__ void k_u1_table(double *tab, int nx, int ny, double Lx, double Ly, double hx, double hy, double sigma) {
     const int64_t N = (int64_t)nx * ny;
-    const double C0 = mom[0], M1x = mom[1], M1y = mom[2];
     const double inv4pi = 0.25 / 3.14159265358979323846, inv2pi = 0.5 / 3.14159265358979323846;
     const double euler = 0.57721566490153286061;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
@@ -150,8 +149,25 @@ __global__ void k_u1_add(T *phi, int nx, int ny, double Lx, double Ly, double hx
         } else {
             u11 = (euler - log(2.0 * sigma * sigma)) * inv4pi;
         }
-        phi[q] = (T)((double)phi[q] + C0 * u11 - (M1x * u12x + M1y * u12y));
+        tab[3 * q] = u11;
+        tab[3 * q + 1] = u12x;
+        tab[3 * q + 2] = u12y;
     }
+}
+
+// phi += C0 u_{1,1}(x) - M1 . u_{1,2}(x) from the plan's table (FP64 arithmetic)
+template <typename T> __global__ void k_u1_add(T *phi, int64_t N, const double *__restrict__ tab, const double *mom) {
+    const double C0 = mom[0], M1x = mom[1], M1y = mom[2];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+        phi[q] = (T)((double)phi[q] + C0 * tab[3 * q] - (M1x * tab[3 * q + 1] + M1y * tab[3 * q + 2]));
+}
+
+cudaError_t launch_u1_table(double *tab, int nx, int ny, const double *L, const double *h, double sigma,
+                            cudaStream_t st) {
+    const int64_t N = (int64_t)nx * ny;
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
+    k_u1_table<<<blocks, 256, 0, st>>>(tab, nx, ny, L[1], L[2], h[1], h[2], sigma);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -172,7 +188,9 @@ template <typename T>
 cudaError_t launch_poisson_u1(T *phi, const DevPlan<T> &P, const double *L, const double *h, cudaStream_t st) {
     const int64_t N = (int64_t)P.n[1] * P.n[2];
     const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
-    k_u1_add<T><<<blocks, 256, 0, st>>>(phi, P.n[1], P.n[2], L[1], L[2], h[1], h[2], P.sigma, P.mom);
+    (void)L;
+    (void)h;
+    k_u1_add<T><<<blocks, 256, 0, st>>>(phi, N, P.u1tab, P.mom);
     return cudaGetLastError();
 }
 

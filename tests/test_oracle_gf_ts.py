@@ -89,3 +89,33 @@ def test_ts_temporal_order(ts_setup, order, ratio):
         errs.append(np.max(np.abs(p - ref)))
     r = [a / b for a, b in zip(errs, errs[1:])]
     assert all(0.7 * ratio < x < 1.4 * ratio for x in r), (errs, r)
+
+
+@pytest.mark.parametrize("gam", [1.0, 3.0])
+def test_gf_inner_solve_equals_dense_backward_euler(gam):
+    """One flow step = the backward-Euler solution of (1/tau - Delta/2 + b) x = phi^n / tau,
+    normalised (Sec. 3.1), with the Laplacian of the Fourier pseudospectral discretisation
+    assembled as a dense matrix and solved by numpy.linalg.solve.  Pins the accelerated inner
+    iteration's fixed point; a strongly anisotropic trap (gam = 3) makes q large."""
+    g = W.Grid((12, 16), (4.0, 5.0))
+    V = W.harmonic_trap(g, (1.0, gam))
+    phi0 = W.normalized_gaussian_start(g, (1.3, 0.9))
+    op = potential.ConvolutionOperator(g, "coulomb2d", math.pi / max(g.h), (32, 64))
+    beta, tau = 3.0, 1e-2
+    G = gf.GradientFlow(g, V, beta, op, tau=tau, inner_tol=1e-14, max_inner=5000)
+    got, _ = G.step(phi0)
+    b = V + beta * op(phi0 * phi0)
+    N = phi0.size
+    lap = np.zeros((N, N))
+    mu2 = gf.wavenumbers2(g)
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        lap[:, j] = np.real(np.fft.ifftn(-mu2 * np.fft.fftn(e.reshape(g.n)))).ravel()
+    A = np.eye(N) / tau - 0.5 * lap + np.diag(b.ravel())
+    x = np.linalg.solve(A, (phi0 / tau).ravel()).reshape(g.n)
+    x /= math.sqrt(float(np.prod(g.h)) * float(np.sum(x * x)))
+    assert np.max(np.abs(got - x)) < 1e-12
+    q = 0.5 * (b.max() - b.min()) / (1.0 / tau + 0.5 * (b.max() + b.min()))
+    plain = math.ceil(math.log(1e-14) / math.log(q))
+    assert G.last_inner < plain, (G.last_inner, plain, q)
