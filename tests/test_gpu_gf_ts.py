@@ -7,7 +7,7 @@ import pytest
 
 import workloads as W
 from conftest import load_golden
-from oracle import gf, potential, ts
+from oracle import gf, potential, quadrature, ts
 
 pytestmark = pytest.mark.gpu
 
@@ -103,3 +103,76 @@ def test_ts_step_parity_and_mass(nl, order, prec, tol):
     assert np.max(np.abs(out - ref)) / np.max(np.abs(ref)) < tol
     m0 = float(np.sum(np.abs(psi0) ** 2))
     assert abs(float(np.sum(np.abs(out) ** 2)) - m0) < (1e-12 if prec == "fp64" else 1e-5) * m0
+
+
+@pytest.mark.parametrize("beta", [-10.0, -5.0, -1.0, 1.0, 5.0, 10.0])
+def test_gpu_2d_coulomb_ground_states_match_paper_table(nl, beta):
+    """Example 3.2 (Table virial_2d_Coulomb) at the paper's own mesh: V = (x^2 + 4 y^2)/2,
+    h = 1/8 on [-8,8)^2, GF-NUFFT on the GPU (nlp_gf_solve, FP64) to the Sec. 3.2 stopping
+    rule with eps0 = 1e-10; each printed energy to one unit in its last printed place, and
+    the virial identity I^h of the table (|I| ~ 2e-10 there)."""
+    import torch
+    g = W.cube(128, 8.0, dim=2)
+    gam = (1.0, 2.0)
+    V = W.harmonic_trap(g, gam)
+    plan = nl.Plan(g.n, g.L, "coulomb2d", "fp64", kmax=math.pi / g.h[0])
+    tphi = torch.from_numpy(W.normalized_gaussian_start(g, gam)).cuda()
+    tV = torch.from_numpy(V).cuda()
+    steps, ch, E, st = nl.nlp_gf_solve(plan.handle, tphi, tV, beta, 0.0, 1e-2, 1e-10, 20000, 1e-12, 1000)
+    plan.close()
+    rows = {float(r[0]): r[1:] for r in load_golden("paper_gs_energies_2d_coulomb.txt")}
+    for key, txt in zip(("E", "mu", "Ekin", "Epot", "Eint"), rows[beta]):
+        mant, _, ex = txt.upper().partition("E")
+        ulp = 10.0 ** (-len(mant.split(".")[1]) + (int(ex) if ex else 0))
+        assert abs(E[key] - float(txt)) < ulp, (key, E[key], txt)
+    assert abs(2 * E["Ekin"] - 2 * E["Epot"] + E["Eint"]) < 1e-8
+
+
+def _dyn_run(nl, h, beta, method=1):
+    """Example 4.1 on the GPU: psi_0 = exp(-|x|^2/2), V = |x|^2/2 on [-8,8)^3, fourth-order
+    splitting with tau = 1e-3 to t = 1/8; returns (psi, phi = U * |psi|^2, mass before/after)."""
+    import torch
+    n = int(round(16.0 / h))
+    g = W.cube(n, 8.0)
+    V = W.harmonic_trap(g, (1.0, 1.0, 1.0))
+    X, Y, Z = g.mesh()
+    psi0 = np.exp(-0.5 * (X * X + Y * Y + Z * Z)).astype(np.complex128)
+    P = quadrature.density_P(1.0, h)
+    plan = nl.Plan(g.n, g.L, "coulomb3d", "fp64", kmax=P, counts=quadrature.default_counts(g.L, P), method=method)
+    tpsi = torch.from_numpy(psi0).cuda()
+    tV = torch.from_numpy(V).cuda()
+    for _ in range(125):
+        nl.nlp_ts_step(plan.handle, tpsi, tV, beta, 0.0, 1e-3, 4)
+    rho = (tpsi.real ** 2 + tpsi.imag ** 2).contiguous()
+    phi = plan.eval(rho)
+    plan.sync()
+    out, ph = tpsi.cpu().numpy(), phi.cpu().numpy()
+    plan.close()
+    hv = h ** 3
+    return out, ph, hv * float(np.sum(np.abs(psi0) ** 2)), hv * float(np.sum(np.abs(out) ** 2))
+
+
+@pytest.mark.parametrize("beta", [-5.0, 5.0])
+def test_gpu_dynamics_example_4_1_error_levels(nl, beta):
+    """Example 4.1 (Table dy_3d_Coulomb): TS-NUFFT at h = 1, 1/2, 1/4 against our own h = 1/8
+    run (the paper's reference solution is not printed).  The paper's printed errors at t = 1/8
+    are reproduced within a factor 3 at h = 1 and 1/2 (where the mesh error dominates the
+    reference's own), and at h = 1/4 the error is at the 1e-11 level of the table; mass is
+    conserved by the splitting (unitary steps)."""
+    rows = {(r[0], float(r[1])): [float(v) for v in r[2:]] for r in load_golden("paper_dynamics_3d_coulomb_errors.txt")}
+    ref_psi, ref_phi, m0, m1 = _dyn_run(nl, 1.0 / 8, beta)
+    assert abs(m1 - m0) < 1e-12 * m0
+    for k, h in enumerate((1.0, 0.5, 0.25)):
+        psi, phi, a0, a1 = _dyn_run(nl, h, beta)
+        assert abs(a1 - a0) < 1e-12 * a0
+        s = int(round(h * 8))
+        rp, rf = ref_psi[::s, ::s, ::s], ref_phi[::s, ::s, ::s]
+        e_psi = float(np.max(np.abs(psi - rp)) / np.max(np.abs(rp)))
+        e_phi = float(np.max(np.abs(phi - rf)) / np.max(np.abs(rf)))
+        p_psi, p_phi = rows[("psi", beta)][k], rows[("phi", beta)][k]
+        print("beta %g h %g: e_psi %.3e (paper %.3e), e_phi %.3e (paper %.3e)" % (beta, h, e_psi, p_psi, e_phi, p_phi))
+        if h >= 0.5:
+            assert p_psi / 3 < e_psi < 3 * p_psi
+            assert p_phi / 3 < e_phi < 3 * p_phi
+        else:
+            assert e_psi < 1e-10 and e_phi < 1e-10
