@@ -269,6 +269,7 @@ def gpu_arm(args):
             "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "L": L_BOX, "kernel": "coulomb3d",
                        "P": P, "quadrature": [res32["info"]["n_r"], res32["info"]["n_theta"], res32["info"]["n_phi"]],
                        "nodes": res32["info"]["nodes_total"], "width_fp32": res32["info"]["width"],
+                       "spread_pieces_fp32": res32["info"]["segments"], "tile_fp32": res32["info"]["tile"],
                        "width_fp64": res64["info"]["width"], "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "rel_linf_vs_oracle": err32,

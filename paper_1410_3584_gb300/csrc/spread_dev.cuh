@@ -165,10 +165,14 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
     const int w = P.w;
     const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
     const int WW = Wt0 * Wt1 * Wt2;
+    // window cells (a, b, c) at (a Wt1 + b) P2 + c with the z pitch padded by one cell: with
+    // x fastest across the lanes, the 8-byte column accesses of a warp (tile 8, w 7: pitches
+    // 210 and 15 cells) hit every bank pair exactly twice
+    const int P2 = Wt2 + 1, WWp = Wt0 * Wt1 * P2;
     cpx<T> *sF = (cpx<T> *)smraw;
-    cpx<T> *sG = sF + WW;
+    cpx<T> *sG = sF + WWp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    T *psi = (T *)(sG + WW) + warp * (NB * 3 * W + V);
+    T *psi = (T *)(sG + WWp) + warp * (NB * 3 * W + V);
     T *cb = psi + NB * 3 * W;
     const Chunk ch = P.rchunks[bid];
     __shared__ int next_seg;
@@ -176,23 +180,24 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
 
     for (int q = threadIdx.x; q < WW; q += blockDim.x) {
         const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        sF[q] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
-        sG[q] = mk<T>(0, 0);
+        const int cell = t * P2 + c;
+        sF[cell] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
+        sG[cell] = mk<T>(0, 0);
     }
     __syncthreads();
 
     const int ca = lane, cbc = lane + 32;
     const bool act_b = cbc < W * W;
-    const int xa = ca / W, ya = ca % W;                 // W*W > 32 for W >= 6: column a always active
-    const int xb = act_b ? cbc / W : 0, yb = act_b ? cbc % W : 0;
+    const int xa = ca % W, ya = ca / W;                 // W*W > 32 for W >= 6: column a always active
+    const int xb = act_b ? cbc % W : 0, yb = act_b ? cbc / W : 0;
     const bool act_a = ca < W * W;
     // pieces are sorted heaviest first; each warp takes the next free one
     for (int sg = ch.j0 + warp; sg < ch.j1;) {
         const uint32_t so = P.seg_sub[sg];
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
         const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
-        const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * Wt2 + so2;
-        const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * Wt2 + so2;
+        const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * P2 + so2;
+        const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * P2 + so2;
         T fax[W], fay[W], fbx[W], fby[W], gax[W], gay[W], gbx[W], gby[W];
 #pragma unroll
         for (int z = 0; z < W; ++z) {
@@ -295,9 +300,9 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
     }
     __syncthreads();
     for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const cpx<T> v = sG[q];
-        if (v.x == (T)0 && v.y == (T)0) continue;
         const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
+        const cpx<T> v = sG[t * P2 + c];
+        if (v.x == (T)0 && v.y == (T)0) continue;
         store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
     }
 }

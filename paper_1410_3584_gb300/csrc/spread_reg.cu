@@ -171,7 +171,10 @@ template <typename T> static constexpr int nb_of() { return 4; }   // nodes per 
 template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
     const size_t WW = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
     constexpr int NB = nb_of<T>();
-    if constexpr (W * W <= 64) return 2 * WW * sizeof(cpx<T>) + 8 * (NB * 3 * W + 2 * NB) * sizeof(T);
+    if constexpr (W * W <= 64) {   // warp kernel: z pitch padded by one cell
+        const size_t WWp = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w);
+        return 2 * WWp * sizeof(cpx<T>) + 8 * (NB * 3 * W + 2 * NB) * sizeof(T);
+    }
     return 2 * WW * sizeof(cpx<T>) +
            (size_t)RegCfg<W>::NT * (NB * 3 * W + RegCfg<W>::TW * 2 * NB + 2 * NB) * sizeof(T);
 }
