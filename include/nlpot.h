@@ -137,7 +137,7 @@ nlp_status nlp_eval_potential_host(nlp_plan plan, const void *rho_host, void *ph
  * Outputs (host, may be NULL): *max_change = max|phi^{n+1} - phi^n| / tau (stopping rule of
  * Sec. 3.2), *inner_iters, energies[5] = {E, E_kin, E_pot, E_int, mu} of phi^{n+1}.
  * Synchronizes the plan stream.  NLP_ERR_DIVERGED if a non-finite value appears.
- * Not available for NLP_POISSON_2D plans (NLP_ERR_UNSUPPORTED). */
+ * All kernels, NLP_POISSON_2D included (its potential through Algorithm 1). */
 nlp_status nlp_gf_step(nlp_plan plan, void *phi_dev, const void *V_dev, double beta, double g,
                        double tau, double inner_tol, int max_inner, double *max_change,
                        int *inner_iters, double *energies);

@@ -205,7 +205,6 @@ nlp_status nlp_eval_potential_host(nlp_plan p, const void *rho_host, void *phi_h
 nlp_status nlp_gf_step(nlp_plan p, void *phi_dev, const void *V_dev, double beta, double g, double tau,
                        double inner_tol, int max_inner, double *max_change, int *inner_iters, double *energies) {
     if (!p || !phi_dev || !V_dev || !(tau > 0) || !(inner_tol > 0) || max_inner < 1) return NLP_ERR_INVALID_ARG;
-    if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
     return gf_step_impl(p, phi_dev, V_dev, beta, g, tau, inner_tol, max_inner, max_change, inner_iters, energies);
 }
 
@@ -215,7 +214,6 @@ nlp_status nlp_gf_solve(nlp_plan p, void *phi_dev, const void *V_dev, double bet
     if (!p || !phi_dev || !V_dev || !(tau > 0) || !(stop_tol > 0) || max_steps < 1 || !(inner_tol > 0) ||
         max_inner < 1)
         return NLP_ERR_INVALID_ARG;
-    if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
     double ch = INFINITY;
     int n = 0;
     nlp_status s = NLP_OK;
@@ -236,7 +234,6 @@ nlp_status nlp_gf_solve(nlp_plan p, void *phi_dev, const void *V_dev, double bet
 
 nlp_status nlp_energies(nlp_plan p, const void *phi_dev, const void *V_dev, double beta, double g, double *energies) {
     if (!p || !phi_dev || !V_dev || !energies) return NLP_ERR_INVALID_ARG;
-    if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
     return energies_impl(p, phi_dev, V_dev, beta, g, energies);
 }
 

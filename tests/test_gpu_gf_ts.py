@@ -178,3 +178,48 @@ def test_gpu_dynamics_example_4_1_error_levels(nl, beta):
             assert e_phi < 10 * e_psi
         else:
             assert e_psi < 1e-10 and e_phi < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_gf_step_parity_poisson2d(nl, prec, tol):
+    """One gradient-flow step with the 2D Laplace kernel (potential through Algorithm 1)
+    against the oracle's step with its own Algorithm 1 evaluation."""
+    import torch
+    g = W.Grid((48, 40), (8.0, 7.0))
+    V = W.harmonic_trap(g, (1.0, 2.0))
+    P = math.pi / max(g.h)
+    counts = (64, 128)
+    phi0 = W.normalized_gaussian_start(g, (1.2, 1.8))
+    G = gf.GradientFlow(g, V, 5.0, lambda r: potential.eval_nufft(r, g, "poisson2d", P, counts), tau=1e-2,
+                        inner_tol=1e-12 if prec == "fp64" else 1e-6)
+    ref, ch_ref = G.step(phi0)
+    plan = nl.Plan(g.n, g.L, "poisson2d", prec, kmax=P, counts=counts)
+    tphi = torch.from_numpy(phi0).to("cuda", plan.torch_dtype)
+    tV = torch.from_numpy(V).to("cuda", plan.torch_dtype)
+    ch, it, E, st = nl.nlp_gf_step(plan.handle, tphi, tV, 5.0, 0.0, 1e-2, 1e-12 if prec == "fp64" else 1e-6, 200)
+    out = tphi.double().cpu().numpy()
+    plan.close()
+    assert np.max(np.abs(out - ref)) / np.max(np.abs(ref)) < tol
+
+
+@pytest.mark.parametrize("beta", [-10.0, -5.0, -1.0, 1.0, 5.0, 10.0])
+def test_gpu_2d_poisson_ground_states_match_paper_table(nl, beta):
+    """Example 3.3 (Table virial_2d_Poisson): V = (x^2 + 4 y^2)/2, h = 1/8 on [-8,8)^2, the
+    2D Laplace kernel through Algorithm 1, GF-NUFFT on the GPU (FP64) to eps0 = 1e-10; each
+    printed energy to one unit in its last printed place; the virial identity of a
+    logarithmic kernel, 2 E_kin - 2 E_pot + beta/(4 pi) = 0 (unit mass)."""
+    import torch
+    g = W.cube(128, 8.0, dim=2)
+    gam = (1.0, 2.0)
+    V = W.harmonic_trap(g, gam)
+    plan = nl.Plan(g.n, g.L, "poisson2d", "fp64", kmax=math.pi / g.h[0])
+    tphi = torch.from_numpy(W.normalized_gaussian_start(g, gam)).cuda()
+    tV = torch.from_numpy(V).cuda()
+    steps, ch, E, st = nl.nlp_gf_solve(plan.handle, tphi, tV, beta, 0.0, 1e-2, 1e-10, 20000, 1e-12, 1000)
+    plan.close()
+    rows = {float(r[0]): r[1:] for r in load_golden("paper_gs_energies_2d_poisson.txt")}
+    for key, txt in zip(("E", "mu", "Ekin", "Epot", "Eint"), rows[beta]):
+        mant, _, ex = txt.upper().partition("E")
+        ulp = 10.0 ** (-len(mant.split(".")[1]) + (int(ex) if ex else 0))
+        assert abs(E[key] - float(txt)) < ulp, (key, E[key], txt)
+    assert abs(2 * E["Ekin"] - 2 * E["Epot"] + beta / (4 * math.pi)) < 1e-8
