@@ -24,6 +24,7 @@
 namespace nlp {
 
 enum { ST_R2C = 0, ST_A1, ST_A0, ST_CLEAR, ST_SPREAD, ST_B0, ST_B1, ST_C2R, kStages };
+constexpr int kRegLines = 16;          // lines (pairs) per register-engine FFT task: 16 x 16 threads
 constexpr int kClearChunk = 1 << 16;   // complex elements of G zeroed per clear task
 
 struct BatchItem {
@@ -33,6 +34,7 @@ struct BatchItem {
     int ntask[kStages];
     int dep[kStages];        // stage this stage waits for (-1: none)
     int spread_warp;         // 1: register kernel (W = 8), 0: shared-atomics kernel
+    int reg_fft;             // 1: FFT passes on the register radix engine (16 lines per task)
     int64_t gsize;           // complex elements of G
 };
 
@@ -54,7 +56,7 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
-__global__ void __launch_bounds__(256, 1) k_batch_persistent(BatchArgs A) {
+__global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_task, s_ok;
     for (;;) {
@@ -94,9 +96,18 @@ __global__ void __launch_bounds__(256, 1) k_batch_persistent(BatchArgs A) {
         __syncthreads();
         if (!s_ok) continue;   // drain: tickets are still taken so every CTA reaches the end
         switch (k) {
-            case ST_R2C: fwd_r2c_block<float>(A.rho[p], B.P, B.nb_r2c, i, smraw); break;
-            case ST_A1: fft_strided_block<float, -1>(B.P.F, B.a1, B.P.len[1], B.nb_a1, i, smraw); break;
-            case ST_A0: fft_strided_block<float, -1>(B.P.F, B.a0, B.P.len[0], B.nb_a0, i, smraw); break;
+            case ST_R2C:
+                if (B.reg_fft) fwd_r2c_reg_block<float, kRegLines>(A.rho[p], B.P, i, smraw);
+                else fwd_r2c_block<float>(A.rho[p], B.P, B.nb_r2c, i, smraw);
+                break;
+            case ST_A1:
+                if (B.reg_fft) fft_cols_block<float, -1, kRegLines>(B.P.F, B.a1, B.P.len[1], i, smraw);
+                else fft_strided_block<float, -1>(B.P.F, B.a1, B.P.len[1], B.nb_a1, i, smraw);
+                break;
+            case ST_A0:
+                if (B.reg_fft) fft_cols_block<float, -1, kRegLines>(B.P.F, B.a0, B.P.len[0], i, smraw);
+                else fft_strided_block<float, -1>(B.P.F, B.a0, B.P.len[0], B.nb_a0, i, smraw);
+                break;
             case ST_CLEAR: {
                 const int64_t e0 = (int64_t)i * kClearChunk, e1 = min(e0 + kClearChunk, B.gsize);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) B.P.G[e] = mk<float>(0.f, 0.f);
@@ -106,9 +117,18 @@ __global__ void __launch_bounds__(256, 1) k_batch_persistent(BatchArgs A) {
                 if (B.spread_warp) spread_warp_block<float, 8, 4>(B.P, i, smraw);
                 else spread_generic_block<float>(B.P, i, smraw);
                 break;
-            case ST_B0: fft_strided_block<float, +1>(B.P.G, B.b0, B.P.len[0], B.nb_a0, i, smraw); break;
-            case ST_B1: fft_strided_block<float, +1>(B.P.G, B.b1, B.P.len[1], B.nb_a1, i, smraw); break;
-            case ST_C2R: inv_c2r_block<float>(A.phi[p], B.P, B.nb_c2r, i, smraw); break;
+            case ST_B0:
+                if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(B.P.G, B.b0, B.P.len[0], i, smraw);
+                else fft_strided_block<float, +1>(B.P.G, B.b0, B.P.len[0], B.nb_a0, i, smraw);
+                break;
+            case ST_B1:
+                if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(B.P.G, B.b1, B.P.len[1], i, smraw);
+                else fft_strided_block<float, +1>(B.P.G, B.b1, B.P.len[1], B.nb_a1, i, smraw);
+                break;
+            case ST_C2R:
+                if (B.reg_fft) inv_c2r_reg_block<float, kRegLines>(A.phi[p], B.P, i, smraw);
+                else inv_c2r_block<float>(A.phi[p], B.P, B.nb_c2r, i, smraw);
+                break;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -223,9 +243,23 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
             B.a0.nouter = D.nf[1]; B.a0.os = nh;
             B.b0 = B.a0; B.b0.n_in = D.nf[0]; B.b0.n_out = D.n[0];
         }
-        B.nb_r2c = B.nb_c2r = lpb(D.len[2].N);
-        B.nb_a1 = nh >= 16 ? lpb(D.len[1].N) : (int)nh;
-        B.nb_a0 = three ? (nh >= 16 ? lpb(D.len[0].N) : (int)nh) : 1;
+        // register-engine FFT tasks where every axis has its factorisation and the task's shared
+        // memory stays within the budget of the single-plan launchers' widest choice
+        const size_t kRegBudget = 112 * 1024;
+        B.reg_fft = D.len[2].nrad_reg > 0 && D.len[1].nrad_reg > 0 && (!three || D.len[0].nrad_reg > 0);
+        if (B.reg_fft) {
+            const size_t r2c = sizeof(cpx<float>) * (size_t)kRegLines * line_ld(D.len[2].N) * 2;
+            size_t cols = cols_smem_bytes<float>(D.len[1], kRegLines);
+            if (three) cols = std::max(cols, cols_smem_bytes<float>(D.len[0], kRegLines));
+            if (r2c > kRegBudget || cols > kRegBudget) B.reg_fft = 0;
+        }
+        if (B.reg_fft) {
+            B.nb_r2c = B.nb_c2r = B.nb_a1 = B.nb_a0 = kRegLines;
+        } else {
+            B.nb_r2c = B.nb_c2r = lpb(D.len[2].N);
+            B.nb_a1 = nh >= 16 ? lpb(D.len[1].N) : (int)nh;
+            B.nb_a0 = three ? (nh >= 16 ? lpb(D.len[0].N) : (int)nh) : 1;
+        }
         const int64_t npairs = (int64_t)D.n[0] * D.n[1] / 2;
         B.ntask[ST_R2C] = (int)((npairs + B.nb_r2c - 1) / B.nb_r2c);
         B.ntask[ST_A1] = B.a1.nouter * (int)((nh + B.nb_a1 - 1) / B.nb_a1);
@@ -244,9 +278,15 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
             if (B.ntask[k] > 0) last = k;
         }
         // fixed-size sums of the FFT and spreading shared memory
-        smem = std::max(smem, fft_bytes(D.len[2].N, B.nb_r2c));
-        smem = std::max(smem, fft_bytes(D.len[1].N, B.nb_a1));
-        if (three) smem = std::max(smem, fft_bytes(D.len[0].N, B.nb_a0));
+        if (B.reg_fft) {
+            smem = std::max(smem, sizeof(cpx<float>) * (size_t)kRegLines * line_ld(D.len[2].N) * 2);
+            smem = std::max(smem, cols_smem_bytes<float>(D.len[1], kRegLines));
+            if (three) smem = std::max(smem, cols_smem_bytes<float>(D.len[0], kRegLines));
+        } else {
+            smem = std::max(smem, fft_bytes(D.len[2].N, B.nb_r2c));
+            smem = std::max(smem, fft_bytes(D.len[1].N, B.nb_a1));
+            if (three) smem = std::max(smem, fft_bytes(D.len[0].N, B.nb_a0));
+        }
         smem = std::max(smem, B.spread_warp ? interp_spread_reg_smem<float>(D) : interp_spread_smem<float>(D));
     }
     b->smem = smem;

@@ -397,14 +397,14 @@ __device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cp
 // contiguous columns per block, 16 threads per column.  Pruned input / output windows
 // are predicated loads / stores (positions outside the input window read as zero).
 template <typename T, int SGN, int NBC>
-__global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int bid,
+                                               unsigned char *smraw) {
     const int N = L.N;
     cpx<T> *sA = (cpx<T> *)smraw;
     cpx<T> *sB = sA + (size_t)N * NBC;
     const int b = threadIdx.x % NBC, t = threadIdx.x / NBC;
     const int ctiles = (d.ncol + NBC - 1) / NBC;
-    const int o = blockIdx.x / ctiles, c0 = (blockIdx.x % ctiles) * NBC;
+    const int o = bid / ctiles, c0 = (bid % ctiles) * NBC;
     const int oo = d.outer_map_n > 0 ? wrapi(o - d.outer_map_n / 2, d.outer_map_N) : o;
     const bool colok = c0 + b < d.ncol;
     cpx<T> *base = data + (int64_t)oo * d.os + c0 + b;
@@ -421,6 +421,17 @@ __global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedD
     fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
 }
 
+template <typename T, int SGN, int NBC>
+__global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fft_cols_block<T, SGN, NBC>(data, d, L, blockIdx.x, smraw);
+}
+
+// shared-memory bytes of the register-engine passes for line length N
+template <typename T> __host__ __device__ inline size_t cols_smem_bytes(const FftLen<T> &L, int nbc) {
+    return sizeof(cpx<T>) * (size_t)L.N * nbc * (L.nrad_reg > 2 ? 2 : 1);
+}
+
 // Padded line-major shared layout for the contiguous-axis kernels: position l of line b at
 // b * LDL + l + l / 16, so that unit-stride and stride-16 position accesses of 16 threads of
 // one line fall on distinct banks.
@@ -432,15 +443,15 @@ __host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; 
 // deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
 // where the spectra of the two real lines are separated and written as half spectra.
 template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16, 3) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, const DevPlan<T> &P, int bid,
+                                                  unsigned char *smraw) {
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
     cpx<T> *sB = sA + (size_t)NBC * LDL;
     const int t = threadIdx.x & 15, b = threadIdx.x >> 4;
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
-    const int64_t p = (int64_t)blockIdx.x * NBC + b;
+    const int64_t p = (int64_t)bid * NBC + b;
     const bool ok = p < npairs;
     const int64_t line0 = 2 * p, line1 = 2 * p + 1;
     const int i0a = ok ? (int)(line0 / P.n[1]) : 0, i1a = ok ? (int)(line0 % P.n[1]) : 0;
@@ -469,20 +480,26 @@ __global__ void __launch_bounds__(NBC * 16, 3) k_fwd_r2c_reg(const T *__restrict
     }
 }
 
+template <typename T, int NBC>
+__global__ void __launch_bounds__(NBC * 16, 3) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fwd_r2c_reg_block<T, NBC>(rho, P, blockIdx.x, smraw);
+}
+
 // Inverse C2R along the last axis on the register engine: the same operation as
 // k_inv_c2r.  The first pass reads the half spectra of a line pair from HBM and forms
 // Z = X1 + i X2 on the fly (Z[N - k] = conj(X1[k]) + i conj(X2[k])); the last pass writes
 // the output window, deconvolved, straight to HBM.
 template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const DevPlan<T> &P, int bid,
+                                                  unsigned char *smraw) {
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
     cpx<T> *sB = sA + (size_t)NBC * LDL;
     const int t = threadIdx.x & 15, b = threadIdx.x >> 4;
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
-    const int64_t p = (int64_t)blockIdx.x * NBC + b;
+    const int64_t p = (int64_t)bid * NBC + b;
     const bool ok = p < npairs;
     const int64_t line0 = 2 * p, line1 = 2 * p + 1;
     const int i0a = ok ? (int)(line0 / P.n[1]) : 0, i1a = ok ? (int)(line0 % P.n[1]) : 0;
@@ -515,6 +532,12 @@ __global__ void __launch_bounds__(NBC * 16) k_inv_c2r_reg(T *__restrict__ phi, D
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
     fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+}
+
+template <typename T, int NBC>
+__global__ void __launch_bounds__(NBC * 16) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    inv_c2r_reg_block<T, NBC>(phi, P, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ contiguous C2C pass
