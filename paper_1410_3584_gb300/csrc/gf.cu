@@ -202,8 +202,10 @@ __global__ void k_cheb_update(T *x, const T *xn, T *d, const double *scal, int i
         c2 = 2.0 * scal[S_CHEB_R1] / q;
     }
     double m = 0.0;
+    const bool first = c1 == 0.0;   // d holds no previous update yet (it may be uninitialised)
     GRID_STRIDE(k, N) {
-        const T dn = (T)(c1 * (double)d[k] + c2 * ((double)xn[k] - (double)x[k]));
+        const double r = (double)xn[k] - (double)x[k];
+        const T dn = (T)(first ? c2 * r : c1 * (double)d[k] + c2 * r);
         d[k] = dn;
         x[k] = x[k] + dn;
         m = fmax(m, fabs((double)dn));

@@ -666,9 +666,14 @@ nlp_status nlp_surrogate_create(double box_L, unsigned long long seed, int mode,
     fill(L.W[4], kHeadPad, kHid, kHeadOut, kHid, kHid);
     for (int c = 0; c < kConv; ++c)
         fill(L.cw[c], kConvCo[c] * kConvCi[c], 27, kConvCo[c] * kConvCi[c], 27, kConvCi[c] * 27.0);
-    bool ok = cudaMemcpy(s->P, h.data(), 4 * L.total, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemset(s->Mm, 0, 4 * L.total) == cudaSuccess && cudaMemset(s->Vv, 0, 4 * L.total) == cudaSuccess &&
-              cudaMemset(s->Gr, 0, 4 * L.total) == cudaSuccess && cudaMemset(s->err, 0, sizeof(int)) == cudaSuccess;
+    // everything on the network's stream (a stream created non-blocking does not order
+    // against the legacy default stream)
+    cudaStream_t st = s->stream;
+    bool ok = cudaMemcpyAsync(s->P, h.data(), 4 * L.total, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+              cudaMemsetAsync(s->Mm, 0, 4 * L.total, st) == cudaSuccess &&
+              cudaMemsetAsync(s->Vv, 0, 4 * L.total, st) == cudaSuccess &&
+              cudaMemsetAsync(s->Gr, 0, 4 * L.total, st) == cudaSuccess &&
+              cudaMemsetAsync(s->err, 0, sizeof(int), st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
     if (ok) {
         refresh_weights(s);
         ok = cudaStreamSynchronize(s->stream) == cudaSuccess;
