@@ -223,3 +223,53 @@ def test_gpu_2d_poisson_ground_states_match_paper_table(nl, beta):
         ulp = 10.0 ** (-len(mant.split(".")[1]) + (int(ex) if ex else 0))
         assert abs(E[key] - float(txt)) < ulp, (key, E[key], txt)
     assert abs(2 * E["Ekin"] - 2 * E["Epot"] + beta / (4 * math.pi)) < 1e-8
+
+
+def _dyn2d_run(nl, kernel, h, beta):
+    """Examples 4.2 / 4.3 on the GPU: psi_0 = exp(-|x|^2/2), V = |x|^2/2 on [-16,16)^2,
+    fourth-order splitting with tau = 1e-4 to t = 0.5; returns (psi, phi = U * |psi|^2)."""
+    import torch
+    n = int(round(32.0 / h))
+    g = W.cube(n, 16.0, dim=2)
+    V = W.harmonic_trap(g, (1.0, 1.0))
+    X, Y = g.mesh()
+    psi0 = np.exp(-0.5 * (X * X + Y * Y)).astype(np.complex128)
+    P = quadrature.density_P(1.0, h)
+    plan = nl.Plan(g.n, g.L, kernel, "fp64", kmax=P, counts=quadrature.default_counts(g.L, P),
+                   method=1 if kernel == "coulomb2d" else 0)
+    tpsi = torch.from_numpy(psi0).cuda()
+    tV = torch.from_numpy(V).cuda()
+    for _ in range(5000):
+        nl.nlp_ts_step(plan.handle, tpsi, tV, beta, 0.0, 1e-4, 4)
+    rho = (tpsi.real ** 2 + tpsi.imag ** 2).contiguous()
+    phi = plan.eval(rho)
+    plan.sync()
+    out, ph = tpsi.cpu().numpy(), phi.cpu().numpy()
+    plan.close()
+    m0, m1 = float(np.sum(np.abs(psi0) ** 2)), float(np.sum(np.abs(out) ** 2))
+    assert abs(m1 - m0) < 1e-11 * m0
+    return out, ph
+
+
+@pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
+@pytest.mark.parametrize("beta", [-5.0, 5.0])
+def test_gpu_dynamics_examples_4_2_4_3_error_levels(nl, kernel, beta):
+    """Examples 4.2 (2D Coulomb, Table dy_2d_Coulomb) and 4.3 (2D Poisson through Algorithm 1,
+    Table dy_2d_Poisson): TS-NUFFT at h = 1, 1/2, 1/4 against our own h = 1/8 run.  Printed
+    wave-function errors above 1e-10 (where our reference's own error, ~1e-12 by the table,
+    is negligible) are reproduced within a factor 3; smaller ones are bounded by 1e-9."""
+    rows = {(r[0], r[1], float(r[2])): [float(v) for v in r[3:]] for r in load_golden("paper_dynamics_2d_errors.txt")}
+    ref_psi, ref_phi = _dyn2d_run(nl, kernel, 1.0 / 8, beta)
+    for k, h in enumerate((1.0, 0.5, 0.25)):
+        psi, phi = _dyn2d_run(nl, kernel, h, beta)
+        s = int(round(h * 8))
+        rp, rf = ref_psi[::s, ::s], ref_phi[::s, ::s]
+        e_psi = float(np.max(np.abs(psi - rp)) / np.max(np.abs(rp)))
+        e_phi = float(np.max(np.abs(phi - rf)) / np.max(np.abs(rf)))
+        p_psi, p_phi = rows[(kernel, "psi", beta)][k], rows[(kernel, "phi", beta)][k]
+        print("%s beta %g h %g: e_psi %.3e (paper %.3e), e_phi %.3e (paper %.3e)"
+              % (kernel, beta, h, e_psi, p_psi, e_phi, p_phi))
+        if p_psi > 1e-10:
+            assert p_psi / 3 < e_psi < 3 * p_psi
+        else:
+            assert e_psi < 1e-9
