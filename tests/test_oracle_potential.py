@@ -221,3 +221,50 @@ def test_planted_mistakes_are_caught(mutation, monkeypatch):
         monkeypatch.setattr(potential, "u1_parts", lambda X, Y, sig: orig(X, Y, 1.5 * sig))
     u = potential.eval_direct(rho, g, "poisson2d", P)
     assert cf.rel_linf(u, exact) > 1e-6
+
+
+def test_split_evaluation_matches_closed_form_and_plain():
+    """Improved algorithm (Sec. 2.1, Eq. (3.9)): I_1 on the doubled grid's frequencies plus I_2
+    on a small ball reproduces the erf closed form at the paper's setting (L = 8, h = 1/4,
+    sigma = 1.1: Table tab:exmp1 level) and the plain quadrature of Eq. (ifft)."""
+    g = W.cube(64, 8.0)
+    rho = W.gaussian(g, [1.1] * 3)
+    P = quadrature.density_P(1.1, g.h[0])
+    phi, parts = potential.evaluate_split(rho, g, "coulomb3d", P, return_parts=True)
+    X, Y, Z = g.mesh()
+    ex = cf.coulomb3d_iso(np.sqrt(X * X + Y * Y + Z * Z), 1.1)
+    assert cf.rel_linf(phi, ex) < 5e-13
+    assert cf.rel_linf(phi, potential.eval_nufft(rho, g, "coulomb3d", P)) < 5e-13
+    # the small ball holds far fewer nodes than the full one
+    assert parts["k2"] < 0.5 * P
+
+
+def test_split_evaluation_dipolar_anisotropic():
+    """Dipolar kernel (axis z), anisotropic Gaussian: split = plain quadrature = closed form."""
+    g = W.Grid((48, 48, 56), (7.0, 7.0, 8.0))
+    a = (1.0, 1.3, 1.6)
+    rho = W.gaussian(g, a)
+    P = quadrature.density_P(min(a), max(g.h))
+    phi = potential.evaluate_split(rho, g, "dipole3d", P)
+    plain = potential.eval_nufft(rho, g, "dipole3d", P)
+    assert cf.rel_linf(phi, plain) < 5e-12   # both at their own ~1e-12 level for this grid
+    X, Y, Z = g.mesh()
+    sl = (slice(None, None, 6), slice(None, None, 6), slice(None, None, 7))
+    ex = cf.dipole3d_triaxial(X[sl], Y[sl], Z[sl], a)
+    assert cf.rel_linf(phi[sl], ex) < 1e-9
+
+
+def test_split_planted_mistake_is_caught(monkeypatch):
+    """A multiplier that drops the partition (w = U-hat) double counts the ball of I_2."""
+    g = W.cube(48, 6.0)
+    rho = W.gaussian(g, [1.0] * 3)
+    P = quadrature.density_P(1.0, g.h[0])
+    good = potential.evaluate_split(rho, g, "coulomb3d", P)
+    orig = potential.split_multiplier
+
+    def no_partition(kernel, K, a, dipole_axis=(0.0, 0.0, 1.0)):
+        return orig(kernel, K, 1e-30, dipole_axis)   # a -> 0: (1 - p) -> 1
+
+    monkeypatch.setattr(potential, "split_multiplier", no_partition)
+    bad = potential.evaluate_split(rho, g, "coulomb3d", P)
+    assert cf.rel_linf(bad, good) > 1e-2
