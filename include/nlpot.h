@@ -81,7 +81,15 @@ typedef struct {
                                the plan computes K once (type-1 NUFFT of the weights onto the doubled
                                grid) and each evaluation is an aperiodic convolution by FFT on the
                                2n grid.  Not for NLP_POISSON_2D (its operator is not translation
-                               invariant): NLP_ERR_UNSUPPORTED. */
+                               invariant): NLP_ERR_UNSUPPORTED.
+                               2 = the improved algorithm (Sec. 2.1, Eq. (3.9)), 3D kernels only: with
+                               the partition p(k) = exp(-|k|^2/a), phi = I_1 + I_2 where I_1 takes
+                               (1 - p) U-hat by the rectangle rule on the 2n grid's frequencies (an FFT
+                               convolution with an analytic multiplier) and I_2 takes p U-hat by the
+                               quadrature of Eq. (ifft) on the ball |k| <= k2 = min(P, sqrt(a ln 1/eps))
+                               (NUFFT with few nodes); a = (kappa / min L)^2 with (kappa, eps) =
+                               (5.5, 1e-16) for FP64 and (3.8, 1e-8) for FP32 plans.  Default counts
+                               then follow from k2 instead of P.  2D kernels: NLP_ERR_UNSUPPORTED. */
     int reserved[5];        /* must be zero */
 } nlp_opts;
 
@@ -103,6 +111,8 @@ typedef struct {
     double sigma_poisson;   /* NLP_POISSON_2D: width of the auxiliary Gaussian */
     int sub_tile;           /* register kernel sub-tile edge (0: shared-memory-atomics kernel) */
     int64_t segments;       /* register kernel work units (node runs of one sub-tile) */
+    double split_a;         /* method 2: partition parameter a (0 otherwise) */
+    double split_radius;    /* method 2: radius k2 of the NUFFT ball of I_2 (0 otherwise) */
 } nlp_plan_info;
 
 /* Create a plan: quadrature nodes and weights (FP64), their binning by fine-grid tile,
@@ -196,7 +206,7 @@ nlp_status nlp_ts_step(nlp_plan plan, void *psi_dev, const void *V_dev, double b
  * be evaluated while a batch evaluation is in flight.  Not thread-safe. */
 typedef struct nlp_batch_s *nlp_batch;
 
-/* plans: count FP32 plans (no NLP_POISSON_2D: NLP_ERR_UNSUPPORTED).  stream: cudaStream_t
+/* plans: count FP32 plans of method 0 (NLP_POISSON_2D or another method: NLP_ERR_UNSUPPORTED).  stream: cudaStream_t
  * for all batch work (must not be the legacy NULL stream: graph capture). */
 nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_batch *out);
 

@@ -38,7 +38,8 @@ class nlp_plan_info(ctypes.Structure):
                 ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int), ("nodes_total", ctypes.c_int64),
                 ("nodes_half", ctypes.c_int64), ("tiles", ctypes.c_int64), ("chunks", ctypes.c_int64),
                 ("tile", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t), ("sigma_poisson", ctypes.c_double),
-                ("sub_tile", ctypes.c_int), ("segments", ctypes.c_int64)]
+                ("sub_tile", ctypes.c_int), ("segments", ctypes.c_int64), ("split_a", ctypes.c_double),
+                ("split_radius", ctypes.c_double)]
 
 
 class NlpError(RuntimeError):
@@ -255,10 +256,10 @@ def nlp_set_stage_timing(plan, on: bool):
 
 def nlp_get_stage_times(plan):
     """[(stage name, ms), ...] of the most recent evaluation (timers must be on)."""
-    ids = (ctypes.c_int * 16)()
-    ms = (ctypes.c_double * 16)()
+    ids = (ctypes.c_int * 32)()
+    ms = (ctypes.c_double * 32)()
     cnt = ctypes.c_int(0)
-    _check(_lib.nlp_get_stage_times(plan, ids, ms, 16, ctypes.byref(cnt)), "nlp_get_stage_times")
+    _check(_lib.nlp_get_stage_times(plan, ids, ms, 32, ctypes.byref(cnt)), "nlp_get_stage_times")
     return [(STAGES.get(ids[i], str(ids[i])), ms[i]) for i in range(cnt.value)]
 
 

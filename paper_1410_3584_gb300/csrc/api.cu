@@ -17,7 +17,7 @@ nlp_status energies_noalloc_impl(nlp_plan_s *p, const void *phi, const void *V, 
 
 // Stage markers for the optional event timers (ids are part of the ABI: nlpot.h).
 static inline void mark(nlp_plan_s *p, int stage) {
-    if (!p->timing || p->nev >= 16) return;
+    if (!p->timing || p->nev >= 32) return;
     cudaEventRecord(p->ev[p->nev], p->stream);
     p->ev_stage[p->nev++] = stage;
 }
@@ -26,8 +26,6 @@ static inline void mark(nlp_plan_s *p, int stage) {
 template <typename T>
 nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     cudaStream_t st = p->stream;
-    p->nev = 0;
-    mark(p, -1);
     const bool three = p->grid.dim == 3;
     const bool pois = p->kernel == NLP_POISSON_2D;
     const int64_t nh = D.nh;
@@ -99,8 +97,18 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
 }
 
 nlp_status eval_any(nlp_plan_s *p, const void *rho, void *phi) {
-    if (p->prec == NLP_FP64) return eval_impl<double>(p, p->pd, (const double *)rho, (double *)phi);
-    return eval_impl<float>(p, p->pf, (const float *)rho, (float *)phi);
+    p->nev = 0;
+    mark(p, -1);
+    nlp_status s;
+    if (p->prec == NLP_FP64) {
+        s = eval_impl<double>(p, p->pd, (const double *)rho, (double *)phi);
+        // improved algorithm: I_2 (above, small-ball NUFFT) + I_1 (FFT convolution, accumulated)
+        if (!s && p->split) s = eval_impl<double>(p, p->pd1, (const double *)rho, (double *)phi);
+        return s;
+    }
+    s = eval_impl<float>(p, p->pf, (const float *)rho, (float *)phi);
+    if (!s && p->split) s = eval_impl<float>(p, p->pf1, (const float *)rho, (float *)phi);
+    return s;
 }
 
 size_t grid_points(const nlp_plan_s *p) {
@@ -139,7 +147,7 @@ void nlp_plan_destroy(nlp_plan p) {
     else cudaDeviceSynchronize();
     for (void *a : p->allocs) cudaFree(a);
     if (p->d_work && p->work_free) p->work_free(p->d_work);
-    for (int i = 0; i < 16; ++i)
+    for (int i = 0; i < 32; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     delete p;
 }
@@ -252,7 +260,7 @@ nlp_status nlp_ts_step(nlp_plan p, void *psi_dev, const void *V_dev, double beta
 nlp_status nlp_set_stage_timing(nlp_plan p, int on) {
     if (!p) return NLP_ERR_INVALID_ARG;
     if (on && !p->ev[0])
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < 32; ++i)
             if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return NLP_ERR_CUDA;
     p->timing = on ? 1 : 0;
     p->nev = 0;

@@ -217,7 +217,8 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
     *out = nullptr;
     for (int p = 0; p < count; ++p) {
         if (!plans[p]) return NLP_ERR_INVALID_ARG;
-        if (plans[p]->prec != NLP_FP32 || plans[p]->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+        if (plans[p]->prec != NLP_FP32 || plans[p]->kernel == NLP_POISSON_2D || plans[p]->opts.method != 0)
+            return NLP_ERR_UNSUPPORTED;
     }
     nlp_batch_s *b = new (std::nothrow) nlp_batch_s();
     if (!b) return NLP_ERR_OOM;

@@ -209,8 +209,9 @@ __device__ __forceinline__ void inv_c2r_block(T *__restrict__ phi, const DevPlan
         const cpx<T> z = R[l * ldb + b];
         const int64_t line = 2 * p + which;
         const int i0 = (int)(line / P.n[1]), i1 = (int)(line % P.n[1]);
-        const T v = which == 0 ? z.x : z.y;
-        phi[line * n2 + i] = v * (P.deconv[0][i0] * P.deconv[1][i1] * P.deconv[2][i]);
+        const T v = (which == 0 ? z.x : z.y) * (P.deconv[0][i0] * P.deconv[1][i1] * P.deconv[2][i]);
+        if (P.accumulate) phi[line * n2 + i] += v;
+        else phi[line * n2 + i] = v;
     }
 }
 
@@ -527,8 +528,14 @@ __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const Dev
         else if (l >= lo1) i = l - lo1;
         else return;
         const T d2 = P.deconv[2][i];
-        phi[line0 * n2 + i] = z.x * (fa * d2);
-        phi[line1 * n2 + i] = z.y * (fb * d2);
+        const T va = z.x * (fa * d2), vb = z.y * (fb * d2);
+        if (P.accumulate) {
+            phi[line0 * n2 + i] += va;
+            phi[line1 * n2 + i] += vb;
+        } else {
+            phi[line0 * n2 + i] = va;
+            phi[line1 * n2 + i] = vb;
+        }
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
     fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);

@@ -458,6 +458,7 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     return NLP_OK;
 }
 
+nlp_status build_split(nlp_plan_s *p);
 nlp_status build_toeplitz(nlp_plan_s *p);
 
 static int roundup16(double x) { return (int)(16.0 * std::ceil(x / 16.0)); }
@@ -480,7 +481,22 @@ nlp_status plan_build(nlp_plan_s *p) {
     }
     for (int a = 0; a < d; ++a) R2 += g.L[a] * g.L[a];
     Rp2 = g.L[0] * g.L[0] + g.L[1] * g.L[1];
-    const double P = p->opts.kmax > 0 ? p->opts.kmax : M_PI / hmax;
+    const double Ptrunc = p->opts.kmax > 0 ? p->opts.kmax : M_PI / hmax;
+    // improved algorithm (method 2): the NUFFT part I_2 only needs the ball where the
+    // partition p(k) = exp(-|k|^2/a) is above eps (Eq. (3.9)); I_1 is built after the nodes
+    double P = Ptrunc;
+    if (p->opts.method == 2) {
+        const bool f64 = p->prec == NLP_FP64;
+        const double kappa = f64 ? 5.5 : 3.8, eps = f64 ? 1e-16 : 1e-8;
+        double Lmin = g.L[0];
+        for (int a = 1; a < d; ++a) Lmin = std::min(Lmin, g.L[a]);
+        p->split = 1;
+        p->split_a = (kappa / Lmin) * (kappa / Lmin);
+        p->split_k2 = std::min(Ptrunc, std::sqrt(p->split_a * std::log(1.0 / eps)));
+        P = p->split_k2;
+        p->info.split_a = p->split_a;
+        p->info.split_radius = p->split_k2;
+    }
     int nr = p->opts.n_r, nth = p->opts.n_theta, nph = p->opts.n_phi;
     if (nr <= 0) nr = roundup16(P * std::sqrt(R2) / 2.0 + 16.0);
     if (d == 3 && nth <= 0) nth = nr;
@@ -501,7 +517,7 @@ nlp_status plan_build(nlp_plan_s *p) {
     }
     p->info.width = w;
     p->info.beta_es = beta;
-    p->info.kmax = P;
+    p->info.kmax = Ptrunc;
     p->info.n_r = nr;
     p->info.n_theta = nth;
     p->info.n_phi = nph;
@@ -544,6 +560,7 @@ nlp_status plan_build(nlp_plan_s *p) {
                         J = 3.0 * nk * nk - r[ia] * r[ia];
                     }
                     hn.omega = pref * wr[ia] * wu[ib] * wph * J;
+                    if (p->split) hn.omega *= std::exp(-r[ia] * r[ia] / p->split_a);   // p(k) of Eq. (3.9)
                     for (int a = 0; a < 3; ++a) hn.z[a] = k[a] * p->h[a] * (2.0 * p->n3[a]) / twopi;
                 }
             }
@@ -578,6 +595,7 @@ nlp_status plan_build(nlp_plan_s *p) {
         std::vector<HostNode>().swap(nodes);
         if ((s = build_toeplitz(p))) return s;
     }
+    if (p->opts.method == 2 && (s = build_split(p))) return s;
     p->info.workspace_bytes = p->bytes;
     return NLP_OK;
 }
@@ -602,8 +620,9 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
         if (o->tile != 0 && (o->tile < 2 || o->tile > 32)) return NLP_ERR_INVALID_ARG;
         if (o->spread_variant != 0 && o->spread_variant != 1) return NLP_ERR_INVALID_ARG;
-        if (o->method != 0 && o->method != 1) return NLP_ERR_INVALID_ARG;
+        if (o->method < 0 || o->method > 2) return NLP_ERR_INVALID_ARG;
         if (o->method == 1 && kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+        if (o->method == 2 && g->dim != 3) return NLP_ERR_UNSUPPORTED;
         if (o->method == 1)   // the kernel is built on a 4n-point fine grid
             for (int a = 0; a < g->dim; ++a)
                 if (4 * g->n[a] > kMaxFftLen) return NLP_ERR_UNSUPPORTED;

@@ -36,8 +36,14 @@ struct nlp_plan_s {
     // stage timers (CUDA events on the plan stream), off unless enabled
     int timing = 0;
     int nev = 0;
-    cudaEvent_t ev[16] = {};
-    int ev_stage[16] = {};
+    cudaEvent_t ev[32] = {};
+    int ev_stage[32] = {};
+    // improved algorithm (method 2): I_2 is the NUFFT of pf / pd (small ball), I_1 the FFT
+    // convolution described by pf1 / pd1 (analytic multiplier, accumulating into phi)
+    int split = 0;
+    double split_a = 0, split_k2 = 0;
+    nlp::DevPlan<float> pf1{};
+    nlp::DevPlan<double> pd1{};
 };
 
 namespace nlp {

@@ -73,3 +73,11 @@ def test_null_handles_rejected(nl):
     assert lib.nlp_batch_eval(None, None, None) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_batch_sync(None) == nl.NLP_ERR_INVALID_ARG
     lib.nlp_batch_destroy(None)
+
+
+@pytest.mark.parametrize("kernel,n", [("coulomb2d", (64, 64)), ("poisson2d", (64, 64))])
+def test_split_method_rejects_2d(nl, kernel, n):
+    """method = 2 (the improved algorithm with the Gaussian partition) is 3D only."""
+    with pytest.raises(nl.NlpError) as e:
+        nl.nlp_plan_create(n, (8, 8), kernel, "fp64", method=2, stream=0)
+    assert e.value.status == nl.NLP_ERR_UNSUPPORTED

@@ -217,3 +217,42 @@ def test_2d_full_size_vs_oracle_and_closed_form(nl, kernel, prec):
                                                                               info["nodes_total"]))
     assert err < TOL[prec]
     assert err_cf < (1e-9 if prec == "fp64" else 1e-5)
+
+
+SPLIT = {"fp64": dict(eps=1e-16, kappa=5.5), "fp32": dict(eps=1e-8, kappa=3.8)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel,shape,widths", [
+    ("coulomb3d", ((48, 40, 36), (6.0, 5.0, 5.5)), (1.0, 0.9, 1.2)),
+    ("dipole3d", ((40, 48, 60), (6.0, 7.0, 8.0)), (1.0, 1.3, 1.6))])
+def test_split_method_parity(nl, prec, kernel, shape, widths):
+    """method = 2, the improved algorithm (Sec. 2.1, Eq. (3.9)): I_1 by FFT convolution with the
+    analytic multiplier plus I_2 by the small-ball NUFFT, against the oracle's split evaluation
+    with the same partition parameters; and the node ball really is small."""
+    g = W.Grid(*shape)
+    rho = W.gaussian(g, widths, center=(0.2, -0.1, 0.15))
+    P = quadrature.density_P(min(widths), max(g.h))
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, method=2)
+    ref, parts = potential.evaluate_split(rho, g, kernel, P, return_parts=True, **SPLIT[prec])
+    assert abs(info["split_a"] - parts["a"]) < 1e-12 * parts["a"]
+    assert abs(info["split_radius"] - parts["k2"]) < 1e-12 * parts["k2"]
+    assert cf.rel_linf(phi, ref) < TOL[prec]
+    assert info["split_radius"] < 0.7 * P
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_split_method_full_size(nl, prec):
+    """The benchmark's 128^3 workload through method 2, against the plain FP64 NUFFT of the
+    full ball (the same continuum integral): within the FP64/FP32 parity bars."""
+    g = W.cube(128, 12.0)
+    a = (1.0, math.sqrt(2.0), 2.0)
+    rho = W.gaussian(g, a)
+    P = quadrature.density_P(min(a), g.h[0])
+    phi, info = gpu_eval(nl, g, rho, "coulomb3d", prec, kmax=P, method=2,
+                         tol=1e-12 if prec == "fp64" else 1e-6)
+    ref = potential.eval_nufft(rho, g, "coulomb3d", P, quadrature.default_counts(g.L, P), tol=1e-13)
+    err = cf.rel_linf(phi, ref)
+    print("128^3 split %s: vs plain oracle %.3e, I_2 nodes %d (radius %.3f)" % (prec, err, info["nodes_total"],
+                                                                            info["split_radius"]))
+    assert err < TOL[prec]
