@@ -52,6 +52,23 @@ def workload():
     return g, rho, P, (nr, nr, nph)
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (the replicas' slowest time
+    bounds the whole job); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(world_size: int, units_per_rank: int, t_max: float) -> float:
+    """Throughput of N independent replicas: all ranks' units over the slowest rank's time."""
+    return world_size * units_per_rank / t_max
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -238,9 +255,7 @@ def gpu_arm(args):
     t64 = sum(res64["times"]) / 1e3
     e2e = res32["e2e_s"]
     if ws > 1:
-        tt = torch.tensor([t32, t64, e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t32, t64, e2e = (float(x) for x in tt)
+        t32, t64, e2e = max_over_ranks([t32, t64, e2e], "cuda")
     if rank == 0:
         from oracle import closed_forms as cf
         from oracle import native, potential
@@ -260,7 +275,7 @@ def gpu_arm(args):
         K = args.steps
         line = {
             "metric": METRIC,
-            "value": ws * K / t32,
+            "value": whole_job_rate(ws, K, t32),
             "unit": "evals/s",
             "n_gpus": ws,
             "steps": K,
