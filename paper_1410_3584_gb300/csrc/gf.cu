@@ -25,6 +25,7 @@ enum { S_MIN = 0, S_MAX, S_DIFF, S_NORM, S_CHANGE, S_EPOT, S_EINT, S_EKIN,
 template <typename T> struct Work {
     T *rho, *pot, *b, *x, *xn, *r, *xf;   // xf: inner iterate captured at convergence
     T *d;                                 // last inner update (Chebyshev recurrence)
+    T *dtab;                              // Fourier diagonal of the inner solve (per step)
     int *iflag;                           // [0] first converged inner iteration, [1] first non-finite one
     cpx<T> *spec;       // plain-grid spectrum (R2C half for GF)
     double *part;       // kRedBlocks x 2 partials
@@ -55,6 +56,8 @@ template <typename T> static nlp_status ensure_work(nlp_plan_s *p, Work<T> *&W) 
     W->iflag = (int *)d;
     if ((s = alloc_dev(p, &d, sizeof(cpx<T>) * (size_t)n0 * n1 * nh))) return s;
     W->spec = (cpx<T> *)d;
+    if ((s = alloc_dev(p, &d, sizeof(T) * (size_t)n0 * n1 * nh))) return s;
+    W->dtab = (T *)d;
     if ((s = alloc_dev(p, &d, sizeof(double) * 2 * kRedBlocks))) return s;
     W->part = (double *)d;
     if ((s = alloc_dev(p, &d, sizeof(double) * S_COUNT))) return s;
@@ -154,10 +157,11 @@ __device__ __forceinline__ double wave2(int l, int n, double L) {
     return mu * mu;
 }
 
-// spec *= 1 / ((1/tau + alpha + |mu|^2/2) N) on the R2C half spectrum [n0][n1][nh]
+// dtab = 1 / ((1/tau + alpha + |mu|^2/2) N) on the R2C half spectrum [n0][n1][nh]: the Fourier
+// diagonal of the inner solve, fixed for one gradient-flow step (alpha from device scalars)
 template <typename T>
-__global__ void k_diag(cpx<T> *spec, int n0, int n1, int n2, int nh, double L0, double L1, double L2,
-                       double inv_tau, const double *scal, double invN) {
+__global__ void k_diag_table(T *dtab, int n0, int n1, int n2, int nh, double L0, double L1, double L2,
+                             double inv_tau, const double *scal, double invN) {
     const double alpha = 0.5 * (scal[S_MIN] + scal[S_MAX]);
     const int64_t M = (int64_t)n0 * n1 * nh;
     GRID_STRIDE(q, M) {
@@ -166,9 +170,13 @@ __global__ void k_diag(cpx<T> *spec, int n0, int n1, int n2, int nh, double L0, 
         const int l1 = (int)(t % n1), l0 = (int)(t / n1);
         double m2 = (n2 > 1 ? wave2(l2, n2, L2) : 0.0) + (n1 > 1 ? wave2(l1, n1, L1) : 0.0) +
                     (n0 > 1 ? wave2(l0, n0, L0) : 0.0);
-        const T f = (T)(invN / (inv_tau + alpha + 0.5 * m2));
-        spec[q] = scale(spec[q], f);
+        dtab[q] = (T)(invN / (inv_tau + alpha + 0.5 * m2));
     }
+}
+
+// spec *= dtab (one inner iteration's Fourier-diagonal solve)
+template <typename T> __global__ void k_diag_apply(cpx<T> *spec, const T *__restrict__ dtab, int64_t M) {
+    GRID_STRIDE(q, M) spec[q] = scale(spec[q], dtab[q]);
 }
 
 
@@ -397,12 +405,14 @@ static nlp_status gf_step_t(nlp_plan_s *p, T *phi, const T *V, double beta, doub
     constexpr int kCheckEvery = 4;
     if (cudaMemsetAsync(W->iflag, 0, sizeof(int) * 2, st)) return NLP_ERR_CUDA;
     k_cheb_init<<<1, 1, 0, st>>>(W->scal, 1.0 / tau);
+    const int64_t Mspec = (int64_t)D.n[0] * D.n[1] * D.nh;
+    k_diag_table<T><<<eg(), 256, 0, st>>>(W->dtab, D.n[0], D.n[1], D.n[2], D.nh, p->L3[0], p->L3[1], p->L3[2],
+                                          1.0 / tau, W->scal, 1.0 / (double)N);
     int flags[2] = {0, 0};
     for (int it = 1; it <= max_inner; ++it) {
         k_rhs<T><<<eg(), 256, 0, st>>>(phi, W->b, W->x, (T)(1.0 / tau), W->scal, W->r, N);
         if (r2c_plain<T>(W->r, D, st)) return NLP_ERR_CUDA;
-        k_diag<T><<<eg(), 256, 0, st>>>(D.F, D.n[0], D.n[1], D.n[2], D.nh, p->L3[0], p->L3[1], p->L3[2], 1.0 / tau,
-                                        W->scal, 1.0 / (double)N);
+        k_diag_apply<T><<<eg(), 256, 0, st>>>(D.F, W->dtab, Mspec);
         if (c2r_plain<T>(W->xn, D, st)) return NLP_ERR_CUDA;
         k_cheb_update<T><<<eg(), 256, 0, st>>>(W->x, W->xn, W->d, W->scal, it, N, W->part);
         if ((s = reduce_to(p, W, 0, 1, 1.0, S_DIFF))) return s;
