@@ -96,3 +96,30 @@ def poisson2d_iso(r, s):
 def rel_linf(u, ref):
     """Relative L-infinity error e_h of Eq. (error_infty)."""
     return float(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))
+
+
+def confined2d_W1(k, eps):
+    """W_1(k) = |k| U-hat_Con(k) of the 2D confined Coulomb kernel (Eqs. (Kernal124d), (2Dw1)):
+    (2/pi) int_0^inf exp(-eps^2 k^2 s^2 / 2) / (1 + s^2) ds = exp(a) erfc(sqrt(a)), a = eps^2 k^2 / 2,
+    i.e. erfcx(eps |k| / sqrt 2) (the integral of exp(-a s^2)/(1 + s^2) is a classical one)."""
+    return special.erfcx(eps * np.asarray(k, dtype=np.float64) / math.sqrt(2.0))
+
+
+def confined2d_W1_quad(k, eps):
+    """The same integral by adaptive quadrature (the paper's route, Gauss-Kronrod)."""
+    from scipy import integrate
+    f = lambda s: math.exp(-0.5 * (eps * k * s) ** 2) / (1.0 + s * s)
+    return 2.0 / math.pi * integrate.quad(f, 0.0, np.inf, epsabs=1e-15, epsrel=1e-14, limit=400)[0]
+
+
+def confined2d_gaussian(r, sigma, eps):
+    """Confined Coulomb potential of rho = exp(-|x|^2 / sigma^2) in 2D, by the radial inverse
+    transform phi(r) = (2 pi)^{-1} int_0^inf W_1(k) rho-hat(k) J_0(k r) dk with
+    rho-hat(k) = pi sigma^2 exp(-sigma^2 k^2 / 4) (adaptive quadrature, one radius at a time)."""
+    from scipy import integrate
+    out = np.empty(np.shape(r))
+    for i, rr in enumerate(np.ravel(r)):
+        f = lambda k: float(confined2d_W1(k, eps)) * math.exp(-0.25 * sigma * sigma * k * k) * special.j0(k * rr)
+        kmax = 2.0 * math.sqrt(math.log(1e18)) / sigma
+        out.flat[i] = 0.5 * sigma * sigma * integrate.quad(f, 0.0, kmax, epsabs=1e-15, epsrel=1e-13, limit=800)[0]
+    return out

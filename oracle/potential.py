@@ -11,6 +11,8 @@ U-hat(k) the Jacobian-weighted symbol:
                the dipolar kernel; this is the standard form of the cited works)
                J = 3 (n.k)^2 - |k|^2
     poisson2d  U-hat = 1/|k|^2 in 2D: Algorithm 1 (Sec. 2.2, Eqs. (GG1)-(phi2fourier)).
+    confined2d the 2D confined Coulomb kernel of Eq. (Kernal124d) with parameter eps:
+               J = W_1(|k|) of Eq. (2Dw1) (closed_forms.confined2d_W1)
 Real part: phi is real; with the symmetric node set the imaginary part is rounding.
 """
 from __future__ import annotations
@@ -25,11 +27,11 @@ from . import nufft, quadrature
 
 EULER_GAMMA = 0.57721566490153286061
 
-KERNELS = ("coulomb3d", "dipole3d", "coulomb2d", "poisson2d")
-DIM = {"coulomb3d": 3, "dipole3d": 3, "coulomb2d": 2, "poisson2d": 2}
+KERNELS = ("coulomb3d", "dipole3d", "coulomb2d", "poisson2d", "confined2d")
+DIM = {"coulomb3d": 3, "dipole3d": 3, "coulomb2d": 2, "poisson2d": 2, "confined2d": 2}
 
 
-def node_set(kernel: str, P: float, counts, dipole_axis=(0.0, 0.0, 1.0)):
+def node_set(kernel: str, P: float, counts, dipole_axis=(0.0, 0.0, 1.0), eps: float = 0.0):
     """Nodes k (M x d), plain weights wq, radii r, and Jacobian-weighted
     weights wq * J(k) (for poisson2d J is applied inside Algorithm 1)."""
     if DIM[kernel] == 3:
@@ -42,7 +44,11 @@ def node_set(kernel: str, P: float, counts, dipole_axis=(0.0, 0.0, 1.0)):
             J = 3.0 * (k @ nv) ** 2 - r * r
     else:
         k, wq, r = quadrature.polar_rule(P, *counts)
-        J = np.ones_like(r)
+        if kernel == "confined2d":
+            from .closed_forms import confined2d_W1
+            J = confined2d_W1(r, eps)
+        else:
+            J = np.ones_like(r)
     return k, wq, r, wq * J
 
 
@@ -108,7 +114,7 @@ def poisson2d(rho, grid, P, counts, method="nufft", tol=1e-13, sigma=None, retur
 
 
 def evaluate(rho, grid, kernel, P, counts=None, method="nufft", tol=1e-13,
-             dipole_axis=(0.0, 0.0, 1.0)):
+             dipole_axis=(0.0, 0.0, 1.0), eps=0.0):
     """phi = U * rho on the grid (Eq. (ifft) quadrature; Algorithm 1 for poisson2d)."""
     if counts is None:
         counts = quadrature.default_counts(grid.L, P)
@@ -116,7 +122,7 @@ def evaluate(rho, grid, kernel, P, counts=None, method="nufft", tol=1e-13,
         return poisson2d(rho, grid, P, counts, method=method, tol=tol)
     t2, t1 = _transforms(method, tol)
     d = grid.dim
-    k, wq, r, wj = node_set(kernel, P, counts, dipole_axis)
+    k, wq, r, wj = node_set(kernel, P, counts, dipole_axis, eps)
     rh = t2(rho, grid.h, k)
     c = wj * rh / (2.0 * math.pi) ** d
     return t1(c, k, grid.n, grid.h)
@@ -202,13 +208,13 @@ class ConvolutionOperator:
     evaluations are needed (gradient flow, time splitting)."""
 
     def __init__(self, grid, kernel, P, counts=None, method="nufft", tol=1e-13,
-                 dipole_axis=(0.0, 0.0, 1.0)):
+                 dipole_axis=(0.0, 0.0, 1.0), eps=0.0):
         assert kernel != "poisson2d"
         if counts is None:
             counts = quadrature.default_counts(grid.L, P)
         d = grid.dim
         self.grid = grid
-        k, wq, r, wj = node_set(kernel, P, counts, dipole_axis)
+        k, wq, r, wj = node_set(kernel, P, counts, dipole_axis, eps)
         n2 = [2 * v for v in grid.n]
         c = wj * float(np.prod(grid.h)) / (2.0 * math.pi) ** d
         if method == "direct":

@@ -268,3 +268,33 @@ def test_split_planted_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(potential, "split_multiplier", no_partition)
     bad = potential.evaluate_split(rho, g, "coulomb3d", P)
     assert cf.rel_linf(bad, good) > 1e-2
+
+
+@pytest.mark.parametrize("k,eps", [(0.0, 0.3), (0.4, 0.1), (3.0, 0.5), (25.0, 0.2), (60.0, 1.0)])
+def test_confined2d_W1_closed_form_vs_quadrature(k, eps):
+    """Eq. (2Dw1): the closed form exp(a) erfc(sqrt a) equals the defining integral (adaptive
+    quadrature, the paper's route); W_1(0) = 1."""
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        q = cf.confined2d_W1_quad(k, eps)
+    assert abs(float(cf.confined2d_W1(k, eps)) - q) < 1e-13
+
+
+def test_confined2d_potential_vs_radial_integral_and_coulomb_limit():
+    """2D confined Coulomb (Eq. (Kernal124d)) through the quadrature of Eq. (ifft2d): the
+    potential of a Gaussian equals its radial inverse transform (adaptive quadrature); at
+    eps = 0 the kernel is the 2D Coulomb one (identical weights, identical potential)."""
+    g = W.cube(128, 12.0, dim=2)
+    s, eps = 1.5, 0.3
+    rho = W.gaussian(g, [s, s])
+    P = quadrature.density_P(s, g.h[0])
+    phi = potential.evaluate(rho, g, "confined2d", P, eps=eps)
+    X, Y = g.mesh()
+    sl = (slice(None, None, 9), slice(None, None, 11))
+    ex = cf.confined2d_gaussian(np.sqrt(X * X + Y * Y)[sl], s, eps)
+    assert cf.rel_linf(phi[sl], ex) < 1e-12
+    phi0 = potential.evaluate(rho, g, "confined2d", P, eps=0.0)
+    assert np.array_equal(phi0, potential.evaluate(rho, g, "coulomb2d", P))
+    # the confinement weakens the interaction at large |k|: phi decreases with eps
+    assert np.max(phi) < np.max(phi0)
