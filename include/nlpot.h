@@ -53,8 +53,17 @@ typedef enum {
  *   NLP_DIPOLE_3D   U-hat = 3 (n.k)^2/|k|^2 - 1 for dipole axis n (the paper names the
  *                   dipolar kernel without writing it; this is the standard form)
  *   NLP_COULOMB_2D  U = 1/(2 pi |x|),      U-hat = 1/|k|
- *   NLP_POISSON_2D  U = -ln|x| / (2 pi),   U-hat = 1/|k|^2 (Algorithm 1)                  */
-typedef enum { NLP_COULOMB_3D = 0, NLP_DIPOLE_3D = 1, NLP_COULOMB_2D = 2, NLP_POISSON_2D = 3 } nlp_kernel;
+ *   NLP_POISSON_2D  U = -ln|x| / (2 pi),   U-hat = 1/|k|^2 (Algorithm 1)
+ *   NLP_CONFINED_2D the 2D confined Coulomb kernel of Eq. (Kernal124d) with parameter
+ *                   eps = nlp_opts.confine_eps >= 0: |k| U-hat = W_1(|k|) of Eq. (2Dw1),
+ *                   = exp(a) erfc(sqrt a), a = eps^2 |k|^2 / 2 (eps = 0: NLP_COULOMB_2D)    */
+typedef enum {
+    NLP_COULOMB_3D = 0,
+    NLP_DIPOLE_3D = 1,
+    NLP_COULOMB_2D = 2,
+    NLP_POISSON_2D = 3,
+    NLP_CONFINED_2D = 4
+} nlp_kernel;
 
 typedef enum { NLP_FP64 = 0, NLP_FP32 = 1 } nlp_precision;
 
@@ -91,6 +100,7 @@ typedef struct {
                                (5.5, 1e-16) for FP64 and (3.8, 1e-8) for FP32 plans.  Default counts
                                then follow from k2 instead of P.  2D kernels: NLP_ERR_UNSUPPORTED. */
     int reserved[5];        /* must be zero */
+    double confine_eps;     /* NLP_CONFINED_2D: the confinement ratio eps >= 0 (else ignored) */
 } nlp_opts;
 
 typedef struct nlp_plan_s *nlp_plan;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libnlpot.so")
 
 NLP_OK, NLP_ERR_INVALID_ARG, NLP_ERR_UNSUPPORTED, NLP_ERR_OOM = 0, 1, 2, 3
 NLP_ERR_CUDA, NLP_ERR_TIMEOUT, NLP_ERR_DIVERGED, NLP_ERR_NOT_CONVERGED = 4, 5, 6, 7
-KERNELS = {"coulomb3d": 0, "dipole3d": 1, "coulomb2d": 2, "poisson2d": 3}
+KERNELS = {"coulomb3d": 0, "dipole3d": 1, "coulomb2d": 2, "poisson2d": 3, "confined2d": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 
 
@@ -28,7 +28,8 @@ class nlp_grid(ctypes.Structure):
 class nlp_opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_double), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
                 ("n_phi", ctypes.c_int), ("dipole_axis", ctypes.c_double * 3), ("nufft_tol", ctypes.c_double),
-                ("tile", ctypes.c_int), ("spread_variant", ctypes.c_int), ("method", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("tile", ctypes.c_int), ("spread_variant", ctypes.c_int), ("method", ctypes.c_int), ("reserved", ctypes.c_int * 5),
+                ("confine_eps", ctypes.c_double)]
 
 
 class nlp_plan_info(ctypes.Structure):
@@ -128,7 +129,7 @@ def _stream_handle(stream):
 
 
 def _grid_opts(n, L, kmax=0.0, counts=None, dipole_axis=(0.0, 0.0, 0.0), tol=0.0, tile=0, spread_variant=0,
-               method=0):
+               method=0, eps=0.0):
     g = nlp_grid()
     g.dim = len(n)
     for a in range(len(n)):
@@ -147,14 +148,15 @@ def _grid_opts(n, L, kmax=0.0, counts=None, dipole_axis=(0.0, 0.0, 0.0), tol=0.0
     o.tile = int(tile)
     o.spread_variant = int(spread_variant)
     o.method = int(method)
+    o.confine_eps = float(eps)
     return g, o
 
 
 def nlp_plan_create(n, L, kernel: str, precision: str = "fp64", kmax: float = 0.0, counts=None,
                     dipole_axis=(0.0, 0.0, 0.0), tol: float = 0.0, tile: int = 0, spread_variant: int = 0,
-                    method: int = 0, stream=None):
+                    method: int = 0, stream=None, eps: float = 0.0):
     """Create a plan; returns an opaque handle (ctypes.c_void_p).  See nlpot.h."""
-    g, o = _grid_opts(n, L, kmax, counts, dipole_axis, tol, tile, spread_variant, method)
+    g, o = _grid_opts(n, L, kmax, counts, dipole_axis, tol, tile, spread_variant, method, eps)
     h = ctypes.c_void_p()
     _check(_lib.nlp_plan_create(ctypes.byref(g), KERNELS[kernel], PRECISIONS[precision], ctypes.byref(o),
                                 _stream_handle(stream), ctypes.byref(h)), "nlp_plan_create")

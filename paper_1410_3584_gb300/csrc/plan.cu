@@ -143,6 +143,16 @@ template <typename T> nlp_status make_fft_len(nlp_plan_s *p, int N, FftLen<T> *o
 template nlp_status make_fft_len<float>(nlp_plan_s *, int, FftLen<float> *);
 template nlp_status make_fft_len<double>(nlp_plan_s *, int, FftLen<double> *);
 
+// W_1 of the 2D confined Coulomb kernel at eps |k| = t: (2/pi) int_0^inf exp(-t^2 s^2 / 2) / (1 + s^2) ds
+// = exp(a) erfc(sqrt a) with a = t^2 / 2 (a classical integral); for large arguments the
+// asymptotic series of exp(x^2) erfc(x), x = t / sqrt 2, avoids overflow
+static double confined_w1(double t) {
+    const double x = t / std::sqrt(2.0);
+    if (x < 20.0) return std::exp(x * x) * std::erfc(x);
+    const double y = 1.0 / (2.0 * x * x);
+    return (1.0 - y * (1.0 - 3.0 * y * (1.0 - 5.0 * y * (1.0 - 7.0 * y)))) / (x * std::sqrt(M_PI));
+}
+
 static bool good_len(int n) {
     if (n < 1) return false;
     while (n % 2 == 0) n /= 2;
@@ -573,6 +583,8 @@ nlp_status plan_build(nlp_plan_s *p) {
                 const double k[2] = {r[ia] * cph[ic], r[ia] * sph[ic]};
                 if (p->kernel == NLP_POISSON_2D)       // W(k) form of Algorithm 1; h^2 applied in-kernel
                     hn.omega = wr[ia] * wph / (twopi * twopi * r[ia]);
+                else if (p->kernel == NLP_CONFINED_2D) // |k| U-hat = W_1(|k|), Eq. (2Dw1)
+                    hn.omega = pref * wr[ia] * wph * confined_w1(p->opts.confine_eps * r[ia]);
                 else
                     hn.omega = pref * wr[ia] * wph;    // Coulomb 2D: |k| U-hat = 1
                 hn.z[0] = 0.0;
@@ -604,8 +616,11 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
     if (!g) return NLP_ERR_INVALID_ARG;
     if (g->dim != 2 && g->dim != 3) return NLP_ERR_INVALID_ARG;
     if ((kernel == NLP_COULOMB_3D || kernel == NLP_DIPOLE_3D) && g->dim != 3) return NLP_ERR_INVALID_ARG;
-    if ((kernel == NLP_COULOMB_2D || kernel == NLP_POISSON_2D) && g->dim != 2) return NLP_ERR_INVALID_ARG;
-    if ((int)kernel < 0 || (int)kernel > 3) return NLP_ERR_INVALID_ARG;
+    if ((kernel == NLP_COULOMB_2D || kernel == NLP_POISSON_2D || kernel == NLP_CONFINED_2D) && g->dim != 2)
+        return NLP_ERR_INVALID_ARG;
+    if ((int)kernel < 0 || (int)kernel > 4) return NLP_ERR_INVALID_ARG;
+    if (kernel == NLP_CONFINED_2D && o && !(o->confine_eps >= 0.0 && std::isfinite(o->confine_eps)))
+        return NLP_ERR_INVALID_ARG;
     if (prec != NLP_FP64 && prec != NLP_FP32) return NLP_ERR_INVALID_ARG;
     for (int a = 0; a < g->dim; ++a) {
         const int n = g->n[a];

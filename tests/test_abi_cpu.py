@@ -81,3 +81,12 @@ def test_split_method_rejects_2d(nl, kernel, n):
     with pytest.raises(nl.NlpError) as e:
         nl.nlp_plan_create(n, (8, 8), kernel, "fp64", method=2, stream=0)
     assert e.value.status == nl.NLP_ERR_UNSUPPORTED
+
+
+def test_confined2d_rejects_negative_eps_and_3d(nl):
+    with pytest.raises(nl.NlpError) as e:
+        nl.nlp_plan_create((64, 64), (8, 8), "confined2d", "fp64", eps=-0.1, stream=0)
+    assert e.value.status == nl.NLP_ERR_INVALID_ARG
+    with pytest.raises(nl.NlpError) as e:
+        nl.nlp_plan_create((32, 32, 32), (8, 8, 8), "confined2d", "fp64", eps=0.1, stream=0)
+    assert e.value.status == nl.NLP_ERR_INVALID_ARG

@@ -256,3 +256,19 @@ def test_split_method_full_size(nl, prec):
     print("128^3 split %s: vs plain oracle %.3e, I_2 nodes %d (radius %.3f)" % (prec, err, info["nodes_total"],
                                                                             info["split_radius"]))
     assert err < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("eps", [0.1, 0.5])
+def test_confined2d_parity(nl, prec, method, eps):
+    """2D confined Coulomb (Eq. (Kernal124d), W_1 of Eq. (2Dw1)) through both evaluation
+    methods against the oracle's quadrature with the same nodes and the same W_1."""
+    g = W.Grid((96, 80), (10.0, 9.0))
+    cs, ws = W.three_gaussians_2d(11)
+    rho = W.gaussian_sum(g, [(0.4 * c[0], 0.4 * c[1]) for c in cs], ws)
+    P = quadrature.density_P(min(ws), max(g.h))
+    counts = quadrature.default_counts(g.L, P)
+    phi, info = gpu_eval(nl, g, rho, "confined2d", prec, kmax=P, counts=counts, method=method, eps=eps)
+    ref = potential.eval_nufft(rho, g, "confined2d", P, counts, tol=1e-13, eps=eps)
+    assert cf.rel_linf(phi, ref) < TOL[prec]
