@@ -27,7 +27,7 @@ namespace nlp {
 
 template <int W> struct RegCfg {
     static constexpr int TT = ((W * W + 31) / 32) * 32;       // threads per team
-    static constexpr int NT = (256 / TT) > 0 ? (256 / TT) : 1; // teams per CTA
+    static constexpr int NT = (512 / TT) > 0 ? (512 / TT) : 1; // teams per CTA (share the tile window)
     static constexpr int TW = TT / 32;                         // warps per team
 };
 
@@ -68,15 +68,22 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
         const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
         const int colbase = ((so0 + cx) * Wt1 + (so1 + cy)) * Wt2 + so2;
-        T fx[W], fy[W], gx[W], gy[W];
+        // FP32 keeps the F column in registers; FP64 reads it from shared memory per node,
+        // which halves the column registers so that more than one team fits on an SM
+        constexpr bool kFRegs = sizeof(T) == 4;
+        constexpr int WF = kFRegs ? W : 1;
+        T fx[WF], fy[WF], gx[W], gy[W];
 #pragma unroll
         for (int z = 0; z < W; ++z) {
-            const cpx<T> f = active ? sF[colbase + z] : mk<T>(0, 0);
-            fx[z] = f.x;
-            fy[z] = f.y;
+            if constexpr (kFRegs) {
+                const cpx<T> f = active ? sF[colbase + z] : mk<T>(0, 0);
+                fx[z] = f.x;
+                fy[z] = f.y;
+            }
             gx[z] = (T)0;
             gy[z] = (T)0;
         }
+        const cpx<T> *fcol = sF + (active ? colbase : 0);
         for (int jb = j0; jb < j1; jb += NB) {
             const int nb = min(NB, j1 - jb);
             // kernel values of the batch: a contiguous block of the plan-time table
@@ -99,8 +106,14 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
                     load_row<T, W>(pk + 2 * W, pzv);
 #pragma unroll
                     for (int z = 0; z < W; ++z) {
-                        sx += fx[z] * pzv[z];
-                        sy += fy[z] * pzv[z];
+                        if constexpr (kFRegs) {
+                            sx += fx[z] * pzv[z];
+                            sy += fy[z] * pzv[z];
+                        } else {
+                            const cpx<T> f = fcol[z];
+                            sx += f.x * pzv[z];
+                            sy += f.y * pzv[z];
+                        }
                     }
                     if (active) {
                         v[2 * k] = wxy * sx;
