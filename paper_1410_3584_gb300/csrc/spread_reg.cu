@@ -179,7 +179,7 @@ template <typename T> bool reg_kernel_supported(int W) {
     return sizeof(T) == 8 ? (W >= 9 && W <= 16) : (W >= 5 && W <= 11);
 }
 
-template <typename T> static constexpr int nb_of() { return 4; }   // nodes per batch (register budget)
+template <typename T> static constexpr int nb_of() { return sizeof(T) == 8 ? 8 : 4; }   // nodes per batch (register budget)
 
 template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
     const size_t WW = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
