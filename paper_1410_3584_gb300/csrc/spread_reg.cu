@@ -25,6 +25,8 @@
 
 namespace nlp {
 
+constexpr int kWarpBlock = 128;   // threads per CTA of the one-warp-per-piece kernel
+
 template <int W> struct RegCfg {
     static constexpr int TT = ((W * W + 31) / 32) * 32;       // threads per team
     static constexpr int NT = (512 / TT) > 0 ? (512 / TT) : 1; // teams per CTA (share the tile window)
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
 }
 
 template <typename T, int W, int NB>
-__global__ void __launch_bounds__(256) k_interp_spread_warp(DevPlan<T> P) {
+__global__ void __launch_bounds__(kWarpBlock) k_interp_spread_warp(DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     spread_warp_block<T, W, NB>(P, blockIdx.x, smraw);
 }
@@ -197,8 +199,10 @@ template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cu
     const size_t sm = reg_smem<T, W>(P);
     if constexpr (W * W <= 64) {
         cudaError_t e = allow_smem<k_interp_spread_warp<T, W, NB>>();
+        if (e == cudaSuccess)   // several small blocks per SM, each with its own tile window
+            e = cudaFuncSetAttribute(k_interp_spread_warp<T, W, NB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        k_interp_spread_warp<T, W, NB><<<(unsigned)P.nrchunks, 256, sm, st>>>(P);
+        k_interp_spread_warp<T, W, NB><<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
         return cudaGetLastError();
     }
     cudaError_t e =
