@@ -60,6 +60,7 @@ template <typename T, int W> __device__ __forceinline__ void load_row(const T *p
     }
 }
 
+template <bool B> struct BoolC { static constexpr bool value = B; };
 template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
 template <> struct Log2<1> { static constexpr int value = 0; };
 
@@ -187,10 +188,11 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
     __syncthreads();
 
     const int ca = lane, cbc = lane + 32;
-    const bool act_b = cbc < W * W;
-    const int xa = ca % W, ya = ca / W;                 // W*W > 32 for W >= 6: column a always active
+    // W*W > 32 for W >= 6: column a always active; W = 8: both columns of every lane
+    const bool act_a = (W * W >= 32) || ca < W * W;
+    const bool act_b = (W * W == 64) || cbc < W * W;
+    const int xa = ca % W, ya = ca / W;
     const int xb = act_b ? cbc % W : 0, yb = act_b ? cbc / W : 0;
-    const bool act_a = ca < W * W;
     // pieces are sorted heaviest first; each warp takes the next free one
     for (int sg = ch.j0 + warp; sg < ch.j1;) {
         const uint32_t so = P.seg_sub[sg];
@@ -220,23 +222,16 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
             }
             wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : (T)0;
         };
-        fetch(j0, min(NB, j1 - j0));
-        for (int jb = j0; jb < j1; jb += NB) {
-            const int nb = min(NB, j1 - jb);
-#pragma unroll
-            for (int u = 0; u < PQ; ++u) {
-                const int q = lane + 32 * u;
-                if (q < NB * 3 * W) psi[q] = pf[u];
-            }
-            const T wcur = wf;
-            __syncwarp();
-            if (jb + NB < j1) fetch(jb + NB, min(NB, j1 - jb - NB));
+        // one batch of nodes; FULL (nb == NB) runs without per-node guards so that the
+        // independent FMA chains of the batch's nodes interleave
+        auto batch = [&](auto full_tag, int nb, T wcur) {
+            constexpr bool FULL = decltype(full_tag)::value;
             T v[V], wa[NB], wb[NB];
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 v[2 * k] = v[2 * k + 1] = (T)0;
                 wa[k] = wb[k] = (T)0;
-                if (k < nb) {
+                if (FULL || k < nb) {
                     const T *pk = psi + k * 3 * W;
                     wa[k] = act_a ? pk[xa] * pk[W + ya] : (T)0;
                     wb[k] = act_b ? pk[xb] * pk[W + yb] : (T)0;
@@ -260,12 +255,12 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 const int idx = (lane >> SH) & (V - 1);
                 const int k = idx >> 1;
                 const T wk = __shfl_sync(0xffffffffu, wcur, k);   // weight of node k of the batch
-                if ((lane & ((1 << SH) - 1)) == 0) cb[idx] = (k < nb) ? v[0] * wk : (T)0;
+                if ((lane & ((1 << SH) - 1)) == 0) cb[idx] = (FULL || k < nb) ? v[0] * wk : (T)0;
             }
             __syncwarp();
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                if (k < nb) {
+                if (FULL || k < nb) {
                     const T *pk = psi + k * 3 * W;
                     const T cr = cb[2 * k], ci = cb[2 * k + 1];
                     const T ar = cr * wa[k], ai = ci * wa[k], br = cr * wb[k], bi = ci * wb[k];
@@ -281,17 +276,35 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                     }
                 }
             }
+        };
+        fetch(j0, min(NB, j1 - j0));
+        for (int jb = j0; jb < j1; jb += NB) {
+            const int nb = min(NB, j1 - jb);
+#pragma unroll
+            for (int u = 0; u < PQ; ++u) {
+                const int q = lane + 32 * u;
+                if (q < NB * 3 * W) psi[q] = pf[u];
+            }
+            const T wcur = wf;
+            __syncwarp();
+            if (jb + NB < j1) fetch(jb + NB, min(NB, j1 - jb - NB));
+            if (nb == NB)
+                batch(BoolC<true>{}, nb, wcur);
+            else
+                batch(BoolC<false>{}, nb, wcur);
             __syncwarp();
         }
+        // overlapping windows of the block's warps: shared-memory atomics (zeros included: a
+        // zero test per cell costs more than the add it would skip)
 #pragma unroll
         for (int z = 0; z < W; ++z) {
             if (act_a) {
-                if (gax[z] != (T)0) atomicAdd(&sG[basea + z].x, gax[z]);
-                if (gay[z] != (T)0) atomicAdd(&sG[basea + z].y, gay[z]);
+                atomicAdd(&sG[basea + z].x, gax[z]);
+                atomicAdd(&sG[basea + z].y, gay[z]);
             }
             if (act_b) {
-                if (gbx[z] != (T)0) atomicAdd(&sG[baseb + z].x, gbx[z]);
-                if (gby[z] != (T)0) atomicAdd(&sG[baseb + z].y, gby[z]);
+                atomicAdd(&sG[baseb + z].x, gbx[z]);
+                atomicAdd(&sG[baseb + z].y, gby[z]);
             }
         }
         int nxt = 0;
