@@ -156,6 +156,13 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
     }
 }
 
+// Shared memory of the warp kernel: F and G windows (z pitch Wt2 + 1), kernel values and
+// reduced values of up to kWarpSlots warps, then the two row tables of the window.
+constexpr int kWarpSlots = 8;
+template <typename T, int W, int NB> __host__ __device__ constexpr size_t warp_win_table_offset(size_t WWp) {
+    return align16(2 * WWp * sizeof(cpx<T>) + (size_t)kWarpSlots * (NB * 3 * W + 2 * NB) * sizeof(T));
+}
+
 // One warp per segment (W*W <= 64): lane L owns the z-columns L and L + 32 of the sub-window,
 // so interpolation sums reduce inside the warp and the node loop needs no block barrier.
 template <typename T, int W, int NB>
@@ -165,7 +172,6 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
     constexpr int SH = 5 - Log2<V>::value;
     const int w = P.w;
     const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
-    const int WW = Wt0 * Wt1 * Wt2;
     // window cells (a, b, c) at (a Wt1 + b) P2 + c with the z pitch padded by one cell: with
     // x fastest across the lanes, the 8-byte column accesses of a warp (tile 8, w 7: pitches
     // 210 and 15 cells) hit every bank pair exactly twice
@@ -175,16 +181,16 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     T *psi = (T *)(sG + WWp) + warp * (NB * 3 * W + V);
     T *cb = psi + NB * 3 * W;
+    const int rows = Wt0 * Wt1;
+    int64_t *rowoff = (int64_t *)(smraw + warp_win_table_offset<T, W, NB>(WWp)), *rowmir = rowoff + rows;
     const Chunk ch = P.rchunks[bid];
     __shared__ int next_seg;
     if (threadIdx.x == 0) next_seg = ch.j0 + nwarps;
 
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        const int cell = t * P2 + c;
-        sF[cell] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
-        sG[cell] = mk<T>(0, 0);
-    }
+    window_row_table(P, ch, Wt0, Wt1, rowoff, rowmir);
+    const WinCol wc = window_col(P, ch, Wt2, rows);
+    __syncthreads();
+    window_fill(P, wc, rowoff, rowmir, rows, P2, sF, sG);
     __syncthreads();
 
     const int ca = lane, cbc = lane + 32;
@@ -312,12 +318,7 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
         sg = __shfl_sync(0xffffffffu, nxt, 0);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        const cpx<T> v = sG[t * P2 + c];
-        if (v.x == (T)0 && v.y == (T)0) continue;
-        store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
-    }
+    window_fold(P, wc, rowoff, rowmir, rows, P2, sG);
 }
 
 }  // namespace nlp

@@ -37,6 +37,13 @@ __device__ __forceinline__ void team_sync(int team, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(nthreads) : "memory");
 }
 
+// Shared memory of the team kernel: F and G windows, per-team kernel values, partial sums and
+// scaled values, then the two row tables of the window.
+template <typename T, int W, int NB> __host__ __device__ constexpr size_t reg_win_table_offset(size_t WW) {
+    return align16(2 * WW * sizeof(cpx<T>) +
+                   (size_t)RegCfg<W>::NT * (NB * 3 * W + RegCfg<W>::TW * 2 * NB + 2 * NB) * sizeof(T));
+}
+
 template <typename T, int W, int NB>
 __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_reg(DevPlan<T> P) {
     constexpr int TT = RegCfg<W>::TT, TW = RegCfg<W>::TW;
@@ -54,12 +61,13 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
     T *red = psi + NB * 3 * W;
     T *cbuf = red + TW * V;
     const Chunk ch = P.rchunks[blockIdx.x];
+    const int rows = Wt0 * Wt1;
+    int64_t *rowoff = (int64_t *)(smraw + reg_win_table_offset<T, W, NB>(WW)), *rowmir = rowoff + rows;
 
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        sF[q] = load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
-        sG[q] = mk<T>(0, 0);
-    }
+    window_row_table(P, ch, Wt0, Wt1, rowoff, rowmir);
+    const WinCol wc = window_col(P, ch, Wt2, rows);
+    __syncthreads();
+    window_fill(P, wc, rowoff, rowmir, rows, Wt2, sF, sG);
     __syncthreads();
 
     const bool active = tl < W * W;
@@ -161,12 +169,7 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const cpx<T> v = sG[q];
-        if (v.x == (T)0 && v.y == (T)0) continue;
-        const int c = q % Wt2, t = q / Wt2, b = t % Wt1, a = t / Wt1;
-        store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
-    }
+    window_fold(P, wc, rowoff, rowmir, rows, Wt2, sG);
 }
 
 template <typename T, int W, int NB>
@@ -186,12 +189,12 @@ template <typename T> static constexpr int nb_of() { return sizeof(T) == 8 ? 8 :
 template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
     const size_t WW = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
     constexpr int NB = nb_of<T>();
+    const size_t rows = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1);
     if constexpr (W * W <= 64) {   // warp kernel: z pitch padded by one cell
-        const size_t WWp = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w);
-        return 2 * WWp * sizeof(cpx<T>) + 8 * (NB * 3 * W + 2 * NB) * sizeof(T);
+        const size_t WWp = rows * (P.T_tile[2] + P.w);
+        return warp_win_table_offset<T, W, NB>(WWp) + 2 * rows * sizeof(int64_t);
     }
-    return 2 * WW * sizeof(cpx<T>) +
-           (size_t)RegCfg<W>::NT * (NB * 3 * W + RegCfg<W>::TW * 2 * NB + 2 * NB) * sizeof(T);
+    return reg_win_table_offset<T, W, NB>(WW) + 2 * rows * sizeof(int64_t);
 }
 
 template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cudaStream_t st) {
