@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(256) k_interp_spread(DevPlan<T> P) {
 template <typename T> size_t interp_spread_smem(const DevPlan<T> &P) {
     const int w0 = P.dim == 3 ? P.w : 1;
     const size_t WW = (size_t)(P.T_tile[0] + w0 - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
-    return 2 * WW * sizeof(cpx<T>) + 8 * 3 * kMaxWidth * sizeof(T);
+    const size_t rows = (size_t)(P.T_tile[0] + w0 - 1) * (P.T_tile[1] + P.w - 1);
+    return generic_win_table_offset<T>(WW) + 2 * rows * sizeof(int64_t);
 }
 
 template <typename T> cudaError_t launch_interp_spread(const DevPlan<T> &P, cudaStream_t st) {

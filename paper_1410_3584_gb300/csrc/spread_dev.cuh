@@ -64,6 +64,13 @@ template <bool B> struct BoolC { static constexpr bool value = B; };
 template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
 template <> struct Log2<1> { static constexpr int value = 0; };
 
+// Shared memory of the generic kernel: F and G windows, kernel values of up to kGenericSlots
+// warps, then the two row tables of the window.
+constexpr int kGenericSlots = 8;
+template <typename T> __host__ __device__ constexpr size_t generic_win_table_offset(size_t WW) {
+    return align16(2 * WW * sizeof(cpx<T>) + (size_t)kGenericSlots * 3 * kMaxWidth * sizeof(T));
+}
+
 template <typename T>
 __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bid, unsigned char *smraw) {
     const int w = P.w;
@@ -73,12 +80,17 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
     cpx<T> *sF = (cpx<T> *)smraw;
     cpx<T> *sG = sF + WW;
     T *spsi = (T *)(sG + WW);
+    const int rows = W0 * W1;
+    int64_t *rowoff = (int64_t *)(smraw + generic_win_table_offset<T>(WW)), *rowmir = rowoff + rows;
     const Chunk ch = P.chunks[bid];
 
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const int c = q % W2, t = q / W2, b = t % W1, a = t / W1;
-        sF[q] = P.ones_mode ? mk<T>(0, 0) : load_herm(P, ch.bx + a, ch.by + b, ch.bz + c);
-        sG[q] = mk<T>(0, 0);
+    window_row_table(P, ch, W0, W1, rowoff, rowmir);
+    const WinCol wc = window_col(P, ch, W2, rows);
+    __syncthreads();
+    if (P.ones_mode) {
+        for (int q = threadIdx.x; q < WW; q += blockDim.x) sF[q] = sG[q] = mk<T>(0, 0);
+    } else {
+        window_fill(P, wc, rowoff, rowmir, rows, W2, sF, sG);
     }
     __syncthreads();
 
@@ -148,12 +160,7 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
         __syncwarp();
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const cpx<T> v = sG[q];
-        if (v.x == (T)0 && v.y == (T)0) continue;
-        const int c = q % W2, t = q / W2, b = t % W1, a = t / W1;
-        store_fold(P, ch.bx + a, ch.by + b, ch.bz + c, v);
-    }
+    window_fold(P, wc, rowoff, rowmir, rows, W2, sG);
 }
 
 // Shared memory of the warp kernel: F and G windows (z pitch Wt2 + 1), kernel values and
