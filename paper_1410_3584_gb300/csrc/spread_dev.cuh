@@ -206,11 +206,47 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
     const bool act_b = (W * W == 64) || cbc < W * W;
     const int xa = ca % W, ya = ca / W;
     const int xb = act_b ? cbc % W : 0, yb = act_b ? cbc / W : 0;
-    // pieces are sorted heaviest first; each warp takes the next free one
-    for (int sg = ch.j0 + warp; sg < ch.j1;) {
-        const uint32_t so = P.seg_sub[sg];
+    constexpr bool kSameX = 32 % W == 0;   // then column b has the x of column a
+    // the batch's kernel values are a contiguous block of the plan-time table; the next
+    // block (of this piece or of the warp's next piece) is fetched into registers while the
+    // current batch computes
+    constexpr int PQ = (NB * 3 * W + 31) / 32;
+    T pf[PQ], wf;
+    auto fetch = [&](int jbn, int nbn) {
+        const T *src = P.psi_tab + (int64_t)jbn * 3 * W;
+#pragma unroll
+        for (int u = 0; u < PQ; ++u) {
+            const int q = lane + 32 * u;
+            pf[u] = (q < nbn * 3 * W) ? __ldg(src + q) : (T)0;
+        }
+        wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : (T)0;
+    };
+    // pieces are sorted heaviest first; each warp takes the next free one, claiming it (and
+    // loading its descriptor) while the current piece computes
+    int sg = ch.j0 + warp;
+    uint32_t so = 0;
+    int j0 = 0, j1 = 0;
+    if (sg < ch.j1) {
+        so = P.seg_sub[sg];
+        j0 = P.seg_node[2 * sg];
+        j1 = P.seg_node[2 * sg + 1];
+        fetch(j0, min(NB, j1 - j0));
+    }
+    // lanes of odd x add the imaginary word of a cell first: with x fastest across the lanes
+    // the two lanes that share a bank have x of opposite parity, so each add is conflict-free
+    const int sw = xa & 1;
+    while (sg < ch.j1) {
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&next_seg, 1);
+        const int sg_n = __shfl_sync(0xffffffffu, nxt, 0);
+        uint32_t so_n = 0;
+        int j0_n = 0, j1_n = 0;
+        if (sg_n < ch.j1) {
+            so_n = P.seg_sub[sg_n];
+            j0_n = P.seg_node[2 * sg_n];
+            j1_n = P.seg_node[2 * sg_n + 1];
+        }
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
-        const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
         const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * P2 + so2;
         const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * P2 + so2;
         T fax[W], fay[W], fbx[W], fby[W], gax[W], gay[W], gbx[W], gby[W];
@@ -221,20 +257,6 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
             fax[z] = fa.x; fay[z] = fa.y; fbx[z] = fb.x; fby[z] = fb.y;
             gax[z] = gay[z] = gbx[z] = gby[z] = (T)0;
         }
-        // the batch's kernel values are a contiguous block of the plan-time table; the next
-        // block is fetched into registers while the current batch computes
-        constexpr int PQ = (NB * 3 * W + 31) / 32;
-        T pf[PQ], wf;
-        // the next batch's kernel values and node weights are fetched while this one computes
-        auto fetch = [&](int jbn, int nbn) {
-            const T *src = P.psi_tab + (int64_t)jbn * 3 * W;
-#pragma unroll
-            for (int u = 0; u < PQ; ++u) {
-                const int q = lane + 32 * u;
-                pf[u] = (q < nbn * 3 * W) ? __ldg(src + q) : (T)0;
-            }
-            wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : (T)0;
-        };
         // one batch of nodes; FULL (nb == NB) runs without per-node guards so that the
         // independent FMA chains of the batch's nodes interleave
         auto batch = [&](auto full_tag, int nb, T wcur) {
@@ -246,8 +268,9 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 wa[k] = wb[k] = (T)0;
                 if (FULL || k < nb) {
                     const T *pk = psi + k * 3 * W;
-                    wa[k] = act_a ? pk[xa] * pk[W + ya] : (T)0;
-                    wb[k] = act_b ? pk[xb] * pk[W + yb] : (T)0;
+                    const T pxa = pk[xa];
+                    wa[k] = act_a ? pxa * pk[W + ya] : (T)0;
+                    wb[k] = act_b ? (kSameX ? pxa : pk[xb]) * pk[W + yb] : (T)0;
                     T sax = 0, say = 0, sbx = 0, sby = 0;
                     T pzv[W];
                     load_row<T, W>(pk + 2 * W, pzv);
@@ -290,7 +313,6 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 }
             }
         };
-        fetch(j0, min(NB, j1 - j0));
         for (int jb = j0; jb < j1; jb += NB) {
             const int nb = min(NB, j1 - jb);
 #pragma unroll
@@ -300,7 +322,10 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
             }
             const T wcur = wf;
             __syncwarp();
-            if (jb + NB < j1) fetch(jb + NB, min(NB, j1 - jb - NB));
+            if (jb + NB < j1)
+                fetch(jb + NB, min(NB, j1 - jb - NB));
+            else if (sg_n < ch.j1)
+                fetch(j0_n, min(NB, j1_n - j0_n));
             if (nb == NB)
                 batch(BoolC<true>{}, nb, wcur);
             else
@@ -312,17 +337,20 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
 #pragma unroll
         for (int z = 0; z < W; ++z) {
             if (act_a) {
-                atomicAdd(&sG[basea + z].x, gax[z]);
-                atomicAdd(&sG[basea + z].y, gay[z]);
+                T *c = &sG[basea + z].x;
+                atomicAdd(c + sw, sw ? gay[z] : gax[z]);
+                atomicAdd(c + (sw ^ 1), sw ? gax[z] : gay[z]);
             }
             if (act_b) {
-                atomicAdd(&sG[baseb + z].x, gbx[z]);
-                atomicAdd(&sG[baseb + z].y, gby[z]);
+                T *c = &sG[baseb + z].x;
+                atomicAdd(c + sw, sw ? gby[z] : gbx[z]);
+                atomicAdd(c + (sw ^ 1), sw ? gbx[z] : gby[z]);
             }
         }
-        int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(&next_seg, 1);
-        sg = __shfl_sync(0xffffffffu, nxt, 0);
+        sg = sg_n;
+        so = so_n;
+        j0 = j0_n;
+        j1 = j1_n;
     }
     __syncthreads();
     window_fold(P, wc, rowoff, rowmir, rows, P2, sG);
