@@ -82,6 +82,7 @@ template <typename T> struct DevPlan {
     const Chunk *rchunks;
     int64_t nrchunks;
     const T *psi_tab;   // per node: kernel values [3][W] in sub-window coordinates (register kernels)
+    const T *psi_gen;   // 2D generic kernel: per node kernel values [3][w] on its own taps (axis 0 unused)
     int ones_mode;      // spreading of the weights alone (rho-hat := 1): builds the discrete kernel
     const cpx<T> *Khat; // precomputed-kernel method: spectrum of K on the 2n grid (else null)
     int accumulate;     // 1: the final pass adds into phi instead of overwriting it

@@ -31,8 +31,12 @@ template <typename T> static size_t fft_smem_bytes(int N, int nb) {
 
 // Lines per block of the register-engine kernels: 16 (FP32) / 8 (FP64) so that one position of
 // a block's lines is a 128-byte row, halved while the shared memory of a block would exceed
-// kRegSmemBudget (long lines, e.g. N = 2048), down to one line (pair) per block.
+// kRegSmemBudget (long lines, e.g. N = 2048).  Below kRegMinLines lines per block (16
+// threads each) a block is too small to hide its latencies and the pass runs on the 256-thread
+// shared-memory Stockham kernels instead (measured on 2D 2048-point lines: 2x faster in FP32
+// C2R, 2.5x in every FP64 pass).
 constexpr size_t kRegSmemBudget = 100 * 1024;
+constexpr int kRegMinLines = 4;
 template <typename T> constexpr int lines_max() { return sizeof(T) == 4 ? 16 : 8; }
 static int pick_lines(int nmax, size_t bytes_per_line) {
     int nb = nmax;
@@ -83,9 +87,11 @@ template <typename T>
 cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     if (P.len[2].nrad_reg > 0) {
         const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)line_ld(P.len[2].N) * 2);
+        if (nb >= kRegMinLines) {
 #define NLP_CALL(K) r2c_reg<T, K>(rho, P, st)
-        NLP_LINES_SWITCH(T, nb, NLP_CALL)
+            NLP_LINES_SWITCH(T, nb, NLP_CALL)
 #undef NLP_CALL
+        }
     }
     const int N = P.len[2].N;
     const int nb = lines_per_block<T>(N);
@@ -101,9 +107,11 @@ cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st) {
     if (P.len[2].nrad_reg > 0) {
         const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)line_ld(P.len[2].N) *
                                                       (P.len[2].nrad_reg > 2 ? 2 : 1));
+        if (nb >= kRegMinLines) {
 #define NLP_CALL(K) c2r_reg<T, K>(phi, P, st)
-        NLP_LINES_SWITCH(T, nb, NLP_CALL)
+            NLP_LINES_SWITCH(T, nb, NLP_CALL)
 #undef NLP_CALL
+        }
     }
     const int N = P.len[2].N;
     const int nb = lines_per_block<T>(N);
@@ -119,9 +127,11 @@ cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<
                                cudaStream_t st) {
     if (L.nrad_reg > 0) {
         const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)L.N * (L.nrad_reg > 2 ? 2 : 1));
+        if (nb >= kRegMinLines) {
 #define NLP_CALL(K) cols_reg<T, K>(data, d, L, sign, st)
-        NLP_LINES_SWITCH(T, nb, NLP_CALL)
+            NLP_LINES_SWITCH(T, nb, NLP_CALL)
 #undef NLP_CALL
+        }
     }
     const int nb = d.ncol >= 16 ? lines_per_block<T>(L.N) : d.ncol;
     const size_t sm = fft_smem_bytes<T>(L.N, nb);

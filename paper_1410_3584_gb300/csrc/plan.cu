@@ -294,7 +294,10 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     for (int64_t j = 0; j < M; ++j) order[pos[key[j]]++] = j;
     // chunks (generic kernel: node ranges of one tile) and segments (register kernel:
     // runs of one sub-tile, chunked at segment boundaries)
-    const int CH = sizeof(T) == 8 ? 256 : 1024;
+    // generic chunks: 3D windows are large (fill and fold amortised over many nodes); the 2D
+    // windows are small and the polar nodes crowd the tiles near k = 0, so short chunks spread
+    // those tiles over many CTAs (measured at 1024^2: spread 0.27 -> 0.05 ms FP32)
+    const int CH = p->grid.dim == 3 ? (sizeof(T) == 8 ? 256 : 1024) : (sizeof(T) == 8 ? 32 : 64);
     std::vector<Chunk> chunks, rchunks;
     std::vector<int> seg_node;
     std::vector<uint32_t> seg_sub;
@@ -433,6 +436,17 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         D.rchunks = (const Chunk *)drc;
         D.nrchunks = (int64_t)rchunks.size();
         p->info.segments = (int64_t)seg_sub.size();
+    }
+    D.psi_gen = nullptr;
+    if (p->grid.dim == 2 && M) {
+        // 2D (generic kernel): the kernel values of every node on its own w taps, evaluated
+        // once per plan in FP64 instead of per evaluation in the plan precision
+        void *dpg;
+        if ((s = alloc_dev(p, &dpg, sizeof(T) * (size_t)M * 3 * D.w))) return s;
+        if (launch_psi_table<T>((T *)dpg, (const T *)dnd, (const uint32_t *)dno, M, D.w, D.w, 1, p->info.beta_es,
+                                p->stream) != cudaSuccess)
+            return NLP_ERR_CUDA;
+        D.psi_gen = (const T *)dpg;
     }
     D.pois = nullptr;
     D.mom = nullptr;

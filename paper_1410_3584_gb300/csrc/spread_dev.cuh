@@ -107,7 +107,8 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
             const int ax = t / kMaxWidth, tt = t % kMaxWidth;
             T v = (T)0;
             if (ax == 0) v = (w0 == 1) ? (tt == 0 ? (T)1 : (T)0) : (tt < w ? es_kernel<T>(((T)tt - d0) * two_w, P.beta) : (T)0);
-            else if (tt < w) v = es_kernel<T>(((T)tt - (ax == 1 ? d1 : d2)) * two_w, P.beta);
+            else if (tt < w) v = P.psi_gen ? P.psi_gen[((int64_t)j * 3 + ax) * w + tt]
+                                           : es_kernel<T>(((T)tt - (ax == 1 ? d1 : d2)) * two_w, P.beta);
             ps[t] = v;
         }
         __syncwarp();
