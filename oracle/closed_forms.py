@@ -8,6 +8,9 @@
       d_nn taken under the integral sign.
   2D Coulomb, rho = exp(-|x|^2/s^2):      Eq. (2.5D-clb-exact) first line (I0 form, via i0e).
   2D Poisson, rho = exp(-|x|^2/s^2):      Eq. (eg-2d-Exact) (E1 form).
+  1D Poisson (U = -|x|/2, Sec. 2.2, 1D case), rho = exp(-(x-c)^2/a^2): integrating
+      -(1/2) int |x - y| rho(y) dy (its second derivative is -rho, its first is
+      -(a sqrt(pi)/2) erf((x-c)/a)) gives -(a^2/2) [t sqrt(pi) erf(t) + exp(-t^2)], t = (x-c)/a.
 Sums of shifted Gaussians follow by superposition.
 """
 from __future__ import annotations
@@ -123,3 +126,18 @@ def confined2d_gaussian(r, sigma, eps):
         kmax = 2.0 * math.sqrt(math.log(1e18)) / sigma
         out.flat[i] = 0.5 * sigma * sigma * integrate.quad(f, 0.0, kmax, epsabs=1e-15, epsrel=1e-13, limit=800)[0]
     return out
+
+
+def poisson1d_gaussian(x, a, c=0.0):
+    """-(1/2) int |x - y| exp(-(y-c)^2/a^2) dy = -(a^2/2) [t sqrt(pi) erf(t) + exp(-t^2)], t = (x-c)/a."""
+    t = (np.asarray(x, dtype=np.float64) - c) / a
+    return -0.5 * a * a * (t * math.sqrt(math.pi) * special.erf(t) + np.exp(-t * t))
+
+
+def poisson1d_gaussian_quad(x, a, c=0.0):
+    """The same convolution by adaptive quadrature (split at the kink y = x)."""
+    f = lambda y: abs(x - y) * math.exp(-((y - c) / a) ** 2)
+    lo, hi = c - 40.0 * a, c + 40.0 * a
+    pts = [p for p in (x,) if lo < p < hi]
+    v = integrate.quad(f, lo, hi, points=pts or None, limit=400, epsabs=0, epsrel=1e-13)[0]
+    return -0.5 * v

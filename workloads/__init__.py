@@ -77,6 +77,15 @@ def three_gaussians_2d(seed: int = SEED_TRAIN):
     return [tuple(c) for c in centers], [float(s) for s in widths]
 
 
+def three_gaussians_1d(seed: int = SEED_TRAIN):
+    """1D: centres uniform in [-4,4], widths uniform in [0.5,2], amplitudes uniform in [0.5,1.5]."""
+    rng = np.random.default_rng(seed)
+    centers = rng.uniform(-4.0, 4.0, size=3)
+    widths = rng.uniform(0.5, 2.0, size=3)
+    amps = rng.uniform(0.5, 1.5, size=3)
+    return [(float(c),) for c in centers], [float(s) for s in widths], [float(a) for a in amps]
+
+
 def harmonic_trap(grid: Grid, gammas) -> np.ndarray:
     """V = sum_d gamma_d^2 x_d^2 / 2."""
     X = grid.mesh()
