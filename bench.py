@@ -480,6 +480,49 @@ def twod_arm(args):
                       "results": out, "clocks": clocks, "dtype": "f32/f64", "data": "synthetic"}))
 
 
+def oned_arm(args):
+    """1D workload: the 1D Poisson potential (Sec. 2.2, 1D case) on 1024 points of [-16,16),
+    rho = three Gaussians (centres in [-4,4], widths in [0.5,2], amplitudes in [0.5,1.5], seed
+    20141014), FP64; error against the FP64 oracle and the closed form."""
+    import torch
+    import paper_1410_3584_gb300 as nl
+    from oracle import closed_forms as cf
+    from oracle import poisson1d as p1
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n, L = 1024, 16.0
+    x = W.cube(n, L, dim=1).axes()[0]
+    cs, ws, amps = W.three_gaussians_1d(W.SEED_TRAIN)
+    rho = np.zeros(n)
+    exact = np.zeros(n)
+    for (c,), s, a in zip(cs, ws, amps):
+        rho += a * np.exp(-((x - c) / s) ** 2)
+        exact += a * cf.poisson1d_gaussian(x, s, c)
+    plan = nl.Plan((n,), (L,), "poisson1d", "fp64", stream=stream)
+    with torch.cuda.stream(stream):
+        r = torch.from_numpy(rho).to("cuda")
+        phi = torch.empty_like(r)
+    stream.synchronize()
+    for _ in range(args.warmup):
+        nl.nlp_eval_potential(plan.handle, r, phi)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        nl.nlp_eval_potential(plan.handle, r, phi)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    out = phi.cpu().numpy()
+    ref = p1.poisson1d(rho, L)
+    plan.close()
+    print(json.dumps({"metric": "1D Poisson phi=U*rho evals/s, 1024 points, three Gaussians", "value": 1e3 / ms,
+                      "unit": "evals/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "rel_linf_vs_oracle": cf.rel_linf(out, ref), "rel_linf_vs_closed_form": cf.rel_linf(out, exact),
+                      "gpu_launches_per_eval": 5, "dtype": "f64", "data": "synthetic",
+                      "l2": "inputs resident (16 KB); launch- and latency-bound"}))
+
+
 def groundstate_arm(args):
     """Ground states with the learned initial guess: training states from the library's own
     gradient flow on 48^3 over [-10,10)^3 (seed 20141014), the network trained by the library's
@@ -577,7 +620,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="metric", choices=["metric", "batch", "2d", "groundstate"])
+    ap.add_argument("--workload", default="metric", choices=["metric", "batch", "2d", "1d", "groundstate"])
     ap.add_argument("--gs-train", type=int, default=192, help="training ground states (groundstate workload)")
     ap.add_argument("--gs-heldout", type=int, default=4, help="held-out problems timed at 96^3")
     ap.add_argument("--gs-train-steps", type=int, default=4000)
@@ -593,6 +636,8 @@ def main():
         batch_arm(args)
     elif args.workload == "2d":
         twod_arm(args)
+    elif args.workload == "1d":
+        oned_arm(args)
     elif args.workload == "groundstate":
         groundstate_arm(args)
     else:

@@ -56,19 +56,29 @@ typedef enum {
  *   NLP_POISSON_2D  U = -ln|x| / (2 pi),   U-hat = 1/|k|^2 (Algorithm 1)
  *   NLP_CONFINED_2D the 2D confined Coulomb kernel of Eq. (Kernal124d) with parameter
  *                   eps = nlp_opts.confine_eps >= 0: |k| U-hat = W_1(|k|) of Eq. (2Dw1),
- *                   = exp(a) erfc(sqrt a), a = eps^2 |k|^2 / 2 (eps = 0: NLP_COULOMB_2D)    */
+ *                   = exp(a) erfc(sqrt a), a = eps^2 |k|^2 / 2 (eps = 0: NLP_COULOMB_2D)
+ *   NLP_POISSON_1D  U = -|x|/2 in 1D (Sec. 2.2, the 1D case), FP64 plans only: the Gaussian
+ *                   G_1 carrying rho-hat(0) and (x rho)-hat(0) is split off, its potential
+ *                   u_1 = rho-hat(0) u_{1,1} - (x rho)-hat(0) u_{1,2} is taken in closed form
+ *                   (Eq. (1DPois)), and u_2 = (1/2pi) int_{-P}^{P} W(k) e^{ikx} dk with
+ *                   W(k) = (rho-hat(k) - G_1-hat(k)) / k^2, W(0) = -(x^2 rho)-hat(0)/2 +
+ *                   sigma^2 rho-hat(0)/2, by the rectangle rule on the frequencies
+ *                   k_l = l pi/(n h), l = -n..n-1, of the zero-padded 2n-point grid, rho-hat by
+ *                   the trapezoid sum; sigma = 6 sqrt(2)/P, P = min(kmax, pi/h) (default pi/h).
+ *                   The nodes, tiles and quadrature counts of nlp_opts do not apply.        */
 typedef enum {
     NLP_COULOMB_3D = 0,
     NLP_DIPOLE_3D = 1,
     NLP_COULOMB_2D = 2,
     NLP_POISSON_2D = 3,
-    NLP_CONFINED_2D = 4
+    NLP_CONFINED_2D = 4,
+    NLP_POISSON_1D = 5
 } nlp_kernel;
 
 typedef enum { NLP_FP64 = 0, NLP_FP32 = 1 } nlp_precision;
 
 typedef struct {
-    int dim;        /* 2 or 3 (must match the kernel) */
+    int dim;        /* 1, 2 or 3 (must match the kernel) */
     int n[3];       /* points per axis: even, 8..1024, of the form 2^a 3^b 5^c; 3D: n <= 256 */
     double L[3];    /* half-widths, > 0 */
 } nlp_grid;
@@ -157,7 +167,9 @@ nlp_status nlp_eval_potential_host(nlp_plan plan, const void *rho_host, void *ph
  * Outputs (host, may be NULL): *max_change = max|phi^{n+1} - phi^n| / tau (stopping rule of
  * Sec. 3.2), *inner_iters, energies[5] = {E, E_kin, E_pot, E_int, mu} of phi^{n+1}.
  * Synchronizes the plan stream.  NLP_ERR_DIVERGED if a non-finite value appears.
- * All kernels, NLP_POISSON_2D included (its potential through Algorithm 1). */
+ * All kernels of 2D and 3D grids, NLP_POISSON_2D included (its potential through
+ * Algorithm 1); NLP_POISSON_1D plans: NLP_ERR_UNSUPPORTED (as for nlp_gf_solve,
+ * nlp_energies, nlp_energies_noalloc and nlp_ts_step). */
 nlp_status nlp_gf_step(nlp_plan plan, void *phi_dev, const void *V_dev, double beta, double g,
                        double tau, double inner_tol, int max_inner, double *max_change,
                        int *inner_iters, double *energies);
@@ -238,7 +250,7 @@ nlp_status nlp_batch_set_wait_limit(nlp_batch batch, long long polls, int block_
 
 void nlp_batch_destroy(nlp_batch batch);
 
-/* Spread-tile autotuner: times complete evaluations of plans built with each candidate
+/* Spread-tile autotuner (2D and 3D grids; 1D: NLP_ERR_UNSUPPORTED): times complete evaluations of plans built with each candidate
  * tile edge (FP32 3D: 4, 8, 16; FP64 3D: 2, 4, 6; 2D: 8, 16, 32) on zero input (the work is
  * data independent) and returns the fastest in *best_tile with its time.  If cache_path
  * is not NULL the choice is looked up in / appended to that text file (one line per

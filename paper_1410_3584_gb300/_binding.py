@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libnlpot.so")
 
 NLP_OK, NLP_ERR_INVALID_ARG, NLP_ERR_UNSUPPORTED, NLP_ERR_OOM = 0, 1, 2, 3
 NLP_ERR_CUDA, NLP_ERR_TIMEOUT, NLP_ERR_DIVERGED, NLP_ERR_NOT_CONVERGED = 4, 5, 6, 7
-KERNELS = {"coulomb3d": 0, "dipole3d": 1, "coulomb2d": 2, "poisson2d": 3, "confined2d": 4}
+KERNELS = {"coulomb3d": 0, "dipole3d": 1, "coulomb2d": 2, "poisson2d": 3, "confined2d": 4, "poisson1d": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 
 

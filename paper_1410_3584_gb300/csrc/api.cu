@@ -96,7 +96,10 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     return NLP_OK;
 }
 
+nlp_status eval_1d(nlp_plan_s *p, const double *rho, double *phi);
+
 nlp_status eval_any(nlp_plan_s *p, const void *rho, void *phi) {
+    if (p->grid.dim == 1) return eval_1d(p, (const double *)rho, (double *)phi);
     p->nev = 0;
     mark(p, -1);
     nlp_status s;
@@ -213,6 +216,7 @@ nlp_status nlp_eval_potential_host(nlp_plan p, const void *rho_host, void *phi_h
 nlp_status nlp_gf_step(nlp_plan p, void *phi_dev, const void *V_dev, double beta, double g, double tau,
                        double inner_tol, int max_inner, double *max_change, int *inner_iters, double *energies) {
     if (!p || !phi_dev || !V_dev || !(tau > 0) || !(inner_tol > 0) || max_inner < 1) return NLP_ERR_INVALID_ARG;
+    if (p->grid.dim == 1) return NLP_ERR_UNSUPPORTED;
     return gf_step_impl(p, phi_dev, V_dev, beta, g, tau, inner_tol, max_inner, max_change, inner_iters, energies);
 }
 
@@ -222,6 +226,7 @@ nlp_status nlp_gf_solve(nlp_plan p, void *phi_dev, const void *V_dev, double bet
     if (!p || !phi_dev || !V_dev || !(tau > 0) || !(stop_tol > 0) || max_steps < 1 || !(inner_tol > 0) ||
         max_inner < 1)
         return NLP_ERR_INVALID_ARG;
+    if (p->grid.dim == 1) return NLP_ERR_UNSUPPORTED;
     double ch = INFINITY;
     int n = 0;
     nlp_status s = NLP_OK;
@@ -242,18 +247,20 @@ nlp_status nlp_gf_solve(nlp_plan p, void *phi_dev, const void *V_dev, double bet
 
 nlp_status nlp_energies(nlp_plan p, const void *phi_dev, const void *V_dev, double beta, double g, double *energies) {
     if (!p || !phi_dev || !V_dev || !energies) return NLP_ERR_INVALID_ARG;
+    if (p->grid.dim == 1) return NLP_ERR_UNSUPPORTED;
     return energies_impl(p, phi_dev, V_dev, beta, g, energies);
 }
 
 nlp_status nlp_energies_noalloc(nlp_plan p, const void *phi_dev, const void *V_dev, double beta, double g,
                                 double *energies) {
     if (!p || !phi_dev || !V_dev || !energies) return NLP_ERR_INVALID_ARG;
-    if (p->kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
+    if (p->kernel == NLP_POISSON_2D || p->grid.dim == 1) return NLP_ERR_UNSUPPORTED;
     return energies_noalloc_impl(p, phi_dev, V_dev, beta, g, energies);
 }
 
 nlp_status nlp_ts_step(nlp_plan p, void *psi_dev, const void *V_dev, double beta, double g, double tau, int order) {
     if (!p || !psi_dev || !V_dev || !(tau > 0) || (order != 2 && order != 4)) return NLP_ERR_INVALID_ARG;
+    if (p->grid.dim == 1) return NLP_ERR_UNSUPPORTED;
     return ts_step_impl(p, psi_dev, V_dev, beta, g, tau, order);
 }
 

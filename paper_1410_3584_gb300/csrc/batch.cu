@@ -408,6 +408,7 @@ extern "C" nlp_status nlp_autotune_tile(const nlp_grid *grid, nlp_kernel kernel,
                                         const nlp_opts *base, void *stream, const char *cache_path, int *best_tile,
                                         double *best_ms) {
     if (!grid || !best_tile) return NLP_ERR_INVALID_ARG;
+    if (grid->dim == 1) return NLP_ERR_UNSUPPORTED;   // no spreading tiles in 1D
     nlp_opts o;
     if (base) o = *base;
     else memset(&o, 0, sizeof(o));

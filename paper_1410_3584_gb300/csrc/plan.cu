@@ -487,9 +487,12 @@ nlp_status build_toeplitz(nlp_plan_s *p);
 
 static int roundup16(double x) { return (int)(16.0 * std::ceil(x / 16.0)); }
 
+nlp_status plan_build_1d(nlp_plan_s *p);
+
 nlp_status plan_build(nlp_plan_s *p) {
     const nlp_grid &g = p->grid;
     const int d = g.dim;
+    if (d == 1) return plan_build_1d(p);
     // collapsed 3D view
     if (d == 3) {
         for (int a = 0; a < 3; ++a) { p->n3[a] = g.n[a]; p->L3[a] = g.L[a]; }
@@ -628,11 +631,14 @@ nlp_status plan_build(nlp_plan_s *p) {
 
 nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, const nlp_opts *o) {
     if (!g) return NLP_ERR_INVALID_ARG;
-    if (g->dim != 2 && g->dim != 3) return NLP_ERR_INVALID_ARG;
+    if (g->dim < 1 || g->dim > 3) return NLP_ERR_INVALID_ARG;
     if ((kernel == NLP_COULOMB_3D || kernel == NLP_DIPOLE_3D) && g->dim != 3) return NLP_ERR_INVALID_ARG;
     if ((kernel == NLP_COULOMB_2D || kernel == NLP_POISSON_2D || kernel == NLP_CONFINED_2D) && g->dim != 2)
         return NLP_ERR_INVALID_ARG;
-    if ((int)kernel < 0 || (int)kernel > 4) return NLP_ERR_INVALID_ARG;
+    if ((kernel == NLP_POISSON_1D) != (g->dim == 1)) return NLP_ERR_INVALID_ARG;
+    if ((int)kernel < 0 || (int)kernel > 5) return NLP_ERR_INVALID_ARG;
+    if (kernel == NLP_POISSON_1D && prec == NLP_FP32) return NLP_ERR_UNSUPPORTED;
+    if (kernel == NLP_POISSON_1D && o && o->method != 0) return NLP_ERR_UNSUPPORTED;
     if (kernel == NLP_CONFINED_2D && o && !(o->confine_eps >= 0.0 && std::isfinite(o->confine_eps)))
         return NLP_ERR_INVALID_ARG;
     if (prec != NLP_FP64 && prec != NLP_FP32) return NLP_ERR_INVALID_ARG;

@@ -6,7 +6,7 @@
 #include "common.cuh"
 
 struct nlp_plan_s {
-    nlp_grid grid{};          // as given (dim 2 or 3)
+    nlp_grid grid{};          // as given (dim 1, 2 or 3)
     nlp_kernel kernel{};
     nlp_precision prec{};
     nlp_opts opts{};
@@ -44,6 +44,12 @@ struct nlp_plan_s {
     double split_a = 0, split_k2 = 0;
     nlp::DevPlan<float> pf1{};
     nlp::DevPlan<double> pd1{};
+    // 1D Poisson (NLP_POISSON_1D): FFT length 2n, zero-padded complex work array, FP64 moments
+    int p1d_n = 0;
+    double p1d_P = 0;
+    nlp::FftLen<double> p1d_len{};
+    void *p1d_work = nullptr;
+    double *p1d_mom = nullptr;
 };
 
 namespace nlp {

@@ -90,3 +90,18 @@ def test_confined2d_rejects_negative_eps_and_3d(nl):
     with pytest.raises(nl.NlpError) as e:
         nl.nlp_plan_create((32, 32, 32), (8, 8, 8), "confined2d", "fp64", eps=0.1, stream=0)
     assert e.value.status == nl.NLP_ERR_INVALID_ARG
+
+
+def test_poisson1d_argument_checks(nl):
+    """NLP_POISSON_1D: 1D grids only, FP64 only, method 0 only; 1D grids take no other kernel."""
+    bad = [((64,), (8,), "coulomb3d", "fp64", {}), ((64, 64), (8, 8), "poisson1d", "fp64", {}),
+           ((63,), (8,), "poisson1d", "fp64", {}), ((2048,), (8,), "poisson1d", "fp64", {}),
+           ((64,), (-1.0,), "poisson1d", "fp64", {})]
+    for n, L, k, prec, kw in bad:
+        with pytest.raises(nl.NlpError) as e:
+            nl.nlp_plan_create(n, L, k, prec, stream=0, **kw)
+        assert e.value.status == nl.NLP_ERR_INVALID_ARG, (n, k)
+    for prec, kw in (("fp32", {}), ("fp64", {"method": 1}), ("fp64", {"method": 2})):
+        with pytest.raises(nl.NlpError) as e:
+            nl.nlp_plan_create((64,), (8,), "poisson1d", prec, stream=0, **kw)
+        assert e.value.status == nl.NLP_ERR_UNSUPPORTED
