@@ -129,10 +129,11 @@ class ClockSampler:
 
 
 def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stream, e2e=True, method=0,
-                  kernel="coulomb3d"):
+                  kernel="coulomb3d", spread_variant=0):
     tol = 1e-6 if prec == "fp32" else 1e-12
     t_plan = time.perf_counter()
-    plan = nl.Plan(g.n, g.L, kernel, prec, kmax=P, counts=counts, tol=tol, stream=stream, method=method)
+    plan = nl.Plan(g.n, g.L, kernel, prec, kmax=P, counts=counts, tol=tol, stream=stream, method=method,
+                   spread_variant=spread_variant)
     t_plan = time.perf_counter() - t_plan
     dt = plan.torch_dtype
     with torch.cuda.stream(stream):
@@ -270,6 +271,9 @@ def gpu_arm(args):
                            method=2)
     ress32 = run_precision(nl, torch, "fp32", g, rho, P, None, args.steps, args.warmup, flush, stream, e2e=False,
                            method=2)
+    # FP32 with the z contractions of interpolation/spreading on the tensor cores (spread_variant 2)
+    rest32 = run_precision(nl, torch, "fp32", g, rho, P, counts, args.steps, args.warmup, flush, stream, e2e=False,
+                           spread_variant=2)
     clocks = clk.stop()
     torch.cuda.synchronize()
     t32 = sum(res32["times"]) / 1e3
@@ -339,6 +343,13 @@ def gpu_arm(args):
                          "ms_per_step": sum(ress32["times"]) / len(ress32["times"]),
                          "rel_linf_vs_oracle": cf.rel_linf(ress32["phi"], ref), "plan_s": ress32["plan_s"],
                          "nodes": ress32["info"]["nodes_total"], "radius": ress32["info"]["split_radius"]}},
+            "fp32_tensor_core_spread": {
+                "note": "plan option spread_variant=2: the z contractions of interpolation and spreading as "
+                        "mma.sync TF32 with hi/lo error compensation (same operator; measured, not the default)",
+                "value": len(rest32["times"]) / (sum(rest32["times"]) / 1e3), "unit": "evals/s",
+                "ms_per_step": sum(rest32["times"]) / len(rest32["times"]),
+                "interp_spread_ms": rest32["stages"].get("interp_spread"),
+                "rel_linf_vs_oracle": cf.rel_linf(rest32["phi"], ref)},
             "stages_ms": res32["stages"],
             "roofline": r32,
             "cpu_baseline": {"value": 1.0 / t_or, "unit": "evals/s", "cores": native.max_threads(), "kind": "oracle",

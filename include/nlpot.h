@@ -93,7 +93,10 @@ typedef struct {
     double nufft_tol;       /* NUFFT tolerance, 1e-14..1e-2; 0 -> 1e-12 (FP64) / 1e-6 (FP32) */
     int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 2..32 */
     int spread_variant;     /* 0 = default (3D: register-column kernel where the width is supported),
-                               1 = shared-memory-atomics kernel everywhere */
+                               1 = shared-memory-atomics kernel everywhere,
+                               2 = as 0, but FP32 plans with sub-window 8 (tol 1e-6) run the z
+                                   contractions on the tensor cores (mma.sync TF32 with hi/lo
+                                   error compensation; same result within FP32 rounding) */
     int method;             /* 0 = NUFFT per evaluation (default).  1 = precomputed discrete kernel:
                                the quadrature sum of Eq. (ifft) equals sum_i' K(i - i') rho_i' with
                                K(m) = sum_j w_j |k_j|^{d-1} U-hat(k_j) cos(k_j . m h) h^d / (2 pi)^d;

@@ -86,6 +86,7 @@ template <typename T> struct DevPlan {
     int ones_mode;      // spreading of the weights alone (rho-hat := 1): builds the discrete kernel
     const cpx<T> *Khat; // precomputed-kernel method: spectrum of K on the 2n grid (else null)
     int accumulate;     // 1: the final pass adds into phi instead of overwriting it
+    int use_mma;        // FP32 register kernel with W = 8: tensor-core variant (spread_mma.cuh)
 };
 
 }  // namespace nlp

@@ -210,7 +210,8 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     // register kernel (3D): sub-tile edge Ts with column length W = Ts + w - 1 (see spread_reg.cu)
     D.sub_T = 0;
     int Tt = p->opts.tile;
-    if (p->grid.dim == 3 && p->opts.spread_variant == 0) {
+    D.use_mma = p->opts.spread_variant == 2 ? 1 : 0;
+    if (p->grid.dim == 3 && p->opts.spread_variant != 1) {
         const int Ts = 2;
         if (reg_kernel_supported<T>(Ts + D.w - 1)) {
             D.sub_T = Ts;
@@ -654,7 +655,7 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if (o->n_r > 4096 || o->n_theta > 4096 || o->n_phi > 8192) return NLP_ERR_INVALID_ARG;
         if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
         if (o->tile != 0 && (o->tile < 2 || o->tile > 32)) return NLP_ERR_INVALID_ARG;
-        if (o->spread_variant != 0 && o->spread_variant != 1) return NLP_ERR_INVALID_ARG;
+        if (o->spread_variant < 0 || o->spread_variant > 2) return NLP_ERR_INVALID_ARG;
         if (o->method < 0 || o->method > 2) return NLP_ERR_INVALID_ARG;
         if (o->method == 1 && kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
         if (o->method == 2 && g->dim != 3) return NLP_ERR_UNSUPPORTED;

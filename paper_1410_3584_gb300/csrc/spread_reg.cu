@@ -22,6 +22,7 @@
 #include "launch.h"
 #include "spread_common.cuh"
 #include "spread_dev.cuh"
+#include "spread_mma.cuh"
 
 namespace nlp {
 
@@ -178,6 +179,11 @@ __global__ void __launch_bounds__(kWarpBlock) k_interp_spread_warp(DevPlan<T> P)
     spread_warp_block<T, W, NB>(P, blockIdx.x, smraw);
 }
 
+__global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_mma(DevPlan<float> P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    spread_mma_block<float>(P, blockIdx.x, smraw);
+}
+
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
 template <typename T> bool reg_kernel_supported(int W) {
@@ -190,8 +196,10 @@ template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
     const size_t WW = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
     constexpr int NB = nb_of<T>();
     const size_t rows = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1);
-    if constexpr (W * W <= 64) {   // warp kernel: z pitch padded by one cell
+    if constexpr (W * W <= 64) {   // warp kernels: z pitch padded by one cell
         const size_t WWp = rows * (P.T_tile[2] + P.w);
+        if constexpr (sizeof(T) == 4 && W == 8)
+            if (P.use_mma) return warp_win_table_offset<T, W, kMmaNB>(WWp) + 2 * rows * sizeof(int64_t);
         return warp_win_table_offset<T, W, NB>(WWp) + 2 * rows * sizeof(int64_t);
     }
     return reg_win_table_offset<T, W, NB>(WW) + 2 * rows * sizeof(int64_t);
@@ -200,6 +208,16 @@ template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
 template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cudaStream_t st) {
     constexpr int NB = nb_of<T>();
     const size_t sm = reg_smem<T, W>(P);
+    if constexpr (sizeof(T) == 4 && W == 8) {
+        if (P.use_mma) {
+            cudaError_t e = allow_smem<k_interp_spread_mma>();
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_interp_spread_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e != cudaSuccess) return e;
+            k_interp_spread_mma<<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (W * W <= 64) {
         cudaError_t e = allow_smem<k_interp_spread_warp<T, W, NB>>();
         if (e == cudaSuccess)   // several small blocks per SM, each with its own tile window

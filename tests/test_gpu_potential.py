@@ -60,6 +60,23 @@ def test_3d_parity_vs_oracle(nl, prec, kernel, shape):
     assert err < TOL[prec], (err, info)
 
 
+@pytest.mark.parametrize("kernel", ["coulomb3d", "dipole3d"])
+@pytest.mark.parametrize("shape", CASES_3D + [((64, 48, 40), (8.0, 6.0, 5.0))], ids=["24x20x16", "30x32x18", "64x48x40"])
+def test_3d_fp32_tensor_core_variant(nl, kernel, shape):
+    """spread_variant 2: the FP32 z contractions on the tensor cores (TF32 hi/lo compensated)
+    give the FP32 bar against the oracle and agree with the FP32-pipe kernel to FP32 rounding."""
+    g = W.Grid(*shape)
+    rho = W.gaussian(g, [1.0, 1.3, 0.8], center=(0.3, -0.2, 0.1))
+    P = math.pi / max(g.h)
+    counts = (32, 32, 64)
+    phi_tc, info = gpu_eval(nl, g, rho, kernel, "fp32", kmax=P, counts=counts, spread_variant=2)
+    phi_fp, _ = gpu_eval(nl, g, rho, kernel, "fp32", kmax=P, counts=counts)
+    assert info["sub_tile"] == 2 and info["width"] == 7
+    ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+    assert cf.rel_linf(phi_tc, ref) < TOL["fp32"]
+    assert cf.rel_linf(phi_tc, phi_fp) < 2e-6
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
 @pytest.mark.parametrize("shape", [((64, 48), (8.0, 6.0)), ((80, 90), (8.0, 9.0))], ids=["64x48", "80x90"])
