@@ -542,7 +542,7 @@ __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const Dev
 }
 
 template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
+__global__ void __launch_bounds__(NBC * 16, 4) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     inv_c2r_reg_block<T, NBC>(phi, P, blockIdx.x, smraw);
 }
