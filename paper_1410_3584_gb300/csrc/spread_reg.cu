@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
                     T sx = (T)0, sy = (T)0;
                     T pzv[W];
                     load_row<T, W>(pk + 2 * W, pzv);
-#pragma unroll
-                    for (int z = 0; z < W; ++z) {
+                    // the node's w z taps are z = 0..W-2 or 1..W-1 of the sub-window (the other
+                    // cell holds an exact zero kernel value): skip it, uniformly across the team
+                    auto tap = [&](int z) {
                         if constexpr (kFRegs) {
                             sx += fx[z] * pzv[z];
                             sy += fy[z] * pzv[z];
@@ -125,6 +126,13 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
                             sx += f.x * pzv[z];
                             sy += f.y * pzv[z];
                         }
+                    };
+                    if (pzv[0] == (T)0) {
+#pragma unroll
+                        for (int z = 1; z < W; ++z) tap(z);
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < W - 1; ++z) tap(z);
                     }
                     if (active) {
                         v[2 * k] = wxy * sx;
@@ -152,10 +160,18 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
                     const T cr = cbuf[2 * k] * wxy, ci = cbuf[2 * k + 1] * wxy;
                     T pzv[W];
                     load_row<T, W>(pk + 2 * W, pzv);
+                    if (pzv[0] == (T)0) {
 #pragma unroll
-                    for (int z = 0; z < W; ++z) {
-                        gx[z] += cr * pzv[z];
-                        gy[z] += ci * pzv[z];
+                        for (int z = 1; z < W; ++z) {
+                            gx[z] += cr * pzv[z];
+                            gy[z] += ci * pzv[z];
+                        }
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < W - 1; ++z) {
+                            gx[z] += cr * pzv[z];
+                            gy[z] += ci * pzv[z];
+                        }
                     }
                 }
             }
