@@ -250,14 +250,12 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
         const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * P2 + so2;
         const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * P2 + so2;
-        T fax[W], fay[W], fbx[W], fby[W], gax[W], gay[W], gbx[W], gby[W];
+        // G columns in registers; the F columns are read from the shared window per node, which
+        // frees their registers for more warps per SM
+        T gax[W], gay[W], gbx[W], gby[W];
 #pragma unroll
-        for (int z = 0; z < W; ++z) {
-            const cpx<T> fa = act_a ? sF[basea + z] : mk<T>(0, 0);
-            const cpx<T> fb = act_b ? sF[baseb + z] : mk<T>(0, 0);
-            fax[z] = fa.x; fay[z] = fa.y; fbx[z] = fb.x; fby[z] = fb.y;
-            gax[z] = gay[z] = gbx[z] = gby[z] = (T)0;
-        }
+        for (int z = 0; z < W; ++z) gax[z] = gay[z] = gbx[z] = gby[z] = (T)0;
+        const cpx<T> *fca = sF + (act_a ? basea : 0), *fcb = sF + (act_b ? baseb : 0);
         // one batch of nodes; FULL (nb == NB) runs without per-node guards so that the
         // independent FMA chains of the batch's nodes interleave
         auto batch = [&](auto full_tag, int nb, T wcur) {
@@ -278,10 +276,11 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
 #pragma unroll
                     for (int z = 0; z < W; ++z) {
                         const T pz = pzv[z];
-                        sax += fax[z] * pz;
-                        say += fay[z] * pz;
-                        sbx += fbx[z] * pz;
-                        sby += fby[z] * pz;
+                        const cpx<T> fa = fca[z], fb = fcb[z];
+                        sax += fa.x * pz;
+                        say += fa.y * pz;
+                        sbx += fb.x * pz;
+                        sby += fb.y * pz;
                     }
                     v[2 * k] = wa[k] * sax + wb[k] * sbx;
                     v[2 * k + 1] = wa[k] * say + wb[k] * sby;

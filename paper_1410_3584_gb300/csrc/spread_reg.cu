@@ -26,7 +26,8 @@
 
 namespace nlp {
 
-constexpr int kWarpBlock = 128;   // threads per CTA of the one-warp-per-piece kernel
+constexpr int kWarpBlock = 160;   // threads per CTA of the one-warp-per-piece kernel
+constexpr int kMmaBlock = 128;    // threads per CTA of the tensor-core kernel
 
 template <int W> struct RegCfg {
     static constexpr int TT = ((W * W + 31) / 32) * 32;       // threads per team
@@ -190,12 +191,12 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
 }
 
 template <typename T, int W, int NB>
-__global__ void __launch_bounds__(kWarpBlock) k_interp_spread_warp(DevPlan<T> P) {
+__global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_warp(DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     spread_warp_block<T, W, NB>(P, blockIdx.x, smraw);
 }
 
-__global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_mma(DevPlan<float> P) {
+__global__ void __launch_bounds__(kMmaBlock, 4) k_interp_spread_mma(DevPlan<float> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     spread_mma_block<float>(P, blockIdx.x, smraw);
 }
@@ -230,7 +231,7 @@ template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cu
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_interp_spread_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e != cudaSuccess) return e;
-            k_interp_spread_mma<<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
+            k_interp_spread_mma<<<(unsigned)P.nrchunks, kMmaBlock, sm, st>>>(P);
             return cudaGetLastError();
         }
     }
