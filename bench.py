@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -86,7 +87,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "nlpot_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -376,7 +377,8 @@ def batch_arm(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     items = W.batch_spec(args.batch_count)
-    cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
+    cache = os.path.join(ROOT, "_cache", "autotune_cache.txt")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
     t0 = time.perf_counter()
     tiles = {}
     for n in sorted(set(it.n for it in items)):
