@@ -188,19 +188,28 @@ def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stre
 # counters no longer describe the kernel and the line reports traffic null.
 TRAFFIC_SOURCES = ("paper_1410_3584_gb300/csrc/spread_reg.cu", "paper_1410_3584_gb300/csrc/spread_dev.cuh",
                    "paper_1410_3584_gb300/csrc/spread_common.cuh", "paper_1410_3584_gb300/csrc/plan.cu")
-CAPTURED_TRAFFIC = {"fp32": ("interp_spread", 330_896_896 + 8_201_728, "3bb40cbf3abc0879")}
+CAPTURED_TRAFFIC = {"fp32": ("interp_spread", 330_896_896 + 8_201_728, "0bb5406c50113077")}
+
+
+def source_digest(files=TRAFFIC_SOURCES):
+    """Digest of the code of the given sources: comments and whitespace removed, so that only a
+    change of the code itself marks the captured counters as stale."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"//[^\n]*|/\*.*?\*/", "", text, flags=re.S)
+        h.update("".join(text.split()).encode())
+    return h.hexdigest()[:16]
 
 
 def captured_traffic(prec, kernel):
-    import hashlib
     ent = CAPTURED_TRAFFIC.get(prec)
     if ent is None or ent[0] != kernel:
         return None
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return ent[1] if h.hexdigest()[:16] == ent[2] else None
+    return ent[1] if source_digest() == ent[2] else None
 
 
 def roofline(res, prec, alu_peak, hbm_peak, sm_mhz_note):

@@ -171,7 +171,8 @@ template <typename T, int W, int NB> __host__ __device__ constexpr size_t warp_w
     return align16(2 * WWp * sizeof(cpx<T>) + (size_t)kWarpSlots * (NB * 3 * W + 2 * NB) * sizeof(T));
 }
 
-// One warp per segment (W*W <= 64): lane L owns the z-columns L and L + 32 of the sub-window,
+// One warp per segment (W*W <= 64): lane L owns the z-columns L and L + 32 of the sub-window
+// (their G accumulators in registers, their F values read from the shared window per node),
 // so interpolation sums reduce inside the warp and the node loop needs no block barrier.
 template <typename T, int W, int NB>
 __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, unsigned char *smraw) {
