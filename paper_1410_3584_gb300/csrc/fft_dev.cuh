@@ -368,6 +368,39 @@ __device__ __forceinline__ void reg_pass_any(int R, Src &src, Dst &dst, int N, i
     }
 }
 
+// One Stockham pass of radix R done in place on shared memory, for lines where every thread
+// owns exactly one butterfly (N / R == tpc, all threads of the block taking part): all inputs
+// are read into registers, the block synchronises, then the outputs overwrite the buffer.
+template <typename T, int SGN, int R, class Src, class Dst>
+__device__ __forceinline__ void reg_pass_inplace(Src &src, Dst &dst, int N, int Ns, const cpx<T> *__restrict__ tw,
+                                                 int t) {
+    const int nbf = N / R, tws = N / (Ns * R);
+    const int j = t;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src(j + r * nbf);
+    const int jq = j / Ns, k = j - jq * Ns;
+    if (k) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            cpx<T> w = tw[k * r * tws];
+            if (SGN > 0) w = conj(w);
+            v[r] = v[r] * w;
+        }
+    }
+    Dft<T, SGN, R>::run(v);
+    __syncthreads();
+    const int base = jq * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst(base + r * Ns, v[r]);
+}
+
+// the R2C kernels transform in one shared buffer when the length is two register passes whose
+// last has one butterfly per thread (16 threads per line)
+template <typename T> __host__ __device__ inline bool r2c_inplace(const FftLen<T> &L) {
+    return L.nrad_reg == 2 && L.rad_reg[1] == 16 && L.N == 16 * 16;
+}
+
 // FFT of the lines of a block, line (column) b of the block handled by the tpc threads with
 // the same b.  The first pass reads the line through gsrc(position), the last pass writes it
 // through gdst(position, value); intermediate results live in shared memory (position p of
@@ -464,10 +497,22 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
         const T d2 = P.deconv[2][i];
         return mk<T>(rho[line0 * n2 + i] * (fa * d2), rho[line1 * n2 + i] * (fb * d2));
     };
-    cpx<T> *res = ((L.nrad_reg - 1) & 1) ? sB : sA;
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
-    auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
-    fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+    cpx<T> *res;
+    if (r2c_inplace(L)) {
+        // 256 = 16 x 16: the first pass lands in sA, the second transforms sA in place
+        res = sA;
+        auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
+        auto ssrc = [&](int l) { return sA[idx(l, b)]; };
+        reg_pass<T, -1, 16>(gsrc, sdst, N, 1, L.tw, t, 16);
+        __syncthreads();
+        reg_pass_inplace<T, -1, 16>(ssrc, sdst, N, 16, L.tw, t);
+        __syncthreads();
+    } else {
+        res = ((L.nrad_reg - 1) & 1) ? sB : sA;
+        auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
+        fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+    }
     if (!ok) return;
     const int l0a = wrapi(i0a - P.n[0] / 2, P.nf[0]), l1a = wrapi(i1a - P.n[1] / 2, P.nf[1]);
     const int l0b = wrapi(i0b - P.n[0] / 2, P.nf[0]), l1b = wrapi(i1b - P.n[1] / 2, P.nf[1]);
@@ -482,7 +527,7 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
 }
 
 template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16, 3) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+__global__ void __launch_bounds__(NBC * 16, 4) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     fwd_r2c_reg_block<T, NBC>(rho, P, blockIdx.x, smraw);
 }

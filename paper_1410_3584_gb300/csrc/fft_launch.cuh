@@ -46,7 +46,7 @@ static int pick_lines(int nmax, size_t bytes_per_line) {
 
 template <typename T, int NBC> static cudaError_t r2c_reg(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
-    const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+    const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (r2c_inplace(P.len[2]) ? 1 : 2);
     allow_smem<k_fwd_r2c_reg<T, NBC>>();
     k_fwd_r2c_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
     return cudaGetLastError();
@@ -86,7 +86,8 @@ static cudaError_t cols_reg(cpx<T> *data, const StridedDesc &d, const FftLen<T> 
 template <typename T>
 cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     if (P.len[2].nrad_reg > 0) {
-        const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)line_ld(P.len[2].N) * 2);
+        const int nb = pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)line_ld(P.len[2].N) *
+                                                      (r2c_inplace(P.len[2]) ? 1 : 2));
         if (nb >= kRegMinLines) {
 #define NLP_CALL(K) r2c_reg<T, K>(rho, P, st)
             NLP_LINES_SWITCH(T, nb, NLP_CALL)
