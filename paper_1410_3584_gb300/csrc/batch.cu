@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
         if (!s_ok) continue;   // drain: tickets are still taken so every CTA reaches the end
         switch (k) {
             case ST_R2C:
-                if (B.reg_fft) fwd_r2c_reg_block<float, kRegLines>(A.rho[p], B.P, i, smraw);
+                // two shared buffers (the persistent kernel sizes its shared memory for every stage)
+                if (B.reg_fft) fwd_r2c_reg_block<float, kRegLines, false>(A.rho[p], B.P, i, smraw);
                 else fwd_r2c_block<float>(A.rho[p], B.P, B.nb_r2c, i, smraw);
                 break;
             case ST_A1:

@@ -476,7 +476,7 @@ __host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; 
 // line, so the global loads and stores are contiguous).  The first pass reads rho,
 // deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
 // where the spectra of the two real lines are separated and written as half spectra.
-template <typename T, int NBC>
+template <typename T, int NBC, bool kInplace = true>
 __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
     const FftLen<T> &L = P.len[2];
@@ -499,7 +499,7 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
     cpx<T> *res;
-    if (r2c_inplace(L)) {
+    if (kInplace && r2c_inplace(L)) {
         // 256 = 16 x 16: the first pass lands in sA, the second transforms sA in place
         res = sA;
         auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
