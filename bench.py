@@ -433,18 +433,23 @@ def batch_arm(args):
     # checks: every item against its own single-plan evaluation, a sample against the oracle
     worst_single, worst_oracle = 0.0, 0.0
     from oracle import closed_forms as cf
-    from oracle import potential
+    from oracle import native, potential
     for i, (pl, r, ph) in enumerate(zip(plans, rhos, phis)):
         ev_out = pl.eval(r)
         pl.sync()
         single = ev_out.double().cpu().numpy()
         out = ph.double().cpu().numpy()
         worst_single = max(worst_single, float(np.max(np.abs(out - single)) / np.max(np.abs(single))))
+    # CPU baseline leg: the FP64 oracle on a sample of the items (its results also state the error)
+    t_or, n_or = 0.0, 0
     for i in range(0, len(items), max(1, len(items) // 4))[:4]:
         g, rho, it, P, counts = host[i]
         if g.n[0] > 96:
             continue
+        t0 = time.perf_counter()
         o = potential.eval_nufft(rho, g, it.kernel, P, counts, tol=1e-12)
+        t_or += time.perf_counter() - t0
+        n_or += 1
         worst_oracle = max(worst_oracle, cf.rel_linf(phis[i].double().cpu().numpy(), o))
     nl.nlp_batch_destroy(b)
     for p in plans:
@@ -457,6 +462,8 @@ def batch_arm(args):
         "items": len(items), "nodes_total": nodes, "tasks": info["tasks"], "grid_ctas": info["grid"],
         "smem_bytes": info["smem"], "tiles": tiles, "plan_s": t_plan, "tune_s": t_tune,
         "max_rel_vs_single_plan": worst_single, "max_rel_vs_oracle_sampled": worst_oracle,
+        "cpu_baseline": {"value": n_or / t_or if t_or > 0 else None, "unit": "evals/s", "cores": native.max_threads(),
+                         "kind": "oracle", "sample": "%d batch items of at most 96^3 by the FP64 oracle (tol 1e-12)" % n_or},
         "dtype": "f32", "data": "synthetic", "l2": "flushed between timed steps (512 MB write)"}))
 
 
@@ -468,21 +475,27 @@ def twod_arm(args):
     import torch
     import paper_1410_3584_gb300 as nl
     from oracle import closed_forms as cf
-    from oracle import potential, quadrature
+    from oracle import native, potential
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     g = W.cube(1024, 16.0, dim=2)
     cs, ws = W.three_gaussians_2d(W.SEED_TRAIN)
     rho = W.gaussian_sum(g, cs, ws)
-    P = quadrature.density_P(min(ws), g.h[0])
-    counts = quadrature.default_counts(g.L, P)
+    # P where rho-hat falls below 1e-16 (never past pi/h); n_r = roundup16(P R/2 + 16),
+    # n_phi = roundup16(P R + 32) with R the half-diagonal of the box
+    P = min(math.pi / g.h[0], 2.0 * math.sqrt(math.log(1e16)) / min(ws))
+    R = math.sqrt(sum(L * L for L in g.L))
+    counts = (int(16 * math.ceil((P * R / 2.0 + 16.0) / 16.0)), int(16 * math.ceil((P * R + 32.0) / 16.0)))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     X, Y = g.mesh()
     out = {}
     clk = ClockSampler(0)
     clk.start()
     for kernel in ("coulomb2d", "poisson2d"):
+        # CPU baseline leg: the FP64 oracle on the host cores (its result also states the error)
+        t0 = time.perf_counter()
         ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+        t_or = time.perf_counter() - t0
         form = cf.coulomb2d_iso if kernel == "coulomb2d" else cf.poisson2d_iso
         exact = np.zeros_like(ref)
         for (cx, cy), s in zip(cs, ws):
@@ -494,7 +507,9 @@ def twod_arm(args):
             out["%s_%s" % (kernel, prec)] = {
                 "value": len(res["times"]) / t, "unit": "evals/s", "ms_per_step": 1e3 * t / len(res["times"]),
                 "rel_linf_vs_oracle": cf.rel_linf(res["phi"], ref), "rel_linf_vs_closed_form": cf.rel_linf(res["phi"], exact),
-                "stages_ms": res["stages"], "nodes": res["info"]["nodes_total"], "width": res["info"]["width"]}
+                "stages_ms": res["stages"], "nodes": res["info"]["nodes_total"], "width": res["info"]["width"],
+                "cpu_baseline": {"value": 1.0 / t_or, "unit": "evals/s", "cores": native.max_threads(), "kind": "oracle",
+                                 "sample": "one full 1024^2 %s evaluation by the FP64 oracle (tol 1e-13)" % kernel}}
     clocks = clk.stop()
     print(json.dumps({"metric": "2D phi=U*rho evals/s, 1024^2, three Gaussians", "steps": args.steps,
                       "warmup": args.warmup, "config": {"grid": [1024, 1024], "L": 16.0, "P": P,
@@ -509,6 +524,7 @@ def oned_arm(args):
     import torch
     import paper_1410_3584_gb300 as nl
     from oracle import closed_forms as cf
+    from oracle import native
     from oracle import poisson1d as p1
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
@@ -536,12 +552,18 @@ def oned_arm(args):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     out = phi.cpu().numpy()
+    # CPU baseline leg: the FP64 oracle (direct sums) on the host (its result also states the error)
+    t0 = time.perf_counter()
     ref = p1.poisson1d(rho, L)
+    t_or = time.perf_counter() - t0
     plan.close()
     print(json.dumps({"metric": "1D Poisson phi=U*rho evals/s, 1024 points, three Gaussians", "value": 1e3 / ms,
                       "unit": "evals/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
                       "rel_linf_vs_oracle": cf.rel_linf(out, ref), "rel_linf_vs_closed_form": cf.rel_linf(out, exact),
                       "gpu_launches_per_eval": 5, "dtype": "f64", "data": "synthetic",
+                      "cpu_baseline": {"value": 1.0 / t_or, "unit": "evals/s", "cores": native.max_threads(),
+                                       "kind": "oracle", "sample": "one 1024-point evaluation by the FP64 oracle "
+                                       "(direct sums)"},
                       "l2": "inputs resident (16 KB); launch- and latency-bound"}))
 
 
