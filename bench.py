@@ -53,6 +53,19 @@ def workload():
     return g, rho, P, (nr, nr, nph)
 
 
+def workload_2d():
+    """2D workload: 1024^2 over [-16,16)^2, three Gaussians (seed 20141014); P where rho-hat falls
+    below 1e-16 (never past pi/h); n_r = roundup16(P R/2 + 16), n_phi = roundup16(P R + 32) with
+    R the half-diagonal of the box."""
+    g = W.cube(1024, 16.0, dim=2)
+    cs, ws = W.three_gaussians_2d(W.SEED_TRAIN)
+    rho = W.gaussian_sum(g, cs, ws)
+    P = min(math.pi / g.h[0], 2.0 * math.sqrt(math.log(1e16)) / min(ws))
+    R = math.sqrt(sum(L * L for L in g.L))
+    counts = (int(16 * math.ceil((P * R / 2.0 + 16.0) / 16.0)), int(16 * math.ceil((P * R + 32.0) / 16.0)))
+    return g, rho, P, counts, cs, ws
+
+
 def max_over_ranks(values, device):
     """Element-wise maximum of per-rank timings over all ranks (the replicas' slowest time
     bounds the whole job); identity on one rank."""
@@ -478,14 +491,7 @@ def twod_arm(args):
     from oracle import native, potential
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    g = W.cube(1024, 16.0, dim=2)
-    cs, ws = W.three_gaussians_2d(W.SEED_TRAIN)
-    rho = W.gaussian_sum(g, cs, ws)
-    # P where rho-hat falls below 1e-16 (never past pi/h); n_r = roundup16(P R/2 + 16),
-    # n_phi = roundup16(P R + 32) with R the half-diagonal of the box
-    P = min(math.pi / g.h[0], 2.0 * math.sqrt(math.log(1e16)) / min(ws))
-    R = math.sqrt(sum(L * L for L in g.L))
-    counts = (int(16 * math.ceil((P * R / 2.0 + 16.0) / 16.0)), int(16 * math.ceil((P * R + 32.0) / 16.0)))
+    g, rho, P, counts, cs, ws = workload_2d()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     X, Y = g.mesh()
     out = {}
