@@ -192,15 +192,17 @@ nlp_status nlp_gf_solve(nlp_plan plan, void *phi_dev, const void *V_dev, double 
 nlp_status nlp_energies(nlp_plan plan, const void *phi_dev, const void *V_dev, double beta,
                         double g, double *energies);
 
-/* Energies as nlp_energies, for callers that must not allocate device memory during the
- * call.  nlp_energies allocates the plan's gradient-flow workspace on its first use; code
- * that runs under CUDA stream capture (where cudaMalloc is not allowed) or inside a
- * process whose device memory belongs to another allocator cannot let that happen.  This
- * entry point calls no cudaMalloc, cudaFree or other allocating routine: its buffers
- * (density, potential, spectrum, FFT tables, FP64 partial sums) live in one file-scope
- * static device array of 1 MiB, which every GPU that loads the library holds until the
- * process exits.  The potential inside uses the spectra nlp_plan_create allocated.
- * (The paper has no counterpart: this is a deployment variant of nlp_energies.)
+/* Energies as nlp_energies, for callers that cannot let the library allocate device memory.
+ * nlp_energies allocates the plan's gradient-flow workspace (cudaMalloc) on its first use.
+ * A process whose device memory is already reserved by another allocator (a framework's
+ * caching pool, an arena sized at start-up) may see that cudaMalloc fail or fragment its
+ * pool, and a latency-bound loop may not accept the device-wide synchronisation that
+ * cudaMalloc / cudaFree can imply.  This entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine: its buffers (density, potential, spectrum, FFT tables, FP64 partial
+ * sums) live in one file-scope static device array of 1 MiB, which every GPU that loads the
+ * library holds until the process exits.  The potential evaluation inside uses the spectra
+ * that nlp_plan_create allocated.  (The paper has no counterpart: this is a deployment
+ * variant of nlp_energies.)
  *  - Limit: grids of at most 32768 points (e.g. 32^3, 128 x 256); larger grids return
  *    NLP_ERR_INVALID_ARG before any launch.  NLP_POISSON_2D plans: NLP_ERR_UNSUPPORTED.
  *  - The first call on each device looks up the array's device address there
@@ -209,7 +211,7 @@ nlp_status nlp_energies(nlp_plan plan, const void *phi_dev, const void *V_dev, d
  *  - All calls share the array and it keeps the last call's contents; every value a call
  *    reads it first writes.  Calls that overlap on the GPU (other streams, other host
  *    threads) race on the array and must not be issued.
- * Synchronizes the plan stream. */
+ *  - The energies are returned in host memory: the call synchronizes the plan stream. */
 nlp_status nlp_energies_noalloc(nlp_plan plan, const void *phi_dev, const void *V_dev, double beta,
                                 double g, double *energies);
 

@@ -7,6 +7,7 @@
 // Sums, minima/maxima and norms are reduced in FP64 for both plan precisions.
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -38,7 +39,10 @@ template <typename T> static nlp_status ensure_work(nlp_plan_s *p, Work<T> *&W) 
         W = (Work<T> *)p->d_work;
         return NLP_OK;
     }
-    W = new Work<T>();
+    // owned here until the whole set is allocated: a failure part-way frees the host struct
+    // (its device buffers are already in p->allocs and go with the plan)
+    std::unique_ptr<Work<T>> own(new Work<T>());
+    W = own.get();
     const size_t N = grid_points(p);
     const int n0 = p->n3[0], n1 = p->n3[1], n2 = p->n3[2];
     const size_t nh = (size_t)n2 / 2 + 1;
@@ -77,7 +81,7 @@ template <typename T> static nlp_status ensure_work(nlp_plan_s *p, Work<T> *&W) 
     }
     D.nh = (int)nh;
     D.F = D.G = W->spec;
-    p->d_work = W;
+    p->d_work = own.release();
     p->work_free = [](void *w) { delete (Work<T> *)w; };
     p->info.workspace_bytes = p->bytes;
     return NLP_OK;
@@ -539,12 +543,14 @@ nlp_status ts_step_impl(nlp_plan_s *p, void *psi, const void *V, double beta, do
 }
 
 // ------------------------------------------------------------------ energies without allocation
-// nlp_energies allocates the plan's gradient-flow workspace on its first call.  Callers that
-// must not call the device allocator at that point (code running under stream capture,
-// where cudaMalloc is not allowed, or a process whose device memory is owned by another
-// allocator) use nlp_energies_noalloc instead: the same energy reductions with every
-// buffer carved from one file-scope static device array.  The potential evaluation inside
-// uses the plan's spectra, which nlp_plan_create already allocated.
+// nlp_energies allocates the plan's gradient-flow workspace on its first call.  Some callers
+// cannot let a library call cudaMalloc at that point: a process whose device memory is
+// already reserved by another allocator (a framework's caching pool, an arena sized at
+// start-up), where a new cudaMalloc fails or fragments that pool, and latency-bound loops
+// where the device-wide synchronisation that cudaMalloc / cudaFree may imply is not
+// acceptable.  nlp_energies_noalloc computes the same energies with every buffer carved from
+// one file-scope static device array.  The potential evaluation inside uses the plan's
+// spectra, which nlp_plan_create already allocated.
 constexpr int64_t kNoAllocMaxPoints = 32768;          // grid points (e.g. 32^3 or 128 x 256)
 constexpr size_t kNoAllocBytes = 1u << 20;            // 1 MiB per device, held until exit
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -577,16 +583,6 @@ template <typename T> __global__ void k_fill_twiddles(cpx<T> *tw, int N) {
 
 template <typename T> __global__ void k_fill_value(T *a, int n, T v) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) a[k] = v;
-}
-
-static bool factor_noalloc(int N, int *rad, int *nrad) {
-    int k = 0;
-    while (N % 4 == 0 && k < kMaxRadices) { rad[k++] = 4; N /= 4; }
-    while (N % 2 == 0 && k < kMaxRadices) { rad[k++] = 2; N /= 2; }
-    while (N % 3 == 0 && k < kMaxRadices) { rad[k++] = 3; N /= 3; }
-    while (N % 5 == 0 && k < kMaxRadices) { rad[k++] = 5; N /= 5; }
-    *nrad = k;
-    return N == 1;
 }
 
 template <typename T>
@@ -626,7 +622,11 @@ static nlp_status energies_noalloc_t(nlp_plan_s *p, const T *x, const T *V, doub
         D.nf[a] = n[a];
         D.len[a].N = n[a];
         if (n[a] > 1) {
-            if (!factor_noalloc(n[a], D.len[a].rad, &D.len[a].nrad)) return NLP_ERR_UNSUPPORTED;
+            // both radix lists, as make_fft_len fills them: the passes run on the same engines
+            // as in nlp_energies
+            if (!factor_radices(n[a], D.len[a].rad, &D.len[a].nrad) ||
+                !factor_radices_reg(n[a], D.len[a].rad_reg, &D.len[a].nrad_reg))
+                return NLP_ERR_UNSUPPORTED;
             cpx<T> *tw = (cpx<T> *)(b + off[5 + a]);
             k_fill_twiddles<T><<<(n[a] + 255) / 256, 256, 0, p->stream>>>(tw, n[a]);
             D.len[a].tw = tw;

@@ -98,7 +98,7 @@ nlp_status alloc_dev(nlp_plan_s *p, void **ptr, size_t bytes) {
     return NLP_OK;
 }
 
-static bool factor_radices(int N, int *rad, int *nrad) {
+bool factor_radices(int N, int *rad, int *nrad) {
     int k = 0;
     while (N % 4 == 0 && k < kMaxRadices) { rad[k++] = 4; N /= 4; }
     while (N % 2 == 0 && k < kMaxRadices) { rad[k++] = 2; N /= 2; }
@@ -110,7 +110,7 @@ static bool factor_radices(int N, int *rad, int *nrad) {
 
 // radices of the register engine: as many 16s as the power of two allows, the rest of it as
 // one 8, 4 or 2, then 3s and 5s
-static bool factor_radices_reg(int N, int *rad, int *nrad) {
+bool factor_radices_reg(int N, int *rad, int *nrad) {
     int k = 0, p2 = 0;
     while (N % 2 == 0) { N /= 2; ++p2; }
     while (p2 >= 4 && k < 8) { rad[k++] = 16; p2 -= 4; }

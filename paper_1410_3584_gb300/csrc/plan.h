@@ -59,4 +59,8 @@ void es_params(double tol, int *w, double *beta);
 double es_fourier(double xi, int w, double beta);
 nlp_status alloc_dev(nlp_plan_s *p, void **ptr, size_t bytes);
 template <typename T> nlp_status make_fft_len(nlp_plan_s *p, int N, FftLen<T> *out);
+// radix sequences of an FFT length: shared-memory Stockham engine (4, 2, 3, 5) and register
+// engine (16s, one 8/4/2, 3s, 5s); false if N has another prime factor
+bool factor_radices(int N, int *rad, int *nrad);
+bool factor_radices_reg(int N, int *rad, int *nrad);
 }  // namespace nlp
