@@ -113,3 +113,47 @@ def test_autotuner_picks_a_candidate_and_caches(nl, tmp_path):
     assert (t2, ms2) == (t1, pytest.approx(ms1, rel=1e-5))
     t3, _ = nl.nlp_autotune_tile((64, 48), (8.0, 6.0), "coulomb2d", "fp32", counts=(64, 128))
     assert t3 in (8, 16, 32)
+
+
+def _batch_item_setup(it):
+    """A batched-workload item: grid, density, P where rho-hat falls below 1e-8 (never past
+    pi/h) and the default quadrature counts."""
+    from oracle import quadrature
+    g = W.cube(it.n, it.L)
+    P = quadrature.density_P(min(it.widths), max(g.h), eps=1e-8)
+    return g, W.gaussian(g, it.widths), P, quadrature.default_counts(g.L, P)
+
+
+def test_batch_largest_grids_vs_oracle(nl):
+    """Items of the batched workload at its largest grids, 160^3 and 192^3 (fine grids 320^3
+    and 384^3: FFT lengths with radix-5 and radix-3 factors on the long-line engine paths),
+    beside a 64^3 and a 96^3 item: each as a single plan and inside one batch, against the
+    FP64 oracle at full size (FP32 bar 1e-5), and batch == single plan."""
+    import torch
+    items = W.batch_spec(64)
+    pick = [next(it for it in items if it.n == n) for n in (64, 96, 160, 192)]
+    stream = torch.cuda.Stream()
+    plans, rhos, phis, singles, refs = [], [], [], [], []
+    for it in pick:
+        g, rho, P, counts = _batch_item_setup(it)
+        pl = nl.Plan(g.n, g.L, it.kernel, "fp32", kmax=P, counts=counts, tol=1e-6, stream=stream)
+        r = torch.from_numpy(rho).to("cuda", torch.float32)
+        out = pl.eval(r)
+        pl.sync()
+        singles.append(out.double().cpu().numpy())
+        plans.append(pl)
+        rhos.append(r)
+        phis.append(torch.zeros_like(r))
+        refs.append(potential.eval_nufft(rho, g, it.kernel, P, counts, tol=1e-10))
+    b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
+    nl.nlp_batch_eval(b, rhos, phis)
+    nl.nlp_batch_sync(b)
+    for it, ph, single, ref in zip(pick, phis, singles, refs):
+        out = ph.double().cpu().numpy()
+        e_single, e_batch = cf.rel_linf(single, ref), cf.rel_linf(out, ref)
+        print("%d^3 %s: single plan %.3e, batch %.3e vs oracle" % (it.n, it.kernel, e_single, e_batch))
+        assert e_single < 1e-5 and e_batch < 1e-5
+        assert np.max(np.abs(out - single)) <= 1e-6 * np.max(np.abs(single))
+    nl.nlp_batch_destroy(b)
+    for p in plans:
+        p.close()

@@ -30,7 +30,7 @@ def _setup3(n=32, L=8.0):
     return g, gam, W.harmonic_trap(g, gam), math.pi / g.h[0]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_gf_step_parity(nl, prec, tol):
     import torch
     g, gam, V, P = _setup3()
@@ -48,7 +48,9 @@ def test_gf_step_parity(nl, prec, tol):
                                    energies=True)
     out = tphi.double().cpu().numpy()
     plan.close()
-    assert np.max(np.abs(out - ref)) / np.max(np.abs(ref)) < tol
+    err = np.max(np.abs(out - ref)) / np.max(np.abs(ref))
+    print("gf_step %s rel L-inf vs oracle %.3e" % (prec, err))
+    assert err < tol
     assert abs(ch - ch_ref) < tol * 50 * max(1.0, ch_ref)
     for k in ("E", "Ekin", "Epot", "Eint", "mu"):
         assert abs(E[k] - E_ref[k]) < tol * max(1.0, abs(E_ref[k])), (k, E[k], E_ref[k])
@@ -56,8 +58,9 @@ def test_gf_step_parity(nl, prec, tol):
         assert abs(it - G.last_inner) <= 1
 
 
-def test_gpu_ground_state_matches_paper_table(nl):
-    """Example 3.1 (Table tab:virial:3d:sps), beta = 1: GF-NUFFT on the GPU to
+@pytest.mark.parametrize("beta", [-10.0, -5.0, -1.0, 1.0, 5.0, 10.0])
+def test_gpu_ground_state_matches_paper_table(nl, beta):
+    """Example 3.1 (Table tab:virial:3d:sps), all six beta: GF-NUFFT on the GPU to
     max|phi^{n+1} - phi^n|/tau <= 1e-8 on [-5,5)^3 with h = 1/3, FP64."""
     import torch
     g, gam, V, P = _setup3(30, 5.0)
@@ -65,13 +68,13 @@ def test_gpu_ground_state_matches_paper_table(nl):
     tphi = torch.from_numpy(W.normalized_gaussian_start(g, gam)).cuda()
     tV = torch.from_numpy(V).cuda()
     for n in range(5000):
-        ch, it, _, _ = nl.nlp_gf_step(plan.handle, tphi, tV, 1.0, 0.0, 1e-2, 1e-12, 200)
+        ch, it, _, _ = nl.nlp_gf_step(plan.handle, tphi, tV, beta, 0.0, 1e-2, 1e-12, 200)
         if ch <= 1e-8:
             break
-    E = nl.nlp_energies(plan.handle, tphi, tV, 1.0, 0.0)
+    E = nl.nlp_energies(plan.handle, tphi, tV, beta, 0.0)
     plan.close()
     rows = {float(r[0]): r[1:] for r in load_golden("paper_gs_energies_3d_coulomb.txt")}
-    for key, txt in zip(("E", "mu", "Ekin", "Epot", "Eint"), rows[1.0]):
+    for key, txt in zip(("E", "mu", "Ekin", "Epot", "Eint"), rows[beta]):
         mant, _, ex = txt.upper().partition("E")
         ulp = 10.0 ** (-len(mant.split(".")[1]) + (int(ex) if ex else 0))
         assert abs(E[key] - float(txt)) < ulp, (key, E[key], txt)
@@ -79,7 +82,7 @@ def test_gpu_ground_state_matches_paper_table(nl):
 
 
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_ts_step_parity_and_mass(nl, order, prec, tol):
     import torch
     g = W.Grid((48, 40), (8.0, 7.0))
@@ -100,7 +103,9 @@ def test_ts_step_parity_and_mass(nl, order, prec, tol):
         nl.nlp_ts_step(plan.handle, tpsi, tV, 5.0, 0.3, 0.01, order)
     out = tpsi.cpu().numpy().astype(np.complex128)
     plan.close()
-    assert np.max(np.abs(out - ref)) / np.max(np.abs(ref)) < tol
+    err = np.max(np.abs(out - ref)) / np.max(np.abs(ref))
+    print("ts_step order %d %s rel L-inf vs oracle %.3e" % (order, prec, err))
+    assert err < tol
     m0 = float(np.sum(np.abs(psi0) ** 2))
     assert abs(float(np.sum(np.abs(out) ** 2)) - m0) < (1e-12 if prec == "fp64" else 1e-5) * m0
 
@@ -180,7 +185,7 @@ def test_gpu_dynamics_example_4_1_error_levels(nl, beta):
             assert e_psi < 1e-10 and e_phi < 1e-10
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_gf_step_parity_poisson2d(nl, prec, tol):
     """One gradient-flow step with the 2D Laplace kernel (potential through Algorithm 1)
     against the oracle's step with its own Algorithm 1 evaluation."""

@@ -74,6 +74,24 @@ def test_truncation_level_matches_erfc():
     assert err < 1e-5
 
 
+def test_config1_counts_doubling_study():
+    """The 32^3 closed-form case (rho = exp(-|x|^2) on [-8,8)^3, P = 2 pi): at its stated
+    32 x 32 x 64 nodes the closed-form error is set by the quadrature (3.44e-5); doubling every
+    count brings it down to the truncation tail erfc(P/2) of the ball, and doubling again
+    changes nothing, so the counts are then converged and the truncation is the whole error."""
+    g = W.cube(32, 8.0)
+    rho = W.gaussian(g, [1.0] * 3)
+    P = 2.0 * math.pi
+    X, r = _mesh_r(g)
+    ex = cf.coulomb3d_iso(r, 1.0)
+    errs = [cf.rel_linf(potential.eval_nufft(rho, g, "coulomb3d", P, c, tol=1e-13), ex)
+            for c in ((32, 32, 64), (64, 64, 128), (96, 96, 192))]
+    tail = special.erfc(P / 2.0)
+    assert 3.3e-5 < errs[0] < 3.6e-5, errs
+    assert 0.9 * tail < errs[1] < 1.0 * tail, (errs, tail)
+    assert abs(errs[2] - errs[1]) < 1e-3 * errs[1], errs
+
+
 def test_anisotropic_and_dipolar_closed_forms():
     a = (1.0, 2.0 ** 0.5, 2.0)
     g = W.Grid((40, 40, 54), (7.0, 7.0, 10.0))
