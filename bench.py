@@ -171,7 +171,7 @@ def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stre
         st = nl.nlp_get_stage_times(plan.handle)     # syncs on the last stage event
         for name, ms in st:
             stage_tot[name] = stage_tot.get(name, 0.0) + ms
-        launches += sum(1 for name, _ in st if name != "clear")
+        launches += len(st)   # one kernel launch per recorded stage
     torch.cuda.synchronize()
     nl.nlp_set_stage_timing(plan.handle, False)
     times = [a.elapsed_time(b) for a, b in ev]
@@ -294,9 +294,6 @@ def gpu_arm(args):
                            method=2)
     ress32 = run_precision(nl, torch, "fp32", g, rho, P, None, args.steps, args.warmup, flush, stream, e2e=False,
                            method=2)
-    # FP32 with the z contractions of interpolation/spreading on the tensor cores (spread_variant 2)
-    rest32 = run_precision(nl, torch, "fp32", g, rho, P, counts, args.steps, args.warmup, flush, stream, e2e=False,
-                           spread_variant=2)
     clocks = clk.stop()
     torch.cuda.synchronize()
     t32 = sum(res32["times"]) / 1e3
@@ -366,13 +363,6 @@ def gpu_arm(args):
                          "ms_per_step": sum(ress32["times"]) / len(ress32["times"]),
                          "rel_linf_vs_oracle": cf.rel_linf(ress32["phi"], ref), "plan_s": ress32["plan_s"],
                          "nodes": ress32["info"]["nodes_total"], "radius": ress32["info"]["split_radius"]}},
-            "fp32_tensor_core_spread": {
-                "note": "plan option spread_variant=2: the z contractions of interpolation and spreading as "
-                        "mma.sync TF32 with hi/lo error compensation (same operator; measured, not the default)",
-                "value": len(rest32["times"]) / (sum(rest32["times"]) / 1e3), "unit": "evals/s",
-                "ms_per_step": sum(rest32["times"]) / len(rest32["times"]),
-                "interp_spread_ms": rest32["stages"].get("interp_spread"),
-                "rel_linf_vs_oracle": cf.rel_linf(rest32["phi"], ref)},
             "stages_ms": res32["stages"],
             "roofline": r32,
             "cpu_baseline": {"value": 1.0 / t_or, "unit": "evals/s", "cores": native.max_threads(), "kind": "oracle",

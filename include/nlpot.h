@@ -92,11 +92,8 @@ typedef struct {
     double dipole_axis[3];  /* NLP_DIPOLE_3D: unit vector (normalised here; zero vector -> z) */
     double nufft_tol;       /* NUFFT tolerance, 1e-14..1e-2; 0 -> 1e-12 (FP64) / 1e-6 (FP32) */
     int tile;               /* spread/interp tile edge in fine cells: 0 = default, else 2..32 */
-    int spread_variant;     /* 0 = default (3D: register-column kernel where the width is supported),
-                               1 = shared-memory-atomics kernel everywhere,
-                               2 = as 0, but FP32 plans with sub-window 8 (tol 1e-6) run the z
-                                   contractions on the tensor cores (mma.sync TF32 with hi/lo
-                                   error compensation; same result within FP32 rounding) */
+    int spread_variant;     /* 0 = default (3D: register-column kernels where the width is supported),
+                               1 = the generic one-warp-per-node kernel everywhere */
     int method;             /* 0 = NUFFT per evaluation (default).  1 = precomputed discrete kernel:
                                the quadrature sum of Eq. (ifft) equals sum_i' K(i - i') rho_i' with
                                K(m) = sum_j w_j |k_j|^{d-1} U-hat(k_j) cos(k_j . m h) h^d / (2 pi)^d;
@@ -136,6 +133,7 @@ typedef struct {
     int64_t segments;       /* register kernel work units (node runs of one sub-tile) */
     double split_a;         /* method 2: partition parameter a (0 otherwise) */
     double split_radius;    /* method 2: radius k2 of the NUFFT ball of I_2 (0 otherwise) */
+    int64_t combine_entries;/* window slots summed by the combine pass, over all tiles of G */
 } nlp_plan_info;
 
 /* Create a plan: quadrature nodes and weights (FP64), their binning by fine-grid tile,
@@ -272,8 +270,8 @@ enum {
     NLP_STAGE_FWD_LAST = 0,   /* deconvolve + zero-pad + R2C FFT along the last axis */
     NLP_STAGE_FWD_MID = 1,    /* forward FFT along axis 1 (3D) / axis 0 (2D) */
     NLP_STAGE_FWD_FIRST = 2,  /* forward FFT along axis 0 (3D only) */
-    NLP_STAGE_CLEAR = 3,      /* zero the spreading target */
-    NLP_STAGE_SPREAD = 4,     /* fused interpolate -> scale -> spread */
+    NLP_STAGE_COMBINE = 3,    /* sum the chunks' windows into the spreading target (writes all of it) */
+    NLP_STAGE_SPREAD = 4,     /* fused interpolate -> scale -> spread (chunk windows to scratch) */
     NLP_STAGE_INV_FIRST = 5,  /* inverse FFT along axis 0 (3D only) */
     NLP_STAGE_INV_MID = 6,    /* inverse FFT along axis 1 (3D) / axis 0 (2D) */
     NLP_STAGE_INV_LAST = 7,   /* C2R FFT along the last axis + deconvolve + crop */

@@ -40,7 +40,7 @@ class nlp_plan_info(ctypes.Structure):
                 ("nodes_half", ctypes.c_int64), ("tiles", ctypes.c_int64), ("chunks", ctypes.c_int64),
                 ("tile", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t), ("sigma_poisson", ctypes.c_double),
                 ("sub_tile", ctypes.c_int), ("segments", ctypes.c_int64), ("split_a", ctypes.c_double),
-                ("split_radius", ctypes.c_double)]
+                ("split_radius", ctypes.c_double), ("combine_entries", ctypes.c_int64)]
 
 
 class NlpError(RuntimeError):
@@ -248,7 +248,7 @@ def nlp_ts_step(plan, psi, V, beta: float, g: float = 0.0, tau: float = 1e-3, or
            "nlp_ts_step")
 
 
-STAGES = {0: "fwd_last", 1: "fwd_mid", 2: "fwd_first", 3: "clear", 4: "interp_spread",
+STAGES = {0: "fwd_last", 1: "fwd_mid", 2: "fwd_first", 3: "combine", 4: "interp_spread",
           5: "inv_first", 6: "inv_mid", 7: "inv_last", 8: "poisson_fp64"}
 
 

@@ -23,9 +23,9 @@
 
 namespace nlp {
 
-enum { ST_R2C = 0, ST_A1, ST_A0, ST_CLEAR, ST_SPREAD, ST_B0, ST_B1, ST_C2R, kStages };
+enum { ST_R2C = 0, ST_A1, ST_A0, ST_SPREAD, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
 constexpr int kRegLines = 16;          // lines (pairs) per register-engine FFT task: 16 x 16 threads
-constexpr int kClearChunk = 1 << 16;   // complex elements of G zeroed per clear task
+constexpr int kCombTiles = 16;         // combine tiles of G per task
 
 struct BatchItem {
     DevPlan<float> P;
@@ -33,9 +33,8 @@ struct BatchItem {
     int nb_r2c, nb_a1, nb_a0, nb_c2r;
     int ntask[kStages];
     int dep[kStages];        // stage this stage waits for (-1: none)
-    int spread_warp;         // 1: register kernel (W = 8), 0: shared-atomics kernel
+    int spread_warp;         // 1: one-warp-per-piece kernel (W = 8), 0: generic kernel
     int reg_fft;             // 1: FFT passes on the register radix engine (16 lines per task)
-    int64_t gsize;           // complex elements of G
 };
 
 struct BatchArgs {
@@ -109,15 +108,15 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
                 if (B.reg_fft) fft_cols_block<float, -1, kRegLines>(B.P.F, B.a0, B.P.len[0], i, smraw);
                 else fft_strided_block<float, -1>(B.P.F, B.a0, B.P.len[0], B.nb_a0, i, smraw);
                 break;
-            case ST_CLEAR: {
-                const int64_t e0 = (int64_t)i * kClearChunk, e1 = min(e0 + kClearChunk, B.gsize);
-                for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) B.P.G[e] = mk<float>(0.f, 0.f);
-                break;
-            }
             case ST_SPREAD:
-                if (B.spread_warp) spread_warp_block<float, 8, 4>(B.P, i, smraw);
+                if (B.spread_warp) spread_warp_block<8, 4>(B.P, i, smraw);
                 else spread_generic_block<float>(B.P, i, smraw);
                 break;
+            case ST_COMBINE: {
+                const int64_t t1 = min((int64_t)(i + 1) * kCombTiles, B.P.cmb_tiles);
+                for (int64_t t = (int64_t)i * kCombTiles; t < t1; ++t) combine_block<float>(B.P, t);
+                break;
+            }
             case ST_B0:
                 if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(B.P.G, B.b0, B.P.len[0], i, smraw);
                 else fft_strided_block<float, +1>(B.P.G, B.b0, B.P.len[0], B.nb_a0, i, smraw);
@@ -220,6 +219,10 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         if (!plans[p]) return NLP_ERR_INVALID_ARG;
         if (plans[p]->prec != NLP_FP32 || plans[p]->kernel == NLP_POISSON_2D || plans[p]->opts.method != 0)
             return NLP_ERR_UNSUPPORTED;
+        // register kernels other than the one-warp-per-piece kernel (FP32 tolerances below
+        // 1e-6) run as their own launches only
+        const DevPlan<float> &D = plans[p]->pf;
+        if (D.sub_T > 0 && !(D.sub_T == 2 && D.w == 7)) return NLP_ERR_UNSUPPORTED;
     }
     nlp_batch_s *b = new (std::nothrow) nlp_batch_s();
     if (!b) return NLP_ERR_OOM;
@@ -266,14 +269,14 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         B.ntask[ST_R2C] = (int)((npairs + B.nb_r2c - 1) / B.nb_r2c);
         B.ntask[ST_A1] = B.a1.nouter * (int)((nh + B.nb_a1 - 1) / B.nb_a1);
         B.ntask[ST_A0] = three ? B.a0.nouter * (int)((nh + B.nb_a0 - 1) / B.nb_a0) : 0;
-        B.gsize = (int64_t)D.nf[0] * D.nf[1] * nh;
-        B.ntask[ST_CLEAR] = (int)((B.gsize + kClearChunk - 1) / kClearChunk);
         B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
         B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);
+        B.ntask[ST_COMBINE] = (int)((D.cmb_tiles + kCombTiles - 1) / kCombTiles);
         B.ntask[ST_B0] = B.ntask[ST_A0];
         B.ntask[ST_B1] = B.ntask[ST_A1];
         B.ntask[ST_C2R] = B.ntask[ST_R2C];
-        // stage dependencies: spreading needs the forward spectrum and the cleared G
+        // stage dependencies: each stage waits for the previous non-empty stage of its item
+        // (the combine reads every window slot; the inverse passes read all of G)
         int last = -1;
         for (int k = 0; k < kStages; ++k) {
             B.dep[k] = last;
@@ -289,12 +292,11 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
             smem = std::max(smem, fft_bytes(D.len[1].N, B.nb_a1));
             if (three) smem = std::max(smem, fft_bytes(D.len[0].N, B.nb_a0));
         }
-        smem = std::max(smem, B.spread_warp ? interp_spread_reg_smem<float>(D) : interp_spread_smem<float>(D));
+        smem = std::max(smem, B.spread_warp ? interp_spread_reg_smem<float>(D, 8) : interp_spread_smem<float>(D, 8));
     }
     b->smem = smem;
-    // CLEAR of G only needs nothing before it, but must finish before SPREAD: SPREAD depends
-    // on CLEAR, which depends on the forward passes (stage order), so G is never cleared
-    // while a previous evaluation still reads it.
+    // Stages run in this order per item, so the window slots and G are never rewritten while
+    // an earlier stage of the same item still reads them.
     b->off.assign((size_t)kStages * count + 1, 0);
     int t = 0;
     for (int k = 0; k < kStages; ++k)

@@ -42,10 +42,23 @@ template <typename T> struct FftLen {
     const cpx<T> *tw;         // device: e^{-2 pi i m / N}, m = 0..N-1
 };
 
-// Interp/spread work item: one chunk of the nodes of one tile.
+// Interp/spread work item: one chunk of the nodes of one tile.  Each chunk accumulates its
+// tile window (tile + w - 1 cells per axis) on chip and writes it, once, to its own slot of
+// the window scratch; the combine pass sums the slots into the spreading target.
 struct Chunk {
     int bx, by, bz;     // unwrapped fine-grid cell of the tile origin
     int j0, j1;         // node range in the sorted node arrays
+    float wsum;         // sum of |omega_j| over the chunk's nodes (bounds its window, see spread_dev.cuh)
+};
+
+// One window slot feeding one combine tile of the spreading target G (the k -> -k half
+// spectrum).  For an output cell l of the tile, the slot's window cell is a_d = l_d + o_d
+// (direct) or a_d = -l_d + o_d (mirror: the conjugate of the window value at -l goes to l),
+// taken only when 0 <= a_d < window extent on every axis.
+struct CombEntry {
+    int chunk;          // window slot
+    int mirror;         // 0 direct, 1 Hermitian mirror
+    int o[3];
 };
 
 // Device pointers and sizes of one plan, in the plan precision T.
@@ -86,7 +99,16 @@ template <typename T> struct DevPlan {
     int ones_mode;      // spreading of the weights alone (rho-hat := 1): builds the discrete kernel
     const cpx<T> *Khat; // precomputed-kernel method: spectrum of K on the 2n grid (else null)
     int accumulate;     // 1: the final pass adds into phi instead of overwriting it
-    int use_mma;        // FP32 register kernel with W = 8: tensor-core variant (spread_mma.cuh)
+    // window scratch and its combine into G (see spread_common.cuh)
+    cpx<T> *win;        // one slot of win_n[0] x win_n[1] x win_n[2] cells per chunk of the active kernel
+    int win_n[3];       // window extent (tile + w - 1 per axis; axis 0 of 2D plans: 1)
+    int64_t win_cells;
+    const int *cmb_off;     // per combine tile: its entries are cmb[cmb_off[t] .. cmb_off[t+1])
+    const CombEntry *cmb;
+    int cmb_t[3];       // combine tile edge per axis
+    int cmb_n[3];       // combine tiles per axis (over nf0 x nf1 x nh)
+    int64_t cmb_tiles;
+    float psi_sum3;     // FP32 warp kernel: (max over node offsets of sum_t psi)^3, bounds the interpolation
 };
 
 }  // namespace nlp

@@ -40,13 +40,17 @@ cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<
 template <typename T>
 cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, int sign, T post, cudaStream_t st);
 
-// Fused interpolate -> scale -> spread over all node chunks (see spread.cu).
+// Fused interpolate -> scale -> spread over all node chunks (see spread.cu): each chunk's
+// tile window goes to its slot of P.win; launch_combine then writes every cell of G.
 template <typename T> cudaError_t launch_interp_spread(const DevPlan<T> &P, cudaStream_t st);
-template <typename T> size_t interp_spread_smem(const DevPlan<T> &P);
-// Register-column variant for 3D (see spread_reg.cu); W = sub-tile edge + w - 1.
+template <typename T> int generic_warps(const DevPlan<T> &P, size_t smem_limit);
+template <typename T> size_t interp_spread_smem(const DevPlan<T> &P, int nwarps);
+// Register-column variants for 3D (see spread_reg.cu); W = sub-tile edge + w - 1.
 template <typename T> bool reg_kernel_supported(int W);
-template <typename T> size_t interp_spread_reg_smem(const DevPlan<T> &P);
+template <typename T> bool warp_kernel_used(int W);   // FP32 one-warp-per-piece kernel
+template <typename T> size_t interp_spread_reg_smem(const DevPlan<T> &P, int nwarps_warp_kernel);
 template <typename T> cudaError_t launch_interp_spread_reg(const DevPlan<T> &P, cudaStream_t st);
+template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st);
 
 // 2D Poisson (Algorithm 1) FP64 parts (see poisson2d.cu).  L, h: collapsed 3D view.
 template <typename T>

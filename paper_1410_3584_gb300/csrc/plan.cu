@@ -197,6 +197,86 @@ struct HostNode {
     double k[2], r;  // 2D Poisson: k and |k|
 };
 
+// Combine entries (see spread_common.cuh): for every chunk window, the output tiles of G its
+// cells reach directly and through the Hermitian mirror, with the index offsets that map an
+// output cell back to the window cell.  Per axis the window cells give a set of (tile, offset)
+// pairs; the entries are the products of the three sets (direct: last-axis cells in [0, nf/2],
+// mirror: last-axis cells at 0 or >= nf/2), sorted by tile, then by chunk.
+template <typename T>
+static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<Chunk> &act) {
+    const int N[3] = {D.nf[0], D.nf[1], D.nf[2]};
+    const int Nout[3] = {D.nf[0], D.nf[1], D.nh};
+    const bool two = p->grid.dim == 2;
+    D.cmb_t[0] = two ? 1 : 8;
+    D.cmb_t[1] = two ? 16 : 8;
+    D.cmb_t[2] = two ? 16 : 8;
+    for (int a = 0; a < 3; ++a) D.cmb_n[a] = (Nout[a] + D.cmb_t[a] - 1) / D.cmb_t[a];
+    D.cmb_tiles = (int64_t)D.cmb_n[0] * D.cmb_n[1] * D.cmb_n[2];
+    struct Key { int64_t tile; CombEntry e; };
+    std::vector<Key> keys;
+    keys.reserve(act.size() * 12);
+    auto wrap = [](int64_t x, int n) { int64_t r = x % n; return (int)(r < 0 ? r + n : r); };
+    for (size_t c = 0; c < act.size(); ++c) {
+        const int b[3] = {act[c].bx, act[c].by, act[c].bz};
+        std::vector<std::pair<int, int>> dir[3], mir[3];
+        for (int a = 0; a < 3; ++a) {
+            for (int u = 0; u < D.win_n[a]; ++u) {
+                const int l = wrap((int64_t)b[a] + u, N[a]);
+                const bool last = a == 2;
+                if (!last || 2 * l <= N[2]) dir[a].push_back({l / D.cmb_t[a], u - l});
+                if (!last || l == 0 || 2 * l >= N[2]) {
+                    const int m = (N[a] - l) % N[a];
+                    mir[a].push_back({m / D.cmb_t[a], u + m});
+                }
+            }
+            for (auto *v : {&dir[a], &mir[a]}) {
+                std::sort(v->begin(), v->end());
+                v->erase(std::unique(v->begin(), v->end()), v->end());
+            }
+        }
+        for (int mr = 0; mr < 2; ++mr) {
+            const auto *S = mr ? mir : dir;
+            for (const auto &x : S[0])
+                for (const auto &y : S[1])
+                    for (const auto &z : S[2]) {
+                        Key k;
+                        k.tile = ((int64_t)x.first * D.cmb_n[1] + y.first) * D.cmb_n[2] + z.first;
+                        k.e.chunk = (int)c;
+                        k.e.mirror = mr;
+                        k.e.o[0] = x.second;
+                        k.e.o[1] = y.second;
+                        k.e.o[2] = z.second;
+                        keys.push_back(k);
+                    }
+        }
+    }
+    std::sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) {
+        if (a.tile != b.tile) return a.tile < b.tile;
+        if (a.e.chunk != b.e.chunk) return a.e.chunk < b.e.chunk;
+        if (a.e.mirror != b.e.mirror) return a.e.mirror < b.e.mirror;
+        for (int d = 0; d < 3; ++d)
+            if (a.e.o[d] != b.e.o[d]) return a.e.o[d] < b.e.o[d];
+        return false;
+    });
+    std::vector<int> off(D.cmb_tiles + 1, 0);
+    std::vector<CombEntry> ent(keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) {
+        off[keys[i].tile + 1]++;
+        ent[i] = keys[i].e;
+    }
+    for (int64_t t = 0; t < D.cmb_tiles; ++t) off[t + 1] += off[t];
+    void *doff = nullptr, *dent = nullptr;
+    nlp_status s;
+    if ((s = alloc_dev(p, &doff, sizeof(int) * off.size()))) return s;
+    if ((s = alloc_dev(p, &dent, sizeof(CombEntry) * std::max<size_t>(1, ent.size())))) return s;
+    cudaMemcpy(doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+    if (!ent.empty()) cudaMemcpy(dent, ent.data(), sizeof(CombEntry) * ent.size(), cudaMemcpyHostToDevice);
+    D.cmb_off = (const int *)doff;
+    D.cmb = (const CombEntry *)dent;
+    p->info.combine_entries = (int64_t)ent.size();
+    return NLP_OK;
+}
+
 template <typename T>
 static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes, DevPlan<T> &D) {
     D.dim = p->grid.dim;
@@ -210,7 +290,6 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     // register kernel (3D): sub-tile edge Ts with column length W = Ts + w - 1 (see spread_reg.cu)
     D.sub_T = 0;
     int Tt = p->opts.tile;
-    D.use_mma = p->opts.spread_variant == 2 ? 1 : 0;
     if (p->grid.dim == 3 && p->opts.spread_variant != 1) {
         const int Ts = 2;
         if (reg_kernel_supported<T>(Ts + D.w - 1)) {
@@ -225,8 +304,13 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.T_tile[2] = Tt;
     p->info.tile = Tt;
     p->info.sub_tile = D.sub_T;
-    if (interp_spread_smem(D) > 227 * 1024) return NLP_ERR_UNSUPPORTED;
-    if (D.sub_T > 0 && interp_spread_reg_smem(D) > 227 * 1024) return NLP_ERR_UNSUPPORTED;
+    D.win_n[0] = D.T_tile[0] + (p->grid.dim == 3 ? D.w : 1) - 1;
+    D.win_n[1] = D.T_tile[1] + D.w - 1;
+    D.win_n[2] = D.T_tile[2] + D.w - 1;
+    D.win_cells = (int64_t)D.win_n[0] * D.win_n[1] * D.win_n[2];
+    const bool warp_k = D.sub_T > 0 && warp_kernel_used<T>(D.sub_T + D.w - 1);
+    if (D.sub_T == 0 && generic_warps(D, (size_t)max_dyn_smem()) < 1) return NLP_ERR_UNSUPPORTED;
+    if (D.sub_T > 0 && interp_spread_reg_smem(D, 4) > (size_t)max_dyn_smem()) return NLP_ERR_UNSUPPORTED;
     for (int a = 0; a < 3; ++a) {
         nlp_status s = make_fft_len<T>(p, D.nf[a], &D.len[a]);
         if (s) return s;
@@ -384,6 +468,18 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     std::vector<T> nd(4 * (size_t)M);
     std::vector<uint32_t> no(M);
     const int Wsub = Ts + D.w - 1;
+    // per-chunk sums of |omega_j| (they bound each chunk's window, see spread_dev.cuh)
+    {
+        std::vector<double> aom(M + 1, 0.0);
+        for (int64_t q = 0; q < M; ++q) aom[q + 1] = aom[q] + std::fabs(nodes[order[q]].omega);
+        auto up = [](double v) { return (float)(v * (1.0 + 1e-6)); };
+        for (Chunk &c : chunks) c.wsum = up(aom[c.j1] - aom[c.j0]);
+        for (Chunk &c : rchunks) {
+            double sum = 0.0;
+            for (int i = c.j0; i < c.j1; ++i) sum += aom[seg_node[2 * i + 1]] - aom[seg_node[2 * i]];
+            c.wsum = up(sum);
+        }
+    }
     std::vector<double> pois;
     if (p->kernel == NLP_POISSON_2D) pois.resize(3 * (size_t)M);
     for (int64_t q = 0; q < M; ++q) {
@@ -392,7 +488,11 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         for (int a = 0; a < 3; ++a) {
             const int64_t sj = s0[3 * j + a];
             const int64_t o = sj - tb[3 * j + a] * D.T_tile[a];
-            nd[4 * q + a] = (T)(nodes[j].z[a] - (double)sj);
+            // offset of the node from its first tap; for the FP32 warp kernel, from the origin
+            // of its sub-window (first tap + tile offset mod Ts), which that kernel evaluates
+            // the kernel values against
+            const double base = warp_k ? (double)(sj - o % Ts) : (double)sj;
+            nd[4 * q + a] = (T)(nodes[j].z[a] - base);
             packed |= (uint32_t)o << (8 * a);
         }
         nd[4 * q + 3] = (T)nodes[j].omega;
@@ -417,14 +517,17 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.nrchunks = 0;
     D.psi_tab = nullptr;
     if (Ts > 0 && M) {
-        // kernel values of every node (the nodes are fixed per plan), placed in the
-        // sub-window of its segment; computed on the device from (delta, offsets)
-        void *dpt;
-        if ((s = alloc_dev(p, &dpt, sizeof(T) * (size_t)M * 3 * Wsub))) return s;
-        if (launch_psi_table<T>((T *)dpt, (const T *)dnd, (const uint32_t *)dno, M, D.w, Wsub, Ts, p->info.beta_es,
-                                p->stream) != cudaSuccess)
-            return NLP_ERR_CUDA;
-        D.psi_tab = (const T *)dpt;
+        // team kernel: kernel values of every node (the nodes are fixed per plan), placed in
+        // the sub-window of its segment; computed on the device from (delta, offsets).  The
+        // FP32 warp kernel evaluates them per evaluation instead.
+        if (!warp_k) {
+            void *dpt;
+            if ((s = alloc_dev(p, &dpt, sizeof(T) * (size_t)M * 3 * Wsub))) return s;
+            if (launch_psi_table<T>((T *)dpt, (const T *)dnd, (const uint32_t *)dno, M, D.w, Wsub, Ts,
+                                    p->info.beta_es, p->stream) != cudaSuccess)
+                return NLP_ERR_CUDA;
+            D.psi_tab = (const T *)dpt;
+        }
         void *dsn, *dss, *drc;
         if ((s = alloc_dev(p, &dsn, sizeof(int) * seg_node.size()))) return s;
         if ((s = alloc_dev(p, &dss, sizeof(uint32_t) * seg_sub.size()))) return s;
@@ -479,6 +582,31 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.nchunks = (int64_t)chunks.size();
     p->info.tiles = ntiles_used;
     p->info.chunks = D.nchunks;
+    // (max over node offsets of the sum of the w kernel values)^3: with the F window's
+    // largest component it bounds |rho-hat_j| in the FP32 warp kernel's fixed-point spreading
+    {
+        double cmax = 0.0;
+        const int ns = 4000;
+        for (int i = 0; i <= ns; ++i) {
+            const double d = 0.5 * D.w - 1.0 + (double)i / ns;   // offset from the first tap
+            double sum = 0.0;
+            for (int t = 0; t < D.w; ++t) {
+                const double x = 2.0 * (t - d) / D.w, sv = 1.0 - x * x;
+                if (sv > 0) sum += std::exp(p->info.beta_es * (std::sqrt(sv) - 1.0));
+            }
+            cmax = std::max(cmax, sum);
+        }
+        cmax *= 1.001;
+        D.psi_sum3 = (float)(cmax * cmax * cmax);
+    }
+    // window scratch (one slot per chunk of the kernel that runs) and the combine entries
+    {
+        const std::vector<Chunk> &act = Ts > 0 ? rchunks : chunks;
+        void *dw = nullptr;
+        if ((s = alloc_dev(p, &dw, sizeof(cpx<T>) * (size_t)D.win_cells * std::max<size_t>(1, act.size())))) return s;
+        D.win = (cpx<T> *)dw;
+        if ((s = build_combine<T>(p, D, act))) return s;
+    }
     if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
     return NLP_OK;
 }
@@ -655,7 +783,7 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if (o->n_r > 4096 || o->n_theta > 4096 || o->n_phi > 8192) return NLP_ERR_INVALID_ARG;
         if ((o->n_theta % 2) || (o->n_phi % 2)) return NLP_ERR_INVALID_ARG;
         if (o->tile != 0 && (o->tile < 2 || o->tile > 32)) return NLP_ERR_INVALID_ARG;
-        if (o->spread_variant < 0 || o->spread_variant > 2) return NLP_ERR_INVALID_ARG;
+        if (o->spread_variant < 0 || o->spread_variant > 1) return NLP_ERR_INVALID_ARG;
         if (o->method < 0 || o->method > 2) return NLP_ERR_INVALID_ARG;
         if (o->method == 1 && kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
         if (o->method == 2 && g->dim != 3) return NLP_ERR_UNSUPPORTED;

@@ -1,4 +1,15 @@
-// Device helpers shared by the interpolation/spreading kernels (spread.cu, spread_reg.cu).
+// Device helpers shared by the interpolation/spreading kernels (spread.cu, spread_reg.cu,
+// batch.cu): the spreading function, the tile window of the forward spectrum, and the
+// combine pass that turns the chunks' windows into the spreading target G.
+//
+// Spreading without global atomics.  Every chunk (a run of the nodes of one fine-grid tile)
+// accumulates the spread of its nodes over its tile window on chip, in an order fixed by
+// the kernel, and writes that window once to its own slot of a scratch array.  The combine
+// pass then owns each tile of G: for every output cell it adds, in a fixed order, the window
+// cells of all slots that reach it, including the Hermitian mirror (a tap at position l of
+// the k -> -k half contributes v at l and conj(v) at -l; only last-axis positions in
+// [0, nf/2] are stored).  No value is ever added to global memory by two threads, so two
+// evaluations of the same input give bit-identical results.
 #pragma once
 #include "common.cuh"
 
@@ -16,38 +27,12 @@ __device__ __forceinline__ int wrapn(int l, int N) {
     return r < 0 ? r + N : r;
 }
 
-template <typename T>
-__device__ __forceinline__ cpx<T> load_herm(const DevPlan<T> &P, int g0, int g1, int g2) {
-    const int l0 = wrapn(g0, P.nf[0]), l1 = wrapn(g1, P.nf[1]), l2 = wrapn(g2, P.nf[2]);
-    if (2 * l2 <= P.nf[2]) return P.F[((int64_t)l0 * P.nf[1] + l1) * P.nh + l2];
-    const int m0 = l0 ? P.nf[0] - l0 : 0, m1 = l1 ? P.nf[1] - l1 : 0, m2 = P.nf[2] - l2;
-    return conj(P.F[((int64_t)m0 * P.nf[1] + m1) * P.nh + m2]);
-}
-
-template <typename T>
-__device__ __forceinline__ void red_add(cpx<T> *p, cpx<T> v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-
-template <typename T>
-__device__ __forceinline__ void store_fold(const DevPlan<T> &P, int g0, int g1, int g2, cpx<T> v) {
-    const int l0 = wrapn(g0, P.nf[0]), l1 = wrapn(g1, P.nf[1]), l2 = wrapn(g2, P.nf[2]);
-    const int N2 = P.nf[2];
-    const int m0 = l0 ? P.nf[0] - l0 : 0, m1 = l1 ? P.nf[1] - l1 : 0;
-    if (2 * l2 <= N2) red_add(P.G + ((int64_t)l0 * P.nf[1] + l1) * P.nh + l2, v);
-    if (l2 == 0 || 2 * l2 >= N2) {
-        const int m2 = l2 ? N2 - l2 : 0;
-        red_add(P.G + ((int64_t)m0 * P.nf[1] + m1) * P.nh + m2, conj(v));
-    }
-}
-
 __host__ __device__ __forceinline__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 // Window rows of a tile chunk in the half spectrum.  Row r = a Wt1 + b of the tile window is
 // the fine-grid line (l0, l1) = (bx + a, by + b) mod (nf0, nf1); its Hermitian mirror is the
 // line (-l0, -l1).  The half-spectrum offsets of both lines are tabulated once per chunk, so
-// that filling and folding the window costs one table read and one add per cell.
+// that filling the window costs one table read and one add per cell.
 template <typename T>
 __device__ __forceinline__ void window_row_table(const DevPlan<T> &P, const Chunk &ch, int Wt0, int Wt1,
                                                  int64_t *rowoff, int64_t *rowmir) {
@@ -60,16 +45,13 @@ __device__ __forceinline__ void window_row_table(const DevPlan<T> &P, const Chun
     }
 }
 
-// The window column along the last axis that a thread fills and folds for every row it
-// visits (thread t: column t mod Wt2, rows t / Wt2 + k (blockDim / Wt2)), with the last-axis
-// wrap and the Hermitian decisions of load_herm / store_fold taken once per chunk.
+// The window column along the last axis that a thread fills for every row it visits
+// (thread t: column t mod Wt2, rows t / Wt2 + k (blockDim / Wt2)), with the last-axis wrap
+// and the Hermitian decision taken once per chunk.
 struct WinCol {
     int c, r0, rstep;
     int l2;      // wrapped last-axis index
-    bool herm;   // fill: F read from the mirror line at nf2 - l2, conjugated
-    bool prim;   // fold: add at (l0, l1, l2)
-    bool mir;    // fold: add the conjugate at (m0, m1, mz)
-    int mz;
+    bool herm;   // F read from the mirror line at nf2 - l2, conjugated
 };
 
 template <typename T>
@@ -82,33 +64,56 @@ __device__ __forceinline__ WinCol window_col(const DevPlan<T> &P, const Chunk &c
     const int N2 = P.nf[2];
     k.l2 = wrapn(ch.bz + k.c, N2);
     k.herm = 2 * k.l2 > N2;
-    k.prim = 2 * k.l2 <= N2;
-    k.mir = k.l2 == 0 || 2 * k.l2 >= N2;
-    k.mz = k.l2 ? N2 - k.l2 : 0;
     return k;
 }
 
-// sF := F on the window (cells r * pitch + c), sG := 0
+// sF := F on the window (cell (r, c) at r * pitch + c for rows r < rows, or at
+// (r / Wt1) * plane + (r % Wt1) * pitch + c when plane > 0); returns the largest |re| or |im|
+// of the cells this thread filled.
 template <typename T>
-__device__ __forceinline__ void window_fill(const DevPlan<T> &P, const WinCol &k, const int64_t *rowoff,
-                                            const int64_t *rowmir, int rows, int pitch, cpx<T> *sF, cpx<T> *sG) {
+__device__ __forceinline__ T window_fill(const DevPlan<T> &P, const WinCol &k, const int64_t *rowoff,
+                                         const int64_t *rowmir, int rows, int pitch, cpx<T> *sF, int Wt1 = 1,
+                                         int plane = 0) {
     const int N2 = P.nf[2];
+    T mx = (T)0;
     for (int r = k.r0; r < rows; r += k.rstep) {
         const cpx<T> v = k.herm ? conj(P.F[rowmir[r] + (N2 - k.l2)]) : P.F[rowoff[r] + k.l2];
-        sF[r * pitch + k.c] = v;
-        sG[r * pitch + k.c] = mk<T>(0, 0);
+        const int q = plane > 0 ? (r / Wt1) * plane + (r % Wt1) * pitch + k.c : r * pitch + k.c;
+        sF[q] = v;
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
+    return mx;
 }
 
-// G += the window sG, folded onto the half spectrum
+// ------------------------------------------------------------------ combine
+// Output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G with
+// N = (nf0, nf1, nh).  Every cell of G belongs to exactly one tile and is written exactly once
+// (tiles that no window reaches get zeros), so the pass also replaces clearing G.
 template <typename T>
-__device__ __forceinline__ void window_fold(const DevPlan<T> &P, const WinCol &k, const int64_t *rowoff,
-                                            const int64_t *rowmir, int rows, int pitch, const cpx<T> *sG) {
-    for (int r = k.r0; r < rows; r += k.rstep) {
-        const cpx<T> v = sG[r * pitch + k.c];
-        if (v.x == (T)0 && v.y == (T)0) continue;
-        if (k.prim) red_add(P.G + rowoff[r] + k.l2, v);
-        if (k.mir) red_add(P.G + rowmir[r] + k.mz, conj(v));
+__device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile) {
+    const int T0 = P.cmb_t[0], T1 = P.cmb_t[1], T2 = P.cmb_t[2];
+    const int t2 = (int)(tile % P.cmb_n[2]);
+    const int t1 = (int)((tile / P.cmb_n[2]) % P.cmb_n[1]);
+    const int t0 = (int)(tile / ((int64_t)P.cmb_n[2] * P.cmb_n[1]));
+    const int e0 = P.cmb_off[tile], e1 = P.cmb_off[tile + 1];
+    const int W0 = P.win_n[0], W1 = P.win_n[1], W2 = P.win_n[2];
+    const int N[3] = {P.nf[0], P.nf[1], P.nh};
+    const int cells = T0 * T1 * T2;
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+        const int c2 = q % T2, c1 = (q / T2) % T1, c0 = q / (T1 * T2);
+        const int l0 = t0 * T0 + c0, l1 = t1 * T1 + c1, l2 = t2 * T2 + c2;
+        if (l0 >= N[0] || l1 >= N[1] || l2 >= N[2]) continue;
+        T sx = (T)0, sy = (T)0;
+        for (int e = e0; e < e1; ++e) {
+            const CombEntry E = P.cmb[e];
+            const int s = E.mirror ? -1 : 1;
+            const int a0 = s * l0 + E.o[0], a1 = s * l1 + E.o[1], a2 = s * l2 + E.o[2];
+            if ((unsigned)a0 >= (unsigned)W0 || (unsigned)a1 >= (unsigned)W1 || (unsigned)a2 >= (unsigned)W2) continue;
+            const cpx<T> v = P.win[(int64_t)E.chunk * P.win_cells + ((int64_t)a0 * W1 + a1) * W2 + a2];
+            sx += v.x;
+            sy += E.mirror ? -v.y : v.y;
+        }
+        P.G[((int64_t)l0 * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx, sy);
     }
 }
 

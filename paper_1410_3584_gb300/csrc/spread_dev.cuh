@@ -1,6 +1,7 @@
 // Interpolation/spreading device code shared by the single-plan kernels (spread.cu,
 // spread_reg.cu) and the batched persistent kernel (batch.cu): per-block bodies with the
-// block index passed explicitly.
+// block index passed explicitly.  Each body processes one chunk and writes the chunk's tile
+// window to its scratch slot (the combine pass of spread_common.cuh folds the slots into G).
 #pragma once
 #include "common.cuh"
 #include "spread_common.cuh"
@@ -64,38 +65,45 @@ template <bool B> struct BoolC { static constexpr bool value = B; };
 template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
 template <> struct Log2<1> { static constexpr int value = 0; };
 
-// Shared memory of the generic kernel: F and G windows, kernel values of up to kGenericSlots
-// warps, then the two row tables of the window.
-constexpr int kGenericSlots = 8;
-template <typename T> __host__ __device__ constexpr size_t generic_win_table_offset(size_t WW) {
-    return align16(2 * WW * sizeof(cpx<T>) + (size_t)kGenericSlots * 3 * kMaxWidth * sizeof(T));
+// ======================================================================= generic kernel
+// One warp per node (lanes over the taps of the last two axes, a loop over the first), for
+// 2D plans and for 3D widths the register kernels do not cover.  Each warp spreads into its
+// own copy of the tile window (plain read-modify-write: within a node the lanes own distinct
+// cells, and a warp's nodes follow each other), and the copies are summed in warp order
+// when the chunk's window is written out.
+//
+// Shared memory: F window, nwin warp windows, kernel values of nwin warps, row tables.
+template <typename T> __host__ __device__ constexpr size_t generic_win_table_offset(size_t WW, int nwin) {
+    return align16((size_t)(1 + nwin) * WW * sizeof(cpx<T>) + (size_t)nwin * 3 * kMaxWidth * sizeof(T));
+}
+template <typename T> __host__ __device__ constexpr size_t generic_smem_bytes(size_t WW, size_t rows, int nwin) {
+    return generic_win_table_offset<T>(WW, nwin) + 2 * rows * sizeof(int64_t);
 }
 
 template <typename T>
 __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bid, unsigned char *smraw) {
     const int w = P.w;
     const int w0 = P.dim == 3 ? w : 1;
-    const int W0 = P.T_tile[0] + w0 - 1, W1 = P.T_tile[1] + w - 1, W2 = P.T_tile[2] + w - 1;
+    const int W0 = P.win_n[0], W1 = P.win_n[1], W2 = P.win_n[2];
     const int WW = W0 * W1 * W2;
+    const int nw = blockDim.x >> 5;
     cpx<T> *sF = (cpx<T> *)smraw;
-    cpx<T> *sG = sF + WW;
-    T *spsi = (T *)(sG + WW);
+    cpx<T> *sGall = sF + WW;
+    T *spsi = (T *)(sGall + (size_t)nw * WW);
     const int rows = W0 * W1;
-    int64_t *rowoff = (int64_t *)(smraw + generic_win_table_offset<T>(WW)), *rowmir = rowoff + rows;
+    int64_t *rowoff = (int64_t *)(smraw + generic_win_table_offset<T>(WW, nw)), *rowmir = rowoff + rows;
     const Chunk ch = P.chunks[bid];
 
     window_row_table(P, ch, W0, W1, rowoff, rowmir);
     const WinCol wc = window_col(P, ch, W2, rows);
     __syncthreads();
-    if (P.ones_mode) {
-        for (int q = threadIdx.x; q < WW; q += blockDim.x) sF[q] = sG[q] = mk<T>(0, 0);
-    } else {
-        window_fill(P, wc, rowoff, rowmir, rows, W2, sF, sG);
-    }
+    if (!P.ones_mode) window_fill(P, wc, rowoff, rowmir, rows, W2, sF);
+    for (int q = threadIdx.x; q < nw * WW; q += blockDim.x) sGall[q] = mk<T>(0, 0);
     __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *ps = spsi + warp * 3 * kMaxWidth;
+    cpx<T> *sG = sGall + (size_t)warp * WW;
     const T two_w = (T)2 / (T)w;
     const int sa = W1 * W2;
     for (int j = ch.j0 + warp; j < ch.j1; j += nw) {
@@ -114,20 +122,21 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
         __syncwarp();
         // interpolation
         cpx<T> acc = mk<T>(0, 0);
-        for (int p = lane; p < w * w; p += 32) {
-            const int b = p / w, c = p % w;
-            const T wbc = ps[kMaxWidth + b] * ps[2 * kMaxWidth + c];
-            const cpx<T> *col = sF + (o0 * W1 + (o1 + b)) * W2 + (o2 + c);
-            T sx = 0, sy = 0;
-            for (int a = 0; a < w0; ++a) {
-                const T wa = ps[a];
-                const cpx<T> f = col[a * sa];
-                sx += wa * f.x;
-                sy += wa * f.y;
+        if (!P.ones_mode)
+            for (int p = lane; p < w * w; p += 32) {
+                const int b = p / w, c = p % w;
+                const T wbc = ps[kMaxWidth + b] * ps[2 * kMaxWidth + c];
+                const cpx<T> *col = sF + (o0 * W1 + (o1 + b)) * W2 + (o2 + c);
+                T sx = 0, sy = 0;
+                for (int a = 0; a < w0; ++a) {
+                    const T wa = ps[a];
+                    const cpx<T> f = col[a * sa];
+                    sx += wa * f.x;
+                    sy += wa * f.y;
+                }
+                acc.x += wbc * sx;
+                acc.y += wbc * sy;
             }
-            acc.x += wbc * sx;
-            acc.y += wbc * sy;
-        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -147,7 +156,7 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
             const double im = P.hvol * (double)acc.y + (kx * P.mom[1] + ky * P.mom[2]) * g;
             cj = mk<T>((T)((double)om * re), (T)((double)om * im));
         }
-        // spreading
+        // spreading into this warp's window
         for (int p = lane; p < w * w; p += 32) {
             const int b = p / w, c = p % w;
             const T wbc = ps[kMaxWidth + b] * ps[2 * kMaxWidth + c];
@@ -155,76 +164,156 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
             cpx<T> *col = sG + (o0 * W1 + (o1 + b)) * W2 + (o2 + c);
             for (int a = 0; a < w0; ++a) {
                 const T wa = ps[a];
-                red_add(col + a * sa, scale(v, wa));
+                cpx<T> g = col[a * sa];
+                g.x += v.x * wa;
+                g.y += v.y * wa;
+                col[a * sa] = g;
             }
         }
         __syncwarp();
     }
     __syncthreads();
-    window_fold(P, wc, rowoff, rowmir, rows, W2, sG);
+    cpx<T> *out = P.win + (int64_t)bid * P.win_cells;
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        cpx<T> s = sGall[q];
+        for (int k = 1; k < nw; ++k) s = s + sGall[(size_t)k * WW + q];
+        out[q] = s;
+    }
 }
 
-// Shared memory of the warp kernel: F and G windows (z pitch Wt2 + 1), kernel values and
-// reduced values of up to kWarpSlots warps, then the two row tables of the window.
-constexpr int kWarpSlots = 8;
-template <typename T, int W, int NB> __host__ __device__ constexpr size_t warp_win_table_offset(size_t WWp) {
-    return align16(2 * WWp * sizeof(cpx<T>) + (size_t)kWarpSlots * (NB * 3 * W + 2 * NB) * sizeof(T));
+// ======================================================================= FP32 warp kernel
+// One warp per piece (a run of at most 64 nodes of one 2^3 sub-tile, whose nodes all reach
+// the same sub-window of W^3 cells, W = w + 1): lane L owns the sub-window z-columns
+// a = (L mod W', L div W') and b (32 further columns), where W' = W for W^2 <= 64.  Per piece
+// the lane holds both F columns and both G accumulator columns in registers; per batch of
+// NB nodes it
+//   1. evaluates the 3 W kernel values of each node from its position (lanes (axis, tap)),
+//   2. interpolates: per column a complex z-contraction with packed FP32x2 FMAs, weighted by
+//      the column's x/y kernel values, reduced over the warp for all NB nodes at once,
+//   3. scales by the node weight and spreads: per column a complex x z outer product with
+//      packed FMAs into the G registers.
+// At the end of a piece the G columns are added to the chunk's shared window as 32-bit
+// fixed-point integers: integer addition is associative, so the warps' order does not change
+// the sums.  The quantum q of a chunk is a power of two chosen before any spreading from a
+// bound on every cell of its window: |G| <= sum_j |c_j| (the kernel is at most 1) and
+// |c_j| = |omega_j| |rho-hat_j| <= |omega_j| sqrt(2) max|F| (max_delta sum_t psi)^3, so with
+// S = sum_j |omega_j| (plan time, per chunk) every partial sum of a cell stays below
+// B = sqrt(2) max|F| C^3 S <= 2^30 q.
+template <int W, int NB> struct WarpGeo {
+    static constexpr int V = 2 * NB;
+    static constexpr int SS = 32;               // floats of one node's kernel values: x[8] y[8] z pairs[16]
+    static constexpr int STAGE = NB * SS + V;   // floats per warp
+};
+
+struct WarpLayout {
+    int Wt0, Wt1, Wt2;
+    int RP, SP;       // F window: cell (a, b, c) at a SP + b RP + c (RP even, SP / 2 odd: 16-byte column
+                      // loads of the 8 lanes of a quarter warp fall in distinct bank groups)
+    int RG, SG;       // G window: cell (a, b, c) at a SG + b RG + c (RG odd)
+    size_t offG, offStage, offRows, bytes;
+};
+
+template <int W, int NB>
+__host__ __device__ inline WarpLayout warp_layout(int Wt0, int Wt1, int Wt2, int nwarps) {
+    WarpLayout L;
+    L.Wt0 = Wt0;
+    L.Wt1 = Wt1;
+    L.Wt2 = Wt2;
+    L.RP = (Wt2 + 1) & ~1;
+    L.SP = Wt1 * L.RP;
+    if ((L.SP / 2) % 2 == 0) L.SP += 2;
+    L.RG = Wt2 | 1;
+    L.SG = Wt1 * L.RG;
+    L.offG = align16((size_t)Wt0 * L.SP * sizeof(float2));
+    L.offStage = align16(L.offG + (size_t)Wt0 * L.SG * sizeof(int2));
+    L.offRows = align16(L.offStage + (size_t)nwarps * WarpGeo<W, NB>::STAGE * sizeof(float));
+    L.bytes = L.offRows + 2 * (size_t)Wt0 * Wt1 * sizeof(int64_t);
+    return L;
 }
 
-// One warp per segment (W*W <= 64): lane L owns the z-columns L and L + 32 of the sub-window
-// (their G accumulators in registers, their F values read from the shared window per node),
-// so interpolation sums reduce inside the warp and the node loop needs no block barrier.
-template <typename T, int W, int NB>
-__device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, unsigned char *smraw) {
-    static_assert(W * W <= 64, "two columns per lane");
-    constexpr int V = 2 * NB;
+// exp(beta (sqrt(1 - x^2) - 1)) for x = (i - d) 2/w with the exponent written as
+// -beta x^2 / (1 + sqrt(1 - x^2)) (no cancellation near x = 0); 0 outside |x| < 1.
+// nbl2 = -beta log2(e).  rsqrt / rcp / ex2 are the hardware approximations.
+__device__ __forceinline__ float es_fast(float i_f, float d, float c2w, float nbl2) {
+    const float x = (i_f - d) * c2w;
+    const float x2 = x * x;
+    const float s = 1.0f - x2;
+    float rs, rd, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(s));
+    const float den = fmaf(s, rs, 1.0f);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(den));
+    const float arg = (x * (x * nbl2)) * rd;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(arg));
+    return s > 0.0f ? e : 0.0f;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int W, int NB>
+__device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int bid, unsigned char *smraw) {
+    static_assert(W * W <= 64 && W >= 4 && W <= 8, "two columns per lane, at most 8 z taps");
+    using G = WarpGeo<W, NB>;
+    constexpr int V = G::V;
     constexpr int SH = 5 - Log2<V>::value;
     const int w = P.w;
-    const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
-    // window cells (a, b, c) at (a Wt1 + b) P2 + c with the z pitch padded by one cell: with
-    // x fastest across the lanes, the 8-byte column accesses of a warp (tile 8, w 7: pitches
-    // 210 and 15 cells) hit every bank pair exactly twice
-    const int P2 = Wt2 + 1, WWp = Wt0 * Wt1 * P2;
-    cpx<T> *sF = (cpx<T> *)smraw;
-    cpx<T> *sG = sF + WWp;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    T *psi = (T *)(sG + WWp) + warp * (NB * 3 * W + V);
-    T *cb = psi + NB * 3 * W;
-    const int rows = Wt0 * Wt1;
-    int64_t *rowoff = (int64_t *)(smraw + warp_win_table_offset<T, W, NB>(WWp)), *rowmir = rowoff + rows;
+    const int nwarps = blockDim.x >> 5;
+    const WarpLayout L = warp_layout<W, NB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps);
+    cpx<float> *sF = (cpx<float> *)smraw;
+    int2 *sG = (int2 *)(smraw + L.offG);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *stage = (float *)(smraw + L.offStage) + warp * G::STAGE;
+    float *cb = stage + NB * G::SS;
+    const int rows = L.Wt0 * L.Wt1;
+    int64_t *rowoff = (int64_t *)(smraw + L.offRows), *rowmir = rowoff + rows;
     const Chunk ch = P.rchunks[bid];
-    __shared__ int next_seg;
-    if (threadIdx.x == 0) next_seg = ch.j0 + nwarps;
-
-    window_row_table(P, ch, Wt0, Wt1, rowoff, rowmir);
-    const WinCol wc = window_col(P, ch, Wt2, rows);
+    __shared__ int s_next, s_max;
+    if (threadIdx.x == 0) {
+        s_next = ch.j0 + nwarps;
+        s_max = 0;
+    }
+    window_row_table(P, ch, L.Wt0, L.Wt1, rowoff, rowmir);
+    const WinCol wc = window_col(P, ch, L.Wt2, rows);
     __syncthreads();
-    window_fill(P, wc, rowoff, rowmir, rows, P2, sF, sG);
+    float mx = 0.0f;
+    if (!P.ones_mode) mx = window_fill(P, wc, rowoff, rowmir, rows, L.RP, sF, L.Wt1, L.SP);
+    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = make_int2(0, 0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) atomicMax(&s_max, __float_as_int(mx));   // non-negative floats order as integers
     __syncthreads();
+    // fixed-point quantum of this chunk (a power of two, so that int * q is exact)
+    float B = P.ones_mode ? ch.wsum : 1.41421356f * __int_as_float(s_max) * P.psi_sum3 * ch.wsum;
+    B *= 1.01f;
+    int ex = 0;
+    if (B > 0.0f && B <= 3.0e38f) frexpf(B, &ex);   // B < 2^ex
+    ex = max(ex, -96);
+    const float qinv = ldexpf(1.0f, 30 - ex);
+    const float qf = (B == B) ? ldexpf(1.0f, ex - 30) : B;   // a NaN input stays NaN in the window
 
     const int ca = lane, cbc = lane + 32;
-    // W*W > 32 for W >= 6: column a always active; W = 8: both columns of every lane
     const bool act_a = (W * W >= 32) || ca < W * W;
     const bool act_b = (W * W == 64) || cbc < W * W;
-    const int xa = ca % W, ya = ca / W;
+    const int xa = act_a ? ca % W : 0, ya = act_a ? ca / W : 0;
     const int xb = act_b ? cbc % W : 0, yb = act_b ? cbc / W : 0;
-    constexpr bool kSameX = 32 % W == 0;   // then column b has the x of column a
-    // the batch's kernel values are a contiguous block of the plan-time table; the next
-    // block (of this piece or of the warp's next piece) is fetched into registers while the
-    // current batch computes
-    constexpr int PQ = (NB * 3 * W + 31) / 32;
-    T pf[PQ], wf;
+    // kernel-value lanes: lane = axis * 8 + tap for lanes < 24
+    const int kv_ax = lane >> 3, kv_i = lane & 7;
+    const bool kv_on = lane < 24 && kv_i < W;
+    const float kv_if = (float)kv_i;
+    const float c2w = 2.0f / (float)w, nbl2 = -(float)P.beta * 1.44269504f;
+    const int kv_st = kv_ax == 2 ? 16 + 2 * kv_i : kv_ax * 8 + kv_i;
+    // G flush order: lanes of the upper half of each y quartet add the imaginary word first,
+    // so that the 32 lanes of one atomic instruction hit 32 banks (W = 8 geometry)
+    const int sw = (ya >> 1) & 1;
+    // node records of a batch: per kernel-value lane, the node's offset from its sub-window
+    // origin along the lane's axis (for plans of this kernel the node records hold that
+    // offset, see plan.cu) for each node; per lane k < NB the node weight
+    float pd[NB], wf;
     auto fetch = [&](int jbn, int nbn) {
-        const T *src = P.psi_tab + (int64_t)jbn * 3 * W;
 #pragma unroll
-        for (int u = 0; u < PQ; ++u) {
-            const int q = lane + 32 * u;
-            pf[u] = (q < nbn * 3 * W) ? __ldg(src + q) : (T)0;
-        }
-        wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : (T)0;
+        for (int k = 0; k < NB; ++k)
+            pd[k] = (kv_on && k < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + k) + kv_ax) : 0.0f;
+        wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : 0.0f;
     };
-    // pieces are sorted heaviest first; each warp takes the next free one, claiming it (and
-    // loading its descriptor) while the current piece computes
     int sg = ch.j0 + warp;
     uint32_t so = 0;
     int j0 = 0, j1 = 0;
@@ -234,12 +323,9 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
         j1 = P.seg_node[2 * sg + 1];
         fetch(j0, min(NB, j1 - j0));
     }
-    // lanes of odd x add the imaginary word of a cell first: with x fastest across the lanes
-    // the two lanes that share a bank have x of opposite parity, so each add is conflict-free
-    const int sw = xa & 1;
     while (sg < ch.j1) {
         int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(&next_seg, 1);
+        if (lane == 0) nxt = atomicAdd(&s_next, 1);
         const int sg_n = __shfl_sync(0xffffffffu, nxt, 0);
         uint32_t so_n = 0;
         int j0_n = 0, j1_n = 0;
@@ -249,79 +335,112 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
             j1_n = P.seg_node[2 * sg_n + 1];
         }
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
-        const int basea = ((so0 + (act_a ? xa : 0)) * Wt1 + (so1 + (act_a ? ya : 0))) * P2 + so2;
-        const int baseb = ((so0 + xb) * Wt1 + (so1 + yb)) * P2 + so2;
-        // G columns in registers; the F columns are read from the shared window per node, which
-        // frees their registers for more warps per SM
-        T gax[W], gay[W], gbx[W], gby[W];
+        const int fa0 = (so0 + xa) * L.SP + (so1 + ya) * L.RP + so2;
+        const int fb0 = (so0 + xb) * L.SP + (so1 + yb) * L.RP + so2;
+        const int ga0 = (so0 + xa) * L.SG + (so1 + ya) * L.RG + so2;
+        const int gb0 = (so0 + xb) * L.SG + (so1 + yb) * L.RG + so2;
+        float2 fa[W], fb[W], ga[W], gb[W];
+        // F columns of the piece (16-byte loads: column starts are even cells of an even pitch)
 #pragma unroll
-        for (int z = 0; z < W; ++z) gax[z] = gay[z] = gbx[z] = gby[z] = (T)0;
-        const cpx<T> *fca = sF + (act_a ? basea : 0), *fcb = sF + (act_b ? baseb : 0);
-        // one batch of nodes; FULL (nb == NB) runs without per-node guards so that the
-        // independent FMA chains of the batch's nodes interleave
-        auto batch = [&](auto full_tag, int nb, T wcur) {
+        for (int z = 0; z + 1 < W; z += 2) {
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+            if (!P.ones_mode) {
+                if (act_a) u = *reinterpret_cast<const float4 *>(sF + fa0 + z);
+                if (act_b) v = *reinterpret_cast<const float4 *>(sF + fb0 + z);
+            }
+            fa[z] = f2(u.x, u.y);
+            fa[z + 1] = f2(u.z, u.w);
+            fb[z] = f2(v.x, v.y);
+            fb[z + 1] = f2(v.z, v.w);
+        }
+        if constexpr (W % 2) {
+            const cpx<float> u = (!P.ones_mode && act_a) ? sF[fa0 + W - 1] : mk<float>(0.f, 0.f);
+            const cpx<float> v = (!P.ones_mode && act_b) ? sF[fb0 + W - 1] : mk<float>(0.f, 0.f);
+            fa[W - 1] = f2(u.x, u.y);
+            fb[W - 1] = f2(v.x, v.y);
+        }
+#pragma unroll
+        for (int z = 0; z < W; ++z) ga[z] = gb[z] = f2(0.f, 0.f);
+
+        auto batch = [&](auto full_tag, int nb, float wcur) {
             constexpr bool FULL = decltype(full_tag)::value;
-            T v[V], wa[NB], wb[NB];
+            float v[V], wa[NB], wb[NB];
+            // interpolation partials
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                v[2 * k] = v[2 * k + 1] = (T)0;
-                wa[k] = wb[k] = (T)0;
+                v[2 * k] = v[2 * k + 1] = 0.f;
+                wa[k] = wb[k] = 0.f;
                 if (FULL || k < nb) {
-                    const T *pk = psi + k * 3 * W;
-                    const T pxa = pk[xa];
-                    wa[k] = act_a ? pxa * pk[W + ya] : (T)0;
-                    wb[k] = act_b ? (kSameX ? pxa : pk[xb]) * pk[W + yb] : (T)0;
-                    T sax = 0, say = 0, sbx = 0, sby = 0;
-                    T pzv[W];
-                    load_row<T, W>(pk + 2 * W, pzv);
+                    const float *pk = stage + k * G::SS;
+                    const float px = pk[xa];
+                    wa[k] = act_a ? px * pk[8 + ya] : 0.f;
+                    wb[k] = act_b ? (W == 8 ? px : pk[xb]) * pk[8 + yb] : 0.f;
+                    if (!P.ones_mode) {
+                        float2 sa = f2(0.f, 0.f), sb = f2(0.f, 0.f);
 #pragma unroll
-                    for (int z = 0; z < W; ++z) {
-                        const T pz = pzv[z];
-                        const cpx<T> fa = fca[z], fb = fcb[z];
-                        sax += fa.x * pz;
-                        say += fa.y * pz;
-                        sbx += fb.x * pz;
-                        sby += fb.y * pz;
+                        for (int z = 0; z + 1 < W; z += 2) {
+                            const float4 pz = *reinterpret_cast<const float4 *>(pk + 16 + 2 * z);
+                            sa = __ffma2_rn(fa[z], f2(pz.x, pz.y), sa);
+                            sb = __ffma2_rn(fb[z], f2(pz.x, pz.y), sb);
+                            sa = __ffma2_rn(fa[z + 1], f2(pz.z, pz.w), sa);
+                            sb = __ffma2_rn(fb[z + 1], f2(pz.z, pz.w), sb);
+                        }
+                        if constexpr (W % 2) {
+                            const float2 pz = *reinterpret_cast<const float2 *>(pk + 16 + 2 * (W - 1));
+                            sa = __ffma2_rn(fa[W - 1], pz, sa);
+                            sb = __ffma2_rn(fb[W - 1], pz, sb);
+                        }
+                        v[2 * k] = wa[k] * sa.x + wb[k] * sb.x;
+                        v[2 * k + 1] = wa[k] * sa.y + wb[k] * sb.y;
                     }
-                    v[2 * k] = wa[k] * sax + wb[k] * sbx;
-                    v[2 * k + 1] = wa[k] * say + wb[k] * sby;
                 }
             }
-            warp_reduce_multi<T, V>(v, lane);
+            if (!P.ones_mode) warp_reduce_multi<float, V>(v, lane);
             {
                 const int idx = (lane >> SH) & (V - 1);
                 const int k = idx >> 1;
-                const T wk = __shfl_sync(0xffffffffu, wcur, k);   // weight of node k of the batch
-                if ((lane & ((1 << SH) - 1)) == 0) cb[idx] = (FULL || k < nb) ? v[0] * wk : (T)0;
+                const float wk = __shfl_sync(0xffffffffu, wcur, k);   // weight of node k of the batch
+                if ((lane & ((1 << SH) - 1)) == 0) {
+                    float c = P.ones_mode ? ((idx & 1) ? 0.f : wk) : v[0] * wk;
+                    cb[idx] = (FULL || k < nb) ? c : 0.f;
+                }
             }
             __syncwarp();
+            // spreading into the register columns
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 if (FULL || k < nb) {
-                    const T *pk = psi + k * 3 * W;
-                    const T cr = cb[2 * k], ci = cb[2 * k + 1];
-                    const T ar = cr * wa[k], ai = ci * wa[k], br = cr * wb[k], bi = ci * wb[k];
-                    T pzv[W];
-                    load_row<T, W>(pk + 2 * W, pzv);
+                    const float *pk = stage + k * G::SS;
+                    const float2 c = *reinterpret_cast<const float2 *>(cb + 2 * k);
+                    const float2 ca2 = f2(c.x * wa[k], c.y * wa[k]), cb2 = f2(c.x * wb[k], c.y * wb[k]);
 #pragma unroll
-                    for (int z = 0; z < W; ++z) {
-                        const T pz = pzv[z];
-                        gax[z] += ar * pz;
-                        gay[z] += ai * pz;
-                        gbx[z] += br * pz;
-                        gby[z] += bi * pz;
+                    for (int z = 0; z + 1 < W; z += 2) {
+                        const float4 pz = *reinterpret_cast<const float4 *>(pk + 16 + 2 * z);
+                        ga[z] = __ffma2_rn(ca2, f2(pz.x, pz.y), ga[z]);
+                        gb[z] = __ffma2_rn(cb2, f2(pz.x, pz.y), gb[z]);
+                        ga[z + 1] = __ffma2_rn(ca2, f2(pz.z, pz.w), ga[z + 1]);
+                        gb[z + 1] = __ffma2_rn(cb2, f2(pz.z, pz.w), gb[z + 1]);
+                    }
+                    if constexpr (W % 2) {
+                        const float2 pz = *reinterpret_cast<const float2 *>(pk + 16 + 2 * (W - 1));
+                        ga[W - 1] = __ffma2_rn(ca2, pz, ga[W - 1]);
+                        gb[W - 1] = __ffma2_rn(cb2, pz, gb[W - 1]);
                     }
                 }
             }
         };
         for (int jb = j0; jb < j1; jb += NB) {
             const int nb = min(NB, j1 - jb);
+            // kernel values of the batch from the fetched node offsets
 #pragma unroll
-            for (int u = 0; u < PQ; ++u) {
-                const int q = lane + 32 * u;
-                if (q < NB * 3 * W) psi[q] = pf[u];
+            for (int k = 0; k < NB; ++k) {
+                if (kv_on) {
+                    const float e = (k < nb) ? es_fast(kv_if, pd[k], c2w, nbl2) : 0.f;
+                    if (kv_ax == 2) *reinterpret_cast<float2 *>(stage + k * G::SS + kv_st) = f2(e, e);
+                    else stage[k * G::SS + kv_st] = e;
+                }
             }
-            const T wcur = wf;
+            const float wcur = wf;
             __syncwarp();
             if (jb + NB < j1)
                 fetch(jb + NB, min(NB, j1 - jb - NB));
@@ -333,19 +452,20 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
                 batch(BoolC<false>{}, nb, wcur);
             __syncwarp();
         }
-        // overlapping windows of the block's warps: shared-memory atomics (zeros included: a
-        // zero test per cell costs more than the add it would skip)
+        // add the piece's columns to the window in fixed point
 #pragma unroll
         for (int z = 0; z < W; ++z) {
             if (act_a) {
-                T *c = &sG[basea + z].x;
-                atomicAdd(c + sw, sw ? gay[z] : gax[z]);
-                atomicAdd(c + (sw ^ 1), sw ? gax[z] : gay[z]);
+                int *c = &sG[ga0 + z].x;
+                const int re = __float2int_rn(ga[z].x * qinv), im = __float2int_rn(ga[z].y * qinv);
+                atomicAdd(c + sw, sw ? im : re);
+                atomicAdd(c + (sw ^ 1), sw ? re : im);
             }
             if (act_b) {
-                T *c = &sG[baseb + z].x;
-                atomicAdd(c + sw, sw ? gby[z] : gbx[z]);
-                atomicAdd(c + (sw ^ 1), sw ? gbx[z] : gby[z]);
+                int *c = &sG[gb0 + z].x;
+                const int re = __float2int_rn(gb[z].x * qinv), im = __float2int_rn(gb[z].y * qinv);
+                atomicAdd(c + sw, sw ? im : re);
+                atomicAdd(c + (sw ^ 1), sw ? re : im);
             }
         }
         sg = sg_n;
@@ -354,7 +474,15 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<T> &P, int bid, 
         j1 = j1_n;
     }
     __syncthreads();
-    window_fold(P, wc, rowoff, rowmir, rows, P2, sG);
+    // the chunk's window, dense, to its scratch slot
+    cpx<float> *out = P.win + (int64_t)bid * P.win_cells;
+    const int WW = L.Wt0 * L.Wt1 * L.Wt2;
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        const int c = q % L.Wt2, r = q / L.Wt2;
+        const int b = r % L.Wt1, a = r / L.Wt1;
+        const int2 g = sG[a * L.SG + b * L.RG + c];
+        out[q] = mk<float>((float)g.x * qf, (float)g.y * qf);
+    }
 }
 
 }  // namespace nlp

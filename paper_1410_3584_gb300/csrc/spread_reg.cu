@@ -1,37 +1,34 @@
-// Fused interpolate -> scale -> spread for 3D with register-resident columns.
+// Fused interpolate -> scale -> spread for 3D with register-resident columns, and the combine
+// pass that folds the chunks' windows into the spreading target.
 //
-// Same operation as k_interp_spread (spread.cu); different work decomposition.  The tile
-// window of the forward spectrum F and of the spreading target G stays in shared memory,
-// but per-tap shared-memory traffic is removed:
-//   - nodes of a tile are sorted by sub-tile (edge Ts) at plan time; a run of nodes of one
-//     sub-tile is a segment.  All nodes of a segment share the sub-window of W = Ts + w - 1
-//     cells per axis.
-//   - a team of warps owns one segment at a time: lane (cx, cy) holds the z-column
-//     F[cx, cy, 0..W) of the sub-window and a G accumulator column in registers.
-//   - nodes are processed in batches of NB.  The w kernel values per axis are written to
-//     shared memory shifted to sub-window coordinates (zeros outside the support), so
-//     interpolation is, per lane, W complex-real multiply-adds on registers; the partial
-//     sums of the NB nodes are reduced across the team with one multi-value transpose
-//     reduction (log2(32) shuffle steps for all 2 NB values together) and a short
-//     cross-warp pass; scaled values come back through shared memory and spreading is W
-//     more multiply-adds into the register accumulators.
-//   - at the end of a segment the G columns are added to the shared window (one shared
-//     atomic per cell and segment, not per tap), and at the end of the chunk the window
-//     is added to global G with the Hermitian fold.
+// Same operation as k_interp_spread (spread.cu); different work decomposition.  Nodes of a
+// tile are sorted at plan time by 2^3 sub-tile; a run of at most 64 (FP32) / 32 (FP64) nodes
+// of one sub-tile is a piece, and all nodes of a piece reach the same sub-window of
+// W = 2 + w - 1 cells per axis.  Two kernels:
+//   - k_interp_spread_warp (FP32, W <= 8): one warp per piece, see spread_dev.cuh.
+//   - k_interp_spread_reg (FP64, and FP32 with W > 8): a team of warps owns one piece: lane
+//     (cx, cy) holds the z-column of the sub-window (F in registers for FP32, read from the
+//     shared window per node for FP64) and a G accumulator column in registers.  Nodes are
+//     processed in batches of NB with their kernel values from the plan-time table; the
+//     partial sums of the NB nodes are reduced across the team with one multi-value transpose
+//     reduction (log2(32) shuffle steps for all 2 NB values together) and a short cross-warp
+//     pass; scaled values come back through shared memory and spreading is W more
+//     multiply-adds into the register accumulators.  Each team adds its pieces to its own
+//     copy of the tile window (plain read-modify-write, pieces in sequence), and the copies
+//     are summed in team order when the chunk's window is written to its scratch slot.
 #include "common.cuh"
 #include "launch.h"
 #include "spread_common.cuh"
 #include "spread_dev.cuh"
-#include "spread_mma.cuh"
 
 namespace nlp {
 
-constexpr int kWarpBlock = 160;   // threads per CTA of the one-warp-per-piece kernel
-constexpr int kMmaBlock = 128;    // threads per CTA of the tensor-core kernel
+constexpr int kWarpBlock = 128;   // threads per CTA of the one-warp-per-piece kernel
+constexpr int kWarpNB = 4;        // nodes per batch of the warp kernel
 
 template <int W> struct RegCfg {
     static constexpr int TT = ((W * W + 31) / 32) * 32;       // threads per team
-    static constexpr int NT = (512 / TT) > 0 ? (512 / TT) : 1; // teams per CTA (share the tile window)
+    static constexpr int NT = (512 / TT) > 0 ? (512 / TT) : 1; // most teams per CTA (share the F window)
     static constexpr int TW = TT / 32;                         // warps per team
 };
 
@@ -39,43 +36,44 @@ __device__ __forceinline__ void team_sync(int team, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(nthreads) : "memory");
 }
 
-// Shared memory of the team kernel: F and G windows, per-team kernel values, partial sums and
-// scaled values, then the two row tables of the window.
-template <typename T, int W, int NB> __host__ __device__ constexpr size_t reg_win_table_offset(size_t WW) {
-    return align16(2 * WW * sizeof(cpx<T>) +
-                   (size_t)RegCfg<W>::NT * (NB * 3 * W + RegCfg<W>::TW * 2 * NB + 2 * NB) * sizeof(T));
+// Shared memory of the team kernel for nt teams: F window and nt G windows (dense, as the
+// scratch slot), per-team kernel values, partial sums and scaled values, then the two row
+// tables of the window.
+template <typename T, int W, int NB> __host__ __device__ constexpr size_t reg_win_table_offset(size_t WW, int nt) {
+    return align16((size_t)(1 + nt) * WW * sizeof(cpx<T>) +
+                   (size_t)nt * (NB * 3 * W + RegCfg<W>::TW * 2 * NB + 2 * NB) * sizeof(T));
 }
 
 template <typename T, int W, int NB>
 __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_reg(DevPlan<T> P) {
     constexpr int TT = RegCfg<W>::TT, TW = RegCfg<W>::TW;
-    constexpr int NT = RegCfg<W>::NT;
     constexpr int V = 2 * NB;
     constexpr int SH = 5 - Log2<V>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int w = P.w;
-    const int Wt0 = P.T_tile[0] + w - 1, Wt1 = P.T_tile[1] + w - 1, Wt2 = P.T_tile[2] + w - 1;
+    const int Wt0 = P.win_n[0], Wt1 = P.win_n[1], Wt2 = P.win_n[2];
     const int WW = Wt0 * Wt1 * Wt2;
+    const int nt = blockDim.x / TT;
     cpx<T> *sF = (cpx<T> *)smraw;
-    cpx<T> *sG = sF + WW;
     const int team = threadIdx.x / TT, tl = threadIdx.x % TT;
-    T *psi = (T *)(sG + WW) + team * (NB * 3 * W + TW * V + V);
+    cpx<T> *sG = sF + (size_t)(1 + team) * WW;
+    T *psi = (T *)(sF + (size_t)(1 + nt) * WW) + team * (NB * 3 * W + TW * V + V);
     T *red = psi + NB * 3 * W;
     T *cbuf = red + TW * V;
     const Chunk ch = P.rchunks[blockIdx.x];
     const int rows = Wt0 * Wt1;
-    int64_t *rowoff = (int64_t *)(smraw + reg_win_table_offset<T, W, NB>(WW)), *rowmir = rowoff + rows;
+    int64_t *rowoff = (int64_t *)(smraw + reg_win_table_offset<T, W, NB>(WW, nt)), *rowmir = rowoff + rows;
 
     window_row_table(P, ch, Wt0, Wt1, rowoff, rowmir);
     const WinCol wc = window_col(P, ch, Wt2, rows);
     __syncthreads();
-    window_fill(P, wc, rowoff, rowmir, rows, Wt2, sF, sG);
+    window_fill(P, wc, rowoff, rowmir, rows, Wt2, sF);
+    for (int q = threadIdx.x; q < nt * WW; q += blockDim.x) sF[WW + q] = mk<T>(0, 0);
     __syncthreads();
 
     const bool active = tl < W * W;
     const int cx = active ? tl / W : 0, cy = active ? tl % W : 0;
     const int lane = threadIdx.x & 31, wt = tl >> 5;
-    for (int sg = ch.j0 + team; sg < ch.j1; sg += NT) {
+    for (int sg = ch.j0 + team; sg < ch.j1; sg += nt) {
         const uint32_t so = P.seg_sub[sg];
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
         const int j0 = P.seg_node[2 * sg], j1 = P.seg_node[2 * sg + 1];
@@ -178,76 +176,84 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
             }
             team_sync(team, TT);
         }
+        // this team's window: each lane owns its column; the team's pieces follow each other
+        // (every batch ends with a team barrier), so plain read-modify-write is race free
         if (active) {
 #pragma unroll
             for (int z = 0; z < W; ++z) {
-                if (gx[z] != (T)0) atomicAdd(&sG[colbase + z].x, gx[z]);
-                if (gy[z] != (T)0) atomicAdd(&sG[colbase + z].y, gy[z]);
+                cpx<T> g = sG[colbase + z];
+                g.x += gx[z];
+                g.y += gy[z];
+                sG[colbase + z] = g;
             }
         }
     }
     __syncthreads();
-    window_fold(P, wc, rowoff, rowmir, rows, Wt2, sG);
+    cpx<T> *out = P.win + (int64_t)blockIdx.x * P.win_cells;
+    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
+        cpx<T> s = sF[WW + q];
+        for (int k = 1; k < nt; ++k) s = s + sF[(size_t)(1 + k) * WW + q];
+        out[q] = s;
+    }
 }
 
-template <typename T, int W, int NB>
-__global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_warp(DevPlan<T> P) {
+template <int W>
+__global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_warp(DevPlan<float> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    spread_warp_block<T, W, NB>(P, blockIdx.x, smraw);
+    spread_warp_block<W, kWarpNB>(P, blockIdx.x, smraw);
 }
 
-__global__ void __launch_bounds__(kMmaBlock, 4) k_interp_spread_mma(DevPlan<float> P) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    spread_mma_block<float>(P, blockIdx.x, smraw);
+template <typename T> __global__ void __launch_bounds__(256) k_combine(DevPlan<T> P) {
+    for (int64_t t = blockIdx.x; t < P.cmb_tiles; t += gridDim.x) combine_block<T>(P, t);
 }
-
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
 template <typename T> bool reg_kernel_supported(int W) {
     return sizeof(T) == 8 ? (W >= 9 && W <= 16) : (W >= 5 && W <= 11);
 }
+template <typename T> bool warp_kernel_used(int W) { return sizeof(T) == 4 && W >= 5 && W <= 8; }
 
 template <typename T> static constexpr int nb_of() { return sizeof(T) == 8 ? 8 : 4; }   // nodes per batch (register budget)
 
-template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P) {
-    const size_t WW = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1) * (P.T_tile[2] + P.w - 1);
-    constexpr int NB = nb_of<T>();
-    const size_t rows = (size_t)(P.T_tile[0] + P.w - 1) * (P.T_tile[1] + P.w - 1);
-    if constexpr (W * W <= 64) {   // warp kernels: z pitch padded by one cell
-        const size_t WWp = rows * (P.T_tile[2] + P.w);
-        if constexpr (sizeof(T) == 4 && W == 8)
-            if (P.use_mma) return warp_win_table_offset<T, W, kMmaNB>(WWp) + 2 * rows * sizeof(int64_t);
-        return warp_win_table_offset<T, W, NB>(WWp) + 2 * rows * sizeof(int64_t);
+// teams per CTA of the team kernel: as many as fit (at most NT), each with its own window
+template <typename T, int W> static int reg_teams(const DevPlan<T> &P) {
+    const size_t WW = (size_t)P.win_n[0] * P.win_n[1] * P.win_n[2];
+    const size_t rows = (size_t)P.win_n[0] * P.win_n[1];
+    for (int nt = RegCfg<W>::NT; nt >= 1; --nt)
+        if (reg_win_table_offset<T, W, nb_of<T>()>(WW, nt) + 2 * rows * sizeof(int64_t) <= (size_t)max_dyn_smem()) return nt;
+    return 0;
+}
+
+template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P, int nwarps_warpkernel) {
+    if constexpr (sizeof(T) == 4 && W <= 8) {
+        return warp_layout<W, kWarpNB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps_warpkernel).bytes;
+    } else {
+        const size_t WW = (size_t)P.win_n[0] * P.win_n[1] * P.win_n[2];
+        const size_t rows = (size_t)P.win_n[0] * P.win_n[1];
+        const int nt = std::max(1, reg_teams<T, W>(P));
+        return reg_win_table_offset<T, W, nb_of<T>()>(WW, nt) + 2 * rows * sizeof(int64_t);
     }
-    return reg_win_table_offset<T, W, NB>(WW) + 2 * rows * sizeof(int64_t);
 }
 
 template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cudaStream_t st) {
-    constexpr int NB = nb_of<T>();
-    const size_t sm = reg_smem<T, W>(P);
-    if constexpr (sizeof(T) == 4 && W == 8) {
-        if (P.use_mma) {
-            cudaError_t e = allow_smem<k_interp_spread_mma>();
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_interp_spread_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            if (e != cudaSuccess) return e;
-            k_interp_spread_mma<<<(unsigned)P.nrchunks, kMmaBlock, sm, st>>>(P);
-            return cudaGetLastError();
-        }
-    }
-    if constexpr (W * W <= 64) {
-        cudaError_t e = allow_smem<k_interp_spread_warp<T, W, NB>>();
+    if constexpr (sizeof(T) == 4 && W <= 8) {
+        const size_t sm = reg_smem<T, W>(P, kWarpBlock / 32);
+        cudaError_t e = allow_smem<k_interp_spread_warp<W>>();
         if (e == cudaSuccess)   // several small blocks per SM, each with its own tile window
-            e = cudaFuncSetAttribute(k_interp_spread_warp<T, W, NB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            e = cudaFuncSetAttribute(k_interp_spread_warp<W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        k_interp_spread_warp<T, W, NB><<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
+        k_interp_spread_warp<W><<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
+        return cudaGetLastError();
+    } else {
+        constexpr int NB = nb_of<T>();
+        const int nt = reg_teams<T, W>(P);
+        if (nt < 1) return cudaErrorInvalidValue;
+        const size_t sm = reg_smem<T, W>(P, 0);
+        cudaError_t e = allow_smem<k_interp_spread_reg<T, W, NB>>();
+        if (e != cudaSuccess) return e;
+        k_interp_spread_reg<T, W, NB><<<(unsigned)P.nrchunks, RegCfg<W>::TT * nt, sm, st>>>(P);
         return cudaGetLastError();
     }
-    cudaError_t e =
-        allow_smem<k_interp_spread_reg<T, W, NB>>();
-    if (e != cudaSuccess) return e;
-    k_interp_spread_reg<T, W, NB><<<(unsigned)P.nrchunks, RegCfg<W>::TT * RegCfg<W>::NT, sm, st>>>(P);
-    return cudaGetLastError();
 }
 
 #define NLP_REG_SWITCH(T, W, CALL)                       \
@@ -261,16 +267,16 @@ template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cu
         default: break;                                  \
     }
 
-template <> size_t interp_spread_reg_smem<float>(const DevPlan<float> &P) {
+template <> size_t interp_spread_reg_smem<float>(const DevPlan<float> &P, int nwarps) {
     const int W = P.sub_T + P.w - 1;
-#define SM_F(T, X) if constexpr (X >= 5 && X <= 11) return reg_smem<T, X>(P); break;
+#define SM_F(T, X) if constexpr (X >= 5 && X <= 11) return reg_smem<T, X>(P, nwarps); break;
     NLP_REG_SWITCH(float, W, SM_F)
 #undef SM_F
     return 0;
 }
-template <> size_t interp_spread_reg_smem<double>(const DevPlan<double> &P) {
+template <> size_t interp_spread_reg_smem<double>(const DevPlan<double> &P, int nwarps) {
     const int W = P.sub_T + P.w - 1;
-#define SM_D(T, X) if constexpr (X >= 9 && X <= 16) return reg_smem<T, X>(P); break;
+#define SM_D(T, X) if constexpr (X >= 9 && X <= 16) return reg_smem<T, X>(P, nwarps); break;
     NLP_REG_SWITCH(double, W, SM_D)
 #undef SM_D
     return 0;
@@ -293,7 +299,18 @@ template <> cudaError_t launch_interp_spread_reg<double>(const DevPlan<double> &
     return cudaErrorInvalidValue;
 }
 
+template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st) {
+    if (P.cmb_tiles == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>(P.cmb_tiles, 152 * 16);
+    k_combine<T><<<blocks, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
 template bool reg_kernel_supported<float>(int);
 template bool reg_kernel_supported<double>(int);
+template bool warp_kernel_used<float>(int);
+template bool warp_kernel_used<double>(int);
+template cudaError_t launch_combine<float>(const DevPlan<float> &, cudaStream_t);
+template cudaError_t launch_combine<double>(const DevPlan<double> &, cudaStream_t);
 
 }  // namespace nlp

@@ -89,8 +89,10 @@ template <typename T> static nlp_status build_kernel(nlp_plan_s *p) {
     if ((s = alloc_dev(aux, &dK, sizeof(T) * NK))) { free_aux(); return s; }
     A.ones_mode = 1;
     const int64_t nhA = A.nh;
-    if (cudaMemsetAsync(A.G, 0, sizeof(cpx<T>) * (size_t)A.nf[0] * A.nf[1] * nhA, st) != cudaSuccess ||
-        launch_interp_spread<T>(A, st) != cudaSuccess) { free_aux(); return NLP_ERR_CUDA; }
+    if (launch_interp_spread<T>(A, st) != cudaSuccess || launch_combine<T>(A, st) != cudaSuccess) {
+        free_aux();
+        return NLP_ERR_CUDA;
+    }
     const bool three = p->grid.dim == 3;
     StridedDesc b1{};
     b1.n_in = A.nf[1]; b1.n_out = A.n[1]; b1.es = nhA; b1.ncol = (int)nhA;

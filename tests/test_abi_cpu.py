@@ -47,7 +47,7 @@ def test_status_strings_and_version(nl):
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"counts": (32, 31, 64)}),   # odd n_theta
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"counts": (32, 32, 63)}),   # odd n_phi
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"tile": 64}),
-    ((32, 32, 32), (8, 8, 8), "coulomb3d", {"spread_variant": 3}),
+    ((32, 32, 32), (8, 8, 8), "coulomb3d", {"spread_variant": 2}),
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"method": 3}),
     ((32, 32, 32), (8, 8, 8), "coulomb3d", {"kmax": -1.0}),
 ])

@@ -60,23 +60,6 @@ def test_3d_parity_vs_oracle(nl, prec, kernel, shape):
     assert err < TOL[prec], (err, info)
 
 
-@pytest.mark.parametrize("kernel", ["coulomb3d", "dipole3d"])
-@pytest.mark.parametrize("shape", CASES_3D + [((64, 48, 40), (8.0, 6.0, 5.0))], ids=["24x20x16", "30x32x18", "64x48x40"])
-def test_3d_fp32_tensor_core_variant(nl, kernel, shape):
-    """spread_variant 2: the FP32 z contractions on the tensor cores (TF32 hi/lo compensated)
-    give the FP32 bar against the oracle and agree with the FP32-pipe kernel to FP32 rounding."""
-    g = W.Grid(*shape)
-    rho = W.gaussian(g, [1.0, 1.3, 0.8], center=(0.3, -0.2, 0.1))
-    P = math.pi / max(g.h)
-    counts = (32, 32, 64)
-    phi_tc, info = gpu_eval(nl, g, rho, kernel, "fp32", kmax=P, counts=counts, spread_variant=2)
-    phi_fp, _ = gpu_eval(nl, g, rho, kernel, "fp32", kmax=P, counts=counts)
-    assert info["sub_tile"] == 2 and info["width"] == 7
-    ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
-    assert cf.rel_linf(phi_tc, ref) < TOL["fp32"]
-    assert cf.rel_linf(phi_tc, phi_fp) < 2e-6
-
-
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
 @pytest.mark.parametrize("shape", [((64, 48), (8.0, 6.0)), ((80, 90), (8.0, 9.0))], ids=["64x48", "80x90"])
@@ -130,7 +113,31 @@ def test_linearity_and_repeatability(nl, prec):
     plan.close()
     scale = float(pab.abs().max())
     assert float((pab - (2 * pa - 0.5 * pb)).abs().max()) / scale < (1e-13 if prec == "fp64" else 3e-6)
-    assert float((pa2 - pa).abs().max()) / float(pa.abs().max()) < (1e-14 if prec == "fp64" else 1e-6)
+    # no global atomics and fixed summation orders: the same input gives the same bits
+    assert torch.equal(pa2, pa)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel,shape,variant", [
+    ("coulomb3d", ((128, 128, 128), (12.0, 12.0, 12.0)), 0),
+    ("dipole3d", ((30, 24, 20), (7.0, 6.0, 5.0)), 1),
+    ("coulomb2d", ((256, 192), (16.0, 12.0)), 0),
+    ("poisson2d", ((96, 80), (8.0, 7.0)), 0)], ids=["128^3", "generic3d", "2d", "poisson2d"])
+def test_bitwise_repeatable(nl, prec, kernel, shape, variant):
+    """Two evaluations of the same input are bit-identical: every kernel variant sums its
+    chunk windows in a fixed order and the combine pass writes each cell of G once."""
+    import torch
+    g = W.Grid(*shape)
+    rho = W.random_density(g, 5) if g.dim == 3 and g.n[0] < 64 else W.gaussian(g, [1.0, 1.4, 2.0][: g.dim])
+    P = quadrature.density_P(1.0, max(g.h))
+    plan = nl.Plan(g.n, g.L, kernel, prec, kmax=P, counts=quadrature.default_counts(g.L, P), spread_variant=variant)
+    r = torch.from_numpy(rho).to("cuda", plan.torch_dtype)
+    a = plan.eval(r).clone()
+    b = plan.eval(r).clone()
+    torch.cuda.synchronize()
+    plan.close()
+    assert torch.equal(a, b)
+    assert float(a.abs().max()) > 0
 
 
 def test_host_entry_point_matches_device(nl):
