@@ -275,7 +275,8 @@ enum {
     NLP_STAGE_INV_FIRST = 5,  /* inverse FFT along axis 0 (3D only) */
     NLP_STAGE_INV_MID = 6,    /* inverse FFT along axis 1 (3D) / axis 0 (2D) */
     NLP_STAGE_INV_LAST = 7,   /* C2R FFT along the last axis + deconvolve + crop */
-    NLP_STAGE_POISSON = 8     /* 2D Poisson FP64 parts (moments, rho-hat(0), u_1) */
+    NLP_STAGE_POISSON = 8,    /* 2D Poisson FP64 parts (moments, rho-hat(0), u_1) */
+    NLP_STAGE_WINDOW_SUM = 9  /* sum the windows of tiles split into several chunks (before the combine) */
 };
 nlp_status nlp_set_stage_timing(nlp_plan plan, int on);
 nlp_status nlp_get_stage_times(nlp_plan plan, int *stage_ids, double *ms, int max, int *count);

@@ -72,6 +72,10 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
         if (D.sub_T > 0) NLP_CUDA_TRY(launch_interp_spread_reg<T>(D, st));
         else NLP_CUDA_TRY(launch_interp_spread<T>(D, st));
         mark(p, NLP_STAGE_SPREAD);
+        if (D.ngroups > 0) {
+            NLP_CUDA_TRY(launch_window_sum<T>(D, st));
+            mark(p, NLP_STAGE_WINDOW_SUM);
+        }
         NLP_CUDA_TRY(launch_combine<T>(D, st));
         mark(p, NLP_STAGE_COMBINE);
     }

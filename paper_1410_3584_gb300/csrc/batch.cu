@@ -23,7 +23,7 @@
 
 namespace nlp {
 
-enum { ST_R2C = 0, ST_A1, ST_A0, ST_SPREAD, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
+enum { ST_R2C = 0, ST_A1, ST_A0, ST_SPREAD, ST_WSUM, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
 constexpr int kRegLines = 16;          // lines (pairs) per register-engine FFT task: 16 x 16 threads
 constexpr int kCombTiles = 16;         // combine tiles of G per task
 
@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
             case ST_SPREAD:
                 if (B.spread_warp) spread_warp_block<8, 4>(B.P, i, smraw);
                 else spread_generic_block<float>(B.P, i, smraw);
+                break;
+            case ST_WSUM:
+                window_sum_block<float>(B.P, i);
                 break;
             case ST_COMBINE: {
                 const int64_t t1 = min((int64_t)(i + 1) * kCombTiles, B.P.cmb_tiles);
@@ -271,6 +274,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         B.ntask[ST_A0] = three ? B.a0.nouter * (int)((nh + B.nb_a0 - 1) / B.nb_a0) : 0;
         B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
         B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);
+        B.ntask[ST_WSUM] = (int)(D.ngroups * D.grp_parts);
         B.ntask[ST_COMBINE] = (int)((D.cmb_tiles + kCombTiles - 1) / kCombTiles);
         B.ntask[ST_B0] = B.ntask[ST_A0];
         B.ntask[ST_B1] = B.ntask[ST_A1];

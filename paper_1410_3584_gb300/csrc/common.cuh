@@ -103,6 +103,10 @@ template <typename T> struct DevPlan {
     cpx<T> *win;        // one slot of win_n[0] x win_n[1] x win_n[2] cells per chunk of the active kernel
     int win_n[3];       // window extent (tile + w - 1 per axis; axis 0 of 2D plans: 1)
     int64_t win_cells;
+    const int *grp;         // tiles split into several chunks: {first, count} into grp_list, per group
+    const int *grp_list;    // slots of each such tile, ascending; the first one receives their sum
+    int64_t ngroups;
+    int grp_parts;          // window-sum tasks per group (256-cell parts of the window)
     const int *cmb_off;     // per combine tile: its entries are cmb[cmb_off[t] .. cmb_off[t+1])
     const CombEntry *cmb;
     int cmb_t[3];       // combine tile edge per axis

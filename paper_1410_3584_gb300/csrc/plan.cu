@@ -2,6 +2,7 @@
 // tables, node binning by fine-grid tile, FFT tables and workspace.
 #include <atomic>
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -212,11 +213,42 @@ static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<
     D.cmb_t[2] = two ? 16 : 8;
     for (int a = 0; a < 3; ++a) D.cmb_n[a] = (Nout[a] + D.cmb_t[a] - 1) / D.cmb_t[a];
     D.cmb_tiles = (int64_t)D.cmb_n[0] * D.cmb_n[1] * D.cmb_n[2];
+    // chunks of one tile share its origin: group their slots (ascending); the first slot of
+    // each group receives the group's sum before the combine, which then reads only it
+    std::vector<std::pair<std::array<int, 3>, int>> byorg(act.size());
+    for (size_t c = 0; c < act.size(); ++c) byorg[c] = {{act[c].bx, act[c].by, act[c].bz}, (int)c};
+    std::sort(byorg.begin(), byorg.end());
+    std::vector<int> grp, grp_list, reps;
+    for (size_t i = 0; i < byorg.size();) {
+        size_t k = i;
+        while (k < byorg.size() && byorg[k].first == byorg[i].first) ++k;
+        reps.push_back(byorg[i].second);
+        if (k - i > 1) {
+            grp.push_back((int)grp_list.size());
+            grp.push_back((int)(k - i));
+            for (size_t u = i; u < k; ++u) grp_list.push_back(byorg[u].second);
+        }
+        i = k;
+    }
+    D.ngroups = (int64_t)grp.size() / 2;
+    D.grp_parts = (int)((D.win_cells + 255) / 256);
+    D.grp = nullptr;
+    D.grp_list = nullptr;
+    if (D.ngroups > 0) {
+        void *dg = nullptr, *dl = nullptr;
+        nlp_status s;
+        if ((s = alloc_dev(p, &dg, sizeof(int) * grp.size()))) return s;
+        if ((s = alloc_dev(p, &dl, sizeof(int) * grp_list.size()))) return s;
+        cudaMemcpy(dg, grp.data(), sizeof(int) * grp.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dl, grp_list.data(), sizeof(int) * grp_list.size(), cudaMemcpyHostToDevice);
+        D.grp = (const int *)dg;
+        D.grp_list = (const int *)dl;
+    }
     struct Key { int64_t tile; CombEntry e; };
     std::vector<Key> keys;
-    keys.reserve(act.size() * 12);
+    keys.reserve(reps.size() * 12);
     auto wrap = [](int64_t x, int n) { int64_t r = x % n; return (int)(r < 0 ? r + n : r); };
-    for (size_t c = 0; c < act.size(); ++c) {
+    for (int c : reps) {
         const int b[3] = {act[c].bx, act[c].by, act[c].bz};
         std::vector<std::pair<int, int>> dir[3], mir[3];
         for (int a = 0; a < 3; ++a) {

@@ -86,9 +86,36 @@ __device__ __forceinline__ T window_fill(const DevPlan<T> &P, const WinCol &k, c
 }
 
 // ------------------------------------------------------------------ combine
-// Output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G with
-// N = (nf0, nf1, nh).  Every cell of G belongs to exactly one tile and is written exactly once
-// (tiles that no window reaches get zeros), so the pass also replaces clearing G.
+// Tiles with many nodes are split into several chunks, whose windows share the tile's origin.
+// First pass (window_sum_block): per such tile, the windows of its chunks are added cell by
+// cell, in slot order, into its first slot.  Part p of group g covers window cells
+// [256 p, 256 p + 256).
+template <typename T>
+__device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t task) {
+    const int64_t g = task / P.grp_parts;
+    const int64_t q = (task % P.grp_parts) * 256 + threadIdx.x;
+    if (q >= P.win_cells || threadIdx.x >= 256) return;
+    const int first = P.grp[2 * g], count = P.grp[2 * g + 1];
+    const int *slots = P.grp_list + first;
+    T sx = (T)0, sy = (T)0;
+    for (int i = 0; i < count; i += 8) {
+        cpx<T> v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = (i + u < count) ? P.win[(int64_t)slots[i + u] * P.win_cells + q] : mk<T>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            sx += v[u].x;
+            sy += v[u].y;
+        }
+    }
+    P.win[(int64_t)slots[0] * P.win_cells + q] = mk<T>(sx, sy);
+}
+
+// Second pass: output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G
+// with N = (nf0, nf1, nh).  Every cell of G belongs to exactly one tile and is written exactly
+// once (tiles that no window reaches get zeros), so the pass also replaces clearing G.  A cell
+// adds its entries' window values in entry order, fetched eight at a time.
 template <typename T>
 __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile) {
     const int T0 = P.cmb_t[0], T1 = P.cmb_t[1], T2 = P.cmb_t[2];
@@ -104,14 +131,26 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile)
         const int l0 = t0 * T0 + c0, l1 = t1 * T1 + c1, l2 = t2 * T2 + c2;
         if (l0 >= N[0] || l1 >= N[1] || l2 >= N[2]) continue;
         T sx = (T)0, sy = (T)0;
-        for (int e = e0; e < e1; ++e) {
-            const CombEntry E = P.cmb[e];
-            const int s = E.mirror ? -1 : 1;
-            const int a0 = s * l0 + E.o[0], a1 = s * l1 + E.o[1], a2 = s * l2 + E.o[2];
-            if ((unsigned)a0 >= (unsigned)W0 || (unsigned)a1 >= (unsigned)W1 || (unsigned)a2 >= (unsigned)W2) continue;
-            const cpx<T> v = P.win[(int64_t)E.chunk * P.win_cells + ((int64_t)a0 * W1 + a1) * W2 + a2];
-            sx += v.x;
-            sy += E.mirror ? -v.y : v.y;
+        for (int e = e0; e < e1; e += 8) {
+            cpx<T> v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                v[u] = mk<T>(0, 0);
+                if (e + u < e1) {
+                    const CombEntry E = P.cmb[e + u];
+                    const int s = E.mirror ? -1 : 1;
+                    const int a0 = s * l0 + E.o[0], a1 = s * l1 + E.o[1], a2 = s * l2 + E.o[2];
+                    if ((unsigned)a0 < (unsigned)W0 && (unsigned)a1 < (unsigned)W1 && (unsigned)a2 < (unsigned)W2) {
+                        v[u] = P.win[(int64_t)E.chunk * P.win_cells + ((int64_t)a0 * W1 + a1) * W2 + a2];
+                        if (E.mirror) v[u].y = -v[u].y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                sx += v[u].x;
+                sy += v[u].y;
+            }
         }
         P.G[((int64_t)l0 * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx, sy);
     }

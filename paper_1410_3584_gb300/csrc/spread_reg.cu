@@ -203,8 +203,12 @@ __global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_warp(DevPlan<fl
     spread_warp_block<W, kWarpNB>(P, blockIdx.x, smraw);
 }
 
+template <typename T> __global__ void __launch_bounds__(256) k_window_sum(DevPlan<T> P) {
+    window_sum_block<T>(P, blockIdx.x);
+}
+
 template <typename T> __global__ void __launch_bounds__(256) k_combine(DevPlan<T> P) {
-    for (int64_t t = blockIdx.x; t < P.cmb_tiles; t += gridDim.x) combine_block<T>(P, t);
+    combine_block<T>(P, blockIdx.x);
 }
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
@@ -299,10 +303,15 @@ template <> cudaError_t launch_interp_spread_reg<double>(const DevPlan<double> &
     return cudaErrorInvalidValue;
 }
 
+template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStream_t st) {
+    if (P.ngroups == 0) return cudaSuccess;
+    k_window_sum<T><<<(unsigned)(P.ngroups * P.grp_parts), 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
 template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st) {
     if (P.cmb_tiles == 0) return cudaSuccess;
-    const int blocks = (int)std::min<int64_t>(P.cmb_tiles, 152 * 16);
-    k_combine<T><<<blocks, 256, 0, st>>>(P);
+    k_combine<T><<<(unsigned)P.cmb_tiles, 256, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -310,6 +319,8 @@ template bool reg_kernel_supported<float>(int);
 template bool reg_kernel_supported<double>(int);
 template bool warp_kernel_used<float>(int);
 template bool warp_kernel_used<double>(int);
+template cudaError_t launch_window_sum<float>(const DevPlan<float> &, cudaStream_t);
+template cudaError_t launch_window_sum<double>(const DevPlan<double> &, cudaStream_t);
 template cudaError_t launch_combine<float>(const DevPlan<float> &, cudaStream_t);
 template cudaError_t launch_combine<double>(const DevPlan<double> &, cudaStream_t);
 
