@@ -79,20 +79,28 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
         NLP_CUDA_TRY(launch_combine<T>(D, st));
         mark(p, NLP_STAGE_COMBINE);
     }
-    // type 1: inverse FFT (axis 0, axis 1, last axis), deconvolve, crop
+    // type 1: inverse FFT (axis 0, axis 1, last axis), deconvolve, crop.  After a spread, the
+    // first inverse pass reads G and writes F (free once the spread has read it), so G keeps
+    // the zeros the combine pass does not rewrite; the other passes work on F.
+    const bool oop = D.Khat == nullptr && D.G != D.F;
+    cpx<T> *R = oop ? D.F : D.G;
     if (three) {
         StridedDesc b0 = a0;
         b0.n_in = D.nf[0];
         b0.n_out = D.n[0];
+        b0.out = R;
         NLP_CUDA_TRY(launch_fft_strided<T>(D.G, b0, D.len[0], +1, st));
         mark(p, NLP_STAGE_INV_FIRST);
     }
     StridedDesc b1 = a1;
     b1.n_in = D.nf[1];
     b1.n_out = D.n[1];
-    NLP_CUDA_TRY(launch_fft_strided<T>(D.G, b1, D.len[1], +1, st));
+    b1.out = R;
+    NLP_CUDA_TRY(launch_fft_strided<T>(three ? R : D.G, b1, D.len[1], +1, st));
     mark(p, NLP_STAGE_INV_MID);
-    NLP_CUDA_TRY(launch_inv_c2r<T>(phi, D, st));
+    DevPlan<T> Dr = D;
+    Dr.G = R;
+    NLP_CUDA_TRY(launch_inv_c2r<T>(phi, Dr, st));
     mark(p, NLP_STAGE_INV_LAST);
     if (pois) {
         NLP_CUDA_TRY(launch_poisson_u1<T>(phi, D, p->L3, p->h, st));

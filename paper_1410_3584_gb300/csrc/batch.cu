@@ -29,6 +29,7 @@ constexpr int kCombTiles = 16;         // combine tiles of G per task
 
 struct BatchItem {
     DevPlan<float> P;
+    DevPlan<float> Pr;       // as P with G = F: the inverse passes after the first read and write F
     StridedDesc a1, a0, b0, b1;
     int nb_r2c, nb_a1, nb_a0, nb_c2r;
     int ntask[kStages];
@@ -109,28 +110,32 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
                 else fft_strided_block<float, -1>(B.P.F, B.a0, B.P.len[0], B.nb_a0, i, smraw);
                 break;
             case ST_SPREAD:
-                if (B.spread_warp) spread_warp_block<8, 4>(B.P, i, smraw);
+                if (B.spread_warp) spread_warp_block<8, kWarpNB>(B.P, i, smraw);
                 else spread_generic_block<float>(B.P, i, smraw);
                 break;
             case ST_WSUM:
                 window_sum_block<float>(B.P, i);
                 break;
             case ST_COMBINE: {
-                const int64_t t1 = min((int64_t)(i + 1) * kCombTiles, B.P.cmb_tiles);
-                for (int64_t t = (int64_t)i * kCombTiles; t < t1; ++t) combine_block<float>(B.P, t);
+                CombStage *cst = (CombStage *)smraw;
+                const int64_t t1 = min((int64_t)(i + 1) * kCombTiles, B.P.cmb_nact);
+                for (int64_t t = (int64_t)i * kCombTiles; t < t1; ++t) combine_block<float>(B.P, B.P.cmb_act[t], cst);
                 break;
             }
             case ST_B0:
                 if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(B.P.G, B.b0, B.P.len[0], i, smraw);
                 else fft_strided_block<float, +1>(B.P.G, B.b0, B.P.len[0], B.nb_a0, i, smraw);
                 break;
-            case ST_B1:
-                if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(B.P.G, B.b1, B.P.len[1], i, smraw);
-                else fft_strided_block<float, +1>(B.P.G, B.b1, B.P.len[1], B.nb_a1, i, smraw);
+            case ST_B1: {
+                // 3D: in place on F (the first inverse pass wrote it); 2D: G -> F
+                cpx<float> *src = B.ntask[ST_B0] > 0 ? B.P.F : B.P.G;
+                if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(src, B.b1, B.P.len[1], i, smraw);
+                else fft_strided_block<float, +1>(src, B.b1, B.P.len[1], B.nb_a1, i, smraw);
                 break;
+            }
             case ST_C2R:
-                if (B.reg_fft) inv_c2r_reg_block<float, kRegLines>(A.phi[p], B.P, i, smraw);
-                else inv_c2r_block<float>(A.phi[p], B.P, B.nb_c2r, i, smraw);
+                if (B.reg_fft) inv_c2r_reg_block<float, kRegLines>(A.phi[p], B.Pr, i, smraw);
+                else inv_c2r_block<float>(A.phi[p], B.Pr, B.nb_c2r, i, smraw);
                 break;
         }
         __syncthreads();
@@ -246,11 +251,15 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         B.a1.nouter = three ? D.n[0] : 1; B.a1.os = (int64_t)D.nf[1] * nh;
         B.a1.outer_map_n = three ? D.n[0] : 0; B.a1.outer_map_N = D.nf[0];
         B.b1 = B.a1; B.b1.n_in = D.nf[1]; B.b1.n_out = D.n[1];
+        B.b1.out = D.F;
         if (three) {
             B.a0.n_in = D.n[0]; B.a0.n_out = D.nf[0]; B.a0.es = (int64_t)D.nf[1] * nh; B.a0.ncol = (int)nh;
             B.a0.nouter = D.nf[1]; B.a0.os = nh;
             B.b0 = B.a0; B.b0.n_in = D.nf[0]; B.b0.n_out = D.n[0];
+            B.b0.out = D.F;
         }
+        B.Pr = D;
+        B.Pr.G = D.F;
         // register-engine FFT tasks where every axis has its factorisation and the task's shared
         // memory stays within the budget of the single-plan launchers' widest choice
         const size_t kRegBudget = 112 * 1024;
@@ -275,7 +284,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
         B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);
         B.ntask[ST_WSUM] = (int)(D.ngroups * D.grp_parts);
-        B.ntask[ST_COMBINE] = (int)((D.cmb_tiles + kCombTiles - 1) / kCombTiles);
+        B.ntask[ST_COMBINE] = (int)((D.cmb_nact + kCombTiles - 1) / kCombTiles);
         B.ntask[ST_B0] = B.ntask[ST_A0];
         B.ntask[ST_B1] = B.ntask[ST_A1];
         B.ntask[ST_C2R] = B.ntask[ST_R2C];

@@ -112,6 +112,8 @@ template <typename T> struct DevPlan {
     int cmb_t[3];       // combine tile edge per axis
     int cmb_n[3];       // combine tiles per axis (over nf0 x nf1 x nh)
     int64_t cmb_tiles;
+    const int *cmb_act; // the tiles that windows reach (the others of G stay zero from plan time)
+    int64_t cmb_nact;
     float psi_sum3;     // FP32 warp kernel: (max over node offsets of sum_t psi)^3, bounds the interpolation
 };
 

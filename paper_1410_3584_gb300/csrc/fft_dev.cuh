@@ -237,6 +237,7 @@ __device__ __forceinline__ void fft_strided_block(cpx<T> *data, const StridedDes
     const int c0 = (bid % ctiles) * nb;
     const int oo = d.outer_map_n > 0 ? wrapi(o - d.outer_map_n / 2, d.outer_map_N) : o;
     cpx<T> *base = data + (int64_t)oo * d.os + c0;
+    cpx<T> *obase = (d.out ? (cpx<T> *)d.out : data) + (int64_t)oo * d.os + c0;
     const int ncl = min(nb, d.ncol - c0);
     if (d.n_in < N) {
         for (int q = threadIdx.x; q < N * nb; q += blockDim.x) A[(q / nb) * ldb + (q % nb)] = mk<T>(0, 0);
@@ -255,7 +256,7 @@ __device__ __forceinline__ void fft_strided_block(cpx<T> *data, const StridedDes
         const int b = q % nb, i = q / nb;
         if (b >= ncl) continue;
         const int l = d.n_out < N ? wrapi(i - d.n_out / 2, N) : i;
-        base[(int64_t)l * d.es + b] = R[l * ldb + b];
+        obase[(int64_t)l * d.es + b] = R[l * ldb + b];
     }
 }
 
@@ -442,6 +443,7 @@ __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &
     const int oo = d.outer_map_n > 0 ? wrapi(o - d.outer_map_n / 2, d.outer_map_N) : o;
     const bool colok = c0 + b < d.ncol;
     cpx<T> *base = data + (int64_t)oo * d.os + c0 + b;
+    cpx<T> *obase = (d.out ? (cpx<T> *)d.out : data) + (int64_t)oo * d.os + c0 + b;
     // window of n points: positions [0, n - n/2) and [N - n/2, N)
     const int ilo = d.n_in < N ? d.n_in - d.n_in / 2 : N, ihi = d.n_in < N ? N - d.n_in / 2 : N;
     const int olo = d.n_out < N ? d.n_out - d.n_out / 2 : N, ohi = d.n_out < N ? N - d.n_out / 2 : N;
@@ -449,7 +451,7 @@ __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &
         return (colok && (l < ilo || l >= ihi)) ? base[(int64_t)l * d.es] : mk<T>(0, 0);
     };
     auto gdst = [&](int l, cpx<T> v) {
-        if (colok && (l < olo || l >= ohi)) base[(int64_t)l * d.es] = v;
+        if (colok && (l < olo || l >= ohi)) obase[(int64_t)l * d.es] = v;
     };
     auto idx = [](int l, int c) { return l * NBC + c; };
     fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);

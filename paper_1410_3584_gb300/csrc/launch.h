@@ -30,6 +30,7 @@ struct StridedDesc {
     int64_t os;           // stride between outer lines
     int outer_map_n;      // > 0: outer index o addresses line (o - outer_map_n/2) mod outer_map_N
     int outer_map_N;
+    void *out;            // null: in place; else the output array (same layout as the input)
 };
 
 template <typename T> cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st);

@@ -170,10 +170,11 @@ __global__ void k_psi_table(T *tab, const T *nd, const uint32_t *no, int64_t M, 
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / (3 * Wsub);
         const int r3 = (int)(e - j * 3 * Wsub), a = r3 / Wsub, i = r3 - a * Wsub;
-        const int r = (int)((no[j] >> (8 * a)) & 0xff) % Ts;
+        // Ts < 0: offsets are already taken from the sub-window origin
+        const int r = Ts < 0 ? 0 : (int)((no[j] >> (8 * a)) & 0xff) % Ts;
         const int t = i - r;
         double v = 0.0;
-        if (t >= 0 && t < w) {
+        if (Ts < 0 || (t >= 0 && t < w)) {
             const double x = 2.0 * ((double)t - (double)nd[4 * j + a]) / w;
             const double sv = 1.0 - x * x;
             v = sv > 0 ? exp(beta * (sqrt(sv) - 1.0)) : 0.0;
@@ -208,8 +209,9 @@ static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<
     const int N[3] = {D.nf[0], D.nf[1], D.nf[2]};
     const int Nout[3] = {D.nf[0], D.nf[1], D.nh};
     const bool two = p->grid.dim == 2;
+    // tile edges: a (y, z) face of at most 128 cells (one thread each in blocks of 128)
     D.cmb_t[0] = two ? 1 : 8;
-    D.cmb_t[1] = two ? 16 : 8;
+    D.cmb_t[1] = 8;
     D.cmb_t[2] = two ? 16 : 8;
     for (int a = 0; a < 3; ++a) D.cmb_n[a] = (Nout[a] + D.cmb_t[a] - 1) / D.cmb_t[a];
     D.cmb_tiles = (int64_t)D.cmb_n[0] * D.cmb_n[1] * D.cmb_n[2];
@@ -296,9 +298,17 @@ static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<
         off[keys[i].tile + 1]++;
         ent[i] = keys[i].e;
     }
-    for (int64_t t = 0; t < D.cmb_tiles; ++t) off[t + 1] += off[t];
-    void *doff = nullptr, *dent = nullptr;
+    std::vector<int> live;
+    for (int64_t t = 0; t < D.cmb_tiles; ++t) {
+        if (off[t + 1] > 0) live.push_back((int)t);
+        off[t + 1] += off[t];
+    }
+    void *doff = nullptr, *dent = nullptr, *dact = nullptr;
     nlp_status s;
+    if ((s = alloc_dev(p, &dact, sizeof(int) * std::max<size_t>(1, live.size())))) return s;
+    if (!live.empty()) cudaMemcpy(dact, live.data(), sizeof(int) * live.size(), cudaMemcpyHostToDevice);
+    D.cmb_act = (const int *)dact;
+    D.cmb_nact = (int64_t)live.size();
     if ((s = alloc_dev(p, &doff, sizeof(int) * off.size()))) return s;
     if ((s = alloc_dev(p, &dent, sizeof(CombEntry) * std::max<size_t>(1, ent.size())))) return s;
     cudaMemcpy(doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
@@ -369,6 +379,8 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     if (s) return s;
     D.F = (cpx<T> *)dF;
     D.G = (cpx<T> *)dG;
+    // G: zeros outside the tiles the combine pass writes, kept so by every evaluation
+    if (cudaMemset(dG, 0, sizeof(cpx<T>) * spec) != cudaSuccess) return NLP_ERR_CUDA;
 
     // ---- bin nodes by tile of their first tap, then by sub-tile inside the tile
     const int64_t M = (int64_t)nodes.size();
@@ -414,7 +426,10 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     // generic chunks: 3D windows are large (fill and fold amortised over many nodes); the 2D
     // windows are small and the polar nodes crowd the tiles near k = 0, so short chunks spread
     // those tiles over many CTAs (measured at 1024^2: spread 0.27 -> 0.05 ms FP32)
-    const int CH = p->grid.dim == 3 ? (sizeof(T) == 8 ? 256 : 1024) : (sizeof(T) == 8 ? 32 : 64);
+#ifndef NLP_CHUNK3_F32
+#define NLP_CHUNK3_F32 2048
+#endif
+    const int CH = p->grid.dim == 3 ? (sizeof(T) == 8 ? 256 : NLP_CHUNK3_F32) : (sizeof(T) == 8 ? 32 : 64);
     std::vector<Chunk> chunks, rchunks;
     std::vector<int> seg_node;
     std::vector<uint32_t> seg_sub;
@@ -497,7 +512,9 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         for (size_t i = 0; i < w.size(); ++i) sorted[i] = rchunks[w[i].second];
         rchunks.swap(sorted);
     }
-    std::vector<T> nd(4 * (size_t)M);
+    // node records, padded by 16 zero records: batch loads of the FP32 warp kernel may reach
+    // past a piece's last node (those nodes get weight zero)
+    std::vector<T> nd(4 * (size_t)(M + 16), (T)0);
     std::vector<uint32_t> no(M);
     const int Wsub = Ts + D.w - 1;
     // per-chunk sums of |omega_j| (they bound each chunk's window, see spread_dev.cuh)
@@ -552,11 +569,17 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         // team kernel: kernel values of every node (the nodes are fixed per plan), placed in
         // the sub-window of its segment; computed on the device from (delta, offsets).  The
         // FP32 warp kernel evaluates them per evaluation instead.
-        if (!warp_k) {
+#ifdef NLP_WARP_TABLE
+        const bool tab = true;
+#else
+        const bool tab = !warp_k;
+#endif
+        if (tab) {
             void *dpt;
-            if ((s = alloc_dev(p, &dpt, sizeof(T) * (size_t)M * 3 * Wsub))) return s;
-            if (launch_psi_table<T>((T *)dpt, (const T *)dnd, (const uint32_t *)dno, M, D.w, Wsub, Ts,
-                                    p->info.beta_es, p->stream) != cudaSuccess)
+            if ((s = alloc_dev(p, &dpt, sizeof(T) * (size_t)(M + 16) * 3 * Wsub))) return s;
+            cudaMemsetAsync(dpt, 0, sizeof(T) * (size_t)(M + 16) * 3 * Wsub, p->stream);   // padding records
+            if (launch_psi_table<T>((T *)dpt, (const T *)dnd, (const uint32_t *)dno, M, D.w, Wsub,
+                                    warp_k ? -1 : Ts, p->info.beta_es, p->stream) != cudaSuccess)
                 return NLP_ERR_CUDA;
             D.psi_tab = (const T *)dpt;
         }

@@ -98,13 +98,13 @@ __device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t ta
     const int first = P.grp[2 * g], count = P.grp[2 * g + 1];
     const int *slots = P.grp_list + first;
     T sx = (T)0, sy = (T)0;
-    for (int i = 0; i < count; i += 8) {
-        cpx<T> v[8];
+    for (int i = 0; i < count; i += 16) {
+        cpx<T> v[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 16; ++u)
             v[u] = (i + u < count) ? P.win[(int64_t)slots[i + u] * P.win_cells + q] : mk<T>(0, 0);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             sx += v[u].x;
             sy += v[u].y;
         }
@@ -113,47 +113,83 @@ __device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t ta
 }
 
 // Second pass: output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G
-// with N = (nf0, nf1, nh).  Every cell of G belongs to exactly one tile and is written exactly
-// once (tiles that no window reaches get zeros), so the pass also replaces clearing G.  A cell
-// adds its entries' window values in entry order, fetched eight at a time.
+// with N = (nf0, nf1, nh).  The pass visits the tiles that some window reaches and writes each
+// of their cells exactly once; the other tiles of G hold zeros from plan time (no pass writes
+// G otherwise: the first inverse FFT pass reads G and writes its result elsewhere).  The
+// tile's entries are staged in shared memory, 64 at a time.  A thread owns the cells of one
+// (y, z) position of the tile along x and adds their window values in entry order; the loads
+// of four entries and all its cells are issued together.
+struct CombStage {
+    long long base;    // slot * window cells
+    int o0, o1, o2, s; // offsets and sign (+1 direct, -1 mirror)
+};
+constexpr int kCombStage = 64;
+
 template <typename T>
-__device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile) {
+__device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile, CombStage *st) {
     const int T0 = P.cmb_t[0], T1 = P.cmb_t[1], T2 = P.cmb_t[2];
     const int t2 = (int)(tile % P.cmb_n[2]);
     const int t1 = (int)((tile / P.cmb_n[2]) % P.cmb_n[1]);
     const int t0 = (int)(tile / ((int64_t)P.cmb_n[2] * P.cmb_n[1]));
     const int e0 = P.cmb_off[tile], e1 = P.cmb_off[tile + 1];
     const int W0 = P.win_n[0], W1 = P.win_n[1], W2 = P.win_n[2];
-    const int N[3] = {P.nf[0], P.nf[1], P.nh};
-    const int cells = T0 * T1 * T2;
-    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-        const int c2 = q % T2, c1 = (q / T2) % T1, c0 = q / (T1 * T2);
-        const int l0 = t0 * T0 + c0, l1 = t1 * T1 + c1, l2 = t2 * T2 + c2;
-        if (l0 >= N[0] || l1 >= N[1] || l2 >= N[2]) continue;
-        T sx = (T)0, sy = (T)0;
-        for (int e = e0; e < e1; e += 8) {
-            cpx<T> v[8];
+    const int64_t W12 = (int64_t)W1 * W2;
+    const int N0 = P.nf[0], N1 = P.nf[1], N2 = P.nh;
+    // thread: the (y, z) cell (c1, c2) of the tile for x = c0, c0 + S, ... (S = blockDim / (T1 T2))
+    constexpr int CPT = 8;
+    const int yz = T1 * T2;
+    const int S = max(1, (int)blockDim.x / yz);
+    const int c2 = threadIdx.x % T2, c1 = (threadIdx.x / T2) % T1, c0 = threadIdx.x / yz;
+    const int l1 = t1 * T1 + c1, l2 = t2 * T2 + c2, lx = t0 * T0 + c0;
+    const bool okyz = threadIdx.x < S * yz && l1 < N1 && l2 < N2;
+    int nx = 0;   // cells of this thread along x
+    for (int u = 0; u < CPT; ++u)
+        if (c0 + u * S < T0 && lx + u * S < N0) nx = u + 1;
+    T sx[CPT], sy[CPT];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                v[u] = mk<T>(0, 0);
-                if (e + u < e1) {
-                    const CombEntry E = P.cmb[e + u];
-                    const int s = E.mirror ? -1 : 1;
-                    const int a0 = s * l0 + E.o[0], a1 = s * l1 + E.o[1], a2 = s * l2 + E.o[2];
-                    if ((unsigned)a0 < (unsigned)W0 && (unsigned)a1 < (unsigned)W1 && (unsigned)a2 < (unsigned)W2) {
-                        v[u] = P.win[(int64_t)E.chunk * P.win_cells + ((int64_t)a0 * W1 + a1) * W2 + a2];
-                        if (E.mirror) v[u].y = -v[u].y;
-                    }
+    for (int u = 0; u < CPT; ++u) sx[u] = sy[u] = (T)0;
+    for (int eb = e0; eb < e1; eb += kCombStage) {
+        const int ne = min(kCombStage, e1 - eb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+            const CombEntry E = P.cmb[eb + i];
+            st[i].base = (long long)E.chunk * P.win_cells;
+            st[i].o0 = E.o[0];
+            st[i].o1 = E.o[1];
+            st[i].o2 = E.o[2];
+            st[i].s = E.mirror ? -1 : 1;
+        }
+        __syncthreads();
+        if (!okyz) continue;
+        for (int e = 0; e < ne; e += 4) {
+            cpx<T> v[4][CPT];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const CombStage E = st[min(e + k, ne - 1)];
+                const int a1 = E.s * l1 + E.o1, a2 = E.s * l2 + E.o2;
+                const bool inyz = e + k < ne && (unsigned)a1 < (unsigned)W1 && (unsigned)a2 < (unsigned)W2;
+                const cpx<T> *row = P.win + E.base + (int64_t)a1 * W2 + a2;
+                const int a00 = E.s * lx + E.o0, da = E.s * S;
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) {
+                    const int a0 = a00 + u * da;
+                    v[k][u] = (inyz && u < nx && (unsigned)a0 < (unsigned)W0) ? row[a0 * W12] : mk<T>(0, 0);
+                    if (E.s < 0) v[k][u].y = -v[k][u].y;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                sx += v[u].x;
-                sy += v[u].y;
-            }
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) {
+                    sx[u] += v[k][u].x;
+                    sy[u] += v[k][u].y;
+                }
         }
-        P.G[((int64_t)l0 * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx, sy);
     }
+    if (!okyz) return;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u)
+        if (u < nx) P.G[((int64_t)(lx + u * S) * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx[u], sy[u]);
 }
 
 }  // namespace nlp

@@ -184,25 +184,38 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
 // ======================================================================= FP32 warp kernel
 // One warp per piece (a run of at most 64 nodes of one 2^3 sub-tile, whose nodes all reach
 // the same sub-window of W^3 cells, W = w + 1): lane L owns the sub-window z-columns
-// a = (L mod W', L div W') and b (32 further columns), where W' = W for W^2 <= 64.  Per piece
-// the lane holds both F columns and both G accumulator columns in registers; per batch of
-// NB nodes it
-//   1. evaluates the 3 W kernel values of each node from its position (lanes (axis, tap)),
+// a = (L mod W, L div W) and b = a + 32 (in column order).  Per piece the lane holds both F
+// columns and both G accumulator columns in registers; per batch of NB nodes it
+//   1. evaluates the 3 W kernel values of each node from its position (the 3 W NB values
+//      spread evenly over the lanes) into a per-warp stage, each value stored twice so that
+//      (v, v) pairs load as packed operands,
 //   2. interpolates: per column a complex z-contraction with packed FP32x2 FMAs, weighted by
-//      the column's x/y kernel values, reduced over the warp for all NB nodes at once,
+//      the column's x/y kernel values; the 32 lane partials of each node are summed by one
+//      integer warp reduction each (fixed point, see below), which every lane receives,
 //   3. scales by the node weight and spreads: per column a complex x z outer product with
 //      packed FMAs into the G registers.
-// At the end of a piece the G columns are added to the chunk's shared window as 32-bit
-// fixed-point integers: integer addition is associative, so the warps' order does not change
-// the sums.  The quantum q of a chunk is a power of two chosen before any spreading from a
-// bound on every cell of its window: |G| <= sum_j |c_j| (the kernel is at most 1) and
-// |c_j| = |omega_j| |rho-hat_j| <= |omega_j| sqrt(2) max|F| (max_delta sum_t psi)^3, so with
-// S = sum_j |omega_j| (plan time, per chunk) every partial sum of a cell stays below
-// B = sqrt(2) max|F| C^3 S <= 2^30 q.
+// A piece's last batch is padded with copies of its last node carrying weight zero, so every
+// batch runs the same code.
+//
+// Fixed point.  Integer addition is associative, so sums taken in integers do not depend on
+// the order of the lanes or warps.  Two quanta per chunk, powers of two (int * q is exact),
+// from bounds known before any node is processed: with M the largest |re| or |im| of F on the
+// chunk's window and C = max over node offsets of sum_t psi, every interpolated value obeys
+// |rho-hat_j| <= sqrt(2) M C^3 =: B1, and so does the sum over lanes of the absolute lane
+// partials; and every cell of the window obeys |G| <= sum_j |c_j| <= B1 S (the kernel is at most
+// 1, S = sum_j |omega_j| of the chunk, plan time).  With q1 = 2^(ceil log2 1.01 B1 - 30) for
+// the interpolation sums and q2 = 2^(ceil log2 1.01 B1 S - 30) for the window, all partial sums
+// stay below 2^31 in magnitude.
+#ifndef NLP_WARP_NB
+#define NLP_WARP_NB 4
+#endif
+constexpr int kWarpNB = NLP_WARP_NB;   // nodes per batch of the FP32 warp kernel
+
 template <int W, int NB> struct WarpGeo {
-    static constexpr int V = 2 * NB;
-    static constexpr int SS = 32;               // floats of one node's kernel values: x[8] y[8] z pairs[16]
-    static constexpr int STAGE = NB * SS + V;   // floats per warp
+    static constexpr int SS = 48;               // floats per node: x, y, z kernel values, each as (v, v)
+    static constexpr int STAGE = NB * SS;       // floats per warp
+    static constexpr int KV = 3 * 8 * NB;       // kernel values per batch (8 taps per axis)
+    static constexpr int KR = (KV + 31) / 32;   // evaluation rounds per lane
 };
 
 struct WarpLayout {
@@ -210,7 +223,7 @@ struct WarpLayout {
     int RP, SP;       // F window: cell (a, b, c) at a SP + b RP + c (RP even, SP / 2 odd: 16-byte column
                       // loads of the 8 lanes of a quarter warp fall in distinct bank groups)
     int RG, SG;       // G window: cell (a, b, c) at a SG + b RG + c (RG odd)
-    size_t offG, offStage, offRows, bytes;
+    size_t offG, offStage, offRows, offRowF, offRowG, bytes;
 };
 
 template <int W, int NB>
@@ -224,10 +237,13 @@ __host__ __device__ inline WarpLayout warp_layout(int Wt0, int Wt1, int Wt2, int
     if ((L.SP / 2) % 2 == 0) L.SP += 2;
     L.RG = Wt2 | 1;
     L.SG = Wt1 * L.RG;
+    const size_t rows = (size_t)Wt0 * Wt1;
     L.offG = align16((size_t)Wt0 * L.SP * sizeof(float2));
     L.offStage = align16(L.offG + (size_t)Wt0 * L.SG * sizeof(int2));
     L.offRows = align16(L.offStage + (size_t)nwarps * WarpGeo<W, NB>::STAGE * sizeof(float));
-    L.bytes = L.offRows + 2 * (size_t)Wt0 * Wt1 * sizeof(int64_t);
+    L.offRowF = L.offRows + 2 * rows * sizeof(int64_t);
+    L.offRowG = L.offRowF + rows * sizeof(int);
+    L.bytes = L.offRowG + rows * sizeof(int);
     return L;
 }
 
@@ -236,8 +252,7 @@ __host__ __device__ inline WarpLayout warp_layout(int Wt0, int Wt1, int Wt2, int
 // nbl2 = -beta log2(e).  rsqrt / rcp / ex2 are the hardware approximations.
 __device__ __forceinline__ float es_fast(float i_f, float d, float c2w, float nbl2) {
     const float x = (i_f - d) * c2w;
-    const float x2 = x * x;
-    const float s = 1.0f - x2;
+    const float s = fmaf(-x, x, 1.0f);
     float rs, rd, e;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(s));
     const float den = fmaf(s, rs, 1.0f);
@@ -249,12 +264,29 @@ __device__ __forceinline__ float es_fast(float i_f, float d, float c2w, float nb
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// warp-wide integer sum, received by every lane
+__device__ __forceinline__ int warp_sum_i32(int v) {
+    int r;
+    asm volatile("redux.sync.add.s32 %0, %1, 0xffffffff;" : "=r"(r) : "r"(v));
+    return r;
+}
+
+// power-of-two quantum q = 2^(e - 30) for a bound B (B < 2^e); 2^-126 floor; NaN bound -> NaN
+__device__ __forceinline__ void fixed_quantum(float B, float &q, float &qinv) {
+    B *= 1.01f;
+    int ex = 0;
+    if (B > 0.0f && B <= 3.0e38f) frexpf(B, &ex);
+    ex = max(ex, -96);
+    qinv = ldexpf(1.0f, 30 - ex);
+    q = (B == B) ? ldexpf(1.0f, ex - 30) : B;
+}
+
 template <int W, int NB>
 __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int bid, unsigned char *smraw) {
     static_assert(W * W <= 64 && W >= 4 && W <= 8, "two columns per lane, at most 8 z taps");
     using G = WarpGeo<W, NB>;
-    constexpr int V = G::V;
-    constexpr int SH = 5 - Log2<V>::value;
+    constexpr int SS = G::SS;
+    constexpr int KR = G::KR;
     const int w = P.w;
     const int nwarps = blockDim.x >> 5;
     const WarpLayout L = warp_layout<W, NB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps);
@@ -262,57 +294,97 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
     int2 *sG = (int2 *)(smraw + L.offG);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *stage = (float *)(smraw + L.offStage) + warp * G::STAGE;
-    float *cb = stage + NB * G::SS;
     const int rows = L.Wt0 * L.Wt1;
     int64_t *rowoff = (int64_t *)(smraw + L.offRows), *rowmir = rowoff + rows;
+    int *rowF = (int *)(smraw + L.offRowF), *rowG = (int *)(smraw + L.offRowG);
     const Chunk ch = P.rchunks[bid];
-    __shared__ int s_next, s_max;
-    if (threadIdx.x == 0) {
-        s_next = ch.j0 + nwarps;
-        s_max = 0;
-    }
+    __shared__ int s_max;
+    if (threadIdx.x == 0) s_max = 0;
     window_row_table(P, ch, L.Wt0, L.Wt1, rowoff, rowmir);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int a = r / L.Wt1, b = r - a * L.Wt1;
+        rowF[r] = a * L.SP + b * L.RP;
+        rowG[r] = a * L.SG + b * L.RG;
+    }
+    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = make_int2(0, 0);
     const WinCol wc = window_col(P, ch, L.Wt2, rows);
     __syncthreads();
     float mx = 0.0f;
-    if (!P.ones_mode) mx = window_fill(P, wc, rowoff, rowmir, rows, L.RP, sF, L.Wt1, L.SP);
-    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = make_int2(0, 0);
+    if (!P.ones_mode) {
+        // four loads in flight per thread before their stores
+        const int N2 = P.nf[2];
+        const int64_t *rt = wc.herm ? rowmir : rowoff;
+        const int col = wc.herm ? N2 - wc.l2 : wc.l2;
+        for (int r = wc.r0; r < rows; r += 4 * wc.rstep) {
+            cpx<float> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ru = r + u * wc.rstep;
+                v[u] = ru < rows ? P.F[rt[ru] + col] : mk<float>(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ru = r + u * wc.rstep;
+                if (ru < rows) {
+                    const cpx<float> x = wc.herm ? conj(v[u]) : v[u];
+                    sF[rowF[ru] + wc.c] = x;
+                    mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0) atomicMax(&s_max, __float_as_int(mx));   // non-negative floats order as integers
     __syncthreads();
-    // fixed-point quantum of this chunk (a power of two, so that int * q is exact)
-    float B = P.ones_mode ? ch.wsum : 1.41421356f * __int_as_float(s_max) * P.psi_sum3 * ch.wsum;
-    B *= 1.01f;
-    int ex = 0;
-    if (B > 0.0f && B <= 3.0e38f) frexpf(B, &ex);   // B < 2^ex
-    ex = max(ex, -96);
-    const float qinv = ldexpf(1.0f, 30 - ex);
-    const float qf = (B == B) ? ldexpf(1.0f, ex - 30) : B;   // a NaN input stays NaN in the window
+    const float B1 = 1.41421356f * __int_as_float(s_max) * P.psi_sum3;
+    float q1, q1inv, q2, q2inv;
+    fixed_quantum(B1, q1, q1inv);
+    fixed_quantum(P.ones_mode ? ch.wsum : B1 * ch.wsum, q2, q2inv);
 
     const int ca = lane, cbc = lane + 32;
     const bool act_a = (W * W >= 32) || ca < W * W;
     const bool act_b = (W * W == 64) || cbc < W * W;
     const int xa = act_a ? ca % W : 0, ya = act_a ? ca / W : 0;
     const int xb = act_b ? cbc % W : 0, yb = act_b ? cbc / W : 0;
-    // kernel-value lanes: lane = axis * 8 + tap for lanes < 24
-    const int kv_ax = lane >> 3, kv_i = lane & 7;
-    const bool kv_on = lane < 24 && kv_i < W;
-    const float kv_if = (float)kv_i;
+    // kernel values: round u of lane L evaluates value q = L + 32 u of the batch (node q / 24,
+    // axis (q mod 24) / 8, tap q mod 8); rounds past the batch's values repeat the last one
+    int kv_fo[KR], kv_st[KR];
+    float kv_t[KR];
+#ifdef NLP_WARP_TABLE
+    int kv_tab[KR];
+#endif
+#pragma unroll
+    for (int u = 0; u < KR; ++u) {
+        const int q = min(lane + 32 * u, G::KV - 1);
+        const int k = q / 24, v = q - 24 * (q / 24);
+        kv_fo[u] = 4 * k + (v >> 3);
+        kv_st[u] = k * SS + 2 * v;
+        kv_t[u] = (float)(v & 7);
+#ifdef NLP_WARP_TABLE
+        kv_tab[u] = q;
+#endif
+    }
     const float c2w = 2.0f / (float)w, nbl2 = -(float)P.beta * 1.44269504f;
-    const int kv_st = kv_ax == 2 ? 16 + 2 * kv_i : kv_ax * 8 + kv_i;
     // G flush order: lanes of the upper half of each y quartet add the imaginary word first,
     // so that the 32 lanes of one atomic instruction hit 32 banks (W = 8 geometry)
     const int sw = (ya >> 1) & 1;
-    // node records of a batch: per kernel-value lane, the node's offset from its sub-window
-    // origin along the lane's axis (for plans of this kernel the node records hold that
-    // offset, see plan.cu) for each node; per lane k < NB the node weight
-    float pd[NB], wf;
+    // node records of a batch: per round, the node's offset from its sub-window origin along
+    // the value's axis (for plans of this kernel the node records hold that offset, see
+    // plan.cu); per lane k < NB the node weight times q1, zero past the piece's last node
+    float pd[KR], wf;
     auto fetch = [&](int jbn, int nbn) {
+        // (the node records are padded past the last node, so a batch never reads outside them)
+        const float *base = P.nd + 4 * (int64_t)jbn;
+#ifdef NLP_WARP_TABLE
+        const float *tb = P.psi_tab + 24 * (int64_t)jbn;
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            pd[k] = (kv_on && k < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + k) + kv_ax) : 0.0f;
-        wf = (lane < nbn) ? __ldg(P.nd + 4 * ((int64_t)jbn + lane) + 3) : 0.0f;
+        for (int u = 0; u < KR; ++u) pd[u] = __ldg(tb + kv_tab[u]);
+#else
+#pragma unroll
+        for (int u = 0; u < KR; ++u) pd[u] = __ldg(base + kv_fo[u]);
+#endif
+        wf = (lane < nbn) ? __ldg(base + 4 * lane + 3) * q1 : 0.0f;
     };
     int sg = ch.j0 + warp;
     uint32_t so = 0;
@@ -324,9 +396,8 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
         fetch(j0, min(NB, j1 - j0));
     }
     while (sg < ch.j1) {
-        int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(&s_next, 1);
-        const int sg_n = __shfl_sync(0xffffffffu, nxt, 0);
+        // pieces are sorted heaviest first: warps take them round-robin
+        const int sg_n = sg + nwarps;
         uint32_t so_n = 0;
         int j0_n = 0, j1_n = 0;
         if (sg_n < ch.j1) {
@@ -337,8 +408,6 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
         const int fa0 = (so0 + xa) * L.SP + (so1 + ya) * L.RP + so2;
         const int fb0 = (so0 + xb) * L.SP + (so1 + yb) * L.RP + so2;
-        const int ga0 = (so0 + xa) * L.SG + (so1 + ya) * L.RG + so2;
-        const int gb0 = (so0 + xb) * L.SG + (so1 + yb) * L.RG + so2;
         float2 fa[W], fb[W], ga[W], gb[W];
         // F columns of the piece (16-byte loads: column starts are even cells of an even pitch)
 #pragma unroll
@@ -362,83 +431,16 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
 #pragma unroll
         for (int z = 0; z < W; ++z) ga[z] = gb[z] = f2(0.f, 0.f);
 
-        auto batch = [&](auto full_tag, int nb, float wcur) {
-            constexpr bool FULL = decltype(full_tag)::value;
-            float v[V], wa[NB], wb[NB];
-            // interpolation partials
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                v[2 * k] = v[2 * k + 1] = 0.f;
-                wa[k] = wb[k] = 0.f;
-                if (FULL || k < nb) {
-                    const float *pk = stage + k * G::SS;
-                    const float px = pk[xa];
-                    wa[k] = act_a ? px * pk[8 + ya] : 0.f;
-                    wb[k] = act_b ? (W == 8 ? px : pk[xb]) * pk[8 + yb] : 0.f;
-                    if (!P.ones_mode) {
-                        float2 sa = f2(0.f, 0.f), sb = f2(0.f, 0.f);
-#pragma unroll
-                        for (int z = 0; z + 1 < W; z += 2) {
-                            const float4 pz = *reinterpret_cast<const float4 *>(pk + 16 + 2 * z);
-                            sa = __ffma2_rn(fa[z], f2(pz.x, pz.y), sa);
-                            sb = __ffma2_rn(fb[z], f2(pz.x, pz.y), sb);
-                            sa = __ffma2_rn(fa[z + 1], f2(pz.z, pz.w), sa);
-                            sb = __ffma2_rn(fb[z + 1], f2(pz.z, pz.w), sb);
-                        }
-                        if constexpr (W % 2) {
-                            const float2 pz = *reinterpret_cast<const float2 *>(pk + 16 + 2 * (W - 1));
-                            sa = __ffma2_rn(fa[W - 1], pz, sa);
-                            sb = __ffma2_rn(fb[W - 1], pz, sb);
-                        }
-                        v[2 * k] = wa[k] * sa.x + wb[k] * sb.x;
-                        v[2 * k + 1] = wa[k] * sa.y + wb[k] * sb.y;
-                    }
-                }
-            }
-            if (!P.ones_mode) warp_reduce_multi<float, V>(v, lane);
-            {
-                const int idx = (lane >> SH) & (V - 1);
-                const int k = idx >> 1;
-                const float wk = __shfl_sync(0xffffffffu, wcur, k);   // weight of node k of the batch
-                if ((lane & ((1 << SH) - 1)) == 0) {
-                    float c = P.ones_mode ? ((idx & 1) ? 0.f : wk) : v[0] * wk;
-                    cb[idx] = (FULL || k < nb) ? c : 0.f;
-                }
-            }
-            __syncwarp();
-            // spreading into the register columns
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (FULL || k < nb) {
-                    const float *pk = stage + k * G::SS;
-                    const float2 c = *reinterpret_cast<const float2 *>(cb + 2 * k);
-                    const float2 ca2 = f2(c.x * wa[k], c.y * wa[k]), cb2 = f2(c.x * wb[k], c.y * wb[k]);
-#pragma unroll
-                    for (int z = 0; z + 1 < W; z += 2) {
-                        const float4 pz = *reinterpret_cast<const float4 *>(pk + 16 + 2 * z);
-                        ga[z] = __ffma2_rn(ca2, f2(pz.x, pz.y), ga[z]);
-                        gb[z] = __ffma2_rn(cb2, f2(pz.x, pz.y), gb[z]);
-                        ga[z + 1] = __ffma2_rn(ca2, f2(pz.z, pz.w), ga[z + 1]);
-                        gb[z + 1] = __ffma2_rn(cb2, f2(pz.z, pz.w), gb[z + 1]);
-                    }
-                    if constexpr (W % 2) {
-                        const float2 pz = *reinterpret_cast<const float2 *>(pk + 16 + 2 * (W - 1));
-                        ga[W - 1] = __ffma2_rn(ca2, pz, ga[W - 1]);
-                        gb[W - 1] = __ffma2_rn(cb2, pz, gb[W - 1]);
-                    }
-                }
-            }
-        };
         for (int jb = j0; jb < j1; jb += NB) {
-            const int nb = min(NB, j1 - jb);
             // kernel values of the batch from the fetched node offsets
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (kv_on) {
-                    const float e = (k < nb) ? es_fast(kv_if, pd[k], c2w, nbl2) : 0.f;
-                    if (kv_ax == 2) *reinterpret_cast<float2 *>(stage + k * G::SS + kv_st) = f2(e, e);
-                    else stage[k * G::SS + kv_st] = e;
-                }
+            for (int u = 0; u < KR; ++u) {
+#ifdef NLP_WARP_TABLE
+                const float e = pd[u];
+#else
+                const float e = es_fast(kv_t[u], pd[u], c2w, nbl2);
+#endif
+                *reinterpret_cast<float2 *>(stage + kv_st[u]) = f2(e, e);
             }
             const float wcur = wf;
             __syncwarp();
@@ -446,26 +448,88 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
                 fetch(jb + NB, min(NB, j1 - jb - NB));
             else if (sg_n < ch.j1)
                 fetch(j0_n, min(NB, j1_n - j0_n));
-            if (nb == NB)
-                batch(BoolC<true>{}, nb, wcur);
-            else
-                batch(BoolC<false>{}, nb, wcur);
+            // interpolation: lane partials in fixed point, summed over the warp.  The z sums of
+            // the batch's nodes run interleaved (z pairs outer, nodes inner): 2 NB independent
+            // packed-FMA chains instead of two per node
+            float2 wa2[NB], wb2[NB], cv[NB];
+            float2 sa[NB], sb[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float *pk = stage + k * SS;
+                const float2 px = *reinterpret_cast<const float2 *>(pk + 2 * xa);
+                wa2[k] = __fmul2_rn(px, *reinterpret_cast<const float2 *>(pk + 16 + 2 * ya));
+                wb2[k] = __fmul2_rn(W == 8 ? px : *reinterpret_cast<const float2 *>(pk + 2 * xb),
+                                    *reinterpret_cast<const float2 *>(pk + 16 + 2 * yb));
+                if (!act_a) wa2[k] = f2(0.f, 0.f);
+                if (!act_b) wb2[k] = f2(0.f, 0.f);
+                sa[k] = sb[k] = f2(0.f, 0.f);
+            }
+            if (!P.ones_mode) {
+#pragma unroll
+                for (int z = 0; z + 1 < W; z += 2) {
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        const float4 pz = *reinterpret_cast<const float4 *>(stage + k * SS + 32 + 2 * z);
+                        sa[k] = __ffma2_rn(fa[z], f2(pz.x, pz.y), sa[k]);
+                        sb[k] = __ffma2_rn(fb[z], f2(pz.x, pz.y), sb[k]);
+                        sa[k] = __ffma2_rn(fa[z + 1], f2(pz.z, pz.w), sa[k]);
+                        sb[k] = __ffma2_rn(fb[z + 1], f2(pz.z, pz.w), sb[k]);
+                    }
+                }
+                if constexpr (W % 2) {
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        const float2 pz = *reinterpret_cast<const float2 *>(stage + k * SS + 32 + 2 * (W - 1));
+                        sa[k] = __ffma2_rn(fa[W - 1], pz, sa[k]);
+                        sb[k] = __ffma2_rn(fb[W - 1], pz, sb[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float2 vk = __ffma2_rn(sb[k], wb2[k], __fmul2_rn(sa[k], wa2[k]));
+                const int sr = warp_sum_i32(__float2int_rn(vk.x * q1inv));
+                const int si = warp_sum_i32(__float2int_rn(vk.y * q1inv));
+                // c_k = rho-hat_k omega_k (wf of lane k holds omega_k q1); ones mode: c_k = omega_k
+                const float wk = __shfl_sync(0xffffffffu, wcur, k);
+                cv[k] = P.ones_mode ? f2(wk * q1inv, 0.f) : f2((float)sr * wk, (float)si * wk);
+            }
+            // spreading into the register columns
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float *pk = stage + k * SS;
+                const float2 ca2 = __fmul2_rn(cv[k], wa2[k]), cb2 = __fmul2_rn(cv[k], wb2[k]);
+#pragma unroll
+                for (int z = 0; z + 1 < W; z += 2) {
+                    const float4 pz = *reinterpret_cast<const float4 *>(pk + 32 + 2 * z);
+                    ga[z] = __ffma2_rn(ca2, f2(pz.x, pz.y), ga[z]);
+                    gb[z] = __ffma2_rn(cb2, f2(pz.x, pz.y), gb[z]);
+                    ga[z + 1] = __ffma2_rn(ca2, f2(pz.z, pz.w), ga[z + 1]);
+                    gb[z + 1] = __ffma2_rn(cb2, f2(pz.z, pz.w), gb[z + 1]);
+                }
+                if constexpr (W % 2) {
+                    const float2 pz = *reinterpret_cast<const float2 *>(pk + 32 + 2 * (W - 1));
+                    ga[W - 1] = __ffma2_rn(ca2, pz, ga[W - 1]);
+                    gb[W - 1] = __ffma2_rn(cb2, pz, gb[W - 1]);
+                }
+            }
             __syncwarp();
         }
         // add the piece's columns to the window in fixed point
+        const int ga0 = (so0 + xa) * L.SG + (so1 + ya) * L.RG + so2;
+        const int gb0 = (so0 + xb) * L.SG + (so1 + yb) * L.RG + so2;
+        int *pa = &sG[ga0].x + sw, *pb = &sG[gb0].x + sw;
 #pragma unroll
         for (int z = 0; z < W; ++z) {
             if (act_a) {
-                int *c = &sG[ga0 + z].x;
-                const int re = __float2int_rn(ga[z].x * qinv), im = __float2int_rn(ga[z].y * qinv);
-                atomicAdd(c + sw, sw ? im : re);
-                atomicAdd(c + (sw ^ 1), sw ? re : im);
+                const int re = __float2int_rn(ga[z].x * q2inv), im = __float2int_rn(ga[z].y * q2inv);
+                atomicAdd(pa + 2 * z, sw ? im : re);
+                atomicAdd(pa + 2 * z + 1 - 2 * sw, sw ? re : im);
             }
             if (act_b) {
-                int *c = &sG[gb0 + z].x;
-                const int re = __float2int_rn(gb[z].x * qinv), im = __float2int_rn(gb[z].y * qinv);
-                atomicAdd(c + sw, sw ? im : re);
-                atomicAdd(c + (sw ^ 1), sw ? re : im);
+                const int re = __float2int_rn(gb[z].x * q2inv), im = __float2int_rn(gb[z].y * q2inv);
+                atomicAdd(pb + 2 * z, sw ? im : re);
+                atomicAdd(pb + 2 * z + 1 - 2 * sw, sw ? re : im);
             }
         }
         sg = sg_n;
@@ -474,14 +538,11 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
         j1 = j1_n;
     }
     __syncthreads();
-    // the chunk's window, dense, to its scratch slot
-    cpx<float> *out = P.win + (int64_t)bid * P.win_cells;
-    const int WW = L.Wt0 * L.Wt1 * L.Wt2;
-    for (int q = threadIdx.x; q < WW; q += blockDim.x) {
-        const int c = q % L.Wt2, r = q / L.Wt2;
-        const int b = r % L.Wt1, a = r / L.Wt1;
-        const int2 g = sG[a * L.SG + b * L.RG + c];
-        out[q] = mk<float>((float)g.x * qf, (float)g.y * qf);
+    // the chunk's window, dense, to its scratch slot (thread: column wc.c of rows r0 + k rstep)
+    cpx<float> *out = P.win + (int64_t)bid * P.win_cells + wc.c;
+    for (int r = wc.r0; r < rows; r += wc.rstep) {
+        const int2 g = sG[rowG[r] + wc.c];
+        out[r * L.Wt2] = mk<float>((float)g.x * q2, (float)g.y * q2);
     }
 }
 

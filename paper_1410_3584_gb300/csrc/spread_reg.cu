@@ -24,7 +24,7 @@
 namespace nlp {
 
 constexpr int kWarpBlock = 128;   // threads per CTA of the one-warp-per-piece kernel
-constexpr int kWarpNB = 4;        // nodes per batch of the warp kernel
+
 
 template <int W> struct RegCfg {
     static constexpr int TT = ((W * W + 31) / 32) * 32;       // threads per team
@@ -197,8 +197,11 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
     }
 }
 
+#ifndef NLP_WARP_MINB
+#define NLP_WARP_MINB 4
+#endif
 template <int W>
-__global__ void __launch_bounds__(kWarpBlock, 4) k_interp_spread_warp(DevPlan<float> P) {
+__global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_interp_spread_warp(DevPlan<float> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     spread_warp_block<W, kWarpNB>(P, blockIdx.x, smraw);
 }
@@ -207,8 +210,9 @@ template <typename T> __global__ void __launch_bounds__(256) k_window_sum(DevPla
     window_sum_block<T>(P, blockIdx.x);
 }
 
-template <typename T> __global__ void __launch_bounds__(256) k_combine(DevPlan<T> P) {
-    combine_block<T>(P, blockIdx.x);
+template <typename T> __global__ void __launch_bounds__(128) k_combine(DevPlan<T> P) {
+    __shared__ CombStage st[kCombStage];
+    combine_block<T>(P, P.cmb_act[blockIdx.x], st);
 }
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
@@ -310,8 +314,8 @@ template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStr
 }
 
 template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st) {
-    if (P.cmb_tiles == 0) return cudaSuccess;
-    k_combine<T><<<(unsigned)P.cmb_tiles, 256, 0, st>>>(P);
+    if (P.cmb_nact == 0) return cudaSuccess;
+    k_combine<T><<<(unsigned)P.cmb_nact, 128, 0, st>>>(P);
     return cudaGetLastError();
 }
 
