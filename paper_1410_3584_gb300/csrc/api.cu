@@ -69,6 +69,10 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     } else {
         // interpolate, scale, spread (each chunk's window to its scratch slot), then combine
         // the windows into G (every cell of G written once, in a fixed order)
+        if (D.cnode) {
+            NLP_CUDA_TRY(launch_interp_warp<T>(D, st));
+            mark(p, NLP_STAGE_INTERP);
+        }
         if (D.sub_T > 0) NLP_CUDA_TRY(launch_interp_spread_reg<T>(D, st));
         else NLP_CUDA_TRY(launch_interp_spread<T>(D, st));
         mark(p, NLP_STAGE_SPREAD);

@@ -23,7 +23,7 @@
 
 namespace nlp {
 
-enum { ST_R2C = 0, ST_A1, ST_A0, ST_SPREAD, ST_WSUM, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
+enum { ST_R2C = 0, ST_A1, ST_A0, ST_INTERP, ST_SPREAD, ST_WSUM, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
 constexpr int kRegLines = 16;          // lines (pairs) per register-engine FFT task: 16 x 16 threads
 constexpr int kCombTiles = 16;         // combine tiles of G per task
 
@@ -108,6 +108,9 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
             case ST_A0:
                 if (B.reg_fft) fft_cols_block<float, -1, kRegLines>(B.P.F, B.a0, B.P.len[0], i, smraw);
                 else fft_strided_block<float, -1>(B.P.F, B.a0, B.P.len[0], B.nb_a0, i, smraw);
+                break;
+            case ST_INTERP:
+                interp_warp_block<8, kWarpNB>(B.P, i, smraw);
                 break;
             case ST_SPREAD:
                 if (B.spread_warp) spread_warp_block<8, kWarpNB>(B.P, i, smraw);
@@ -282,6 +285,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         B.ntask[ST_A1] = B.a1.nouter * (int)((nh + B.nb_a1 - 1) / B.nb_a1);
         B.ntask[ST_A0] = three ? B.a0.nouter * (int)((nh + B.nb_a0 - 1) / B.nb_a0) : 0;
         B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
+        B.ntask[ST_INTERP] = (int)(B.spread_warp ? D.nrchunks : 0);
         B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);
         B.ntask[ST_WSUM] = (int)(D.ngroups * D.grp_parts);
         B.ntask[ST_COMBINE] = (int)((D.cmb_nact + kCombTiles - 1) / kCombTiles);

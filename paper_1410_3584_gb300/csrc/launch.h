@@ -51,6 +51,9 @@ template <typename T> bool reg_kernel_supported(int W);
 template <typename T> bool warp_kernel_used(int W);   // FP32 one-warp-per-piece kernel
 template <typename T> size_t interp_spread_reg_smem(const DevPlan<T> &P, int nwarps_warp_kernel);
 template <typename T> cudaError_t launch_interp_spread_reg(const DevPlan<T> &P, cudaStream_t st);
+// FP32 plans of the one-warp-per-piece kernels (P.cnode set): interpolation half, before
+// launch_interp_spread_reg (which then runs the spreading half)
+template <typename T> cudaError_t launch_interp_warp(const DevPlan<T> &P, cudaStream_t st);
 template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStream_t st);   // tiles of several chunks
 template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st);
 

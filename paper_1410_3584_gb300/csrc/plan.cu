@@ -654,6 +654,17 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         cmax *= 1.001;
         D.psi_sum3 = (float)(cmax * cmax * cmax);
     }
+    // FP32 warp kernels: per-node c_j (padded like the node records) and per-chunk bounds
+    D.cnode = nullptr;
+    D.csum = nullptr;
+    if (warp_k && D.nrchunks > 0) {
+        void *dc = nullptr, *ds = nullptr;
+        if ((s = alloc_dev(p, &dc, sizeof(cpx<T>) * (size_t)(M + 16)))) return s;
+        if ((s = alloc_dev(p, &ds, sizeof(T) * (size_t)D.nrchunks))) return s;
+        cudaMemset(dc, 0, sizeof(cpx<T>) * (size_t)(M + 16));
+        D.cnode = (cpx<T> *)dc;
+        D.csum = (T *)ds;
+    }
     // window scratch (one slot per chunk of the kernel that runs) and the combine entries
     {
         const std::vector<Chunk> &act = Ts > 0 ? rchunks : chunks;

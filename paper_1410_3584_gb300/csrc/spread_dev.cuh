@@ -181,35 +181,39 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
     }
 }
 
-// ======================================================================= FP32 warp kernel
-// One warp per piece (a run of at most 64 nodes of one 2^3 sub-tile, whose nodes all reach
-// the same sub-window of W^3 cells, W = w + 1): lane L owns the sub-window z-columns
-// a = (L mod W, L div W) and b = a + 32 (in column order).  Per piece the lane holds both F
-// columns and both G accumulator columns in registers; per batch of NB nodes it
+// ======================================================================= FP32 warp kernels
+// Interpolation and spreading run as two kernels over the same chunks and pieces (a piece: a
+// run of at most 64 nodes of one 2^3 sub-tile, whose nodes all reach the same sub-window of
+// W^3 cells, W = w + 1), one warp per piece; lane L owns the sub-window z-columns
+// a = (L mod W, L div W) and b = a + 32 (in column order).  Holding only F (interpolation) or
+// only G (spreading) in registers keeps each kernel's register and shared-memory footprint
+// at half of a fused one, for more resident warps.  Per batch of NB nodes a warp
 //   1. evaluates the 3 W kernel values of each node from its position (the 3 W NB values
 //      spread evenly over the lanes) into a per-warp stage, each value stored twice so that
 //      (v, v) pairs load as packed operands,
-//   2. interpolates: per column a complex z-contraction with packed FP32x2 FMAs, weighted by
-//      the column's x/y kernel values; the 32 lane partials of each node are summed by one
-//      integer warp reduction each (fixed point, see below), which every lane receives,
-//   3. scales by the node weight and spreads: per column a complex x z outer product with
-//      packed FMAs into the G registers.
-// A piece's last batch is padded with copies of its last node carrying weight zero, so every
+//   2. (interpolation) per column a complex z-contraction with packed FP32x2 FMAs, the
+//      batch's nodes interleaved, weighted by the column's x/y kernel values; the 32 lane
+//      partials of a node are summed by one integer warp reduction per component (fixed
+//      point, below); c_j = rho-hat_j omega_j goes to the node array and |c_j| into the chunk's
+//      bound,
+//   2'. (spreading) per column a complex x z outer product of c_j with packed FMAs into the G
+//      registers; at the end of a piece the columns are added to the chunk's shared window
+//      in fixed point, and the window goes to the chunk's scratch slot.
+// A piece's last batch is padded with the records that follow it, given weight zero, so every
 // batch runs the same code.
 //
 // Fixed point.  Integer addition is associative, so sums taken in integers do not depend on
-// the order of the lanes or warps.  Two quanta per chunk, powers of two (int * q is exact),
-// from bounds known before any node is processed: with M the largest |re| or |im| of F on the
-// chunk's window and C = max over node offsets of sum_t psi, every interpolated value obeys
-// |rho-hat_j| <= sqrt(2) M C^3 =: B1, and so does the sum over lanes of the absolute lane
-// partials; and every cell of the window obeys |G| <= sum_j |c_j| <= B1 S (the kernel is at most
-// 1, S = sum_j |omega_j| of the chunk, plan time).  With q1 = 2^(ceil log2 1.01 B1 - 30) for
-// the interpolation sums and q2 = 2^(ceil log2 1.01 B1 S - 30) for the window, all partial sums
-// stay below 2^31 in magnitude.
+// the order of lanes or warps.  Quanta are powers of two (int * q is exact) chosen from bounds
+// known before the sums: interpolation, with M the largest |re| or |im| of F on the chunk's
+// window and C = max over node offsets of sum_t psi, every lane partial sum obeys
+// sum_lanes |partial| <= sqrt(2) M C^3 =: B1, q1 = 2^(ceil log2 1.01 B1 - 30); spreading, every
+// cell obeys |re G|, |im G| <= sum_j (|re c_j| + |im c_j|) =: B2 (the kernel is at most 1),
+// summed by the interpolation kernel in a fixed order, q2 = 2^(ceil log2 1.01 B2 - 30).  All
+// partial sums stay below 2^31 in magnitude.
 #ifndef NLP_WARP_NB
 #define NLP_WARP_NB 4
 #endif
-constexpr int kWarpNB = NLP_WARP_NB;   // nodes per batch of the FP32 warp kernel
+constexpr int kWarpNB = NLP_WARP_NB;   // nodes per batch of the FP32 warp kernels
 
 template <int W, int NB> struct WarpGeo {
     static constexpr int SS = 48;               // floats per node: x, y, z kernel values, each as (v, v)
@@ -218,16 +222,19 @@ template <int W, int NB> struct WarpGeo {
     static constexpr int KR = (KV + 31) / 32;   // evaluation rounds per lane
 };
 
+// Shared memory of the two kernels.  F window cell (a, b, c) at a SP + b RP + c (RP even,
+// SP / 2 odd: 16-byte column loads of the 8 lanes of a quarter warp fall in distinct bank
+// groups); G window cell (a, b, c) at a SG + b RG + c (RG odd).
 struct WarpLayout {
     int Wt0, Wt1, Wt2;
-    int RP, SP;       // F window: cell (a, b, c) at a SP + b RP + c (RP even, SP / 2 odd: 16-byte column
-                      // loads of the 8 lanes of a quarter warp fall in distinct bank groups)
-    int RG, SG;       // G window: cell (a, b, c) at a SG + b RG + c (RG odd)
-    size_t offG, offStage, offRows, offRowF, offRowG, bytes;
+    int RP, SP, RG, SG;
+    size_t offStage, offRec, offRows, offRowW, bytes;
 };
+// per warp: node records (and, spreading, c_j) of two pieces, staged one piece ahead
+constexpr int kRecNodes = 64 + 8;   // a piece (<= 64 nodes) and the padding its last batch reads
 
 template <int W, int NB>
-__host__ __device__ inline WarpLayout warp_layout(int Wt0, int Wt1, int Wt2, int nwarps) {
+__host__ __device__ inline WarpLayout warp_layout(int Wt0, int Wt1, int Wt2, int nwarps, bool spreading) {
     WarpLayout L;
     L.Wt0 = Wt0;
     L.Wt1 = Wt1;
@@ -238,12 +245,13 @@ __host__ __device__ inline WarpLayout warp_layout(int Wt0, int Wt1, int Wt2, int
     L.RG = Wt2 | 1;
     L.SG = Wt1 * L.RG;
     const size_t rows = (size_t)Wt0 * Wt1;
-    L.offG = align16((size_t)Wt0 * L.SP * sizeof(float2));
-    L.offStage = align16(L.offG + (size_t)Wt0 * L.SG * sizeof(int2));
-    L.offRows = align16(L.offStage + (size_t)nwarps * WarpGeo<W, NB>::STAGE * sizeof(float));
-    L.offRowF = L.offRows + 2 * rows * sizeof(int64_t);
-    L.offRowG = L.offRowF + rows * sizeof(int);
-    L.bytes = L.offRowG + rows * sizeof(int);
+    const size_t win = spreading ? (size_t)Wt0 * L.SG * sizeof(int2) : (size_t)Wt0 * L.SP * sizeof(float2);
+    L.offStage = align16(win);
+    L.offRec = align16(L.offStage + (size_t)nwarps * WarpGeo<W, NB>::STAGE * sizeof(float));
+    const size_t rec = (size_t)kRecNodes * (spreading ? sizeof(float4) + sizeof(float2) : sizeof(float4));
+    L.offRows = align16(L.offRec + (size_t)nwarps * 2 * rec);
+    L.offRowW = L.offRows + (spreading ? 0 : 2 * rows * sizeof(int64_t));
+    L.bytes = L.offRowW + rows * sizeof(int) + 32 * sizeof(float);
     return L;
 }
 
@@ -271,7 +279,7 @@ __device__ __forceinline__ int warp_sum_i32(int v) {
     return r;
 }
 
-// power-of-two quantum q = 2^(e - 30) for a bound B (B < 2^e); 2^-126 floor; NaN bound -> NaN
+// power-of-two quantum q = 2^(e - 30) for a bound B (1.01 B < 2^e); 2^-126 floor; NaN bound -> NaN
 __device__ __forceinline__ void fixed_quantum(float B, float &q, float &qinv) {
     B *= 1.01f;
     int ex = 0;
@@ -281,36 +289,114 @@ __device__ __forceinline__ void fixed_quantum(float B, float &q, float &qinv) {
     q = (B == B) ? ldexpf(1.0f, ex - 30) : B;
 }
 
+__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes16or8) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes16or8 == 16) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stage the records (and c_j) of the nodes [j0, j0 + n + NB) of a piece into a warp's buffer.
+template <int NB>
+__device__ __forceinline__ void stage_piece(const DevPlan<float> &P, int j0, int n, float4 *rec, float2 *cbuf,
+                                            int lane) {
+    const int m = min(n + NB, kRecNodes);
+    for (int i = lane; i < m; i += 32) {
+        cp_async(rec + i, P.nd + 4 * ((int64_t)j0 + i), 16);
+        if (cbuf) cp_async(cbuf + i, P.cnode + j0 + i, 8);
+    }
+    cp_async_commit();
+}
+
+// Per-lane set-up shared by both warp kernels: column ownership and the kernel-value rounds.
+template <int W, int NB> struct WarpLane {
+    static constexpr int KR = WarpGeo<W, NB>::KR;
+    bool act_a, act_b;
+    int xa, ya, xb, yb;
+    int kv_fo[KR], kv_st[KR];   // per round: record offset (4 node + axis) and stage offset
+    float kv_t[KR];             // per round: tap index
+    float c2w, nbl2;
+    __device__ __forceinline__ WarpLane(int lane, int w, float beta) {
+        const int ca = lane, cbc = lane + 32;
+        act_a = (W * W >= 32) || ca < W * W;
+        act_b = (W * W == 64) || cbc < W * W;
+        xa = act_a ? ca % W : 0;
+        ya = act_a ? ca / W : 0;
+        xb = act_b ? cbc % W : 0;
+        yb = act_b ? cbc / W : 0;
+        // round u evaluates value q = lane + 32 u of the batch (node q / 24, axis (q mod 24) / 8,
+        // tap q mod 8); rounds past the batch's values repeat the last one
+#pragma unroll
+        for (int u = 0; u < KR; ++u) {
+            const int q = min(lane + 32 * u, WarpGeo<W, NB>::KV - 1);
+            const int k = q / 24, v = q - 24 * (q / 24);
+            kv_fo[u] = 4 * k + (v >> 3);
+            kv_st[u] = k * WarpGeo<W, NB>::SS + 2 * v;
+            kv_t[u] = (float)(v & 7);
+        }
+        c2w = 2.0f / (float)w;
+        nbl2 = -beta * 1.44269504f;
+    }
+    // node offsets of the batch starting at staged record b (the records hold each node's
+    // offset from its sub-window origin)
+    __device__ __forceinline__ void fetch(const float *rec, int b, float (&pd)[KR]) const {
+        const float *base = rec + 4 * b;
+#pragma unroll
+        for (int u = 0; u < KR; ++u) pd[u] = base[kv_fo[u]];
+    }
+    __device__ __forceinline__ void evaluate(const float (&pd)[KR], float *stage) const {
+#pragma unroll
+        for (int u = 0; u < KR; ++u) {
+            const float e = es_fast(kv_t[u], pd[u], c2w, nbl2);
+            *reinterpret_cast<float2 *>(stage + kv_st[u]) = f2(e, e);
+        }
+    }
+    // x/y weights (w, w) of the lane's two columns for node k of the stage
+    __device__ __forceinline__ void weights(const float *pk, float2 &wa2, float2 &wb2) const {
+        const float2 px = *reinterpret_cast<const float2 *>(pk + 2 * xa);
+        wa2 = __fmul2_rn(px, *reinterpret_cast<const float2 *>(pk + 16 + 2 * ya));
+        wb2 = __fmul2_rn(W == 8 ? px : *reinterpret_cast<const float2 *>(pk + 2 * xb),
+                         *reinterpret_cast<const float2 *>(pk + 16 + 2 * yb));
+        if (!act_a) wa2 = f2(0.f, 0.f);
+        if (!act_b) wb2 = f2(0.f, 0.f);
+    }
+};
+
+// the chunk window's rows: offsets in the half spectrum (line and mirror) and in the window
+template <typename T>
+__device__ __forceinline__ void warp_window_rows(const DevPlan<T> &P, const Chunk &ch, const WarpLayout &L,
+                                                 bool spreading, int64_t *rowoff, int *rowW) {
+    const int rows = L.Wt0 * L.Wt1;
+    if (!spreading) window_row_table(P, ch, L.Wt0, L.Wt1, rowoff, rowoff + rows);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int a = r / L.Wt1, b = r - a * L.Wt1;
+        rowW[r] = spreading ? a * L.SG + b * L.RG : a * L.SP + b * L.RP;
+    }
+}
+
 template <int W, int NB>
-__device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int bid, unsigned char *smraw) {
+__device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int bid, unsigned char *smraw) {
     static_assert(W * W <= 64 && W >= 4 && W <= 8, "two columns per lane, at most 8 z taps");
     using G = WarpGeo<W, NB>;
-    constexpr int SS = G::SS;
-    constexpr int KR = G::KR;
-    const int w = P.w;
+    constexpr int SS = G::SS, KR = G::KR;
     const int nwarps = blockDim.x >> 5;
-    const WarpLayout L = warp_layout<W, NB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps);
+    const WarpLayout L = warp_layout<W, NB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps, false);
     cpx<float> *sF = (cpx<float> *)smraw;
-    int2 *sG = (int2 *)(smraw + L.offG);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *stage = (float *)(smraw + L.offStage) + warp * G::STAGE;
     const int rows = L.Wt0 * L.Wt1;
     int64_t *rowoff = (int64_t *)(smraw + L.offRows), *rowmir = rowoff + rows;
-    int *rowF = (int *)(smraw + L.offRowF), *rowG = (int *)(smraw + L.offRowG);
+    int *rowF = (int *)(smraw + L.offRowW);
+    float *wsum = (float *)(rowF + rows);
     const Chunk ch = P.rchunks[bid];
     __shared__ int s_max;
     if (threadIdx.x == 0) s_max = 0;
-    window_row_table(P, ch, L.Wt0, L.Wt1, rowoff, rowmir);
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        const int a = r / L.Wt1, b = r - a * L.Wt1;
-        rowF[r] = a * L.SP + b * L.RP;
-        rowG[r] = a * L.SG + b * L.RG;
-    }
-    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = make_int2(0, 0);
+    warp_window_rows(P, ch, L, false, rowoff, rowF);
     const WinCol wc = window_col(P, ch, L.Wt2, rows);
     __syncthreads();
     float mx = 0.0f;
-    if (!P.ones_mode) {
+    {
         // four loads in flight per thread before their stores
         const int N2 = P.nf[2];
         const int64_t *rt = wc.herm ? rowmir : rowoff;
@@ -337,66 +423,25 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0) atomicMax(&s_max, __float_as_int(mx));   // non-negative floats order as integers
     __syncthreads();
-    const float B1 = 1.41421356f * __int_as_float(s_max) * P.psi_sum3;
-    float q1, q1inv, q2, q2inv;
-    fixed_quantum(B1, q1, q1inv);
-    fixed_quantum(P.ones_mode ? ch.wsum : B1 * ch.wsum, q2, q2inv);
+    float q1, q1inv;
+    fixed_quantum(1.41421356f * __int_as_float(s_max) * P.psi_sum3, q1, q1inv);
 
-    const int ca = lane, cbc = lane + 32;
-    const bool act_a = (W * W >= 32) || ca < W * W;
-    const bool act_b = (W * W == 64) || cbc < W * W;
-    const int xa = act_a ? ca % W : 0, ya = act_a ? ca / W : 0;
-    const int xb = act_b ? cbc % W : 0, yb = act_b ? cbc / W : 0;
-    // kernel values: round u of lane L evaluates value q = L + 32 u of the batch (node q / 24,
-    // axis (q mod 24) / 8, tap q mod 8); rounds past the batch's values repeat the last one
-    int kv_fo[KR], kv_st[KR];
-    float kv_t[KR];
-#ifdef NLP_WARP_TABLE
-    int kv_tab[KR];
-#endif
-#pragma unroll
-    for (int u = 0; u < KR; ++u) {
-        const int q = min(lane + 32 * u, G::KV - 1);
-        const int k = q / 24, v = q - 24 * (q / 24);
-        kv_fo[u] = 4 * k + (v >> 3);
-        kv_st[u] = k * SS + 2 * v;
-        kv_t[u] = (float)(v & 7);
-#ifdef NLP_WARP_TABLE
-        kv_tab[u] = q;
-#endif
-    }
-    const float c2w = 2.0f / (float)w, nbl2 = -(float)P.beta * 1.44269504f;
-    // G flush order: lanes of the upper half of each y quartet add the imaginary word first,
-    // so that the 32 lanes of one atomic instruction hit 32 banks (W = 8 geometry)
-    const int sw = (ya >> 1) & 1;
-    // node records of a batch: per round, the node's offset from its sub-window origin along
-    // the value's axis (for plans of this kernel the node records hold that offset, see
-    // plan.cu); per lane k < NB the node weight times q1, zero past the piece's last node
-    float pd[KR], wf;
-    auto fetch = [&](int jbn, int nbn) {
-        // (the node records are padded past the last node, so a batch never reads outside them)
-        const float *base = P.nd + 4 * (int64_t)jbn;
-#ifdef NLP_WARP_TABLE
-        const float *tb = P.psi_tab + 24 * (int64_t)jbn;
-#pragma unroll
-        for (int u = 0; u < KR; ++u) pd[u] = __ldg(tb + kv_tab[u]);
-#else
-#pragma unroll
-        for (int u = 0; u < KR; ++u) pd[u] = __ldg(base + kv_fo[u]);
-#endif
-        wf = (lane < nbn) ? __ldg(base + 4 * lane + 3) * q1 : 0.0f;
-    };
-    int sg = ch.j0 + warp;
+    const WarpLane<W, NB> ln(lane, P.w, (float)P.beta);
+    float4 *recb = (float4 *)(smraw + L.offRec) + warp * 2 * kRecNodes;   // two piece buffers
+    float pd[KR];
+    float bsum = 0.0f;   // lanes 8k: sum of |re c| + |im c| of the warp's k-th batch nodes
+    int sg = ch.j0 + warp, buf = 0;
     uint32_t so = 0;
     int j0 = 0, j1 = 0;
     if (sg < ch.j1) {
         so = P.seg_sub[sg];
         j0 = P.seg_node[2 * sg];
         j1 = P.seg_node[2 * sg + 1];
-        fetch(j0, min(NB, j1 - j0));
+        stage_piece<NB>(P, j0, j1 - j0, recb, nullptr, lane);
     }
     while (sg < ch.j1) {
-        // pieces are sorted heaviest first: warps take them round-robin
+        // pieces are sorted heaviest first: warps take them round-robin; the next piece's
+        // records are staged while this one computes
         const int sg_n = sg + nwarps;
         uint32_t so_n = 0;
         int j0_n = 0, j1_n = 0;
@@ -404,101 +449,196 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
             so_n = P.seg_sub[sg_n];
             j0_n = P.seg_node[2 * sg_n];
             j1_n = P.seg_node[2 * sg_n + 1];
+            stage_piece<NB>(P, j0_n, j1_n - j0_n, recb + (buf ^ 1) * kRecNodes, nullptr, lane);
+        } else {
+            cp_async_commit();
         }
+        cp_async_wait<1>();
+        __syncwarp();
+        const float *rec = (const float *)(recb + buf * kRecNodes);
         const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
-        const int fa0 = (so0 + xa) * L.SP + (so1 + ya) * L.RP + so2;
-        const int fb0 = (so0 + xb) * L.SP + (so1 + yb) * L.RP + so2;
-        float2 fa[W], fb[W], ga[W], gb[W];
+        const int fa0 = (so0 + ln.xa) * L.SP + (so1 + ln.ya) * L.RP + so2;
+        const int fb0 = (so0 + ln.xb) * L.SP + (so1 + ln.yb) * L.RP + so2;
+        float2 fa[W], fb[W];
         // F columns of the piece (16-byte loads: column starts are even cells of an even pitch)
 #pragma unroll
         for (int z = 0; z + 1 < W; z += 2) {
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
-            if (!P.ones_mode) {
-                if (act_a) u = *reinterpret_cast<const float4 *>(sF + fa0 + z);
-                if (act_b) v = *reinterpret_cast<const float4 *>(sF + fb0 + z);
-            }
+            if (ln.act_a) u = *reinterpret_cast<const float4 *>(sF + fa0 + z);
+            if (ln.act_b) v = *reinterpret_cast<const float4 *>(sF + fb0 + z);
             fa[z] = f2(u.x, u.y);
             fa[z + 1] = f2(u.z, u.w);
             fb[z] = f2(v.x, v.y);
             fb[z + 1] = f2(v.z, v.w);
         }
         if constexpr (W % 2) {
-            const cpx<float> u = (!P.ones_mode && act_a) ? sF[fa0 + W - 1] : mk<float>(0.f, 0.f);
-            const cpx<float> v = (!P.ones_mode && act_b) ? sF[fb0 + W - 1] : mk<float>(0.f, 0.f);
+            const cpx<float> u = ln.act_a ? sF[fa0 + W - 1] : mk<float>(0.f, 0.f);
+            const cpx<float> v = ln.act_b ? sF[fb0 + W - 1] : mk<float>(0.f, 0.f);
             fa[W - 1] = f2(u.x, u.y);
             fb[W - 1] = f2(v.x, v.y);
         }
-#pragma unroll
-        for (int z = 0; z < W; ++z) ga[z] = gb[z] = f2(0.f, 0.f);
-
         for (int jb = j0; jb < j1; jb += NB) {
-            // kernel values of the batch from the fetched node offsets
-#pragma unroll
-            for (int u = 0; u < KR; ++u) {
-#ifdef NLP_WARP_TABLE
-                const float e = pd[u];
-#else
-                const float e = es_fast(kv_t[u], pd[u], c2w, nbl2);
-#endif
-                *reinterpret_cast<float2 *>(stage + kv_st[u]) = f2(e, e);
-            }
-            const float wcur = wf;
+            const int nb = min(NB, j1 - jb), b = jb - j0;
+            ln.fetch(rec, b, pd);
+            const float wcur = lane < nb ? rec[4 * (b + lane) + 3] * q1 : 0.0f;   // omega q1, zero past the piece
+            ln.evaluate(pd, stage);
             __syncwarp();
-            if (jb + NB < j1)
-                fetch(jb + NB, min(NB, j1 - jb - NB));
-            else if (sg_n < ch.j1)
-                fetch(j0_n, min(NB, j1_n - j0_n));
-            // interpolation: lane partials in fixed point, summed over the warp.  The z sums of
-            // the batch's nodes run interleaved (z pairs outer, nodes inner): 2 NB independent
-            // packed-FMA chains instead of two per node
-            float2 wa2[NB], wb2[NB], cv[NB];
-            float2 sa[NB], sb[NB];
+            // the z sums of the batch's nodes interleaved (z pairs outer, nodes inner)
+            float2 wa2[NB], wb2[NB], sa[NB], sb[NB];
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                const float *pk = stage + k * SS;
-                const float2 px = *reinterpret_cast<const float2 *>(pk + 2 * xa);
-                wa2[k] = __fmul2_rn(px, *reinterpret_cast<const float2 *>(pk + 16 + 2 * ya));
-                wb2[k] = __fmul2_rn(W == 8 ? px : *reinterpret_cast<const float2 *>(pk + 2 * xb),
-                                    *reinterpret_cast<const float2 *>(pk + 16 + 2 * yb));
-                if (!act_a) wa2[k] = f2(0.f, 0.f);
-                if (!act_b) wb2[k] = f2(0.f, 0.f);
+                ln.weights(stage + k * SS, wa2[k], wb2[k]);
                 sa[k] = sb[k] = f2(0.f, 0.f);
             }
-            if (!P.ones_mode) {
 #pragma unroll
-                for (int z = 0; z + 1 < W; z += 2) {
+            for (int z = 0; z + 1 < W; z += 2) {
 #pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        const float4 pz = *reinterpret_cast<const float4 *>(stage + k * SS + 32 + 2 * z);
-                        sa[k] = __ffma2_rn(fa[z], f2(pz.x, pz.y), sa[k]);
-                        sb[k] = __ffma2_rn(fb[z], f2(pz.x, pz.y), sb[k]);
-                        sa[k] = __ffma2_rn(fa[z + 1], f2(pz.z, pz.w), sa[k]);
-                        sb[k] = __ffma2_rn(fb[z + 1], f2(pz.z, pz.w), sb[k]);
-                    }
-                }
-                if constexpr (W % 2) {
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        const float2 pz = *reinterpret_cast<const float2 *>(stage + k * SS + 32 + 2 * (W - 1));
-                        sa[k] = __ffma2_rn(fa[W - 1], pz, sa[k]);
-                        sb[k] = __ffma2_rn(fb[W - 1], pz, sb[k]);
-                    }
+                for (int k = 0; k < NB; ++k) {
+                    const float4 pz = *reinterpret_cast<const float4 *>(stage + k * SS + 32 + 2 * z);
+                    sa[k] = __ffma2_rn(fa[z], f2(pz.x, pz.y), sa[k]);
+                    sb[k] = __ffma2_rn(fb[z], f2(pz.x, pz.y), sb[k]);
+                    sa[k] = __ffma2_rn(fa[z + 1], f2(pz.z, pz.w), sa[k]);
+                    sb[k] = __ffma2_rn(fb[z + 1], f2(pz.z, pz.w), sb[k]);
                 }
             }
+            if constexpr (W % 2) {
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const float2 pz = *reinterpret_cast<const float2 *>(stage + k * SS + 32 + 2 * (W - 1));
+                    sa[k] = __ffma2_rn(fa[W - 1], pz, sa[k]);
+                    sb[k] = __ffma2_rn(fb[W - 1], pz, sb[k]);
+                }
+            }
+#ifdef NLP_INTERP_REDUX
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 const float2 vk = __ffma2_rn(sb[k], wb2[k], __fmul2_rn(sa[k], wa2[k]));
                 const int sr = warp_sum_i32(__float2int_rn(vk.x * q1inv));
                 const int si = warp_sum_i32(__float2int_rn(vk.y * q1inv));
-                // c_k = rho-hat_k omega_k (wf of lane k holds omega_k q1); ones mode: c_k = omega_k
-                const float wk = __shfl_sync(0xffffffffu, wcur, k);
-                cv[k] = P.ones_mode ? f2(wk * q1inv, 0.f) : f2((float)sr * wk, (float)si * wk);
+                // c_k = rho-hat_k omega_k; wf of lane k holds omega_k q1 (zero past the piece)
+                if (lane == k) {
+                    const float2 c = f2((float)sr * wcur, (float)si * wcur);
+                    if (k < nb) P.cnode[jb + k] = mk<float>(c.x, c.y);
+                    bsum += fabsf(c.x) + fabsf(c.y);
+                }
             }
-            // spreading into the register columns
+#else
+            // all 2 NB sums reduced together (recursive halving, fixed shuffle order): the
+            // real part of node k lands in lanes 8k .. 8k+3, its imaginary part in 8k+4 .. 8k+7
+            constexpr int V = 2 * NB;
+            static_assert(V == 8, "lane layout of the batch sums");
+            float v[V];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float2 vk = __ffma2_rn(sb[k], wb2[k], __fmul2_rn(sa[k], wa2[k]));
+                v[2 * k] = vk.x;
+                v[2 * k + 1] = vk.y;
+            }
+            warp_reduce_multi<float, V>(v, lane);
+            const float im = __shfl_down_sync(0xffffffffu, v[0], 4);
+            const int k = lane >> 3;
+            const float wk = __shfl_sync(0xffffffffu, wcur, k);   // omega_k q1, zero past the piece
+            if ((lane & 7) == 0) {
+                const float2 c = f2(v[0] * wk * q1inv, im * wk * q1inv);
+                if (k < nb) P.cnode[jb + k] = mk<float>(c.x, c.y);
+                bsum += fabsf(c.x) + fabsf(c.y);
+            }
+#endif
+            __syncwarp();
+        }
+        buf ^= 1;
+        sg = sg_n;
+        so = so_n;
+        j0 = j0_n;
+        j1 = j1_n;
+    }
+    cp_async_wait<0>();
+    // the chunk's bound for the spreading kernel: lane sums, then warps, in fixed order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, off);
+    if (lane == 0) wsum[warp] = bsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int u = 0; u < nwarps; ++u) t += wsum[u];
+        P.csum[bid] = t;
+    }
+}
+
+template <int W, int NB>
+__device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int bid, unsigned char *smraw) {
+    static_assert(W * W <= 64 && W >= 4 && W <= 8, "two columns per lane, at most 8 z taps");
+    using G = WarpGeo<W, NB>;
+    constexpr int SS = G::SS, KR = G::KR;
+    const int nwarps = blockDim.x >> 5;
+    const WarpLayout L = warp_layout<W, NB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps, true);
+    int2 *sG = (int2 *)smraw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *stage = (float *)(smraw + L.offStage) + warp * G::STAGE;
+    const int rows = L.Wt0 * L.Wt1;
+    int *rowG = (int *)(smraw + L.offRowW);
+    const Chunk ch = P.rchunks[bid];
+    warp_window_rows(P, ch, L, true, nullptr, rowG);
+    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = make_int2(0, 0);
+    const WinCol wc = window_col(P, ch, L.Wt2, rows);
+    __syncthreads();
+    float q2, q2inv;
+    fixed_quantum(P.ones_mode ? ch.wsum : P.csum[bid], q2, q2inv);
+
+    const WarpLane<W, NB> ln(lane, P.w, (float)P.beta);
+    // G flush order: lanes of the upper half of each y quartet add the imaginary word first,
+    // so that the 32 lanes of one atomic instruction hit 32 banks (W = 8 geometry)
+    const int sw = (ln.ya >> 1) & 1;
+    // this warp's region: two piece buffers of records, then their c_j
+    float4 *recb = (float4 *)(smraw + L.offRec + (size_t)warp * 2 * kRecNodes * (sizeof(float4) + sizeof(float2)));
+    float2 *cbb = (float2 *)(recb + 2 * kRecNodes);
+    float pd[KR];
+    int sg = ch.j0 + warp, buf = 0;
+    uint32_t so = 0;
+    int j0 = 0, j1 = 0;
+    if (sg < ch.j1) {
+        so = P.seg_sub[sg];
+        j0 = P.seg_node[2 * sg];
+        j1 = P.seg_node[2 * sg + 1];
+        stage_piece<NB>(P, j0, j1 - j0, recb, P.ones_mode ? nullptr : cbb, lane);
+    }
+    while (sg < ch.j1) {
+        const int sg_n = sg + nwarps;
+        uint32_t so_n = 0;
+        int j0_n = 0, j1_n = 0;
+        if (sg_n < ch.j1) {
+            so_n = P.seg_sub[sg_n];
+            j0_n = P.seg_node[2 * sg_n];
+            j1_n = P.seg_node[2 * sg_n + 1];
+            stage_piece<NB>(P, j0_n, j1_n - j0_n, recb + (buf ^ 1) * kRecNodes,
+                            P.ones_mode ? nullptr : cbb + (buf ^ 1) * kRecNodes, lane);
+        } else {
+            cp_async_commit();
+        }
+        cp_async_wait<1>();
+        __syncwarp();
+        const float *rec = (const float *)(recb + buf * kRecNodes);
+        const float2 *cpc = cbb + buf * kRecNodes;
+        const int so0 = so & 0xff, so1 = (so >> 8) & 0xff, so2 = (so >> 16) & 0xff;
+        float2 ga[W], gb[W];
+#pragma unroll
+        for (int z = 0; z < W; ++z) ga[z] = gb[z] = f2(0.f, 0.f);
+        for (int jb = j0; jb < j1; jb += NB) {
+            const int nb = min(NB, j1 - jb), b = jb - j0;
+            ln.fetch(rec, b, pd);
+            // the batch's c_j, zero past the piece; ones mode: (omega_j, 0)
+            float2 cv[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                cv[k] = k >= nb ? f2(0.f, 0.f) : (P.ones_mode ? f2(rec[4 * (b + k) + 3], 0.f) : cpc[b + k]);
+            ln.evaluate(pd, stage);
+            __syncwarp();
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 const float *pk = stage + k * SS;
-                const float2 ca2 = __fmul2_rn(cv[k], wa2[k]), cb2 = __fmul2_rn(cv[k], wb2[k]);
+                float2 wa2, wb2;
+                ln.weights(pk, wa2, wb2);
+                const float2 ca2 = __fmul2_rn(cv[k], wa2), cb2 = __fmul2_rn(cv[k], wb2);
 #pragma unroll
                 for (int z = 0; z + 1 < W; z += 2) {
                     const float4 pz = *reinterpret_cast<const float4 *>(pk + 32 + 2 * z);
@@ -516,27 +656,29 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
             __syncwarp();
         }
         // add the piece's columns to the window in fixed point
-        const int ga0 = (so0 + xa) * L.SG + (so1 + ya) * L.RG + so2;
-        const int gb0 = (so0 + xb) * L.SG + (so1 + yb) * L.RG + so2;
+        const int ga0 = (so0 + ln.xa) * L.SG + (so1 + ln.ya) * L.RG + so2;
+        const int gb0 = (so0 + ln.xb) * L.SG + (so1 + ln.yb) * L.RG + so2;
         int *pa = &sG[ga0].x + sw, *pb = &sG[gb0].x + sw;
 #pragma unroll
         for (int z = 0; z < W; ++z) {
-            if (act_a) {
+            if (ln.act_a) {
                 const int re = __float2int_rn(ga[z].x * q2inv), im = __float2int_rn(ga[z].y * q2inv);
                 atomicAdd(pa + 2 * z, sw ? im : re);
                 atomicAdd(pa + 2 * z + 1 - 2 * sw, sw ? re : im);
             }
-            if (act_b) {
+            if (ln.act_b) {
                 const int re = __float2int_rn(gb[z].x * q2inv), im = __float2int_rn(gb[z].y * q2inv);
                 atomicAdd(pb + 2 * z, sw ? im : re);
                 atomicAdd(pb + 2 * z + 1 - 2 * sw, sw ? re : im);
             }
         }
+        buf ^= 1;
         sg = sg_n;
         so = so_n;
         j0 = j0_n;
         j1 = j1_n;
     }
+    cp_async_wait<0>();
     __syncthreads();
     // the chunk's window, dense, to its scratch slot (thread: column wc.c of rows r0 + k rstep)
     cpx<float> *out = P.win + (int64_t)bid * P.win_cells + wc.c;

@@ -5,7 +5,7 @@
 // tile are sorted at plan time by 2^3 sub-tile; a run of at most 64 (FP32) / 32 (FP64) nodes
 // of one sub-tile is a piece, and all nodes of a piece reach the same sub-window of
 // W = 2 + w - 1 cells per axis.  Two kernels:
-//   - k_interp_spread_warp (FP32, W <= 8): one warp per piece, see spread_dev.cuh.
+//   - k_interp_warp then k_spread_warp (FP32, W <= 8): one warp per piece, see spread_dev.cuh.
 //   - k_interp_spread_reg (FP64, and FP32 with W > 8): a team of warps owns one piece: lane
 //     (cx, cy) holds the z-column of the sub-window (F in registers for FP32, read from the
 //     shared window per node for FP64) and a G accumulator column in registers.  Nodes are
@@ -198,10 +198,16 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
 }
 
 #ifndef NLP_WARP_MINB
-#define NLP_WARP_MINB 4
+#define NLP_WARP_MINB 5
 #endif
 template <int W>
-__global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_interp_spread_warp(DevPlan<float> P) {
+__global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_interp_warp(DevPlan<float> P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    interp_warp_block<W, kWarpNB>(P, blockIdx.x, smraw);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_spread_warp(DevPlan<float> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     spread_warp_block<W, kWarpNB>(P, blockIdx.x, smraw);
 }
@@ -234,7 +240,8 @@ template <typename T, int W> static int reg_teams(const DevPlan<T> &P) {
 
 template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P, int nwarps_warpkernel) {
     if constexpr (sizeof(T) == 4 && W <= 8) {
-        return warp_layout<W, kWarpNB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps_warpkernel).bytes;
+        return std::max(warp_layout<W, kWarpNB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps_warpkernel, false).bytes,
+                        warp_layout<W, kWarpNB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps_warpkernel, true).bytes);
     } else {
         const size_t WW = (size_t)P.win_n[0] * P.win_n[1] * P.win_n[2];
         const size_t rows = (size_t)P.win_n[0] * P.win_n[1];
@@ -245,12 +252,13 @@ template <typename T, int W> static size_t reg_smem(const DevPlan<T> &P, int nwa
 
 template <typename T, int W> static cudaError_t launch_w(const DevPlan<T> &P, cudaStream_t st) {
     if constexpr (sizeof(T) == 4 && W <= 8) {
-        const size_t sm = reg_smem<T, W>(P, kWarpBlock / 32);
-        cudaError_t e = allow_smem<k_interp_spread_warp<W>>();
+        // spreading half (the interpolation half runs first, launch_interp_warp)
+        const size_t sm = warp_layout<W, kWarpNB>(P.win_n[0], P.win_n[1], P.win_n[2], kWarpBlock / 32, true).bytes;
+        cudaError_t e = allow_smem<k_spread_warp<W>>();
         if (e == cudaSuccess)   // several small blocks per SM, each with its own tile window
-            e = cudaFuncSetAttribute(k_interp_spread_warp<W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            e = cudaFuncSetAttribute(k_spread_warp<W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        k_interp_spread_warp<W><<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
+        k_spread_warp<W><<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
         return cudaGetLastError();
     } else {
         constexpr int NB = nb_of<T>();
@@ -306,6 +314,27 @@ template <> cudaError_t launch_interp_spread_reg<double>(const DevPlan<double> &
 #undef L_D
     return cudaErrorInvalidValue;
 }
+
+template <int W> static cudaError_t launch_interp_w(const DevPlan<float> &P, cudaStream_t st) {
+    const size_t sm = warp_layout<W, kWarpNB>(P.win_n[0], P.win_n[1], P.win_n[2], kWarpBlock / 32, false).bytes;
+    cudaError_t e = allow_smem<k_interp_warp<W>>();
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_interp_warp<W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    k_interp_warp<W><<<(unsigned)P.nrchunks, kWarpBlock, sm, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <> cudaError_t launch_interp_warp<float>(const DevPlan<float> &P, cudaStream_t st) {
+    if (P.nrchunks == 0) return cudaSuccess;
+    switch (P.sub_T + P.w - 1) {
+        case 5: return launch_interp_w<5>(P, st);
+        case 6: return launch_interp_w<6>(P, st);
+        case 7: return launch_interp_w<7>(P, st);
+        case 8: return launch_interp_w<8>(P, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template <> cudaError_t launch_interp_warp<double>(const DevPlan<double> &, cudaStream_t) { return cudaErrorInvalidValue; }
 
 template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStream_t st) {
     if (P.ngroups == 0) return cudaSuccess;
