@@ -196,9 +196,9 @@ def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stre
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
-# 128^3 Coulomb workload (profiles/interp_spread_fp32_128cube.md), keyed by precision, with a
-# digest of the sources that decide the kernel's traffic: once any of them changes, the
-# counters no longer describe the kernel and the line reports traffic null.
+# 128^3 Coulomb workload, keyed by precision, with a digest of the sources that decide the
+# kernel's traffic: once any of them changes, the counters no longer describe the kernel and
+# the line reports traffic null.
 TRAFFIC_SOURCES = ("paper_1410_3584_gb300/csrc/spread_reg.cu", "paper_1410_3584_gb300/csrc/spread_dev.cuh",
                    "paper_1410_3584_gb300/csrc/spread_common.cuh", "paper_1410_3584_gb300/csrc/plan.cu")
 CAPTURED_TRAFFIC = {"fp32": ("interp_spread", 330_896_896 + 8_201_728, "0bb5406c50113077")}
@@ -225,7 +225,7 @@ def captured_traffic(prec, kernel):
     return ent[1] if source_digest() == ent[2] else None
 
 
-def roofline(res, prec, alu_peak, hbm_peak, sm_mhz_note):
+def roofline(res, prec, alu_peak, hbm_peak, hbm_source):
     """Dominant kernel: the stage with the largest average time."""
     st = res["stages"]
     name = max(st, key=st.get)
@@ -235,13 +235,21 @@ def roofline(res, prec, alu_peak, hbm_peak, sm_mhz_note):
     elt = 8 if prec == "fp32" else 16          # complex element bytes
     n, nf = info["n"], info["nf"]
     nh = nf[2] // 2 + 1
-    if name == "interp_spread":
-        # algorithmic work: per processed node w^3 taps of interpolation (2 FMA) and of
-        # spreading (2 mul + 2 add) = 8 flop per tap
-        flops = 8.0 * info["nodes_half"] * w ** 3
+    if name in ("interp", "interp_spread"):
+        # algorithmic work per processed node and tap: interpolation 2 FMA (4 flop), spreading
+        # 2 FMA (4 flop).  FP32 plans run them as two kernels ("interp", then "interp_spread"
+        # for the spreading half); the FP64 kernel fuses them (8 flop per tap)
+        split = "interp" in st
+        flops = (4.0 if split else 8.0) * info["nodes_half"] * w ** 3
         ach = flops / t
-        return dict(kernel=name, bound="alu", achieved=ach / 1e12, peak=alu_peak / 1e12, unit="TFLOP/s",
-                    frac=ach / alu_peak, traffic=captured_traffic(prec, name), peak_source="measured FMA microbenchmark (nlp_measure_alu_peak)")
+        traffic = captured_traffic(prec, name)
+        out = dict(kernel="interpolate" if name == "interp" else ("spread" if split else "interp_spread"),
+                   bound="alu", achieved=ach / 1e12, peak=alu_peak / 1e12, unit="TFLOP/s", frac=ach / alu_peak,
+                   traffic=traffic, peak_source="measured FMA microbenchmark (nlp_measure_alu_peak)")
+        if traffic:
+            out["hbm"] = {"achieved_gbs": traffic / t / 1e9, "frac": traffic / t / 1e9 / hbm_peak,
+                          "peak_source": hbm_source}
+        return out
     # FFT passes: algorithmic bytes = one read + one write of the pass's data
     spec = nf[0] * nf[1] * nh * elt
     if name == "fwd_last" or name == "inv_last":
@@ -254,7 +262,7 @@ def roofline(res, prec, alu_peak, hbm_peak, sm_mhz_note):
         byt = spec
     ach = byt / t
     return dict(kernel=name, bound="hbm", achieved=ach / 1e9, peak=hbm_peak, unit="GB/s", frac=ach / 1e9 / hbm_peak,
-                traffic=None, peak_source="MEASURED_PEAKS.json hbm_gbs")
+                traffic=None, peak_source=hbm_source)
 
 
 def gpu_arm(args):
@@ -273,8 +281,12 @@ def gpu_arm(args):
                             e2e=False)
         print(json.dumps({"profile": args.profile, "ms": res["times"], "stages_ms": res["stages"]}))
         return
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_source = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    else:
+        peaks = {"hbm_gbs": 6800.0}
+        hbm_source = "fallback 6800 GB/s (MEASURED_PEAKS.json absent)"
     alu = {p: nl.nlp_measure_alu_peak(p, stream) for p in ("fp32", "fp64")}
     clk = ClockSampler(local)
     if ws > 1:
@@ -315,8 +327,8 @@ def gpu_arm(args):
         ex = cf.coulomb3d_triaxial(X[sl], Y[sl], Z[sl], WIDTHS)
         err_cf = float(np.max(np.abs(res64["phi"][sl] - ex)) / np.max(np.abs(ex)))
         sm = clocks.get("sm_mhz")
-        r32 = roofline(res32, "fp32", alu["fp32"], peaks["hbm_gbs"], sm)
-        r64 = roofline(res64, "fp64", alu["fp64"], peaks["hbm_gbs"], sm)
+        r32 = roofline(res32, "fp32", alu["fp32"], peaks["hbm_gbs"], hbm_source)
+        r64 = roofline(res64, "fp64", alu["fp64"], peaks["hbm_gbs"], hbm_source)
         K = args.steps
         line = {
             "metric": METRIC,
@@ -418,6 +430,11 @@ def batch_arm(args):
     stream.synchronize()
     t_plan = time.perf_counter() - t0
     b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
+    grid0 = nl.nlp_batch_get_info(b)["grid"]
+    # the batch's own launch knob: persistent CTAs per SM, timed on these inputs
+    t0 = time.perf_counter()
+    grid_best, tune_ms = nl.nlp_batch_autotune(b, rhos, phis)
+    t_btune = time.perf_counter() - t0
     info = nl.nlp_batch_get_info(b)
     for _ in range(args.warmup):
         nl.nlp_batch_eval(b, rhos, phis)
@@ -433,6 +450,38 @@ def batch_arm(args):
     nl.nlp_batch_sync(b)
     torch.cuda.synchronize()
     times = [a.elapsed_time(c) for a, c in ev]
+    # the same items one plan at a time (every kernel of every plan as its own launch on the
+    # same stream), and the same sequence replayed from a captured CUDA graph
+    seq = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for pl, r, ph in zip(plans, rhos, phis):
+            nl.nlp_eval_potential(pl.handle, r, ph)
+        e1.record(stream)
+        e1.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    seq_graph = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for pl, r, ph in zip(plans, rhos, phis):
+                nl.nlp_eval_potential(pl.handle, r, ph)
+        sg_t = []
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            sg_t.append(e0.elapsed_time(e1))
+        seq_graph = sum(sg_t) / len(sg_t)
+    except Exception as exc:   # capture not possible here: report it, keep the other numbers
+        seq_graph = "not captured: %s" % type(exc).__name__
     # checks: every item against its own single-plan evaluation, a sample against the oracle
     worst_single, worst_oracle = 0.0, 0.0
     from oracle import closed_forms as cf
@@ -464,6 +513,9 @@ def batch_arm(args):
         "ms_per_batch": 1e3 * tsum / args.steps, "steps": args.steps, "warmup": args.warmup,
         "items": len(items), "nodes_total": nodes, "tasks": info["tasks"], "grid_ctas": info["grid"],
         "smem_bytes": info["smem"], "tiles": tiles, "plan_s": t_plan, "tune_s": t_tune,
+        "batch_autotune": {"grid_default": grid0, "grid_best": grid_best, "ms_best": tune_ms, "tune_s": t_btune},
+        "sequential_ms": sum(seq) / len(seq), "sequential_graph_ms": seq_graph,
+        "speedup_vs_sequential": (sum(seq) / len(seq)) / (1e3 * tsum / args.steps),
         "max_rel_vs_single_plan": worst_single, "max_rel_vs_oracle_sampled": worst_oracle,
         "cpu_baseline": {"value": n_or / t_or if t_or > 0 else None, "unit": "evals/s", "cores": native.max_threads(),
                          "kind": "oracle", "sample": "%d batch items of at most 96^3 by the FP64 oracle (tol 1e-12)" % n_or},

@@ -245,6 +245,13 @@ nlp_status nlp_batch_sync(nlp_batch batch);
 
 nlp_status nlp_batch_get_info(nlp_batch batch, int *tasks, int *grid_ctas, size_t *smem_bytes);
 
+/* Autotuner of the batch's own launch: times the graph (4 replays, the first a warm-up) with
+ * the persistent grid at 1, 2, ... up to the occupancy limit of CTAs per SM on these inputs
+ * and keeps the fastest (the graph is re-captured).  Outputs (may be NULL): *best_grid CTAs,
+ * *best_ms per evaluation of the batch.  Synchronous; the outputs phi_dev are overwritten. */
+nlp_status nlp_batch_autotune(nlp_batch batch, const void *const *rho_dev, void *const *phi_dev,
+                              int *best_grid, double *best_ms);
+
 /* Test hook: set the poll limit of the dependency waits and, if block_item and block_stage
  * are >= 0, make that stage of that item never count as complete, so the stages after it
  * run out of polls (failure injection on the host; the device only sees an unreachable

@@ -72,6 +72,7 @@ def _load():
         "nlp_batch_eval": ([P, ctypes.POINTER(P), ctypes.POINTER(P)], I),
         "nlp_batch_sync": ([P], I),
         "nlp_batch_get_info": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t)], I),
+        "nlp_batch_autotune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "nlp_batch_set_wait_limit": ([P, ctypes.c_longlong, I, I], I),
         "nlp_batch_destroy": ([P], None),
         "nlp_autotune_tile": ([ctypes.POINTER(nlp_grid), I, I, ctypes.POINTER(nlp_opts), P, ctypes.c_char_p,
@@ -311,6 +312,15 @@ def nlp_batch_get_info(batch) -> dict:
     t, g, sm = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
     _check(_lib.nlp_batch_get_info(batch, ctypes.byref(t), ctypes.byref(g), ctypes.byref(sm)), "nlp_batch_get_info")
     return {"tasks": t.value, "grid": g.value, "smem": sm.value}
+
+
+def nlp_batch_autotune(batch, rhos, phis):
+    """Pick the persistent grid of the batch by timing it on these inputs: (grid, ms)."""
+    rp = (ctypes.c_void_p * len(rhos))(*[t.data_ptr() for t in rhos])
+    pp = (ctypes.c_void_p * len(phis))(*[t.data_ptr() for t in phis])
+    g, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(_lib.nlp_batch_autotune(batch, rp, pp, ctypes.byref(g), ctypes.byref(ms)), "nlp_batch_autotune")
+    return g.value, ms.value
 
 
 def nlp_batch_set_wait_limit(batch, polls: int, block_item: int = -1, block_stage: int = -1):

@@ -400,6 +400,48 @@ nlp_status nlp_batch_get_info(nlp_batch b, int *tasks, int *grid, size_t *smem_b
     return NLP_OK;
 }
 
+nlp_status nlp_batch_autotune(nlp_batch b, const void *const *rho_dev, void *const *phi_dev, int *best_grid,
+                              double *best_ms) {
+    if (!b || !rho_dev || !phi_dev) return NLP_ERR_INVALID_ARG;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent, 256, b->smem) != cudaSuccess)
+        return NLP_ERR_CUDA;
+    per = std::max(1, per);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NLP_ERR_CUDA;
+    int best = 0;
+    double bms = 1e300;
+    nlp_status s = NLP_OK;
+    // resident persistent CTAs per SM: every count from one to the occupancy limit
+    for (int k = 1; k <= per && s == NLP_OK; ++k) {
+        b->grid = sms * k;
+        if ((s = batch_graph(b))) break;
+        double tmin = 1e300;
+        for (int rep = 0; rep < 4 && s == NLP_OK; ++rep) {
+            cudaEventRecord(e0, b->stream);
+            if ((s = nlp_batch_eval(b, rho_dev, phi_dev))) break;
+            cudaEventRecord(e1, b->stream);
+            if ((s = nlp_batch_sync(b))) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, (double)ms);   // the first replay warms up
+        }
+        if (tmin < bms) {
+            bms = tmin;
+            best = b->grid;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    b->grid = best;
+    if ((s = batch_graph(b))) return s;
+    if (best_grid) *best_grid = best;
+    if (best_ms) *best_ms = bms;
+    return NLP_OK;
+}
+
 nlp_status nlp_batch_set_wait_limit(nlp_batch b, long long polls, int block_item, int block_stage) {
     if (!b || polls < 1 || block_item >= b->count || block_stage >= kStages) return NLP_ERR_INVALID_ARG;
     if (b->pending && cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;

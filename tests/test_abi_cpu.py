@@ -72,6 +72,7 @@ def test_null_handles_rejected(nl):
     assert lib.nlp_batch_create(None, 0, None, None) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_batch_eval(None, None, None) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_batch_sync(None) == nl.NLP_ERR_INVALID_ARG
+    assert lib.nlp_batch_autotune(None, None, None, None, None) == nl.NLP_ERR_INVALID_ARG
     lib.nlp_batch_destroy(None)
 
 

@@ -81,6 +81,28 @@ def test_batch_matches_single_plans_and_oracle(nl):
         p.close()
 
 
+def test_batch_autotune_keeps_results(nl):
+    """The batch autotuner picks a persistent grid (CTAs per SM from 1 to the occupancy limit)
+    by timing; the results of the tuned graph equal the single-plan evaluations."""
+    import torch
+    stream = torch.cuda.Stream()
+    plans, rhos, phis, refs, grids = _build(nl, torch, stream)
+    b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
+    grid, ms = nl.nlp_batch_autotune(b, rhos, phis)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert grid % sms == 0 and grid >= sms and ms > 0
+    assert nl.nlp_batch_get_info(b)["grid"] == grid
+    for ph in phis:
+        ph.zero_()
+    nl.nlp_batch_eval(b, rhos, phis)
+    nl.nlp_batch_sync(b)
+    for ph, ref in zip(phis, refs):
+        assert np.max(np.abs(ph.double().cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
+    nl.nlp_batch_destroy(b)
+    for p in plans:
+        p.close()
+
+
 def test_batch_wait_timeout_is_reported_and_recoverable(nl):
     import torch
     stream = torch.cuda.Stream()
