@@ -475,8 +475,7 @@ def batch_arm(args):
                 flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            with torch.cuda.stream(stream):
-                g.replay()
+            g.replay()
             e1.record(stream)
             e1.synchronize()
             sg_t.append(e0.elapsed_time(e1))

@@ -277,12 +277,13 @@ enum {
     NLP_STAGE_FWD_LAST = 0,   /* deconvolve + zero-pad + R2C FFT along the last axis */
     NLP_STAGE_FWD_MID = 1,    /* forward FFT along axis 1 (3D) / axis 0 (2D) */
     NLP_STAGE_FWD_FIRST = 2,  /* forward FFT along axis 0 (3D only) */
-    NLP_STAGE_SPREAD = 4,     /* interpolate -> scale -> spread, ending with the fold of the chunks'
-                                 windows into the spreading target */
+    NLP_STAGE_COMBINE = 3,    /* sum the chunks' windows into the spreading target (writes all of it) */
+    NLP_STAGE_SPREAD = 4,     /* interpolate -> scale -> spread (chunk windows to scratch) */
     NLP_STAGE_INV_FIRST = 5,  /* inverse FFT along axis 0 (3D only) */
     NLP_STAGE_INV_MID = 6,    /* inverse FFT along axis 1 (3D) / axis 0 (2D) */
     NLP_STAGE_INV_LAST = 7,   /* C2R FFT along the last axis + deconvolve + crop */
     NLP_STAGE_POISSON = 8,    /* 2D Poisson FP64 parts (moments, rho-hat(0), u_1) */
+    NLP_STAGE_WINDOW_SUM = 9, /* sum the windows of tiles split into several chunks (before the combine) */
     NLP_STAGE_INTERP = 10     /* FP32 plans of the default 3D kernels: interpolation and scaling; the
                                  spreading follows as NLP_STAGE_SPREAD */
 };

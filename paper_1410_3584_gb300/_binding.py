@@ -249,8 +249,9 @@ def nlp_ts_step(plan, psi, V, beta: float, g: float = 0.0, tau: float = 1e-3, or
            "nlp_ts_step")
 
 
-STAGES = {0: "fwd_last", 1: "fwd_mid", 2: "fwd_first", 4: "interp_spread",
-          5: "inv_first", 6: "inv_mid", 7: "inv_last", 8: "poisson_fp64", 10: "interp"}
+STAGES = {0: "fwd_last", 1: "fwd_mid", 2: "fwd_first", 3: "combine", 4: "interp_spread",
+          5: "inv_first", 6: "inv_mid", 7: "inv_last", 8: "poisson_fp64", 9: "window_sum",
+          10: "interp"}
 
 
 def nlp_set_stage_timing(plan, on: bool):

@@ -67,8 +67,8 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
         NLP_CUDA_TRY(launch_mul_spec<T>(D.F, D.Khat, (int64_t)D.nf[0] * D.nf[1] * nh, st));
         mark(p, NLP_STAGE_SPREAD);
     } else {
-        // interpolate, scale, spread: each chunk's window to its scratch slot, folded into G by
-        // the kernels' combine tail (every reached cell of G written once, in a fixed order)
+        // interpolate, scale, spread (each chunk's window to its scratch slot), then combine
+        // the windows into G (every cell of G written once, in a fixed order)
         if (D.cnode) {
             NLP_CUDA_TRY(launch_interp_warp<T>(D, st));
             mark(p, NLP_STAGE_INTERP);
@@ -76,6 +76,12 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
         if (D.sub_T > 0) NLP_CUDA_TRY(launch_interp_spread_reg<T>(D, st));
         else NLP_CUDA_TRY(launch_interp_spread<T>(D, st));
         mark(p, NLP_STAGE_SPREAD);
+        if (D.ngroups > 0) {
+            NLP_CUDA_TRY(launch_window_sum<T>(D, st));
+            mark(p, NLP_STAGE_WINDOW_SUM);
+        }
+        NLP_CUDA_TRY(launch_combine<T>(D, st));
+        mark(p, NLP_STAGE_COMBINE);
     }
     // type 1: inverse FFT (axis 0, axis 1, last axis), deconvolve, crop.  After a spread, the
     // first inverse pass reads G and writes F (free once the spread has read it), so G keeps

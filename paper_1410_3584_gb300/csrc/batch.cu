@@ -23,8 +23,9 @@
 
 namespace nlp {
 
-enum { ST_R2C = 0, ST_A1, ST_A0, ST_INTERP, ST_SPREAD, ST_B0, ST_B1, ST_C2R, kStages };
+enum { ST_R2C = 0, ST_A1, ST_A0, ST_INTERP, ST_SPREAD, ST_WSUM, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
 constexpr int kRegLines = 16;          // lines (pairs) per register-engine FFT task: 16 x 16 threads
+constexpr int kCombTiles = 16;         // combine tiles of G per task
 
 struct BatchItem {
     DevPlan<float> P;
@@ -115,6 +116,15 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
                 if (B.spread_warp) spread_warp_block<8, kWarpNB>(B.P, i, smraw);
                 else spread_generic_block<float>(B.P, i, smraw);
                 break;
+            case ST_WSUM:
+                window_sum_block<float>(B.P, i);
+                break;
+            case ST_COMBINE: {
+                CombStage *cst = (CombStage *)smraw;
+                const int64_t t1 = min((int64_t)(i + 1) * kCombTiles, B.P.cmb_nact);
+                for (int64_t t = (int64_t)i * kCombTiles; t < t1; ++t) combine_block<float>(B.P, B.P.cmb_act[t], cst);
+                break;
+            }
             case ST_B0:
                 if (B.reg_fft) fft_cols_block<float, +1, kRegLines>(B.P.G, B.b0, B.P.len[0], i, smraw);
                 else fft_strided_block<float, +1>(B.P.G, B.b0, B.P.len[0], B.nb_a0, i, smraw);
@@ -277,6 +287,8 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
         B.ntask[ST_INTERP] = (int)(B.spread_warp ? D.nrchunks : 0);
         B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);
+        B.ntask[ST_WSUM] = (int)(D.ngroups * D.grp_parts);
+        B.ntask[ST_COMBINE] = (int)((D.cmb_nact + kCombTiles - 1) / kCombTiles);
         B.ntask[ST_B0] = B.ntask[ST_A0];
         B.ntask[ST_B1] = B.ntask[ST_A1];
         B.ntask[ST_C2R] = B.ntask[ST_R2C];

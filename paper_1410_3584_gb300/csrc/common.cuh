@@ -106,6 +106,7 @@ template <typename T> struct DevPlan {
     const int *grp;         // tiles split into several chunks: {first, count} into grp_list, per group
     const int *grp_list;    // slots of each such tile, ascending; the first one receives their sum
     int64_t ngroups;
+    int grp_parts;          // window-sum tasks per group (256-cell parts of the window)
     const int *cmb_off;     // per combine tile: its entries are cmb[cmb_off[t] .. cmb_off[t+1])
     const CombEntry *cmb;
     int cmb_t[3];       // combine tile edge per axis
@@ -113,13 +114,6 @@ template <typename T> struct DevPlan {
     int64_t cmb_tiles;
     const int *cmb_act; // the tiles that windows reach (the others of G stay zero from plan time)
     int64_t cmb_nact;
-    // arrival counters of the combine in the spreading kernels' tail (see spread_common.cuh)
-    const int *slot_group;  // per slot: its group (tiles of several chunks) or -1
-    int *grp_cnt;           // per group: members still to finish (re-armed by the last one)
-    const int *rep_off;     // per slot: its output tiles are rep_tiles[rep_off[s] .. rep_off[s+1])
-    const int *rep_tiles;   // positions in cmb_act
-    int *tile_cnt;          // per position in cmb_act: windows still to finish (re-armed by the last one)
-    const int *tile_init;
     float psi_sum3;     // FP32 warp kernels: (max over node offsets of sum_t psi)^3, bounds the interpolation
     cpx<T> *cnode;      // FP32 warp kernels: c_j = rho-hat_j omega_j per node (interpolation -> spreading)
     T *csum;            // FP32 warp kernels: per chunk sum of |re c_j| + |im c_j| (bounds the window)

@@ -42,8 +42,7 @@ template <typename T>
 cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, int sign, T post, cudaStream_t st);
 
 // Fused interpolate -> scale -> spread over all node chunks (see spread.cu): each chunk's
-// tile window goes to its slot of P.win, and the kernels' combine tail writes the tiles of G
-// that windows reach (the others hold zeros from plan time).
+// tile window goes to its slot of P.win; launch_combine then writes every cell of G.
 template <typename T> cudaError_t launch_interp_spread(const DevPlan<T> &P, cudaStream_t st);
 template <typename T> int generic_warps(const DevPlan<T> &P, size_t smem_limit);
 template <typename T> size_t interp_spread_smem(const DevPlan<T> &P, int nwarps);
@@ -55,6 +54,8 @@ template <typename T> cudaError_t launch_interp_spread_reg(const DevPlan<T> &P, 
 // FP32 plans of the one-warp-per-piece kernels (P.cnode set): interpolation half, before
 // launch_interp_spread_reg (which then runs the spreading half)
 template <typename T> cudaError_t launch_interp_warp(const DevPlan<T> &P, cudaStream_t st);
+template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStream_t st);   // tiles of several chunks
+template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st);
 
 // 2D Poisson (Algorithm 1) FP64 parts (see poisson2d.cu).  L, h: collapsed 3D view.
 template <typename T>

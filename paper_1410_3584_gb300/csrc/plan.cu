@@ -233,6 +233,7 @@ static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<
         i = k;
     }
     D.ngroups = (int64_t)grp.size() / 2;
+    D.grp_parts = (int)((D.win_cells + 255) / 256);
     D.grp = nullptr;
     D.grp_list = nullptr;
     if (D.ngroups > 0) {
@@ -315,44 +316,6 @@ static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<
     D.cmb_off = (const int *)doff;
     D.cmb = (const CombEntry *)dent;
     p->info.combine_entries = (int64_t)ent.size();
-    // arrival counters of the combine tail: per slot its group, per group the members to
-    // finish, per first slot of a tile the output tiles (positions in cmb_act) its window
-    // reaches, per output tile the number of distinct windows that reach it
-    std::vector<int> slot_group(std::max<size_t>(1, act.size()), -1), gcnt(std::max<size_t>(1, D.ngroups), 0);
-    for (int64_t g = 0; g < D.ngroups; ++g) {
-        gcnt[g] = grp[2 * g + 1];
-        for (int i = 0; i < grp[2 * g + 1]; ++i) slot_group[grp_list[grp[2 * g] + i]] = (int)g;
-    }
-    std::vector<int> pos_of(D.cmb_tiles, -1);
-    for (size_t a = 0; a < live.size(); ++a) pos_of[live[a]] = (int)a;
-    std::vector<std::pair<int, int>> rt;   // (slot, position), distinct
-    for (const Key &k : keys) rt.push_back({k.e.chunk, pos_of[k.tile]});
-    std::sort(rt.begin(), rt.end());
-    rt.erase(std::unique(rt.begin(), rt.end()), rt.end());
-    std::vector<int> rep_off(act.size() + 1, 0), rep_tiles(std::max<size_t>(1, rt.size())),
-        tinit(std::max<size_t>(1, live.size()), 0);
-    for (size_t i = 0; i < rt.size(); ++i) {
-        rep_off[rt[i].first + 1]++;
-        rep_tiles[i] = rt[i].second;
-        tinit[rt[i].second]++;
-    }
-    for (size_t c = 0; c < act.size(); ++c) rep_off[c + 1] += rep_off[c];
-    auto up = [&](const std::vector<int> &v, void **d) -> nlp_status {
-        nlp_status st = alloc_dev(p, d, sizeof(int) * v.size());
-        if (st) return st;
-        cudaMemcpy(*d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice);
-        return NLP_OK;
-    };
-    void *d1, *d2, *d3, *d4, *d5, *d6;
-    if ((s = up(slot_group, &d1)) || (s = up(gcnt, &d2)) || (s = up(rep_off, &d3)) || (s = up(rep_tiles, &d4)) ||
-        (s = up(tinit, &d5)) || (s = up(tinit, &d6)))
-        return s;
-    D.slot_group = (const int *)d1;
-    D.grp_cnt = (int *)d2;
-    D.rep_off = (const int *)d3;
-    D.rep_tiles = (const int *)d4;
-    D.tile_cnt = (int *)d5;
-    D.tile_init = (const int *)d6;
     return NLP_OK;
 }
 

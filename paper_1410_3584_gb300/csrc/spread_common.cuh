@@ -86,21 +86,36 @@ __device__ __forceinline__ T window_fill(const DevPlan<T> &P, const WinCol &k, c
 }
 
 // ------------------------------------------------------------------ combine
-// window values are read through L2 only (ld.global.cg): a block may read a window another
-// block has just written
-__device__ __forceinline__ cpx<float> ldcg(const cpx<float> *p) {
-    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
-    return mk<float>(v.x, v.y);
-}
-__device__ __forceinline__ cpx<double> ldcg(const cpx<double> *p) {
-    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
-    return mk<double>(v.x, v.y);
+// Tiles with many nodes are split into several chunks, whose windows share the tile's origin.
+// First pass (window_sum_block): per such tile, the windows of its chunks are added cell by
+// cell, in slot order, into its first slot.  Part p of group g covers window cells
+// [256 p, 256 p + 256).
+template <typename T>
+__device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t task) {
+    const int64_t g = task / P.grp_parts;
+    const int64_t q = (task % P.grp_parts) * 256 + threadIdx.x;
+    if (q >= P.win_cells || threadIdx.x >= 256) return;
+    const int first = P.grp[2 * g], count = P.grp[2 * g + 1];
+    const int *slots = P.grp_list + first;
+    T sx = (T)0, sy = (T)0;
+    for (int i = 0; i < count; i += 16) {
+        cpx<T> v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            v[u] = (i + u < count) ? P.win[(int64_t)slots[i + u] * P.win_cells + q] : mk<T>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            sx += v[u].x;
+            sy += v[u].y;
+        }
+    }
+    P.win[(int64_t)slots[0] * P.win_cells + q] = mk<T>(sx, sy);
 }
 
-// Output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G
-// with N = (nf0, nf1, nh).  The tiles that some window reaches are combined once each per
-// evaluation, every cell written exactly once; the other tiles of G hold zeros from plan time
-// (nothing else writes G: the first inverse FFT pass reads G and writes its result elsewhere).  The
+// Second pass: output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G
+// with N = (nf0, nf1, nh).  The pass visits the tiles that some window reaches and writes each
+// of their cells exactly once; the other tiles of G hold zeros from plan time (no pass writes
+// G otherwise: the first inverse FFT pass reads G and writes its result elsewhere).  The
 // tile's entries are staged in shared memory, 64 at a time.  A thread owns the cells of one
 // (y, z) position of the tile along x and adds their window values in entry order; the loads
 // of four entries and all its cells are issued together.
@@ -158,7 +173,7 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile,
 #pragma unroll
                 for (int u = 0; u < CPT; ++u) {
                     const int a0 = a00 + u * da;
-                    v[k][u] = (inyz && u < nx && (unsigned)a0 < (unsigned)W0) ? ldcg(row + a0 * W12) : mk<T>(0, 0);
+                    v[k][u] = (inyz && u < nx && (unsigned)a0 < (unsigned)W0) ? row[a0 * W12] : mk<T>(0, 0);
                     if (E.s < 0) v[k][u].y = -v[k][u].y;
                 }
             }
@@ -175,72 +190,6 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile,
 #pragma unroll
     for (int u = 0; u < CPT; ++u)
         if (u < nx) P.G[((int64_t)(lx + u * S) * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx[u], sy[u]);
-}
-
-// ------------------------------------------------------------------ combine in the spreading tail
-// Called by every block of a spreading kernel once its chunk's window is in its slot.  Two
-// kinds of arrival counters (synchronisation only: no value is ever accumulated by an atomic)
-// let the last block to finish a unit do that unit's work, so no separate passes are needed:
-//   - a tile split into several chunks: the last of its chunks sums the group's windows, in
-//     slot order, into the group's first slot;
-//   - an output tile of G: the block that completes the last window reaching it combines the
-//     tile (combine_block, fixed entry order).
-// Each counter is re-armed by the block that drove it to zero, for the next evaluation.  The
-// writer side fences its window before its block's counter update; the last arriver fences
-// again before reading the other windows (the threadfence-reduction pattern), and reads them
-// through L2.  smem: at least kCombStage CombStage entries of the block's shared memory.
-template <typename T>
-__device__ __forceinline__ void window_done(const DevPlan<T> &P, int slot, void *smem) {
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    int rep = slot;
-    const int g = P.slot_group[slot];
-    if (g >= 0) {
-        if (threadIdx.x == 0) {
-            const int old = atomicSub(P.grp_cnt + g, 1);
-            s_last = old == 1;
-            if (old == 1) atomicExch(P.grp_cnt + g, P.grp[2 * g + 1]);
-        }
-        __syncthreads();
-        if (!s_last) return;
-        __threadfence();
-        const int first = P.grp[2 * g], count = P.grp[2 * g + 1];
-        const int *slots = P.grp_list + first;
-        for (int64_t q = threadIdx.x; q < P.win_cells; q += blockDim.x) {
-            T sx = (T)0, sy = (T)0;
-            for (int i = 0; i < count; i += 8) {
-                cpx<T> v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    v[u] = (i + u < count) ? ldcg(P.win + (int64_t)slots[i + u] * P.win_cells + q) : mk<T>(0, 0);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    sx += v[u].x;
-                    sy += v[u].y;
-                }
-            }
-            P.win[(int64_t)slots[0] * P.win_cells + q] = mk<T>(sx, sy);
-        }
-        rep = slots[0];
-        __threadfence();
-        __syncthreads();
-    }
-    for (int i = P.rep_off[rep]; i < P.rep_off[rep + 1]; ++i) {
-        const int a = P.rep_tiles[i];
-        if (threadIdx.x == 0) {
-            const int old = atomicSub(P.tile_cnt + a, 1);
-            s_last = old == 1;
-            if (old == 1) atomicExch(P.tile_cnt + a, P.tile_init[a]);
-        }
-        __syncthreads();
-        const bool last = s_last;
-        if (last) {
-            __threadfence();
-            combine_block<T>(P, P.cmb_act[a], (CombStage *)smem);
-        }
-        __syncthreads();
-    }
 }
 
 }  // namespace nlp

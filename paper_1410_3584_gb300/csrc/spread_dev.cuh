@@ -1,7 +1,7 @@
 // Interpolation/spreading device code shared by the single-plan kernels (spread.cu,
 // spread_reg.cu) and the batched persistent kernel (batch.cu): per-block bodies with the
-// block index passed explicitly.  Each body processes one chunk, writes the chunk's tile window
-// to its scratch slot and ends with the combine tail of spread_common.cuh (window_done).
+// block index passed explicitly.  Each body processes one chunk and writes the chunk's tile
+// window to its scratch slot (the combine pass of spread_common.cuh folds the slots into G).
 #pragma once
 #include "common.cuh"
 #include "spread_common.cuh"
@@ -179,7 +179,6 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
         for (int k = 1; k < nw; ++k) s = s + sGall[(size_t)k * WW + q];
         out[q] = s;
     }
-    window_done<T>(P, bid, smraw);
 }
 
 // ======================================================================= FP32 warp kernels
@@ -687,7 +686,6 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
         const int2 g = sG[rowG[r] + wc.c];
         out[r * L.Wt2] = mk<float>((float)g.x * q2, (float)g.y * q2);
     }
-    window_done<float>(P, bid, smraw);
 }
 
 }  // namespace nlp

@@ -1,5 +1,5 @@
-// Interpolate -> scale -> spread for 3D with register-resident columns.  Every kernel ends with
-// the combine tail that folds the chunks' windows into the spreading target (spread_common.cuh).
+// Fused interpolate -> scale -> spread for 3D with register-resident columns, and the combine
+// pass that folds the chunks' windows into the spreading target.
 //
 // Same operation as k_interp_spread (spread.cu); different work decomposition.  Nodes of a
 // tile are sorted at plan time by 2^3 sub-tile; a run of at most 64 (FP32) / 32 (FP64) nodes
@@ -195,7 +195,6 @@ __global__ void __launch_bounds__(RegCfg<W>::TT *RegCfg<W>::NT) k_interp_spread_
         for (int k = 1; k < nt; ++k) s = s + sF[(size_t)(1 + k) * WW + q];
         out[q] = s;
     }
-    window_done<T>(P, blockIdx.x, smraw);
 }
 
 #ifndef NLP_WARP_MINB
@@ -211,6 +210,15 @@ template <int W>
 __global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_spread_warp(DevPlan<float> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     spread_warp_block<W, kWarpNB>(P, blockIdx.x, smraw);
+}
+
+template <typename T> __global__ void __launch_bounds__(256) k_window_sum(DevPlan<T> P) {
+    window_sum_block<T>(P, blockIdx.x);
+}
+
+template <typename T> __global__ void __launch_bounds__(128) k_combine(DevPlan<T> P) {
+    __shared__ CombStage st[kCombStage];
+    combine_block<T>(P, P.cmb_act[blockIdx.x], st);
 }
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
@@ -328,9 +336,25 @@ template <> cudaError_t launch_interp_warp<float>(const DevPlan<float> &P, cudaS
 }
 template <> cudaError_t launch_interp_warp<double>(const DevPlan<double> &, cudaStream_t) { return cudaErrorInvalidValue; }
 
+template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStream_t st) {
+    if (P.ngroups == 0) return cudaSuccess;
+    k_window_sum<T><<<(unsigned)(P.ngroups * P.grp_parts), 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st) {
+    if (P.cmb_nact == 0) return cudaSuccess;
+    k_combine<T><<<(unsigned)P.cmb_nact, 128, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
 template bool reg_kernel_supported<float>(int);
 template bool reg_kernel_supported<double>(int);
 template bool warp_kernel_used<float>(int);
 template bool warp_kernel_used<double>(int);
+template cudaError_t launch_window_sum<float>(const DevPlan<float> &, cudaStream_t);
+template cudaError_t launch_window_sum<double>(const DevPlan<double> &, cudaStream_t);
+template cudaError_t launch_combine<float>(const DevPlan<float> &, cudaStream_t);
+template cudaError_t launch_combine<double>(const DevPlan<double> &, cudaStream_t);
 
 }  // namespace nlp

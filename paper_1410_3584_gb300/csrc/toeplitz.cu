@@ -89,7 +89,8 @@ template <typename T> static nlp_status build_kernel(nlp_plan_s *p) {
     if ((s = alloc_dev(aux, &dK, sizeof(T) * NK))) { free_aux(); return s; }
     A.ones_mode = 1;
     const int64_t nhA = A.nh;
-    if (launch_interp_spread<T>(A, st) != cudaSuccess) {
+    if (launch_interp_spread<T>(A, st) != cudaSuccess || launch_window_sum<T>(A, st) != cudaSuccess ||
+        launch_combine<T>(A, st) != cudaSuccess) {
         free_aux();
         return NLP_ERR_CUDA;
     }
