@@ -117,12 +117,16 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
                 else spread_generic_block<float>(B.P, i, smraw);
                 break;
             case ST_WSUM:
-                window_sum_block<float>(B.P, i);
+                window_sum_block<float>(B.P, i, (long long *)smraw);
                 break;
             case ST_COMBINE: {
                 CombStage *cst = (CombStage *)smraw;
                 const int64_t t1 = min((int64_t)(i + 1) * kCombTiles, B.P.cmb_nact);
-                for (int64_t t = (int64_t)i * kCombTiles; t < t1; ++t) combine_block<float>(B.P, B.P.cmb_act[t], cst);
+                // 256 threads: a 3D tile is 2 cells per thread, a 2D tile one
+                for (int64_t t = (int64_t)i * kCombTiles; t < t1; ++t) {
+                    if (B.P.cmb_t[0] == 1) combine_block<float, 1>(B.P, B.P.cmb_act[t], cst);
+                    else combine_block<float, 2>(B.P, B.P.cmb_act[t], cst);
+                }
                 break;
             }
             case ST_B0:

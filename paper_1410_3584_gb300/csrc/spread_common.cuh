@@ -91,25 +91,31 @@ __device__ __forceinline__ T window_fill(const DevPlan<T> &P, const WinCol &k, c
 // cell, in slot order, into its first slot.  Part p of group g covers window cells
 // [256 p, 256 p + 256).
 template <typename T>
-__device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t task) {
+__device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t task, long long *sb) {
     const int64_t g = task / P.grp_parts;
     const int64_t q = (task % P.grp_parts) * 256 + threadIdx.x;
-    if (q >= P.win_cells || threadIdx.x >= 256) return;
+    const bool act = q < P.win_cells && threadIdx.x < 256;
     const int first = P.grp[2 * g], count = P.grp[2 * g + 1];
-    const int *slots = P.grp_list + first;
     T sx = (T)0, sy = (T)0;
-    for (int i = 0; i < count; i += 16) {
-        cpx<T> v[16];
+    // the members' slot offsets, staged 256 at a time
+    for (int m0 = 0; m0 < count; m0 += 256) {
+        const int mc = min(256, count - m0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < mc; i += blockDim.x) sb[i] = (long long)P.grp_list[first + m0 + i] * P.win_cells;
+        __syncthreads();
+        if (!act) continue;
+        for (int i = 0; i < mc; i += 16) {
+            cpx<T> v[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-            v[u] = (i + u < count) ? P.win[(int64_t)slots[i + u] * P.win_cells + q] : mk<T>(0, 0);
+            for (int u = 0; u < 16; ++u) v[u] = (i + u < mc) ? P.win[sb[i + u] + q] : mk<T>(0, 0);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            sx += v[u].x;
-            sy += v[u].y;
+            for (int u = 0; u < 16; ++u) {
+                sx += v[u].x;
+                sy += v[u].y;
+            }
         }
     }
-    P.win[(int64_t)slots[0] * P.win_cells + q] = mk<T>(sx, sy);
+    if (act) P.win[(long long)P.grp_list[first] * P.win_cells + q] = mk<T>(sx, sy);
 }
 
 // Second pass: output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G
@@ -125,7 +131,7 @@ struct CombStage {
 };
 constexpr int kCombStage = 64;
 
-template <typename T>
+template <typename T, int CPT>
 __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile, CombStage *st) {
     const int T0 = P.cmb_t[0], T1 = P.cmb_t[1], T2 = P.cmb_t[2];
     const int t2 = (int)(tile % P.cmb_n[2]);
@@ -135,19 +141,20 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile,
     const int W0 = P.win_n[0], W1 = P.win_n[1], W2 = P.win_n[2];
     const int64_t W12 = (int64_t)W1 * W2;
     const int N0 = P.nf[0], N1 = P.nf[1], N2 = P.nh;
-    // thread: the (y, z) cell (c1, c2) of the tile for x = c0, c0 + S, ... (S = blockDim / (T1 T2))
-    constexpr int CPT = 8;
+    // thread: the (y, z) cell (c1, c2) of the tile for x = c0, c0 + S, ... (S = blockDim / (T1 T2),
+    // CPT = ceil(T0 / S) cells)
     const int yz = T1 * T2;
     const int S = max(1, (int)blockDim.x / yz);
     const int c2 = threadIdx.x % T2, c1 = (threadIdx.x / T2) % T1, c0 = threadIdx.x / yz;
     const int l1 = t1 * T1 + c1, l2 = t2 * T2 + c2, lx = t0 * T0 + c0;
     const bool okyz = threadIdx.x < S * yz && l1 < N1 && l2 < N2;
-    int nx = 0;   // cells of this thread along x
-    for (int u = 0; u < CPT; ++u)
-        if (c0 + u * S < T0 && lx + u * S < N0) nx = u + 1;
+    bool okx[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) okx[u] = okyz && c0 + u * S < T0 && lx + u * S < N0;
     T sx[CPT], sy[CPT];
 #pragma unroll
     for (int u = 0; u < CPT; ++u) sx[u] = sy[u] = (T)0;
+    constexpr int EB = CPT >= 4 ? 4 : 8;   // entries per batch of loads
     for (int eb = e0; eb < e1; eb += kCombStage) {
         const int ne = min(kCombStage, e1 - eb);
         __syncthreads();
@@ -161,10 +168,10 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile,
         }
         __syncthreads();
         if (!okyz) continue;
-        for (int e = 0; e < ne; e += 4) {
-            cpx<T> v[4][CPT];
+        for (int e = 0; e < ne; e += EB) {
+            cpx<T> v[EB][CPT];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < EB; ++k) {
                 const CombStage E = st[min(e + k, ne - 1)];
                 const int a1 = E.s * l1 + E.o1, a2 = E.s * l2 + E.o2;
                 const bool inyz = e + k < ne && (unsigned)a1 < (unsigned)W1 && (unsigned)a2 < (unsigned)W2;
@@ -173,12 +180,12 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile,
 #pragma unroll
                 for (int u = 0; u < CPT; ++u) {
                     const int a0 = a00 + u * da;
-                    v[k][u] = (inyz && u < nx && (unsigned)a0 < (unsigned)W0) ? row[a0 * W12] : mk<T>(0, 0);
+                    v[k][u] = (inyz && okx[u] && (unsigned)a0 < (unsigned)W0) ? row[a0 * W12] : mk<T>(0, 0);
                     if (E.s < 0) v[k][u].y = -v[k][u].y;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < EB; ++k)
 #pragma unroll
                 for (int u = 0; u < CPT; ++u) {
                     sx[u] += v[k][u].x;
@@ -186,10 +193,9 @@ __device__ __forceinline__ void combine_block(const DevPlan<T> &P, int64_t tile,
                 }
         }
     }
-    if (!okyz) return;
 #pragma unroll
     for (int u = 0; u < CPT; ++u)
-        if (u < nx) P.G[((int64_t)(lx + u * S) * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx[u], sy[u]);
+        if (okx[u]) P.G[((int64_t)(lx + u * S) * P.nf[1] + l1) * P.nh + l2] = mk<T>(sx[u], sy[u]);
 }
 
 }  // namespace nlp

@@ -213,12 +213,14 @@ __global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_spread_warp(DevPl
 }
 
 template <typename T> __global__ void __launch_bounds__(256) k_window_sum(DevPlan<T> P) {
-    window_sum_block<T>(P, blockIdx.x);
+    __shared__ long long sb[256];
+    window_sum_block<T>(P, blockIdx.x, sb);
 }
 
-template <typename T> __global__ void __launch_bounds__(128) k_combine(DevPlan<T> P) {
+// 128 threads: a 3D tile (8 x 8 x 8) is 4 cells per thread, a 2D tile (1 x 8 x 16) one
+template <typename T, int CPT> __global__ void __launch_bounds__(128) k_combine(DevPlan<T> P) {
     __shared__ CombStage st[kCombStage];
-    combine_block<T>(P, P.cmb_act[blockIdx.x], st);
+    combine_block<T, CPT>(P, P.cmb_act[blockIdx.x], st);
 }
 
 // supported column lengths: FP32 W = 5..11 (w = 4..10 with Ts = 2), FP64 W = 9..16 (w = 8..15)
@@ -344,7 +346,8 @@ template <typename T> cudaError_t launch_window_sum(const DevPlan<T> &P, cudaStr
 
 template <typename T> cudaError_t launch_combine(const DevPlan<T> &P, cudaStream_t st) {
     if (P.cmb_nact == 0) return cudaSuccess;
-    k_combine<T><<<(unsigned)P.cmb_nact, 128, 0, st>>>(P);
+    if (P.cmb_t[0] == 1) k_combine<T, 1><<<(unsigned)P.cmb_nact, 128, 0, st>>>(P);
+    else k_combine<T, 4><<<(unsigned)P.cmb_nact, 128, 0, st>>>(P);
     return cudaGetLastError();
 }
 
