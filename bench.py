@@ -195,13 +195,14 @@ def run_precision(nl, torch, prec, g, rho, P, counts, steps, warmup, flush, stre
                 launches=launches, e2e_s=e2e_s, bytes_io=int(hr.numel() * hr.element_size()))
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
-# 128^3 Coulomb workload, keyed by precision, with a digest of the sources that decide the
+# DRAM bytes (read + write) per launch of the interpolation and spreading kernels from one ncu
+# capture of the 128^3 Coulomb workload, keyed by (precision, stage), with a digest of the sources that decide the
 # kernel's traffic: once any of them changes, the counters no longer describe the kernel and
 # the line reports traffic null.
 TRAFFIC_SOURCES = ("paper_1410_3584_gb300/csrc/spread_reg.cu", "paper_1410_3584_gb300/csrc/spread_dev.cuh",
                    "paper_1410_3584_gb300/csrc/spread_common.cuh", "paper_1410_3584_gb300/csrc/plan.cu")
-CAPTURED_TRAFFIC = {"fp32": ("interp_spread", 330_896_896 + 8_201_728, "0bb5406c50113077")}
+CAPTURED_TRAFFIC = {("fp32", "interp"): (65_091_584 + 1_541_888, "13693f64db2525b5"),
+                    ("fp32", "interp_spread"): (62_787_840 + 38_981_632, "13693f64db2525b5")}
 
 
 def source_digest(files=TRAFFIC_SOURCES):
@@ -219,10 +220,10 @@ def source_digest(files=TRAFFIC_SOURCES):
 
 
 def captured_traffic(prec, kernel):
-    ent = CAPTURED_TRAFFIC.get(prec)
-    if ent is None or ent[0] != kernel:
+    ent = CAPTURED_TRAFFIC.get((prec, kernel))
+    if ent is None:
         return None
-    return ent[1] if source_digest() == ent[2] else None
+    return ent[0] if source_digest() == ent[1] else None
 
 
 def roofline(res, prec, alu_peak, hbm_peak, hbm_source):

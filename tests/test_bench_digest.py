@@ -27,10 +27,11 @@ def test_digest_ignores_comments_and_whitespace_but_not_code(tmp_path, monkeypat
 
 
 def test_captured_traffic_only_for_the_captured_kernel_and_code(monkeypatch):
-    ent = bench.CAPTURED_TRAFFIC["fp32"]
-    assert bench.captured_traffic("fp64", ent[0]) is None
-    assert bench.captured_traffic("fp32", "fwd_last") is None
-    monkeypatch.setattr(bench, "source_digest", lambda files=None: ent[2])
-    assert bench.captured_traffic("fp32", ent[0]) == ent[1]
-    monkeypatch.setattr(bench, "source_digest", lambda files=None: "0" * 16)
-    assert bench.captured_traffic("fp32", ent[0]) is None
+    for (prec, kernel), (traffic, digest) in bench.CAPTURED_TRAFFIC.items():
+        assert bench.captured_traffic("fp64" if prec == "fp32" else "fp32", kernel) is None
+        assert bench.captured_traffic(prec, "fwd_last") is None
+        monkeypatch.setattr(bench, "source_digest", lambda files=None, d=digest: d)
+        assert bench.captured_traffic(prec, kernel) == traffic
+        monkeypatch.setattr(bench, "source_digest", lambda files=None: "0" * 16)
+        assert bench.captured_traffic(prec, kernel) is None
+
