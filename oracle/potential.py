@@ -85,13 +85,16 @@ def u1_parts(X, Y, sigma: float):
     return u11, u12x, u12y
 
 
-def poisson2d(rho, grid, P, counts, method="nufft", tol=1e-13, sigma=None, return_parts=False):
+def poisson2d(rho, grid, P, counts, method="nufft", tol=1e-13, sigma=None, return_parts=False, partition=None,
+              sigma_u1=None):
     """Algorithm 1 (Sec. 2.2): u = u_1 + u_2.
     Step 1: rho-hat(k_j) and the moments rho-hat(0) = C0, (x rho)-hat(0) = M1 (trapezoid).
     Step 2: u_1 = C0 u_{1,1} - M1 . u_{1,2}                      (Eqs. (u2u3), (phi1_exct), (phi12_ext)).
     Step 3: u_2 = (2pi)^{-2} int_0^P int_0^{2pi} W(k) e^{ik.x} d|k| dtheta with
             W = (rho-hat - (C0 - i k.M1) e^{-sigma^2|k|^2/2}) / |k|  (Eq. (phi2fourier) and the W that follows it).
-    Step 4: u = u_1 + u_2."""
+    Step 4: u = u_1 + u_2.
+    For the improved algorithm (evaluate_split) the integrand of step 3 carries a partition
+    factor p(|k|) and u_1 is taken with the width sigma_u1 (see evaluate_split)."""
     t2, t1 = _transforms(method, tol)
     h = grid.h
     X, Y = grid.mesh()
@@ -105,8 +108,10 @@ def poisson2d(rho, grid, P, counts, method="nufft", tol=1e-13, sigma=None, retur
     G1 = (C0 - 1j * (k @ M1)) * np.exp(-0.5 * sigma * sigma * r * r)
     W = (rh - G1) / r
     c = wq * W / (2.0 * math.pi) ** 2
+    if partition is not None:
+        c = c * partition(r)
     u2 = t1(c, k, grid.n, h)
-    u11, u12x, u12y = u1_parts(X, Y, sigma)
+    u11, u12x, u12y = u1_parts(X, Y, sigma if sigma_u1 is None else sigma_u1)
     u1 = C0 * u11 - (M1[0] * u12x + M1[1] * u12y)
     if return_parts:
         return u1 + u2, dict(C0=C0, M1=M1, sigma=sigma, u1=u1, u2=u2)
@@ -128,30 +133,51 @@ def evaluate(rho, grid, kernel, P, counts=None, method="nufft", tol=1e-13,
     return t1(c, k, grid.n, grid.h)
 
 
-def split_params(grid, P: float, eps: float = 1e-16, kappa: float = 5.5):
-    """Parameters of the split of Sec. 2.1 (Eq. (3.9)) with the Gaussian partition of unity
-    p(k) = exp(-|k|^2 / a) (smooth w = (1 - p) U-hat in 3D).  Reading: the kernel of I_1 in x,
-    erfc(sqrt(a) |x| / 2) / (4 pi |x|) for Coulomb, must decay by the doubled grid's period
-    (images at distance >= 2 L_min), erfc(sqrt(a) L_min) ~ eps: a = (kappa / L_min)^2; I_2 is
-    needed where p >= eps: radius k2 = min(P, sqrt(a ln(1/eps)))."""
+def split_params(grid, P: float, eps: float = 1e-16, kappa: float = 5.5, kernel: str = "coulomb3d"):
+    """Parameters of the split of Sec. 2.1 (Eq. (3.9)).  Returns (s, k2): the scale s of the
+    partition of unity and the radius k2 of the ball that carries I_2.
+      3D kernels and poisson2d: p(k) = exp(-|k|^2 / a), s = a.  Reading: the x-space kernel of
+        I_1 (3D Coulomb: erfc(sqrt(a) |x| / 2) / (4 pi |x|); 2D Laplace: E_1(a |x|^2 / 4) / (4 pi))
+        must have decayed at the doubled grid's nearest image (distance >= 2 L_min):
+        a = (kappa / L_min)^2; I_2 is needed where p >= eps: k2 = min(P, sqrt(a ln(1/eps))).
+      coulomb2d: p(k) = erfc(|k| / l), s = l = kappa / L_min.  The x-space kernel of I_1 is
+        erfc(l |x| / 2) / (2 pi |x|), so the same kappa gives the same decay at 2 L_min;
+        k2 = min(P, l erfc^{-1}(eps))."""
     Lmin = min(grid.L)
+    if kernel == "coulomb2d":
+        ell = kappa / Lmin
+        return ell, min(P, ell * float(special.erfcinv(eps)))
     a = (kappa / Lmin) ** 2
     return a, min(P, math.sqrt(a * math.log(1.0 / eps)))
 
 
+def partition(kernel: str, r, s: float):
+    """The partition of unity p(|k|) of Eq. (3.9) for this kernel (see split_params)."""
+    r = np.asarray(r, dtype=np.float64)
+    if kernel == "coulomb2d":
+        return special.erfc(r / s)
+    return np.exp(-r * r / s)
+
+
 def split_multiplier(kernel: str, K, a: float, dipole_axis=(0.0, 0.0, 1.0)):
-    """w(k) = (1 - exp(-|k|^2/a)) U-hat(k) at wave vectors K (list of d arrays); its value at
-    k = 0 is the limit (1/a for Coulomb, 0 for the dipolar kernel)."""
+    """w(k) = (1 - p(k)) U-hat(k) at wave vectors K (list of d arrays), with its limit at k = 0:
+      coulomb3d, poisson2d  (1 - exp(-|k|^2/a)) / |k|^2      -> 1/a      (an entire function of |k|^2)
+      dipole3d              (1 - exp(-|k|^2/a)) (3 (n.k)^2/|k|^2 - 1)  -> 0
+      coulomb2d             erf(|k| / l) / |k|  (a = l)          -> 2 / (l sqrt(pi))  (entire in |k|^2)"""
     k2 = sum(k * k for k in K)
-    one_m_p = -np.expm1(-k2 / a)
     with np.errstate(divide="ignore", invalid="ignore"):
-        if kernel == "coulomb3d":
+        if kernel in ("coulomb3d", "poisson2d"):
+            one_m_p = -np.expm1(-k2 / a)
             w = np.where(k2 > 0, one_m_p / k2, 1.0 / a)
         elif kernel == "dipole3d":
+            one_m_p = -np.expm1(-k2 / a)
             nv = np.asarray(dipole_axis, dtype=np.float64)
             nv = nv / np.linalg.norm(nv)
             nk = sum(c * k for c, k in zip(nv, K))
             w = np.where(k2 > 0, one_m_p * (3.0 * nk * nk / k2 - 1.0), 0.0)
+        elif kernel == "coulomb2d":
+            kr = np.sqrt(k2)
+            w = np.where(k2 > 0, special.erf(kr / a) / kr, 2.0 / (a * math.sqrt(math.pi)))
         else:
             raise ValueError(kernel)
     return w
@@ -159,14 +185,20 @@ def split_multiplier(kernel: str, K, a: float, dipole_axis=(0.0, 0.0, 1.0)):
 
 def evaluate_split(rho, grid, kernel, P, counts2=None, tol=1e-13, eps=1e-16, kappa=5.5,
                    dipole_axis=(0.0, 0.0, 1.0), return_parts=False):
-    """The improved algorithm (Sec. 2.1, Eq. (3.9)), 3D kernels: phi = I_1 + I_2.
+    """The improved algorithm (Sec. 2.1, Eq. (3.9)): phi = I_1 + I_2.
     I_1 = (2pi)^{-d} int w(k) rho-hat(k) e^{ik.x} dk by the rectangle rule on the frequencies of
           the doubled grid (spacing pi/L per axis) with the trapezoid rho-hat: the aperiodic
           layout x = (i - n/2) h placed at index (i - n/2) mod 2n, plain FFTs;
     I_2 = the quadrature of Eq. (ifft) on the ball |k| <= k2 with node weights multiplied by
-          p(k) = exp(-|k|^2/a), plain NUFFT."""
+          p(k), plain NUFFT.
+    poisson2d (U-hat = 1/|k|^2, d = 2): w = (1 - p)/|k|^2 is smooth, but p/|k|^2 is not
+          integrable at k = 0 in polar coordinates, so I_2 follows Algorithm 1 (Sec. 2.2): with
+          G_1 of Eq. (GG1), p rho-hat = p (rho-hat - G_1-hat) + p G_1-hat; the first term is
+          step 3 of Algorithm 1 with the factor p, the second is the potential of G_1 with
+          the Gaussian widened to sigma_u1^2 = sigma^2 + 2/a (p G_1-hat = G_1-hat at that
+          width), i.e. step 2 of Algorithm 1 with sigma_u1."""
     d = grid.dim
-    a, k2 = split_params(grid, P, eps, kappa)
+    a, k2 = split_params(grid, P, eps, kappa, kernel)
     n, h = grid.n, grid.h
     big = np.zeros(tuple(2 * m for m in n))
     idx = np.ix_(*[(np.arange(m) - m // 2) % (2 * m) for m in n])
@@ -177,13 +209,21 @@ def evaluate_split(rho, grid, kernel, P, counts2=None, tol=1e-13, eps=1e-16, kap
     I1 = np.real(np.fft.ifftn(w * np.fft.fftn(big)))[idx]
     if counts2 is None:
         counts2 = quadrature.default_counts(grid.L, k2)
-    t2, t1 = _transforms("nufft", tol)
-    k, wq, r, wj = node_set(kernel, k2, counts2, dipole_axis)
-    rh = t2(rho, h, k)
-    c = wj * np.exp(-r * r / a) * rh / (2.0 * math.pi) ** d
-    I2 = t1(c, k, n, h)
+    extra = {}
+    if kernel == "poisson2d":
+        sigma = poisson2d_sigma(k2)
+        sigma_u1 = math.sqrt(sigma * sigma + 2.0 / a)
+        I2 = poisson2d(rho, grid, k2, counts2, method="nufft", tol=tol, sigma=sigma,
+                       partition=lambda r: partition(kernel, r, a), sigma_u1=sigma_u1)
+        extra = dict(sigma=sigma, sigma_u1=sigma_u1)
+    else:
+        t2, t1 = _transforms("nufft", tol)
+        k, wq, r, wj = node_set(kernel, k2, counts2, dipole_axis)
+        rh = t2(rho, h, k)
+        c = wj * partition(kernel, r, a) * rh / (2.0 * math.pi) ** d
+        I2 = t1(c, k, n, h)
     if return_parts:
-        return I1 + I2, dict(a=a, k2=k2, I1=I1, I2=I2, counts2=counts2)
+        return I1 + I2, dict(a=a, k2=k2, I1=I1, I2=I2, counts2=counts2, **extra)
     return I1 + I2
 
 
