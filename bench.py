@@ -573,11 +573,77 @@ def twod_arm(args):
                 "stages_ms": res["stages"], "nodes": res["info"]["nodes_total"], "width": res["info"]["width"],
                 "cpu_baseline": {"value": 1.0 / t_or, "unit": "evals/s", "cores": native.max_threads(), "kind": "oracle",
                                  "sample": "one full 1024^2 %s evaluation by the FP64 oracle (tol 1e-13)" % kernel}}
+        # the improved algorithm (method 2) on the same workload
+        for prec in ("fp32", "fp64"):
+            res = run_precision(nl, torch, prec, g, rho, P, None, args.steps, args.warmup, flush, stream,
+                                e2e=False, kernel=kernel, method=2)
+            t = sum(res["times"]) / 1e3
+            out["%s_%s_method2" % (kernel, prec)] = {
+                "value": len(res["times"]) / t, "unit": "evals/s", "ms_per_step": 1e3 * t / len(res["times"]),
+                "rel_linf_vs_oracle": cf.rel_linf(res["phi"], ref),
+                "rel_linf_vs_closed_form": cf.rel_linf(res["phi"], exact),
+                "nodes": res["info"]["nodes_total"], "radius": res["info"]["split_radius"]}
+    out["paper_timing_table"] = paper_2d_poisson_table(nl, torch, args, flush, stream)
     clocks = clk.stop()
     print(json.dumps({"metric": "2D phi=U*rho evals/s, 1024^2, three Gaussians", "steps": args.steps,
                       "warmup": args.warmup, "config": {"grid": [1024, 1024], "L": 16.0, "P": P,
                       "quadrature": list(counts), "l2": "flushed between timed steps (512 MB write)"},
                       "results": out, "clocks": clocks, "dtype": "f32/f64", "data": "synthetic"}))
+
+
+# Table tab:2d:Poisson:time: CPU seconds of the paper's Fortran code (one i7-3520M core, debug
+# build) for the 2D Poisson potential of rho = exp(-r^2/1.3) on [-16,16]^2: (h, T_FFT, T_NUFFT, T_total)
+PAPER_2D_POISSON_TIME = ((1.0, 0.01, 0.05, 0.06), (0.5, 0.02, 0.08, 0.10), (0.25, 0.12, 0.20, 0.32),
+                         (0.125, 0.60, 0.78, 1.38))
+
+
+def paper_2d_poisson_table(nl, torch, args, flush, stream):
+    """The configuration of Table tab:2d:Poisson:time through method 2 (FP64): per h the device
+    time of I_2 (small-ball NUFFT with Algorithm 1) and of I_1 (FFT convolution), from the
+    stage events of each timed evaluation, beside the printed CPU seconds; the error against the
+    E_1 closed form beside the printed e_h of Table tab_NUFFT_2D_Poisson."""
+    from oracle import closed_forms as cf
+    rows = []
+    s = math.sqrt(1.3)
+    for h, t_fft, t_nufft, t_tot in PAPER_2D_POISSON_TIME:
+        n = int(round(32 / h))
+        g = W.Grid((n, n), (16.0, 16.0))
+        X, Y = g.mesh()
+        rho = np.exp(-(X * X + Y * Y) / (s * s))
+        plan = nl.Plan(g.n, g.L, "poisson2d", "fp64", kmax=math.pi / h, method=2, stream=stream)
+        with torch.cuda.stream(stream):
+            r = torch.from_numpy(rho).to("cuda", torch.float64)
+            phi = torch.empty_like(r)
+        for _ in range(args.warmup):
+            nl.nlp_eval_potential(plan.handle, r, phi)
+        nl.nlp_set_stage_timing(plan.handle, True)
+        tot, i1, i2 = [], 0.0, 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nl.nlp_eval_potential(plan.handle, r, phi)
+            b.record(stream)
+            st = nl.nlp_get_stage_times(plan.handle)
+            names = [nm for nm, _ in st]
+            cut = [i for i, nm in enumerate(names) if nm == "fwd_last"][-1]   # I_1 starts at its R2C pass
+            i2 += sum(ms for _, ms in st[:cut])
+            i1 += sum(ms for _, ms in st[cut:])
+            b.synchronize()
+            tot.append(a.elapsed_time(b))
+        nl.nlp_set_stage_timing(plan.handle, False)
+        stream.synchronize()
+        err = cf.rel_linf(phi.double().cpu().numpy(), cf.poisson2d_iso(np.sqrt(X * X + Y * Y), s))
+        info = plan.info
+        plan.close()
+        K = args.steps
+        rows.append({"h": h, "grid": [n, n], "ms_total": sum(tot) / K, "ms_I1_fft": i1 / K, "ms_I2_nufft": i2 / K,
+                     "nodes_I2": info["nodes_total"], "radius_I2": info["split_radius"],
+                     "rel_linf_vs_closed_form": err,
+                     "paper_cpu_s": {"T_FFT": t_fft, "T_NUFFT": t_nufft, "T_total": t_tot}})
+    return {"note": "Table tab:2d:Poisson:time configuration, FP64 method 2; paper: one i7-3520M core, "
+                    "Fortran -g, seconds (context, other hardware)", "rows": rows}
 
 
 def oned_arm(args):

@@ -101,14 +101,22 @@ typedef struct {
                                grid) and each evaluation is an aperiodic convolution by FFT on the
                                2n grid.  Not for NLP_POISSON_2D (its operator is not translation
                                invariant): NLP_ERR_UNSUPPORTED.
-                               2 = the improved algorithm (Sec. 2.1, Eq. (3.9)), 3D kernels only: with
-                               the partition p(k) = exp(-|k|^2/a), phi = I_1 + I_2 where I_1 takes
-                               (1 - p) U-hat by the rectangle rule on the 2n grid's frequencies (an FFT
-                               convolution with an analytic multiplier) and I_2 takes p U-hat by the
-                               quadrature of Eq. (ifft) on the ball |k| <= k2 = min(P, sqrt(a ln 1/eps))
-                               (NUFFT with few nodes); a = (kappa / min L)^2 with (kappa, eps) =
-                               (5.5, 1e-16) for FP64 and (3.8, 1e-8) for FP32 plans.  Default counts
-                               then follow from k2 instead of P.  2D kernels: NLP_ERR_UNSUPPORTED. */
+                               2 = the improved algorithm (Sec. 2.1, Eq. (3.9); Fig. 3.1): with a
+                               partition of unity p(k), phi = I_1 + I_2 where I_1 takes (1 - p) U-hat
+                               by the rectangle rule on the 2n grid's frequencies (an FFT convolution
+                               with an analytic multiplier over the whole frequency box) and I_2 takes
+                               p U-hat by the quadrature of Eq. (ifft) on the ball |k| <= k2 where
+                               p >= eps (NUFFT with few nodes).  (kappa, eps) = (5.5, 1e-16) for FP64
+                               and (3.8, 1e-8) for FP32 plans; default counts follow from k2.
+                               NLP_COULOMB_3D, NLP_DIPOLE_3D: p = exp(-|k|^2/a), a = (kappa/min L)^2,
+                                 k2 = min(P, sqrt(a ln 1/eps)).
+                               NLP_COULOMB_2D: p = erfc(|k|/l), l = kappa/min L (w = erf(|k|/l)/|k| is
+                                 smooth at k = 0, which no Gaussian p gives for U-hat = 1/|k|),
+                                 k2 = min(P, l erfc^-1(eps)).
+                               NLP_POISSON_2D: p = exp(-|k|^2/a) (w = (1 - p)/|k|^2 is smooth); I_2 is
+                                 Algorithm 1 on the small ball with the integrand of u_2 times p and
+                                 u_1 taken with the width sqrt(sigma^2 + 2/a), sigma = 6 sqrt(2)/k2.
+                               NLP_CONFINED_2D and 1D plans: NLP_ERR_UNSUPPORTED. */
     int reserved[5];        /* must be zero */
     double confine_eps;     /* NLP_CONFINED_2D: the confinement ratio eps >= 0 (else ignored) */
 } nlp_opts;
@@ -129,9 +137,9 @@ typedef struct {
     int tile;
     size_t workspace_bytes; /* device memory owned by the plan */
     double sigma_poisson;   /* NLP_POISSON_2D: width of the auxiliary Gaussian */
-    int sub_tile;           /* register kernel sub-tile edge (0: shared-memory-atomics kernel) */
+    int sub_tile;           /* register-column kernel sub-tile edge (0: the generic one-warp-per-node kernel) */
     int64_t segments;       /* register kernel work units (node runs of one sub-tile) */
-    double split_a;         /* method 2: partition parameter a (0 otherwise) */
+    double split_a;         /* method 2: partition parameter, a (Gaussian p) or l (erfc p); 0 otherwise */
     double split_radius;    /* method 2: radius k2 of the NUFFT ball of I_2 (0 otherwise) */
     int64_t combine_entries;/* window slots summed by the combine pass, over all tiles of G */
 } nlp_plan_info;

@@ -27,7 +27,7 @@ template <typename T>
 nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     cudaStream_t st = p->stream;
     const bool three = p->grid.dim == 3;
-    const bool pois = p->kernel == NLP_POISSON_2D;
+    const bool pois = p->kernel == NLP_POISSON_2D && D.mom != nullptr;   // not the I_1 part of method 2
     const int64_t nh = D.nh;
     if (pois) {
         NLP_CUDA_TRY(launch_poisson_moments<T>(rho, D, p->L3, p->h, p->d_red, p->red_blocks, (double *)D.mom, st));

@@ -627,7 +627,7 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         void *du;
         const int64_t Ng = (int64_t)p->n3[1] * p->n3[2];
         if ((s = alloc_dev(p, &du, sizeof(double) * 3 * (size_t)Ng))) return s;
-        if (launch_u1_table((double *)du, p->n3[1], p->n3[2], p->L3, p->h, p->sigma, p->stream) != cudaSuccess)
+        if (launch_u1_table((double *)du, p->n3[1], p->n3[2], p->L3, p->h, p->sigma_u1, p->stream) != cudaSuccess)
             return NLP_ERR_CUDA;
         D.u1tab = (const double *)du;
     }
@@ -682,6 +682,16 @@ nlp_status build_toeplitz(nlp_plan_s *p);
 
 static int roundup16(double x) { return (int)(16.0 * std::ceil(x / 16.0)); }
 
+// x with erfc(x) = y, 0 < y < 1: bisection on [0, 30] to the last bit (erfc is decreasing)
+static double erfc_inverse(double y) {
+    double lo = 0.0, hi = 30.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        (std::erfc(mid) > y ? lo : hi) = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
 nlp_status plan_build_1d(nlp_plan_s *p);
 
 nlp_status plan_build(nlp_plan_s *p) {
@@ -705,7 +715,10 @@ nlp_status plan_build(nlp_plan_s *p) {
     Rp2 = g.L[0] * g.L[0] + g.L[1] * g.L[1];
     const double Ptrunc = p->opts.kmax > 0 ? p->opts.kmax : M_PI / hmax;
     // improved algorithm (method 2): the NUFFT part I_2 only needs the ball where the
-    // partition p(k) = exp(-|k|^2/a) is above eps (Eq. (3.9)); I_1 is built after the nodes
+    // partition p(k) is above eps (Eq. (3.9)); I_1 is built after the nodes.  p = exp(-|k|^2/a)
+    // for the 3D kernels and the 2D Laplace kernel, p = erfc(|k|/l) for 2D Coulomb (the only
+    // choice of the two for which (1 - p)/|k| is smooth at k = 0); the scale puts the decay of
+    // I_1's x-space kernel at the doubled grid's nearest image (distance 2 min L) near eps.
     double P = Ptrunc;
     if (p->opts.method == 2) {
         const bool f64 = p->prec == NLP_FP64;
@@ -713,8 +726,14 @@ nlp_status plan_build(nlp_plan_s *p) {
         double Lmin = g.L[0];
         for (int a = 1; a < d; ++a) Lmin = std::min(Lmin, g.L[a]);
         p->split = 1;
-        p->split_a = (kappa / Lmin) * (kappa / Lmin);
-        p->split_k2 = std::min(Ptrunc, std::sqrt(p->split_a * std::log(1.0 / eps)));
+        if (p->kernel == NLP_COULOMB_2D) {
+            p->split_erfc = 1;
+            p->split_a = kappa / Lmin;
+            p->split_k2 = std::min(Ptrunc, p->split_a * erfc_inverse(eps));
+        } else {
+            p->split_a = (kappa / Lmin) * (kappa / Lmin);
+            p->split_k2 = std::min(Ptrunc, std::sqrt(p->split_a * std::log(1.0 / eps)));
+        }
         P = p->split_k2;
         p->info.split_a = p->split_a;
         p->info.split_radius = p->split_k2;
@@ -799,6 +818,8 @@ nlp_status plan_build(nlp_plan_s *p) {
                     hn.omega = pref * wr[ia] * wph * confined_w1(p->opts.confine_eps * r[ia]);
                 else
                     hn.omega = pref * wr[ia] * wph;    // Coulomb 2D: |k| U-hat = 1
+                if (p->split)                          // p(k) of Eq. (3.9)
+                    hn.omega *= p->split_erfc ? std::erfc(r[ia] / p->split_a) : std::exp(-r[ia] * r[ia] / p->split_a);
                 hn.z[0] = 0.0;
                 hn.z[1] = k[0] * p->h[1] * (2.0 * p->n3[1]) / twopi;
                 hn.z[2] = k[1] * p->h[2] * (2.0 * p->n3[2]) / twopi;
@@ -812,6 +833,9 @@ nlp_status plan_build(nlp_plan_s *p) {
     p->info.nodes_half = (int64_t)nodes.size();
     if (p->kernel == NLP_POISSON_2D) p->sigma = 6.0 * std::sqrt(2.0) / P;
     p->info.sigma_poisson = p->sigma;
+    // u_1 of Algorithm 1; with the partition, p G_1-hat is G_1-hat of the Gaussian widened by
+    // exp(-|k|^2/a) = exp(-(2/a)|k|^2/2), whose potential u_1 has sigma^2 + 2/a
+    p->sigma_u1 = p->split ? std::sqrt(p->sigma * p->sigma + 2.0 / p->split_a) : p->sigma;
 
     nlp_status s = (p->prec == NLP_FP64) ? build_device<double>(p, nodes, p->pd) : build_device<float>(p, nodes, p->pf);
     if (s) return s;
@@ -852,7 +876,8 @@ nlp_status validate(const nlp_grid *g, nlp_kernel kernel, nlp_precision prec, co
         if (o->spread_variant < 0 || o->spread_variant > 1) return NLP_ERR_INVALID_ARG;
         if (o->method < 0 || o->method > 2) return NLP_ERR_INVALID_ARG;
         if (o->method == 1 && kernel == NLP_POISSON_2D) return NLP_ERR_UNSUPPORTED;
-        if (o->method == 2 && g->dim != 3) return NLP_ERR_UNSUPPORTED;
+        if (o->method == 2 && !(g->dim == 3 || kernel == NLP_COULOMB_2D || kernel == NLP_POISSON_2D))
+            return NLP_ERR_UNSUPPORTED;
         if (o->method == 1)   // the kernel is built on a 4n-point fine grid
             for (int a = 0; a < g->dim; ++a)
                 if (4 * g->n[a] > kMaxFftLen) return NLP_ERR_UNSUPPORTED;

@@ -21,6 +21,7 @@ struct nlp_plan_s {
     size_t bytes = 0;
     // 2D Poisson (Algorithm 1) extras
     double sigma = 0;
+    double sigma_u1 = 0;   // width of u_1's Gaussian (sigma, or widened by the method-2 partition)
     double *d_pois = nullptr;           // per-node FP64 data: kx, ky, r (hemisphere order)
     double *d_red = nullptr;            // FP64 reduction scratch
     int red_blocks = 0;
@@ -41,7 +42,8 @@ struct nlp_plan_s {
     // improved algorithm (method 2): I_2 is the NUFFT of pf / pd (small ball), I_1 the FFT
     // convolution described by pf1 / pd1 (analytic multiplier, accumulating into phi)
     int split = 0;
-    double split_a = 0, split_k2 = 0;
+    double split_a = 0, split_k2 = 0;   // partition scale (a, or l for the erfc partition), ball radius
+    int split_erfc = 0;                 // 1: p = erfc(|k|/l) (2D Coulomb), 0: p = exp(-|k|^2/a)
     nlp::DevPlan<float> pf1{};
     nlp::DevPlan<double> pd1{};
     // 1D Poisson (NLP_POISSON_1D): FFT length 2n, zero-padded complex work array, FP64 moments

@@ -76,11 +76,11 @@ def test_null_handles_rejected(nl):
     lib.nlp_batch_destroy(None)
 
 
-@pytest.mark.parametrize("kernel,n", [("coulomb2d", (64, 64)), ("poisson2d", (64, 64))])
-def test_split_method_rejects_2d(nl, kernel, n):
-    """method = 2 (the improved algorithm with the Gaussian partition) is 3D only."""
+def test_split_method_rejects_confined2d(nl):
+    """method = 2 (the improved algorithm) covers 3D Coulomb/dipolar and 2D Coulomb/Poisson; the
+    confined 2D kernel has no partition here."""
     with pytest.raises(nl.NlpError) as e:
-        nl.nlp_plan_create(n, (8, 8), kernel, "fp64", method=2, stream=0)
+        nl.nlp_plan_create((64, 64), (8, 8), "confined2d", "fp64", method=2, eps=0.5, stream=0)
     assert e.value.status == nl.NLP_ERR_UNSUPPORTED
 
 

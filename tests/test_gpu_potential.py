@@ -290,6 +290,65 @@ def test_split_method_full_size(nl, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
+@pytest.mark.parametrize("shape", [((96, 80), (10.0, 9.0)), ((250, 216), (12.0, 11.0))])
+def test_split_method_parity_2d(nl, prec, kernel, shape):
+    """method = 2 in 2D (Sec. 2.1, Eq. (3.9), Fig. 3.1): erfc partition for 2D Coulomb, Gaussian
+    partition with Algorithm 1 on the small ball for 2D Poisson; ragged grids (several tiles and
+    partial ones, radix-5 fine sizes), against the oracle's split with the same parameters."""
+    g = W.Grid(*shape)
+    cs, ws = W.three_gaussians_2d(17)
+    rho = W.gaussian_sum(g, [(0.5 * c[0], 0.5 * c[1]) for c in cs], ws)
+    P = quadrature.density_P(min(ws), max(g.h))
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, method=2)
+    ref, parts = potential.evaluate_split(rho, g, kernel, P, return_parts=True, **SPLIT[prec])
+    assert abs(info["split_a"] - parts["a"]) < 1e-12 * parts["a"]
+    assert abs(info["split_radius"] - parts["k2"]) < 1e-12 * parts["k2"]
+    err = cf.rel_linf(phi, ref)
+    print("%s %s %s split: vs oracle split %.3e, radius %.3f of P %.3f" % (shape[0], kernel, prec, err,
+                                                                          info["split_radius"], P))
+    assert err < TOL[prec]
+    assert info["split_radius"] < 0.5 * P
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
+def test_split_method_2d_full_size(nl, kernel, prec):
+    """The 2D workload at full size (1024^2 over [-16,16)^2, three Gaussians) through method 2,
+    against the oracle's split and against the plain FP64 quadrature of the full ball (the same
+    continuum integral), FP64 1e-10 and FP32 1e-5."""
+    g, cs, ws, rho = _config_2d()
+    P = quadrature.density_P(min(ws), g.h[0])
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, method=2, tol=tol)
+    ref = potential.evaluate_split(rho, g, kernel, P, **SPLIT[prec])
+    plain = potential.eval_nufft(rho, g, kernel, P, quadrature.default_counts(g.L, P), tol=1e-13)
+    e1, e2 = cf.rel_linf(phi, ref), cf.rel_linf(phi, plain)
+    print("1024^2 %s %s split: vs oracle split %.3e, vs plain %.3e, I_2 nodes %d" % (kernel, prec, e1, e2,
+                                                                                    info["nodes_total"]))
+    assert e1 < TOL[prec] and e2 < TOL[prec]
+
+
+@pytest.mark.parametrize("h,paper", [(0.5, 1.391e-9), (0.25, 4.577e-14), (0.125, 4.561e-14)])
+def test_split_method_reproduces_2d_poisson_table(nl, h, paper):
+    """Ex. 2.3 (rho = exp(-r^2/1.3) on [-16,16]^2), the configuration of Tables
+    tab_NUFFT_2D_Poisson and tab:2d:Poisson:time, FP64 method 2 against the E_1 closed form:
+    the printed truncation level at h = 1/2 within 5%, the FP64 floor (<= 2e-13) below."""
+    n = int(round(32 / h))
+    g = W.Grid((n, n), (16.0, 16.0))
+    X, Y = g.mesh()
+    s = math.sqrt(1.3)
+    rho = np.exp(-(X * X + Y * Y) / (s * s))
+    phi, _ = gpu_eval(nl, g, rho, "poisson2d", "fp64", kmax=math.pi / h, method=2)
+    e = cf.rel_linf(phi, cf.poisson2d_iso(np.sqrt(X * X + Y * Y), s))
+    print("2D Poisson L=16 h=%g: %.3e (printed %.3e)" % (h, e, paper))
+    if h >= 0.5:
+        assert abs(e - paper) < 0.05 * paper
+    else:
+        assert e < 2e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("eps", [0.1, 0.5])
 def test_confined2d_parity(nl, prec, method, eps):
