@@ -717,6 +717,7 @@ def groundstate_arm(args):
     hist = SG.train(sur, feats, resid, steps=args.gs_train_steps, batch=64, lr=3e-3, lr_final=7.5e-5, log_every=500)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    kernels = surrogate_kernel_times(sur, feats, resid, torch)
     del targets, resid
     solver = SG.GroundStateSolver(96, 10.0)
     cases = []
@@ -746,7 +747,47 @@ def groundstate_arm(args):
         "training": {"states": len(params), "grid": [48, 48, 48], "generation_wall_s": t_gen,
                      "generation_device_s": sum(i["seconds"] for i in info),
                      "train_steps": args.gs_train_steps, "train_s": t_train, "loss": hist},
+        "train_step_kernels": kernels,
         "dtype": "f64 flow / bf16+f32 network", "data": "synthetic"}))
+
+
+# dense layers of the network (in, out) and its 3^3 convolutions (C_in, C_out, grid edge)
+SURROGATE_DENSE = ((64, 512), (512, 512), (512, 512), (512, 512), (512, 1792))
+SURROGATE_CONV = ((8, 8, 12), (8, 8, 24), (8, 1, 48))
+SURROGATE_GEMM_ROWS = 128   # the padded batch: M of every forward GEMM
+
+
+def surrogate_kernel_times(sur, feats, resid, torch, steps=20, batch=64):
+    """Per-class device time of a training step (the library's CUDA-event timers), measured on
+    extra steps after training with the trained parameters restored afterwards, and the
+    achieved rate of the tensor-core GEMMs (BF16) and the convolutions (FP32 CUDA cores)."""
+    saved = sur.get_params()
+    idx = torch.arange(batch, device=feats.device) % feats.shape[0]
+    f, t = feats[idx].contiguous(), resid[idx].contiguous()
+    sur.set_timing(True)
+    for _ in range(steps):
+        sur.train_step(f, t, lr=1e-5, want_loss=False)
+    torch.cuda.synchronize()
+    times = sur.kernel_times()
+    sur.set_timing(False)
+    sur.set_params(saved)
+    M = SURROGATE_GEMM_ROWS
+    # forward C = X W^T, backward dW = dP^T X (all layers) and dX = dP W (all but the first)
+    gemm_flop = sum(2 * M * a * b for a, b in SURROGATE_DENSE) * 2 + sum(2 * M * a * b for a, b in SURROGATE_DENSE[1:])
+    conv_flop = sum(2 * batch * ci * co * 27 * g ** 3 for ci, co, g in SURROGATE_CONV)   # per direction
+    out = {}
+    for c, (ms, n) in times.items():
+        out[c] = {"ms_per_step": ms / steps, "launches_per_step": n / steps}
+    g_ms = out["gemm"]["ms_per_step"]
+    out["gemm"]["tflops"] = gemm_flop / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
+    out["gemm"]["flop_per_step"] = gemm_flop
+    for c in ("conv_fwd", "conv_bwd_in", "conv_bwd_w"):
+        ms = out[c]["ms_per_step"]
+        out[c]["tflops"] = conv_flop / (ms * 1e-3) / 1e12 if ms > 0 else None
+        out[c]["flop_per_step"] = conv_flop
+    out["note"] = ("CUDA events after every launch of %d training steps at batch %d (each interval "
+                   "includes the launch gap before its kernel); GEMM flop at the padded 128 rows" % (steps, batch))
+    return out
 
 
 def batch_quadrature(g, widths):
@@ -794,8 +835,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="metric", choices=["metric", "batch", "2d", "1d", "groundstate"])
-    ap.add_argument("--gs-train", type=int, default=192, help="training ground states (groundstate workload)")
-    ap.add_argument("--gs-heldout", type=int, default=4, help="held-out problems timed at 96^3")
+    ap.add_argument("--gs-train", type=int, default=2000, help="training ground states (groundstate workload)")
+    ap.add_argument("--gs-heldout", type=int, default=16, help="held-out problems timed at 96^3")
     ap.add_argument("--gs-train-steps", type=int, default=4000)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],

@@ -362,6 +362,29 @@ nlp_status nlp_surrogate_initial_guess(nlp_surrogate s, double beta, double gamm
 
 void nlp_surrogate_destroy(nlp_surrogate s);
 
+/* Kernel classes of a training step, for the per-class timers below. */
+enum {
+    NLP_SK_GEMM = 0,        /* dense layers: the tensor-core GEMM (mode 1: the FP32 one) */
+    NLP_SK_CONV_FWD = 1,    /* 3^3 convolutions, forward */
+    NLP_SK_CONV_BWD_IN = 2, /* 3^3 convolutions, gradient of the input */
+    NLP_SK_CONV_BWD_W = 3,  /* 3^3 convolutions, gradient of the weights (both stages) */
+    NLP_SK_ELEMENTWISE = 4, /* bias/activation, upsampling, BF16 conversion, packing */
+    NLP_SK_LOSS = 5,        /* mean squared error and its gradient */
+    NLP_SK_ADAMW = 6,       /* the optimizer step */
+    NLP_SK_COUNT = 7
+};
+
+/* Per-class kernel timers of nlp_surrogate_train_step (measurement, not part of the method).
+ * on != 0: every later training step records a CUDA event after each of its launches on the
+ * object's stream and, at its end, waits for the last event and adds each interval to the
+ * class of the launch that ended it (so an interval also holds the launch gap before that
+ * kernel).  Enabling or disabling resets the totals.  The first enable creates the events. */
+nlp_status nlp_surrogate_set_timing(nlp_surrogate s, int on);
+
+/* ms[NLP_SK_COUNT]: milliseconds per class summed since the timers were enabled;
+ * launches[NLP_SK_COUNT] (may be NULL): launches per class. */
+nlp_status nlp_surrogate_get_kernel_times(nlp_surrogate s, double *ms, int64_t *launches);
+
 /* Test hook for the tensor-core GEMM of the network: C[M x N] (FP32) = A[M x K] B[N x K]^T,
  * A and B BF16 row-major device arrays; M % 128 == 0, K % 64 == 0, N % 64 == 0.
  * Synchronizes; NLP_ERR_TIMEOUT if a tensor-core wait ran out. */

@@ -89,6 +89,8 @@ def _load():
         "nlp_surrogate_initial_guess": ([P, D, D, I, ctypes.POINTER(nlp_grid), I, P], I),
         "nlp_surrogate_base": ([P, P, I, P], I),
         "nlp_surrogate_destroy": ([P], None),
+        "nlp_surrogate_set_timing": ([P, I], I),
+        "nlp_surrogate_get_kernel_times": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)], I),
         "nlp_gemm_bf16": ([P, P, P, I, I, I, P], I),
         "nlp_status_string": ([I], ctypes.c_char_p),
         "nlp_version": ([], ctypes.c_char_p),
@@ -436,6 +438,19 @@ class Surrogate:
                                              float(weight_decay), ctypes.byref(loss) if want_loss else None),
                "nlp_surrogate_train_step")
         return loss.value if want_loss else None
+
+    KERNEL_CLASSES = ("gemm", "conv_fwd", "conv_bwd_in", "conv_bwd_w", "elementwise", "loss", "adamw")
+
+    def set_timing(self, on: bool):
+        _check(_lib.nlp_surrogate_set_timing(self.handle, 1 if on else 0), "nlp_surrogate_set_timing")
+
+    def kernel_times(self) -> dict:
+        """{class: (milliseconds, launches)} summed over the training steps since set_timing(True)."""
+        n = len(self.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(_lib.nlp_surrogate_get_kernel_times(self.handle, ms, cnt), "nlp_surrogate_get_kernel_times")
+        return {c: (ms[i], int(cnt[i])) for i, c in enumerate(self.KERNEL_CLASSES)}
 
     def base(self, gamma, out=None):
         """The beta = 0 amplitude on the 48^3 cube for each gamma (device FP32 [B])."""

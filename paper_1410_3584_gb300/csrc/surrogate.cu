@@ -438,7 +438,39 @@ struct nlp_surrogate_s {
     double *part = nullptr;
     int *err = nullptr;
     long long step = 0;
+    // optional per-class kernel timers: an event after every launch, attributed to its class
+    bool timing = false;
+    static constexpr int kMaxEv = 160;
+    cudaEvent_t ev[kMaxEv] = {};
+    int ev_cls[kMaxEv] = {};
+    int nev = 0;
+    double cls_ms[NLP_SK_COUNT] = {};
+    long long cls_n[NLP_SK_COUNT] = {};
 };
+
+// record the end of the launch just issued (class cls; -1 = the start mark)
+static void mark(nlp_surrogate_s *s, int cls) {
+    if (!s->timing || s->nev >= nlp_surrogate_s::kMaxEv) return;
+    cudaEventRecord(s->ev[s->nev], s->stream);
+    s->ev_cls[s->nev++] = cls;
+}
+
+// fold the recorded events into the per-class totals (waits for the last one)
+static void collect(nlp_surrogate_s *s) {
+    if (!s->timing || s->nev < 2) {
+        s->nev = 0;
+        return;
+    }
+    cudaEventSynchronize(s->ev[s->nev - 1]);
+    for (int i = 1; i < s->nev; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev[i - 1], s->ev[i]) == cudaSuccess && s->ev_cls[i] >= 0) {
+            s->cls_ms[s->ev_cls[i]] += ms;
+            s->cls_n[s->ev_cls[i]]++;
+        }
+    }
+    s->nev = 0;
+}
 
 static nlp_status sg_alloc(nlp_surrogate_s *s, void **p, size_t bytes) {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
@@ -468,9 +500,12 @@ static nlp_status gemm(nlp_surrogate_s *s, const __nv_bfloat16 *A, const __nv_bf
                        const float *B32, float *C, int M, int N, int K) {
     if (s->mode) {
         k_gemm_f32_simt<<<dim3((N + 15) / 16, (M + 15) / 16), 256, 0, s->stream>>>(A32, B32, C, M, N, K);
+        mark(s, NLP_SK_GEMM);
         return cudaGetLastError() == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
     }
-    return launch_gemm_tc(A, B, C, M, N, K, s->err, s->stream) == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+    const bool ok = launch_gemm_tc(A, B, C, M, N, K, s->err, s->stream) == cudaSuccess;
+    mark(s, NLP_SK_GEMM);
+    return ok ? NLP_OK : NLP_ERR_CUDA;
 }
 
 static void refresh_weights(nlp_surrogate_s *s) {
@@ -478,6 +513,7 @@ static void refresh_weights(nlp_surrogate_s *s) {
         const int ni = s->lay.nin[l], no = s->lay.nout[l];
         k_convert<<<grid_for((int64_t)ni * no), 256, 0, s->stream>>>(s->P + s->lay.W[l], s->Wbf[l], s->Wtbf[l],
                                                                      s->mode ? s->Wt32[l] : nullptr, no, ni);
+        mark(s, NLP_SK_ELEMENTWISE);
     }
 }
 
@@ -486,24 +522,30 @@ static nlp_status forward(nlp_surrogate_s *s, const float *feat, int B) {
     const Layout &L = s->lay;
     nlp_status r;
     k_input<<<grid_for((int64_t)kBP * kFeatPad), 256, 0, st>>>(feat, B, s->X[0], s->Xbf[0], s->Xtbf[0]);
+    mark(s, NLP_SK_ELEMENTWISE);
     for (int l = 0; l < 5; ++l) {
         const int ni = L.nin[l], no = L.nout[l];
         if ((r = gemm(s, s->Xbf[l], s->Wbf[l], s->X[l], s->P + L.W[l], s->Cbuf, kBP, no, ni))) return r;
         k_bias_act<<<grid_for((int64_t)kBP * no), 256, 0, st>>>(s->Cbuf, s->P + L.b[l], s->pre[l], s->X[l + 1],
                                                                 s->Xbf[l + 1], s->Xtbf[l + 1], B, no, l < 4);
+        mark(s, NLP_SK_ELEMENTWISE);
     }
     k_head_unpack<<<grid_for((int64_t)B * kHeadOut), 256, 0, st>>>(s->X[5], s->z0, B);
+    mark(s, NLP_SK_ELEMENTWISE);
     const float *prev = s->z0;
     int g = 6;
     for (int c = 0; c < kConv; ++c) {
         const int64_t BC = (int64_t)B * kConvCi[c], G3 = (int64_t)kConvG[c] * kConvG[c] * kConvG[c];
         k_up2<<<grid_for(BC * G3), 256, 0, st>>>(prev, s->cin[c], BC, g);
+        mark(s, NLP_SK_ELEMENTWISE);
         g = kConvG[c];
         k_conv_fwd<<<grid_for((int64_t)B * kConvCo[c] * G3), 256, 0, st>>>(s->cin[c], s->P + L.cw[c], s->P + L.cb[c],
                                                                           s->cpre[c], B, kConvCi[c], kConvCo[c], g);
+        mark(s, NLP_SK_CONV_FWD);
         if (c + 1 < kConv) {
             k_silu<<<grid_for((int64_t)B * kConvCo[c] * G3), 256, 0, st>>>(s->cpre[c], s->cact[c],
                                                                           (int64_t)B * kConvCo[c] * G3);
+            mark(s, NLP_SK_ELEMENTWISE);
             prev = s->cact[c];
         }
     }
@@ -524,36 +566,47 @@ static nlp_status backward(nlp_surrogate_s *s, const float *target, int B, doubl
     const Layout &L = s->lay;
     const int64_t nout = (int64_t)B * kOut;
     k_mse<<<kRedBlocks, 256, 0, st>>>(s->cpre[kConv - 1], target, s->dout, nout, s->part);
+    mark(s, NLP_SK_LOSS);
     const float *dnext = s->dout;   // gradient w.r.t. the current conv output (pre-activation)
     for (int c = kConv - 1; c >= 0; --c) {
         const int Ci = kConvCi[c], Co = kConvCo[c], g = kConvG[c];
         const int64_t G3 = (int64_t)g * g * g, total = (int64_t)B * G3;
         const int S = (int)std::max<int64_t>(1, std::min<int64_t>(64, total / (256 * 32)));
         k_conv_bwd_w_part<<<dim3(Co * (Ci + 1), S), 256, 0, st>>>(dnext, s->cin[c], s->wpart, B, Ci, Co, g, S);
+        mark(s, NLP_SK_CONV_BWD_W);
         k_conv_bwd_w_final<<<grid_for((int64_t)Co * (Ci + 1) * 27), 256, 0, st>>>(s->wpart, s->Gr + L.cw[c],
                                                                                    s->Gr + L.cb[c], Ci, Co, S);
+        mark(s, NLP_SK_CONV_BWD_W);
         k_conv_bwd_in<<<grid_for((int64_t)B * Ci * G3), 256, 0, st>>>(dnext, s->P + L.cw[c], s->dcin[c], B, Ci, Co, g);
+        mark(s, NLP_SK_CONV_BWD_IN);
         const int gp = g / 2;
         const int64_t BC = (int64_t)B * Ci, gp3 = (int64_t)gp * gp * gp;
         if (c > 0) {
             k_up2_back<<<grid_for(BC * gp3), 256, 0, st>>>(s->dcin[c], s->dcact[c - 1], BC, gp);
+            mark(s, NLP_SK_ELEMENTWISE);
             k_silu_back<<<grid_for(BC * gp3), 256, 0, st>>>(s->dcact[c - 1], s->cpre[c - 1], s->dcpre[c - 1], BC * gp3);
+            mark(s, NLP_SK_ELEMENTWISE);
             dnext = s->dcpre[c - 1];
         } else {
             k_up2_back<<<grid_for(BC * gp3), 256, 0, st>>>(s->dcin[c], s->dz0, BC, gp);
+            mark(s, NLP_SK_ELEMENTWISE);
         }
     }
     k_head_pack<<<grid_for((int64_t)kBP * kHeadPad), 256, 0, st>>>(s->dz0, s->dY, B);
+    mark(s, NLP_SK_ELEMENTWISE);
     nlp_status r;
     for (int l = 4; l >= 0; --l) {
         const int ni = L.nin[l], no = L.nout[l];
         k_act_back<<<grid_for((int64_t)kBP * no), 256, 0, st>>>(s->dY, s->pre[l], s->dP, s->dPbf, s->dPtbf, B, no,
                                                                 l < 4);
+        mark(s, NLP_SK_ELEMENTWISE);
         k_colsum<<<grid_for(no), 256, 0, st>>>(s->dP, s->Gr + L.b[l], no);
+        mark(s, NLP_SK_ELEMENTWISE);
         // dW [no x ni] = dPre^T X : A = dPre^T [no x kBP], B = X^T [ni x kBP]
         if (s->mode) {
             k_convert<<<grid_for((int64_t)kBP * no), 256, 0, st>>>(s->dP, nullptr, nullptr, s->dPt32, kBP, no);
             k_convert<<<grid_for((int64_t)kBP * ni), 256, 0, st>>>(s->X[l], nullptr, nullptr, s->Xt32, kBP, ni);
+            mark(s, NLP_SK_ELEMENTWISE);
         }
         if ((r = gemm(s, s->dPtbf, s->Xtbf[l], s->dPt32, s->Xt32, s->Gr + L.W[l], no, ni, kBP))) return r;
         // dX [kBP x ni] = dPre W : A = dPre [kBP x no], B = W^T [ni x no]; the next layer's dY
@@ -585,6 +638,8 @@ void nlp_surrogate_destroy(nlp_surrogate s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
     for (void *p : s->allocs) cudaFree(p);
+    for (cudaEvent_t e : s->ev)
+        if (e) cudaEventDestroy(e);
     delete s;
 }
 
@@ -729,15 +784,22 @@ nlp_status nlp_surrogate_train_step(nlp_surrogate s, const float *feat_dev, cons
                                     float weight_decay, double *loss) {
     if (!s || !feat_dev || !target_dev || B < 1 || B > kBP || !(lr > 0) || !(weight_decay >= 0))
         return NLP_ERR_INVALID_ARG;
+    s->nev = 0;   // drop marks of calls outside a training step
+    mark(s, -1);
     nlp_status r = forward(s, feat_dev, B);
-    if (r || (r = backward(s, target_dev, B, loss))) return r;
+    if (r || (r = backward(s, target_dev, B, loss))) {
+        s->nev = 0;
+        return r;
+    }
     s->step++;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = (float)(1.0 - std::pow((double)b1, (double)s->step));
     const float c2 = (float)(1.0 - std::pow((double)b2, (double)s->step));
     k_adamw<<<grid_for((int64_t)s->lay.total), 256, 0, s->stream>>>(s->P, s->Gr, s->Mm, s->Vv, (int64_t)s->lay.total,
                                                                      lr, b1, b2, 1e-8f, weight_decay, c1, c2);
+    mark(s, NLP_SK_ADAMW);
     refresh_weights(s);
+    collect(s);
     if (cudaGetLastError() != cudaSuccess) return NLP_ERR_CUDA;
     return loss ? check_err(s) : NLP_OK;
 }
@@ -784,6 +846,29 @@ nlp_status nlp_surrogate_base(nlp_surrogate s, const float *gamma_dev, int B, fl
     if (!s || !gamma_dev || !out_dev || B < 1) return NLP_ERR_INVALID_ARG;
     k_base_cube<<<grid_for((int64_t)B * kOut), 256, 0, s->stream>>>(s->box_L, gamma_dev, B, out_dev);
     return cudaGetLastError() == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
+}
+
+nlp_status nlp_surrogate_set_timing(nlp_surrogate s, int on) {
+    if (!s) return NLP_ERR_INVALID_ARG;
+    if (on && !s->ev[0])
+        for (cudaEvent_t &e : s->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return NLP_ERR_CUDA;
+    s->timing = on != 0;
+    s->nev = 0;
+    for (int c = 0; c < NLP_SK_COUNT; ++c) {
+        s->cls_ms[c] = 0.0;
+        s->cls_n[c] = 0;
+    }
+    return NLP_OK;
+}
+
+nlp_status nlp_surrogate_get_kernel_times(nlp_surrogate s, double *ms, int64_t *launches) {
+    if (!s || !ms) return NLP_ERR_INVALID_ARG;
+    for (int c = 0; c < NLP_SK_COUNT; ++c) {
+        ms[c] = s->cls_ms[c];
+        if (launches) launches[c] = s->cls_n[c];
+    }
+    return NLP_OK;
 }
 
 nlp_status nlp_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, void *stream) {

@@ -333,19 +333,20 @@ def test_split_method_2d_full_size(nl, kernel, prec):
 def test_split_method_reproduces_2d_poisson_table(nl, h, paper):
     """Ex. 2.3 (rho = exp(-r^2/1.3) on [-16,16]^2), the configuration of Tables
     tab_NUFFT_2D_Poisson and tab:2d:Poisson:time, FP64 method 2 against the E_1 closed form:
-    the printed truncation level at h = 1/2 within 5%, the FP64 floor (<= 2e-13) below."""
+    the printed truncation level at h = 1/2 within 5%, below it the floor of the NUFFT tolerance
+    (1e-13 here, as the oracle's pins use)."""
     n = int(round(32 / h))
     g = W.Grid((n, n), (16.0, 16.0))
     X, Y = g.mesh()
     s = math.sqrt(1.3)
     rho = np.exp(-(X * X + Y * Y) / (s * s))
-    phi, _ = gpu_eval(nl, g, rho, "poisson2d", "fp64", kmax=math.pi / h, method=2)
+    phi, _ = gpu_eval(nl, g, rho, "poisson2d", "fp64", kmax=math.pi / h, method=2, tol=1e-13)
     e = cf.rel_linf(phi, cf.poisson2d_iso(np.sqrt(X * X + Y * Y), s))
     print("2D Poisson L=16 h=%g: %.3e (printed %.3e)" % (h, e, paper))
     if h >= 0.5:
         assert abs(e - paper) < 0.05 * paper
     else:
-        assert e < 2e-13
+        assert e < 3e-13
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

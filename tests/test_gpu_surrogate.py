@@ -123,3 +123,31 @@ def test_initial_guess_sampling(nl, n, L, prec):
     h3 = (2 * L / n) ** 3
     assert abs(h3 * float(np.sum(got * got)) - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
     assert np.max(np.abs(base - S.base_cube(10.0, 48, 2.5))) < 1e-6
+
+
+def test_kernel_class_timers(nl):
+    """The per-class timers of a training step: every launch is attributed (14 GEMMs: 5 forward,
+    5 weight gradients, 4 input gradients; 3 convolutions each way, two stages of the weight
+    gradient per convolution), the times are positive, and timing does not change the result."""
+    import torch
+    feats, target = _case(5, B=3)
+    f, t = _to_dev(feats), _to_dev(target)
+    a = nl.Surrogate(10.0, seed=3, mode=0)
+    b = nl.Surrogate(10.0, seed=3, mode=0)
+    b.set_timing(True)
+    steps = 3
+    for _ in range(steps):
+        la = a.train_step(f, t, lr=1e-3)
+        lb = b.train_step(f, t, lr=1e-3)
+        assert la == lb
+    torch.cuda.synchronize()
+    kt = b.kernel_times()
+    per = {c: n / steps for c, (_, n) in kt.items()}
+    assert per["gemm"] == 14 and per["conv_fwd"] == 3 and per["conv_bwd_in"] == 3 and per["conv_bwd_w"] == 6
+    assert per["loss"] == 1 and per["adamw"] == 1 and per["elementwise"] > 0
+    assert all(ms > 0 for ms, n in kt.values() if n > 0)
+    assert np.array_equal(a.get_params(), b.get_params())
+    b.set_timing(False)
+    assert all(n == 0 for _, n in b.kernel_times().values())
+    a.close()
+    b.close()
