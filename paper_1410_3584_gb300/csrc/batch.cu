@@ -286,8 +286,13 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
         }
         const int64_t npairs = (int64_t)D.n[0] * D.n[1] / 2;
         B.ntask[ST_R2C] = (int)((npairs + B.nb_r2c - 1) / B.nb_r2c);
-        B.ntask[ST_A1] = B.a1.nouter * (int)((nh + B.nb_a1 - 1) / B.nb_a1);
-        B.ntask[ST_A0] = three ? B.a0.nouter * (int)((nh + B.nb_a0 - 1) / B.nb_a0) : 0;
+        if (B.reg_fft) {   // register engine: columns of all outer indices in blocks of kRegLines
+            B.ntask[ST_A1] = (int)cols_blocks<float, kRegLines>(B.a1);
+            B.ntask[ST_A0] = three ? (int)cols_blocks<float, kRegLines>(B.a0) : 0;
+        } else {
+            B.ntask[ST_A1] = B.a1.nouter * (int)((nh + B.nb_a1 - 1) / B.nb_a1);
+            B.ntask[ST_A0] = three ? B.a0.nouter * (int)((nh + B.nb_a0 - 1) / B.nb_a0) : 0;
+        }
         B.spread_warp = (D.sub_T == 2 && D.w == 7) ? 1 : 0;
         B.ntask[ST_INTERP] = (int)(B.spread_warp ? D.nrchunks : 0);
         B.ntask[ST_SPREAD] = (int)(B.spread_warp ? D.nrchunks : D.nchunks);

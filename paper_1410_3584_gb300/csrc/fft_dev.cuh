@@ -429,8 +429,16 @@ __device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cp
 }
 
 // Strided C2C pass on the register engine: the same operation as k_fft_strided, NBC
-// contiguous columns per block, 16 threads per column.  Pruned input / output windows
-// are predicated loads / stores (positions outside the input window read as zero).
+// columns per block, 16 threads per column.  The columns of all outer indices are numbered
+// q = o ncol + c and block bid takes q = bid NBC .. bid NBC + NBC - 1 (a block may span two
+// outer indices), so no block is left mostly idle when ncol is not a multiple of NBC (the
+// half-spectrum width n/2 + 1).  Pruned input / output windows are predicated loads / stores
+// (positions outside the input window read as zero).
+template <typename T, int NBC>
+__host__ __device__ inline int64_t cols_blocks(const StridedDesc &d) {
+    return ((int64_t)d.nouter * d.ncol + NBC - 1) / NBC;
+}
+
 template <typename T, int SGN, int NBC>
 __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int bid,
                                                unsigned char *smraw) {
@@ -438,12 +446,12 @@ __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &
     cpx<T> *sA = (cpx<T> *)smraw;
     cpx<T> *sB = sA + (size_t)N * NBC;
     const int b = threadIdx.x % NBC, t = threadIdx.x / NBC;
-    const int ctiles = (d.ncol + NBC - 1) / NBC;
-    const int o = bid / ctiles, c0 = (bid % ctiles) * NBC;
+    const int64_t q = (int64_t)bid * NBC + b;
+    const bool colok = q < (int64_t)d.nouter * d.ncol;
+    const int o = colok ? (int)(q / d.ncol) : 0, c = colok ? (int)(q - (int64_t)o * d.ncol) : 0;
     const int oo = d.outer_map_n > 0 ? wrapi(o - d.outer_map_n / 2, d.outer_map_N) : o;
-    const bool colok = c0 + b < d.ncol;
-    cpx<T> *base = data + (int64_t)oo * d.os + c0 + b;
-    cpx<T> *obase = (d.out ? (cpx<T> *)d.out : data) + (int64_t)oo * d.os + c0 + b;
+    cpx<T> *base = data + (int64_t)oo * d.os + c;
+    cpx<T> *obase = (d.out ? (cpx<T> *)d.out : data) + (int64_t)oo * d.os + c;
     // window of n points: positions [0, n - n/2) and [N - n/2, N)
     const int ilo = d.n_in < N ? d.n_in - d.n_in / 2 : N, ihi = d.n_in < N ? N - d.n_in / 2 : N;
     const int olo = d.n_out < N ? d.n_out - d.n_out / 2 : N, ohi = d.n_out < N ? N - d.n_out / 2 : N;

@@ -61,8 +61,7 @@ template <typename T, int NBC> static cudaError_t c2r_reg(T *phi, const DevPlan<
 template <typename T, int NBC>
 static cudaError_t cols_reg(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign, cudaStream_t st) {
     const size_t sm = sizeof(cpx<T>) * (size_t)L.N * NBC * (L.nrad_reg > 2 ? 2 : 1);
-    const int ctiles = (d.ncol + NBC - 1) / NBC;
-    const unsigned grid = (unsigned)((int64_t)d.nouter * ctiles);
+    const unsigned grid = (unsigned)cols_blocks<T, NBC>(d);
     if (sign < 0) {
         allow_smem<k_fft_cols<T, -1, NBC>>();
         k_fft_cols<T, -1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);

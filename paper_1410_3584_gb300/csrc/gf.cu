@@ -402,7 +402,7 @@ static nlp_status gf_step_t(nlp_plan_s *p, T *phi, const T *V, double beta, doub
     if ((s = reduce_to(p, W, 0, 2, 1.0, S_MIN)) || (s = reduce_to(p, W, 1, 1, 1.0, S_MAX))) return s;
     if (cudaMemcpyAsync(W->x, phi, sizeof(T) * N, cudaMemcpyDeviceToDevice, st)) return NLP_ERR_CUDA;
     // Inner solve: the Chebyshev-accelerated fixed point (k_cheb_init).  The convergence test
-    // runs on the device every iteration; the host reads its verdict every kCheckEvery
+    // runs on the device every iteration; the host reads its decision every kCheckEvery
     // iterations, so up to kCheckEvery - 1 iterations may run past convergence.  Their results
     // are not used: the iterate of the first converged iteration is captured in xf, so the
     // step equals one that stopped exactly there.
