@@ -114,7 +114,6 @@ template <typename T> struct DevPlan {
     int64_t cmb_tiles;
     const int *cmb_act; // the tiles that windows reach (the others of G stay zero from plan time)
     int64_t cmb_nact;
-    float psi_sum3;     // FP32 warp kernels: (max over node offsets of sum_t psi)^3, bounds the interpolation
     cpx<T> *cnode;      // FP32 warp kernels: c_j = rho-hat_j omega_j per node (interpolation -> spreading)
     T *csum;            // FP32 warp kernels: per chunk sum of |re c_j| + |im c_j| (bounds the window)
 };

@@ -637,23 +637,6 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
     D.nchunks = (int64_t)chunks.size();
     p->info.tiles = ntiles_used;
     p->info.chunks = D.nchunks;
-    // (max over node offsets of the sum of the w kernel values)^3: with the F window's
-    // largest component it bounds |rho-hat_j| in the FP32 warp kernel's fixed-point spreading
-    {
-        double cmax = 0.0;
-        const int ns = 4000;
-        for (int i = 0; i <= ns; ++i) {
-            const double d = 0.5 * D.w - 1.0 + (double)i / ns;   // offset from the first tap
-            double sum = 0.0;
-            for (int t = 0; t < D.w; ++t) {
-                const double x = 2.0 * (t - d) / D.w, sv = 1.0 - x * x;
-                if (sv > 0) sum += std::exp(p->info.beta_es * (std::sqrt(sv) - 1.0));
-            }
-            cmax = std::max(cmax, sum);
-        }
-        cmax *= 1.001;
-        D.psi_sum3 = (float)(cmax * cmax * cmax);
-    }
     // FP32 warp kernels: per-node c_j (padded like the node records) and per-chunk bounds
     D.cnode = nullptr;
     D.csum = nullptr;

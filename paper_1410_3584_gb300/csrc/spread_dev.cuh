@@ -193,23 +193,21 @@ __device__ __forceinline__ void spread_generic_block(const DevPlan<T> &P, int bi
 //      (v, v) pairs load as packed operands,
 //   2. (interpolation) per column a complex z-contraction with packed FP32x2 FMAs, the
 //      batch's nodes interleaved, weighted by the column's x/y kernel values; the 32 lane
-//      partials of a node are summed by one integer warp reduction per component (fixed
-//      point, below); c_j = rho-hat_j omega_j goes to the node array and |c_j| into the chunk's
-//      bound,
+//      partials of the batch's 2 NB sums are reduced together by a shuffle tree in a fixed
+//      order, one batch behind (the shuffles of batch i run while batch i + 1 computes);
+//      c_j = rho-hat_j omega_j goes to the node array and |c_j| into the chunk's bound,
 //   2'. (spreading) per column a complex x z outer product of c_j with packed FMAs into the G
 //      registers; at the end of a piece the columns are added to the chunk's shared window
 //      in fixed point, and the window goes to the chunk's scratch slot.
 // A piece's last batch is padded with the records that follow it, given weight zero, so every
 // batch runs the same code.
 //
-// Fixed point.  Integer addition is associative, so sums taken in integers do not depend on
-// the order of lanes or warps.  Quanta are powers of two (int * q is exact) chosen from bounds
-// known before the sums: interpolation, with M the largest |re| or |im| of F on the chunk's
-// window and C = max over node offsets of sum_t psi, every lane partial sum obeys
-// sum_lanes |partial| <= sqrt(2) M C^3 =: B1, q1 = 2^(ceil log2 1.01 B1 - 30); spreading, every
-// cell obeys |re G|, |im G| <= sum_j (|re c_j| + |im c_j|) =: B2 (the kernel is at most 1),
-// summed by the interpolation kernel in a fixed order, q2 = 2^(ceil log2 1.01 B2 - 30).  All
-// partial sums stay below 2^31 in magnitude.
+// Fixed point (spreading).  The warps of a CTA add their pieces' columns into the chunk's
+// shared window concurrently; integer addition is associative, so the window does not depend
+// on their order.  The quantum is a power of two (int * q is exact) chosen from a bound known
+// before the sums: every cell obeys |re G|, |im G| <= sum_j (|re c_j| + |im c_j|) =: B2 (the
+// kernel is at most 1), summed by the interpolation kernel in a fixed order, and
+// q2 = 2^(ceil log2 1.01 B2 - 30), so all partial sums stay below 2^31 in magnitude.
 #ifndef NLP_WARP_NB
 #define NLP_WARP_NB 4
 #endif
@@ -271,13 +269,6 @@ __device__ __forceinline__ float es_fast(float i_f, float d, float c2w, float nb
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// warp-wide integer sum, received by every lane
-__device__ __forceinline__ int warp_sum_i32(int v) {
-    int r;
-    asm volatile("redux.sync.add.s32 %0, %1, 0xffffffff;" : "=r"(r) : "r"(v));
-    return r;
-}
 
 // power-of-two quantum q = 2^(e - 30) for a bound B (1.01 B < 2^e); 2^-126 floor; NaN bound -> NaN
 __device__ __forceinline__ void fixed_quantum(float B, float &q, float &qinv) {
@@ -375,6 +366,38 @@ __device__ __forceinline__ void warp_window_rows(const DevPlan<T> &P, const Chun
     }
 }
 
+// The lane partials of one batch's 2 NB sums (node k: real part v[2k], imaginary v[2k + 1]),
+// waiting for their reduction; jb < 0: none.
+template <int NB> struct PendingSums {
+    static constexpr int V = 2 * NB;
+    static_assert(V == 8, "lane layout of the batch sums");
+    float v[V];
+    int jb = -1, nb = 0;
+    float w = 0.0f;   // lane k < NB: omega of node k (zero past the piece)
+    __device__ __forceinline__ PendingSums() {
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = 0.0f;
+    }
+    // all 2 NB sums reduced together (recursive halving, fixed shuffle order): the real part of
+    // node k lands in lanes 8k .. 8k+3, its imaginary part in 8k+4 .. 8k+7; lane 8k stores
+    // c_k = rho-hat_k omega_k and adds |c_k| to the bound.  Every lane must call it.
+    __device__ __forceinline__ void emit(const DevPlan<float> &P, int lane, float &bsum) {
+        float r[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) r[i] = v[i];
+        warp_reduce_multi<float, V>(r, lane);
+        const float im = __shfl_down_sync(0xffffffffu, r[0], 4);
+        const int k = lane >> 3;
+        const float wk = __shfl_sync(0xffffffffu, w, k);
+        if ((lane & 7) == 0 && jb >= 0) {
+            const float2 c = f2(r[0] * wk, im * wk);
+            if (k < nb) P.cnode[jb + k] = mk<float>(c.x, c.y);
+            bsum += fabsf(c.x) + fabsf(c.y);
+        }
+        jb = -1;
+    }
+};
+
 template <int W, int NB>
 __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int bid, unsigned char *smraw) {
     static_assert(W * W <= 64 && W >= 4 && W <= 8, "two columns per lane, at most 8 z taps");
@@ -390,12 +413,9 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
     int *rowF = (int *)(smraw + L.offRowW);
     float *wsum = (float *)(rowF + rows);
     const Chunk ch = P.rchunks[bid];
-    __shared__ int s_max;
-    if (threadIdx.x == 0) s_max = 0;
     warp_window_rows(P, ch, L, false, rowoff, rowF);
     const WinCol wc = window_col(P, ch, L.Wt2, rows);
     __syncthreads();
-    float mx = 0.0f;
     {
         // four loads in flight per thread before their stores
         const int N2 = P.nf[2];
@@ -411,25 +431,17 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int ru = r + u * wc.rstep;
-                if (ru < rows) {
-                    const cpx<float> x = wc.herm ? conj(v[u]) : v[u];
-                    sF[rowF[ru] + wc.c] = x;
-                    mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
-                }
+                if (ru < rows) sF[rowF[ru] + wc.c] = wc.herm ? conj(v[u]) : v[u];
             }
         }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) atomicMax(&s_max, __float_as_int(mx));   // non-negative floats order as integers
     __syncthreads();
-    float q1, q1inv;
-    fixed_quantum(1.41421356f * __int_as_float(s_max) * P.psi_sum3, q1, q1inv);
 
     const WarpLane<W, NB> ln(lane, P.w, (float)P.beta);
     float4 *recb = (float4 *)(smraw + L.offRec) + warp * 2 * kRecNodes;   // two piece buffers
     float pd[KR];
     float bsum = 0.0f;   // lanes 8k: sum of |re c| + |im c| of the warp's k-th batch nodes
+    PendingSums<NB> pend;
     int sg = ch.j0 + warp, buf = 0;
     uint32_t so = 0;
     int j0 = 0, j1 = 0;
@@ -480,16 +492,16 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
         for (int jb = j0; jb < j1; jb += NB) {
             const int nb = min(NB, j1 - jb), b = jb - j0;
             ln.fetch(rec, b, pd);
-            const float wcur = lane < nb ? rec[4 * (b + lane) + 3] * q1 : 0.0f;   // omega q1, zero past the piece
+            const float wcur = lane < nb ? rec[4 * (b + lane) + 3] : 0.0f;   // omega, zero past the piece
             ln.evaluate(pd, stage);
             __syncwarp();
+            // the previous batch's sums: their shuffle tree is independent of this batch's
+            // arithmetic below, so the two interleave
+            pend.emit(P, lane, bsum);
             // the z sums of the batch's nodes interleaved (z pairs outer, nodes inner)
-            float2 wa2[NB], wb2[NB], sa[NB], sb[NB];
+            float2 sa[NB], sb[NB];
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                ln.weights(stage + k * SS, wa2[k], wb2[k]);
-                sa[k] = sb[k] = f2(0.f, 0.f);
-            }
+            for (int k = 0; k < NB; ++k) sa[k] = sb[k] = f2(0.f, 0.f);
 #pragma unroll
             for (int z = 0; z + 1 < W; z += 2) {
 #pragma unroll
@@ -509,41 +521,18 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
                     sb[k] = __ffma2_rn(fb[W - 1], pz, sb[k]);
                 }
             }
-#ifdef NLP_INTERP_REDUX
+            // weighted by the columns' x/y kernel values: this batch becomes the pending one
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                const float2 vk = __ffma2_rn(sb[k], wb2[k], __fmul2_rn(sa[k], wa2[k]));
-                const int sr = warp_sum_i32(__float2int_rn(vk.x * q1inv));
-                const int si = warp_sum_i32(__float2int_rn(vk.y * q1inv));
-                // c_k = rho-hat_k omega_k; wf of lane k holds omega_k q1 (zero past the piece)
-                if (lane == k) {
-                    const float2 c = f2((float)sr * wcur, (float)si * wcur);
-                    if (k < nb) P.cnode[jb + k] = mk<float>(c.x, c.y);
-                    bsum += fabsf(c.x) + fabsf(c.y);
-                }
+                float2 wa2, wb2;
+                ln.weights(stage + k * SS, wa2, wb2);
+                const float2 vk = __ffma2_rn(sb[k], wb2, __fmul2_rn(sa[k], wa2));
+                pend.v[2 * k] = vk.x;
+                pend.v[2 * k + 1] = vk.y;
             }
-#else
-            // all 2 NB sums reduced together (recursive halving, fixed shuffle order): the
-            // real part of node k lands in lanes 8k .. 8k+3, its imaginary part in 8k+4 .. 8k+7
-            constexpr int V = 2 * NB;
-            static_assert(V == 8, "lane layout of the batch sums");
-            float v[V];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                const float2 vk = __ffma2_rn(sb[k], wb2[k], __fmul2_rn(sa[k], wa2[k]));
-                v[2 * k] = vk.x;
-                v[2 * k + 1] = vk.y;
-            }
-            warp_reduce_multi<float, V>(v, lane);
-            const float im = __shfl_down_sync(0xffffffffu, v[0], 4);
-            const int k = lane >> 3;
-            const float wk = __shfl_sync(0xffffffffu, wcur, k);   // omega_k q1, zero past the piece
-            if ((lane & 7) == 0) {
-                const float2 c = f2(v[0] * wk * q1inv, im * wk * q1inv);
-                if (k < nb) P.cnode[jb + k] = mk<float>(c.x, c.y);
-                bsum += fabsf(c.x) + fabsf(c.y);
-            }
-#endif
+            pend.jb = jb;
+            pend.nb = nb;
+            pend.w = wcur;
             __syncwarp();
         }
         buf ^= 1;
@@ -553,6 +542,7 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
         j1 = j1_n;
     }
     cp_async_wait<0>();
+    pend.emit(P, lane, bsum);
     // the chunk's bound for the spreading kernel: lane sums, then warps, in fixed order
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, off);
