@@ -382,7 +382,8 @@ enum {
 nlp_status nlp_surrogate_set_timing(nlp_surrogate s, int on);
 
 /* ms[NLP_SK_COUNT]: milliseconds per class summed since the timers were enabled;
- * launches[NLP_SK_COUNT] (may be NULL): launches per class. */
+ * launches[NLP_SK_COUNT] (may be NULL): timed intervals per class (one per launch, except the
+ * two-stage weight gradient of a convolution, timed as one interval). */
 nlp_status nlp_surrogate_get_kernel_times(nlp_surrogate s, double *ms, int64_t *launches);
 
 /* Test hook for the tensor-core GEMM of the network: C[M x N] (FP32) = A[M x K] B[N x K]^T,

@@ -169,104 +169,224 @@ __global__ void k_up2_back(const float *dout, float *din, int64_t BC, int g) {
     }
 }
 
-// 3^3 convolution, zero padding 1: out[b][co](p) = bias[co] + sum_ci sum_d w[co][ci][d] in[b][ci](p + d - 1)
-__global__ void k_conv_fwd(const float *in, const float *w, const float *bias, float *out, int B, int Ci, int Co,
-                           int g) {
-    const int64_t G3 = (int64_t)g * g * g;
-    GS(q, (int64_t)B * Co * G3) {
-        const int64_t p = q % G3;
-        const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
-        const int co = (int)((q / G3) % Co), b = (int)(q / (G3 * Co));
-        float s = bias[co];
-        for (int ci = 0; ci < Ci; ++ci) {
-            const float *src = in + ((int64_t)b * Ci + ci) * G3;
-            const float *wk = w + ((int64_t)co * Ci + ci) * 27;
-#pragma unroll
-            for (int d = 0; d < 27; ++d) {
-                const int zz = z + d / 9 - 1, yy = y + (d / 3) % 3 - 1, xx = x + d % 3 - 1;
-                if (zz >= 0 && zz < g && yy >= 0 && yy < g && xx >= 0 && xx < g)
-                    s += wk[d] * src[((int64_t)zz * g + yy) * g + xx];
-            }
-        }
-        out[q] = s;
-    }
+static dim3 grid_for(int64_t n) {
+    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
 }
 
-// d in[b][ci](p) = sum_co sum_d w[co][ci][d] dout[b][co](p - d + 1)
-__global__ void k_conv_bwd_in(const float *dout, const float *w, float *din, int B, int Ci, int Co, int g) {
-    const int64_t G3 = (int64_t)g * g * g;
-    GS(q, (int64_t)B * Ci * G3) {
-        const int64_t p = q % G3;
-        const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
-        const int ci = (int)((q / G3) % Ci), b = (int)(q / (G3 * Ci));
-        float s = 0.f;
-        for (int co = 0; co < Co; ++co) {
-            const float *src = dout + ((int64_t)b * Co + co) * G3;
-            const float *wk = w + ((int64_t)co * Ci + ci) * 27;
-#pragma unroll
-            for (int d = 0; d < 27; ++d) {
-                const int zz = z - (d / 9 - 1), yy = y - ((d / 3) % 3 - 1), xx = x - (d % 3 - 1);
-                if (zz >= 0 && zz < g && yy >= 0 && yy < g && xx >= 0 && xx < g)
-                    s += wk[d] * src[((int64_t)zz * g + yy) * g + xx];
-            }
-        }
-        din[q] = s;
-    }
+// ---- 3^3 convolutions, zero padding 1, on tiles of 8 x 8 x 8 NZ output points of one sample.
+// Tap d = 9 dz + 3 dy + dx (offsets -1..1).  A block stages the input halo of its tile (every
+// input channel, zero outside the grid) and the layer's weights in shared memory; thread
+// (x, y, z-slab, channel group) computes 8 z outputs of CO_T output channels, each halo plane
+// it loads feeding the three output planes it reaches.
+constexpr int kCT = 8;   // tile edge (x, y; z per slab)
+
+__host__ __device__ inline int conv_tiles(int g, int nz) {
+    const int t = (g + kCT - 1) / kCT, tz = (g + kCT * nz - 1) / (kCT * nz);
+    return t * t * tz;
 }
 
-// weight gradient, stage 1: block (job, slice), job = co * (Ci + 1) + ci; ci < Ci accumulates
-// the 27 taps dw[co][ci][d] = sum_{b,p} dout[b][co](p) in[b][ci](p + d - 1) over one slice of
-// the (b, p) range; ci == Ci accumulates the bias sum.  Partials land in part[(job*27+d)*S+slice].
-__global__ void __launch_bounds__(256) k_conv_bwd_w_part(const float *dout, const float *in, float *part, int B,
-                                                         int Ci, int Co, int g, int S) {
-    const int job = blockIdx.x, co = job / (Ci + 1), ci = job % (Ci + 1);
-    const int64_t G3 = (int64_t)g * g * g, total = (int64_t)B * G3;
-    const int64_t per = (total + S - 1) / S, beg = (int64_t)blockIdx.y * per, end = min(total, beg + per);
-    float acc[27];
-#pragma unroll
-    for (int d = 0; d < 27; ++d) acc[d] = 0.f;
-    for (int64_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
-        const int b = (int)(q / G3);
-        const int64_t p = q % G3;
-        const float go = dout[((int64_t)b * Co + co) * G3 + p];
-        if (ci == Ci) {
-            acc[0] += go;
-        } else {
-            const int x = (int)(p % g), y = (int)((p / g) % g), z = (int)(p / ((int64_t)g * g));
-            const float *src = in + ((int64_t)b * Ci + ci) * G3;
-#pragma unroll
-            for (int d = 0; d < 27; ++d) {
-                const int zz = z + d / 9 - 1, yy = y + (d / 3) % 3 - 1, xx = x + d % 3 - 1;
-                if (zz >= 0 && zz < g && yy >= 0 && yy < g && xx >= 0 && xx < g)
-                    acc[d] += go * src[((int64_t)zz * g + yy) * g + xx];
-            }
-        }
+// out[b][oc](p) = bias[oc] + sum_ic sum_d W(oc, ic, d) in[b][ic](p + d - 1)
+//   forward:        IC = C_in, OC = C_out, W(oc, ic, d) = w[oc][ic][d], bias = the layer's bias
+//   input gradient: IC = C_out, OC = C_in, W(oc, ic, d) = w[ic][oc][26 - d] (the flipped,
+//                   transposed stencil: d in[ci](p) = sum_co sum_d w[co][ci][d] dout[co](p - d + 1)),
+//                   no bias
+template <int CO_T, int NZ, bool BWD>
+__global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, const float *__restrict__ w,
+                                               const float *__restrict__ bias, float *__restrict__ out, int IC,
+                                               int OC, int g) {
+    constexpr int HZ = kCT * NZ + 2, HP = (kCT + 2) * (kCT + 2);   // halo depth, halo plane
+    extern __shared__ float csm[];
+    float *sh = csm;                       // [IC][HZ][10][10]
+    float *sw = csm + (size_t)IC * HZ * HP;  // [OC][IC][27]
+    const int ntile = conv_tiles(g, NZ), tpa = (g + kCT - 1) / kCT;
+    const int tile = blockIdx.x % ntile, b = blockIdx.x / ntile;
+    const int tx = tile % tpa, ty = (tile / tpa) % tpa, tz = tile / (tpa * tpa);
+    const int x0 = tx * kCT - 1, y0 = ty * kCT - 1, z0 = tz * kCT * NZ - 1;
+    const int64_t G3 = (int64_t)g * g * g;
+    for (int i = threadIdx.x; i < IC * HZ * HP; i += blockDim.x) {
+        const int ic = i / (HZ * HP), r = i - ic * (HZ * HP);
+        const int hz = r / HP, hy = (r / 10) % 10, hx = r % 10;
+        const int z = z0 + hz, y = y0 + hy, x = x0 + hx;
+        float v = 0.f;
+        if ((unsigned)z < (unsigned)g && (unsigned)y < (unsigned)g && (unsigned)x < (unsigned)g)
+            v = in[((int64_t)b * IC + ic) * G3 + ((int64_t)z * g + y) * g + x];
+        sh[i] = v;
     }
-    __shared__ float red[8][27];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        float v = acc[d];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][d] = v;
+    for (int i = threadIdx.x; i < OC * IC * 27; i += blockDim.x) {
+        const int oc = i / (IC * 27), r = i - oc * (IC * 27), ic = r / 27, d = r - ic * 27;
+        sw[i] = BWD ? w[((int64_t)ic * OC + oc) * 27 + (26 - d)] : w[i];
     }
     __syncthreads();
-    if (threadIdx.x < 27) {
-        float s = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        part[((int64_t)job * 27 + threadIdx.x) * S + blockIdx.y] = s;
+    const int ng = OC / CO_T;
+    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, rest = threadIdx.x >> 6;
+    const int gq = rest % ng, zs = rest / ng;
+    if (zs >= NZ) return;
+    const int oc0 = gq * CO_T;
+    float acc[CO_T][kCT];
+#pragma unroll
+    for (int c = 0; c < CO_T; ++c)
+#pragma unroll
+        for (int z = 0; z < kCT; ++z) acc[c][z] = BWD ? 0.f : bias[oc0 + c];
+    for (int ic = 0; ic < IC; ++ic) {
+        const float *hb = sh + (size_t)ic * HZ * HP + zs * kCT * HP + ly * 10 + lx;
+        const float *wb = sw + ((size_t)oc0 * IC + ic) * 27;
+#pragma unroll
+        for (int hz = 0; hz < kCT + 2; ++hz) {
+            float v[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = hb[hz * HP + (k / 3) * 10 + (k % 3)];
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz) {
+                const int zo = hz - dz;   // the output plane this halo plane reaches through tap dz
+                if (zo < 0 || zo >= kCT) continue;
+#pragma unroll
+                for (int c = 0; c < CO_T; ++c)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) acc[c][zo] = fmaf(wb[c * IC * 27 + dz * 9 + k], v[k], acc[c][zo]);
+            }
+        }
+    }
+    const int x = tx * kCT + lx, y = ty * kCT + ly;
+    if (x >= g || y >= g) return;
+#pragma unroll
+    for (int c = 0; c < CO_T; ++c)
+#pragma unroll
+        for (int zo = 0; zo < kCT; ++zo) {
+            const int z = tz * kCT * NZ + zs * kCT + zo;
+            if (z < g) out[((int64_t)b * OC + oc0 + c) * G3 + ((int64_t)z * g + y) * g + x] = acc[c][zo];
+        }
+}
+
+template <int CO_T, int NZ, bool BWD>
+static cudaError_t launch_conv3(const float *in, const float *w, const float *bias, float *out, int B, int IC, int OC,
+                                int g, cudaStream_t st) {
+    const int threads = 64 * (OC / CO_T) * NZ;
+    const size_t smem = sizeof(float) * ((size_t)IC * (kCT * NZ + 2) * 100 + (size_t)OC * IC * 27);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3<CO_T, NZ, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_conv3<CO_T, NZ, BWD><<<(unsigned)(B * conv_tiles(g, NZ)), threads, smem, st>>>(in, w, bias, out, IC, OC, g);
+    return cudaGetLastError();
+}
+
+// one layer's convolution (forward or input gradient) with the tile shape for its channel counts:
+// 8 output channels: 4 groups of 2 (256 threads, 8^3 tiles); 1 output channel: 2 z-slabs
+// (128 threads, 8 x 8 x 16 tiles)
+template <bool BWD>
+static cudaError_t conv3(const float *in, const float *w, const float *bias, float *out, int B, int IC, int OC, int g,
+                         cudaStream_t st) {
+    if (OC == 8) return launch_conv3<2, 1, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    if (OC == 1) return launch_conv3<1, 2, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    return cudaErrorInvalidValue;
+}
+
+// ---- weight gradient: dw[co][ci][d] = sum_{b,p} dout[b][co](p) in[b][ci](p + d - 1),
+// db[co] = sum_{b,p} dout[b][co](p).  Work items (sample, 8^3 tile) are dealt to the blocks
+// round-robin in a fixed order; thread (pair, q) of a block owns the channel pair
+// pair = co Ci + ci and the tile rows (z, y) = q, q + NQ, ... (NQ = 256 / pairs), accumulating
+// the 27 taps (and, for ci = 0, the bias) over its rows, each row of 8 x points loading 8 dout
+// values and 9 halo rows of 10.  The NQ partials of a pair are summed in q order into the
+// block's slot part[block][pair][28]; k_conv_wgrad_final sums the blocks in order.
+constexpr int kWgBlocks = 608;          // blocks of the first stage (4 per SM)
+constexpr int kWgDoutPitch = 520;       // dout tile channel pitch (520 mod 32 = 8: distinct banks)
+constexpr int kWgHaloPitch = 1004;      // halo channel pitch (1004 mod 32 = 12)
+
+__global__ void __launch_bounds__(256) k_conv_wgrad_part(const float *__restrict__ dout, const float *__restrict__ in,
+                                                         float *__restrict__ part, int B, int Ci, int Co, int g) {
+    extern __shared__ float wsm[];
+    float *sd = wsm;                                  // [Co][8][8][8] (pitch kWgDoutPitch)
+    float *sh = wsm + (size_t)Co * kWgDoutPitch;      // [Ci][10][10][10] (pitch kWgHaloPitch)
+    float *red = sh + (size_t)Ci * kWgHaloPitch;      // [NQ][pairs][28]
+    const int pairs = Co * Ci, NQ = 256 / pairs;
+    const int pair = threadIdx.x % pairs, q = threadIdx.x / pairs;
+    const int co = pair / Ci, ci = pair - co * Ci;
+    const bool active = q < NQ;
+    const int ntile = conv_tiles(g, 1), tpa = (g + kCT - 1) / kCT;
+    const int64_t G3 = (int64_t)g * g * g, items = (int64_t)B * ntile;
+    float acc[28];
+#pragma unroll
+    for (int d = 0; d < 28; ++d) acc[d] = 0.f;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int tile = (int)(it % ntile), b = (int)(it / ntile);
+        const int tx = tile % tpa, ty = (tile / tpa) % tpa, tz = tile / (tpa * tpa);
+        const int x0 = tx * kCT, y0 = ty * kCT, z0 = tz * kCT;
+        __syncthreads();   // the previous item's tiles are no longer read
+        for (int i = threadIdx.x; i < Co * 512; i += blockDim.x) {
+            const int c = i >> 9, r = i & 511, z = z0 + (r >> 6), y = y0 + ((r >> 3) & 7), x = x0 + (r & 7);
+            float v = 0.f;
+            if (z < g && y < g && x < g) v = dout[((int64_t)b * Co + c) * G3 + ((int64_t)z * g + y) * g + x];
+            sd[c * kWgDoutPitch + r] = v;
+        }
+        for (int i = threadIdx.x; i < Ci * 1000; i += blockDim.x) {
+            const int c = i / 1000, r = i - c * 1000;
+            const int z = z0 - 1 + r / 100, y = y0 - 1 + (r / 10) % 10, x = x0 - 1 + r % 10;
+            float v = 0.f;
+            if ((unsigned)z < (unsigned)g && (unsigned)y < (unsigned)g && (unsigned)x < (unsigned)g)
+                v = in[((int64_t)b * Ci + c) * G3 + ((int64_t)z * g + y) * g + x];
+            sh[c * kWgHaloPitch + r] = v;
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int row = q; row < 64; row += NQ) {
+            const int zr = row >> 3, yr = row & 7;
+            float o[kCT];
+#pragma unroll
+            for (int x = 0; x < kCT; ++x) o[x] = sd[co * kWgDoutPitch + row * 8 + x];
+            if (ci == 0) {
+#pragma unroll
+                for (int x = 0; x < kCT; ++x) acc[27] += o[x];
+            }
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    const float *hr = sh + ci * kWgHaloPitch + (zr + dz) * 100 + (yr + dy) * 10;
+                    float v[kCT + 2];
+#pragma unroll
+                    for (int x = 0; x < kCT + 2; ++x) v[x] = hr[x];
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int x = 0; x < kCT; ++x) acc[dz * 9 + dy * 3 + dx] = fmaf(o[x], v[x + dx], acc[dz * 9 + dy * 3 + dx]);
+                }
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int d = 0; d < 28; ++d) red[((size_t)q * pairs + pair) * 28 + d] = acc[d];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < pairs * 28; i += blockDim.x) {
+        float t = 0.f;
+        for (int u = 0; u < NQ; ++u) t += red[(size_t)u * pairs * 28 + i];
+        part[(size_t)blockIdx.x * pairs * 28 + i] = t;
     }
 }
 
-// stage 2: sum the slices in order into dw [co][ci][27] and db [co]
-__global__ void k_conv_bwd_w_final(const float *part, float *dw, float *db, int Ci, int Co, int S) {
-    GS(q, (int64_t)Co * (Ci + 1) * 27) {
-        const int job = (int)(q / 27), d = (int)(q % 27), co = job / (Ci + 1), ci = job % (Ci + 1);
-        float s = 0.f;
-        for (int i = 0; i < S; ++i) s += part[q * S + i];
-        if (ci < Ci) dw[((int64_t)co * Ci + ci) * 27 + d] = s;
-        else if (d == 0) db[co] = s;
+// stage 2: dw[co][ci][d] and db[co] from the blocks' partials, summed in block order
+__global__ void k_conv_wgrad_final(const float *part, int nblk, float *dw, float *db, int Ci, int Co) {
+    const int pairs = Co * Ci;
+    GS(i, (int64_t)pairs * 28) {
+        float t = 0.f;
+        for (int u = 0; u < nblk; ++u) t += part[(size_t)u * pairs * 28 + i];
+        const int pair = (int)(i / 28), d = (int)(i % 28), co = pair / Ci, ci = pair % Ci;
+        if (d < 27) dw[((int64_t)co * Ci + ci) * 27 + d] = t;
+        else if (ci == 0) db[co] = t;
     }
+}
+
+static cudaError_t conv_wgrad(const float *dout, const float *in, float *part, float *dw, float *db, int B, int Ci,
+                              int Co, int g, cudaStream_t st) {
+    const int pairs = Co * Ci, NQ = 256 / pairs;
+    const size_t smem = sizeof(float) * ((size_t)Co * kWgDoutPitch + (size_t)Ci * kWgHaloPitch + (size_t)NQ * pairs * 28);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t items = (int64_t)B * conv_tiles(g, 1);
+    const int nblk = (int)std::min<int64_t>(kWgBlocks, items);
+    k_conv_wgrad_part<<<nblk, 256, smem, st>>>(dout, in, part, B, Ci, Co, g);
+    k_conv_wgrad_final<<<grid_for((int64_t)pairs * 28), 256, 0, st>>>(part, nblk, dw, db, Ci, Co);
+    return cudaGetLastError();
 }
 
 __global__ void k_silu(const float *pre, float *y, int64_t n) {
@@ -407,10 +527,6 @@ __global__ void k_base_cube(double Ls, const float *gamma, int B, float *out) {
     }
 }
 
-static dim3 grid_for(int64_t n) {
-    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
-}
-
 constexpr int kRedBlocks = 512;
 
 }  // namespace nlp
@@ -539,8 +655,9 @@ static nlp_status forward(nlp_surrogate_s *s, const float *feat, int B) {
         k_up2<<<grid_for(BC * G3), 256, 0, st>>>(prev, s->cin[c], BC, g);
         mark(s, NLP_SK_ELEMENTWISE);
         g = kConvG[c];
-        k_conv_fwd<<<grid_for((int64_t)B * kConvCo[c] * G3), 256, 0, st>>>(s->cin[c], s->P + L.cw[c], s->P + L.cb[c],
-                                                                          s->cpre[c], B, kConvCi[c], kConvCo[c], g);
+        if (conv3<false>(s->cin[c], s->P + L.cw[c], s->P + L.cb[c], s->cpre[c], B, kConvCi[c], kConvCo[c], g, st) !=
+            cudaSuccess)
+            return NLP_ERR_CUDA;
         mark(s, NLP_SK_CONV_FWD);
         if (c + 1 < kConv) {
             k_silu<<<grid_for((int64_t)B * kConvCo[c] * G3), 256, 0, st>>>(s->cpre[c], s->cact[c],
@@ -570,14 +687,11 @@ static nlp_status backward(nlp_surrogate_s *s, const float *target, int B, doubl
     const float *dnext = s->dout;   // gradient w.r.t. the current conv output (pre-activation)
     for (int c = kConv - 1; c >= 0; --c) {
         const int Ci = kConvCi[c], Co = kConvCo[c], g = kConvG[c];
-        const int64_t G3 = (int64_t)g * g * g, total = (int64_t)B * G3;
-        const int S = (int)std::max<int64_t>(1, std::min<int64_t>(64, total / (256 * 32)));
-        k_conv_bwd_w_part<<<dim3(Co * (Ci + 1), S), 256, 0, st>>>(dnext, s->cin[c], s->wpart, B, Ci, Co, g, S);
+        if (conv_wgrad(dnext, s->cin[c], s->wpart, s->Gr + L.cw[c], s->Gr + L.cb[c], B, Ci, Co, g, st) != cudaSuccess)
+            return NLP_ERR_CUDA;
         mark(s, NLP_SK_CONV_BWD_W);
-        k_conv_bwd_w_final<<<grid_for((int64_t)Co * (Ci + 1) * 27), 256, 0, st>>>(s->wpart, s->Gr + L.cw[c],
-                                                                                   s->Gr + L.cb[c], Ci, Co, S);
-        mark(s, NLP_SK_CONV_BWD_W);
-        k_conv_bwd_in<<<grid_for((int64_t)B * Ci * G3), 256, 0, st>>>(dnext, s->P + L.cw[c], s->dcin[c], B, Ci, Co, g);
+        if (conv3<true>(dnext, s->P + L.cw[c], nullptr, s->dcin[c], B, Co, Ci, g, st) != cudaSuccess)
+            return NLP_ERR_CUDA;
         mark(s, NLP_SK_CONV_BWD_IN);
         const int gp = g / 2;
         const int64_t BC = (int64_t)B * Ci, gp3 = (int64_t)gp * gp * gp;
@@ -698,7 +812,7 @@ nlp_status nlp_surrogate_create(double box_L, unsigned long long seed, int mode,
         }
     }
     s->dout = (float *)A(4 * (size_t)kBP * kOut);
-    s->wpart = (float *)A(4 * (size_t)kC * (kC + 1) * 27 * 64);
+    s->wpart = (float *)A(4 * (size_t)kWgBlocks * kC * kC * 28);
     s->feat1 = (float *)A(4 * kFeat);
     s->part = (double *)A(8 * kRedBlocks);
     s->err = (int *)A(sizeof(int));
