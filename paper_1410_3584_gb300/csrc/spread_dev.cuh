@@ -222,8 +222,7 @@ template <int W, int NB> struct WarpGeo {
 
 // Shared memory of the two kernels.  F window cell (a, b, c) at a SP + b RP + c (RP even,
 // SP / 2 odd: 16-byte column loads of the 8 lanes of a quarter warp fall in distinct bank
-// groups); G window cell (a, b, c), one 8-byte word, at a SG + b RG + c (RG odd, SG = 2 mod 16
-// for W = 8: the 16 lanes of a half warp add to 16 distinct 8-byte banks).
+// groups); G window cell (a, b, c) at a SG + b RG + c (RG odd).
 struct WarpLayout {
     int Wt0, Wt1, Wt2;
     int RP, SP, RG, SG;
@@ -279,19 +278,6 @@ __device__ __forceinline__ void fixed_quantum(float B, float &q, float &qinv) {
     ex = max(ex, -96);
     qinv = ldexpf(1.0f, 30 - ex);
     q = (B == B) ? ldexpf(1.0f, ex - 30) : B;
-}
-
-// A complex fixed-point value as one 64-bit word, re 2^32 + im (two's complement): sums of such
-// words are exact, and decode back to (sum re, sum im) while both stay below 2^31 in magnitude,
-// so a cell takes one 64-bit shared atomic instead of two 32-bit ones.
-__device__ __forceinline__ unsigned long long pack_fixed(float2 v, float qinv) {
-    const long long re = __float2int_rn(v.x * qinv), im = __float2int_rn(v.y * qinv);
-    return (unsigned long long)(re * 4294967296ll + im);
-}
-__device__ __forceinline__ int2 unpack_fixed(unsigned long long s) {
-    const int im = (int)(unsigned)(s & 0xffffffffull);
-    const long long re = ((long long)s - (long long)im) / 4294967296ll;
-    return make_int2((int)re, im);
 }
 
 __device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes16or8) {
@@ -393,22 +379,18 @@ template <int NB> struct PendingSums {
         for (int i = 0; i < V; ++i) v[i] = 0.0f;
     }
     // all 2 NB sums reduced together (recursive halving, fixed shuffle order): the real part of
-    // node k lands in lanes 8k .. 8k+3, its imaginary part in 8k+4 .. 8k+7.  Branch free, so
-    // that the shuffle chain can interleave with independent arithmetic; lane 8k then holds
-    // c_k = rho-hat_k omega_k (zero past the piece).  Every lane must call it.
-    __device__ __forceinline__ float2 reduce(int lane) const {
+    // node k lands in lanes 8k .. 8k+3, its imaginary part in 8k+4 .. 8k+7; lane 8k stores
+    // c_k = rho-hat_k omega_k and adds |c_k| to the bound.  Every lane must call it.
+    __device__ __forceinline__ void emit(const DevPlan<float> &P, int lane, float &bsum) {
         float r[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) r[i] = v[i];
         warp_reduce_multi<float, V>(r, lane);
         const float im = __shfl_down_sync(0xffffffffu, r[0], 4);
-        const float wk = __shfl_sync(0xffffffffu, w, lane >> 3);
-        return f2(r[0] * wk, im * wk);
-    }
-    // lane 8k stores c_k (reduce's result) and adds |c_k| to the bound
-    __device__ __forceinline__ void store(const DevPlan<float> &P, int lane, float2 c, float &bsum) {
         const int k = lane >> 3;
+        const float wk = __shfl_sync(0xffffffffu, w, k);
         if ((lane & 7) == 0 && jb >= 0) {
+            const float2 c = f2(r[0] * wk, im * wk);
             if (k < nb) P.cnode[jb + k] = mk<float>(c.x, c.y);
             bsum += fabsf(c.x) + fabsf(c.y);
         }
@@ -514,8 +496,8 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
             ln.evaluate(pd, stage);
             __syncwarp();
             // the previous batch's sums: their shuffle tree is independent of this batch's
-            // arithmetic below (no branch between them), so the two interleave
-            const float2 cprev = pend.reduce(lane);
+            // arithmetic below, so the two interleave
+            pend.emit(P, lane, bsum);
             // the z sums of the batch's nodes interleaved (z pairs outer, nodes inner)
             float2 sa[NB], sb[NB];
 #pragma unroll
@@ -539,7 +521,6 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
                     sb[k] = __ffma2_rn(fb[W - 1], pz, sb[k]);
                 }
             }
-            pend.store(P, lane, cprev, bsum);
             // weighted by the columns' x/y kernel values: this batch becomes the pending one
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
@@ -561,7 +542,7 @@ __device__ __forceinline__ void interp_warp_block(const DevPlan<float> &P, int b
         j1 = j1_n;
     }
     cp_async_wait<0>();
-    pend.store(P, lane, pend.reduce(lane), bsum);
+    pend.emit(P, lane, bsum);
     // the chunk's bound for the spreading kernel: lane sums, then warps, in fixed order
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, off);
@@ -581,20 +562,23 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
     constexpr int SS = G::SS, KR = G::KR;
     const int nwarps = blockDim.x >> 5;
     const WarpLayout L = warp_layout<W, NB>(P.win_n[0], P.win_n[1], P.win_n[2], nwarps, true);
-    unsigned long long *sG = (unsigned long long *)smraw;   // packed fixed-point cells (below)
+    int2 *sG = (int2 *)smraw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *stage = (float *)(smraw + L.offStage) + warp * G::STAGE;
     const int rows = L.Wt0 * L.Wt1;
     int *rowG = (int *)(smraw + L.offRowW);
     const Chunk ch = P.rchunks[bid];
     warp_window_rows(P, ch, L, true, nullptr, rowG);
-    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = 0ull;
+    for (int q = threadIdx.x; q < L.Wt0 * L.SG; q += blockDim.x) sG[q] = make_int2(0, 0);
     const WinCol wc = window_col(P, ch, L.Wt2, rows);
     __syncthreads();
     float q2, q2inv;
     fixed_quantum(P.ones_mode ? ch.wsum : P.csum[bid], q2, q2inv);
 
     const WarpLane<W, NB> ln(lane, P.w, (float)P.beta);
+    // G flush order: lanes of the upper half of each y quartet add the imaginary word first,
+    // so that the 32 lanes of one atomic instruction hit 32 banks (W = 8 geometry)
+    const int sw = (ln.ya >> 1) & 1;
     // this warp's region: two piece buffers of records, then their c_j
     float4 *recb = (float4 *)(smraw + L.offRec + (size_t)warp * 2 * kRecNodes * (sizeof(float4) + sizeof(float2)));
     float2 *cbb = (float2 *)(recb + 2 * kRecNodes);
@@ -664,10 +648,19 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
         // add the piece's columns to the window in fixed point
         const int ga0 = (so0 + ln.xa) * L.SG + (so1 + ln.ya) * L.RG + so2;
         const int gb0 = (so0 + ln.xb) * L.SG + (so1 + ln.yb) * L.RG + so2;
+        int *pa = &sG[ga0].x + sw, *pb = &sG[gb0].x + sw;
 #pragma unroll
         for (int z = 0; z < W; ++z) {
-            if (ln.act_a) atomicAdd(sG + ga0 + z, pack_fixed(ga[z], q2inv));
-            if (ln.act_b) atomicAdd(sG + gb0 + z, pack_fixed(gb[z], q2inv));
+            if (ln.act_a) {
+                const int re = __float2int_rn(ga[z].x * q2inv), im = __float2int_rn(ga[z].y * q2inv);
+                atomicAdd(pa + 2 * z, sw ? im : re);
+                atomicAdd(pa + 2 * z + 1 - 2 * sw, sw ? re : im);
+            }
+            if (ln.act_b) {
+                const int re = __float2int_rn(gb[z].x * q2inv), im = __float2int_rn(gb[z].y * q2inv);
+                atomicAdd(pb + 2 * z, sw ? im : re);
+                atomicAdd(pb + 2 * z + 1 - 2 * sw, sw ? re : im);
+            }
         }
         buf ^= 1;
         sg = sg_n;
@@ -680,7 +673,7 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
     // the chunk's window, dense, to its scratch slot (thread: column wc.c of rows r0 + k rstep)
     cpx<float> *out = P.win + (int64_t)bid * P.win_cells + wc.c;
     for (int r = wc.r0; r < rows; r += wc.rstep) {
-        const int2 g = unpack_fixed(sG[rowG[r] + wc.c]);
+        const int2 g = sG[rowG[r] + wc.c];
         out[r * L.Wt2] = mk<float>((float)g.x * q2, (float)g.y * q2);
     }
 }
