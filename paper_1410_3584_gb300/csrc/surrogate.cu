@@ -173,16 +173,16 @@ static dim3 grid_for(int64_t n) {
     return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
 }
 
-// ---- 3^3 convolutions, zero padding 1, on tiles of 8 x 8 x 8 NZ output points of one sample.
-// Tap d = 9 dz + 3 dy + dx (offsets -1..1).  A block stages the input halo of its tile (every
-// input channel, zero outside the grid) and the layer's weights in shared memory; thread
-// (x, y, z-slab, channel group) computes 8 z outputs of CO_T output channels, each halo plane
-// it loads feeding the three output planes it reaches.
-constexpr int kCT = 8;   // tile edge (x, y; z per slab)
+// ---- 3^3 convolutions, zero padding 1, on tiles of 8 XB x 8 x 8 NZ output points of one
+// sample.  Tap d = 9 dz + 3 dy + dx (offsets -1..1).  A block stages the input halo of its tile
+// (every input channel, zero outside the grid) and the layer's weights in shared memory; thread
+// (x, y, z-slab, channel group) computes 8 z outputs at XB adjacent x of CO_T output channels,
+// each halo plane it loads feeding the three output planes it reaches.
+constexpr int kCT = 8;   // tile edge (x per XB, y; z per slab)
 
-__host__ __device__ inline int conv_tiles(int g, int nz) {
-    const int t = (g + kCT - 1) / kCT, tz = (g + kCT * nz - 1) / (kCT * nz);
-    return t * t * tz;
+__host__ __device__ inline int conv_tiles(int g, int xb, int nz) {
+    const int tx = (g + kCT * xb - 1) / (kCT * xb), ty = (g + kCT - 1) / kCT, tz = (g + kCT * nz - 1) / (kCT * nz);
+    return tx * ty * tz;
 }
 
 // out[b][oc](p) = bias[oc] + sum_ic sum_d W(oc, ic, d) in[b][ic](p + d - 1)
@@ -190,22 +190,23 @@ __host__ __device__ inline int conv_tiles(int g, int nz) {
 //   input gradient: IC = C_out, OC = C_in, W(oc, ic, d) = w[ic][oc][26 - d] (the flipped,
 //                   transposed stencil: d in[ci](p) = sum_co sum_d w[co][ci][d] dout[co](p - d + 1)),
 //                   no bias
-template <int CO_T, int NZ, bool BWD>
+template <int CO_T, int XB, int NZ, bool BWD>
 __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, const float *__restrict__ w,
                                                const float *__restrict__ bias, float *__restrict__ out, int IC,
                                                int OC, int g) {
-    constexpr int HZ = kCT * NZ + 2, HP = (kCT + 2) * (kCT + 2);   // halo depth, halo plane
+    constexpr int HX = kCT * XB + 2, HZ = kCT * NZ + 2, HP = HX * (kCT + 2);   // halo row, depth, plane
     extern __shared__ float csm[];
-    float *sh = csm;                       // [IC][HZ][10][10]
+    float *sh = csm;                         // [IC][HZ][10][HX]
     float *sw = csm + (size_t)IC * HZ * HP;  // [OC][IC][27]
-    const int ntile = conv_tiles(g, NZ), tpa = (g + kCT - 1) / kCT;
+    const int ntx = (g + kCT * XB - 1) / (kCT * XB), nty = (g + kCT - 1) / kCT;
+    const int ntile = conv_tiles(g, XB, NZ);
     const int tile = blockIdx.x % ntile, b = blockIdx.x / ntile;
-    const int tx = tile % tpa, ty = (tile / tpa) % tpa, tz = tile / (tpa * tpa);
-    const int x0 = tx * kCT - 1, y0 = ty * kCT - 1, z0 = tz * kCT * NZ - 1;
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int x0 = tx * kCT * XB - 1, y0 = ty * kCT - 1, z0 = tz * kCT * NZ - 1;
     const int64_t G3 = (int64_t)g * g * g;
     for (int i = threadIdx.x; i < IC * HZ * HP; i += blockDim.x) {
         const int ic = i / (HZ * HP), r = i - ic * (HZ * HP);
-        const int hz = r / HP, hy = (r / 10) % 10, hx = r % 10;
+        const int hz = r / HP, hy = (r / HX) % (kCT + 2), hx = r % HX;
         const int z = z0 + hz, y = y0 + hy, x = x0 + hx;
         float v = 0.f;
         if ((unsigned)z < (unsigned)g && (unsigned)y < (unsigned)g && (unsigned)x < (unsigned)g)
@@ -222,19 +223,23 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, con
     const int gq = rest % ng, zs = rest / ng;
     if (zs >= NZ) return;
     const int oc0 = gq * CO_T;
-    float acc[CO_T][kCT];
+    float acc[CO_T][kCT][XB];
 #pragma unroll
     for (int c = 0; c < CO_T; ++c)
 #pragma unroll
-        for (int z = 0; z < kCT; ++z) acc[c][z] = BWD ? 0.f : bias[oc0 + c];
+        for (int z = 0; z < kCT; ++z)
+#pragma unroll
+            for (int u = 0; u < XB; ++u) acc[c][z][u] = BWD ? 0.f : bias[oc0 + c];
     for (int ic = 0; ic < IC; ++ic) {
-        const float *hb = sh + (size_t)ic * HZ * HP + zs * kCT * HP + ly * 10 + lx;
+        const float *hb = sh + (size_t)ic * HZ * HP + zs * kCT * HP + ly * HX + lx * XB;
         const float *wb = sw + ((size_t)oc0 * IC + ic) * 27;
 #pragma unroll
         for (int hz = 0; hz < kCT + 2; ++hz) {
-            float v[9];
+            float v[3][XB + 2];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = hb[hz * HP + (k / 3) * 10 + (k % 3)];
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int e = 0; e < XB + 2; ++e) v[dy][e] = hb[hz * HP + dy * HX + e];
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz) {
                 const int zo = hz - dz;   // the output plane this halo plane reaches through tap dz
@@ -242,41 +247,51 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, con
 #pragma unroll
                 for (int c = 0; c < CO_T; ++c)
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) acc[c][zo] = fmaf(wb[c * IC * 27 + dz * 9 + k], v[k], acc[c][zo]);
+                    for (int k = 0; k < 9; ++k) {
+                        const float wv = wb[c * IC * 27 + dz * 9 + k];
+#pragma unroll
+                        for (int u = 0; u < XB; ++u) acc[c][zo][u] = fmaf(wv, v[k / 3][u + k % 3], acc[c][zo][u]);
+                    }
             }
         }
     }
-    const int x = tx * kCT + lx, y = ty * kCT + ly;
-    if (x >= g || y >= g) return;
+    const int y = ty * kCT + ly;
+    if (y >= g) return;
 #pragma unroll
     for (int c = 0; c < CO_T; ++c)
 #pragma unroll
         for (int zo = 0; zo < kCT; ++zo) {
             const int z = tz * kCT * NZ + zs * kCT + zo;
-            if (z < g) out[((int64_t)b * OC + oc0 + c) * G3 + ((int64_t)z * g + y) * g + x] = acc[c][zo];
+#pragma unroll
+            for (int u = 0; u < XB; ++u) {
+                const int x = tx * kCT * XB + lx * XB + u;
+                if (z < g && x < g) out[((int64_t)b * OC + oc0 + c) * G3 + ((int64_t)z * g + y) * g + x] = acc[c][zo][u];
+            }
         }
 }
 
-template <int CO_T, int NZ, bool BWD>
+template <int CO_T, int XB, int NZ, bool BWD>
 static cudaError_t launch_conv3(const float *in, const float *w, const float *bias, float *out, int B, int IC, int OC,
                                 int g, cudaStream_t st) {
     const int threads = 64 * (OC / CO_T) * NZ;
-    const size_t smem = sizeof(float) * ((size_t)IC * (kCT * NZ + 2) * 100 + (size_t)OC * IC * 27);
-    cudaError_t e = cudaFuncSetAttribute(k_conv3<CO_T, NZ, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem =
+        sizeof(float) * ((size_t)IC * (kCT * NZ + 2) * (kCT + 2) * (kCT * XB + 2) + (size_t)OC * IC * 27);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3<CO_T, XB, NZ, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv3<CO_T, NZ, BWD><<<(unsigned)(B * conv_tiles(g, NZ)), threads, smem, st>>>(in, w, bias, out, IC, OC, g);
+    k_conv3<CO_T, XB, NZ, BWD><<<(unsigned)(B * conv_tiles(g, XB, NZ)), threads, smem, st>>>(in, w, bias, out, IC,
+                                                                                             OC, g);
     return cudaGetLastError();
 }
 
 // one layer's convolution (forward or input gradient) with the tile shape for its channel counts:
-// 8 output channels: 4 groups of 2 (256 threads, 8^3 tiles); 1 output channel: 2 z-slabs
-// (128 threads, 8 x 8 x 16 tiles)
+// 8 output channels: 4 groups of 2 (256 threads, 8^3 tiles); 1 output channel: 2 x and 2 z-slabs
+// per thread group (128 threads, 16 x 8 x 16 tiles)
 template <bool BWD>
 static cudaError_t conv3(const float *in, const float *w, const float *bias, float *out, int B, int IC, int OC, int g,
                          cudaStream_t st) {
-    if (OC == 8) return launch_conv3<2, 1, BWD>(in, w, bias, out, B, IC, OC, g, st);
-    if (OC == 1) return launch_conv3<1, 2, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    if (OC == 8) return launch_conv3<2, 1, 1, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    if (OC == 1) return launch_conv3<1, 2, 2, BWD>(in, w, bias, out, B, IC, OC, g, st);
     return cudaErrorInvalidValue;
 }
 
@@ -296,12 +311,12 @@ __global__ void __launch_bounds__(256) k_conv_wgrad_part(const float *__restrict
     extern __shared__ float wsm[];
     float *sd = wsm;                                  // [Co][8][8][8] (pitch kWgDoutPitch)
     float *sh = wsm + (size_t)Co * kWgDoutPitch;      // [Ci][10][10][10] (pitch kWgHaloPitch)
-    float *red = sh + (size_t)Ci * kWgHaloPitch;      // [NQ][pairs][28]
+    float *red = wsm;                                 // [NQ][pairs][28], after the last item (aliases the tiles)
     const int pairs = Co * Ci, NQ = 256 / pairs;
     const int pair = threadIdx.x % pairs, q = threadIdx.x / pairs;
     const int co = pair / Ci, ci = pair - co * Ci;
     const bool active = q < NQ;
-    const int ntile = conv_tiles(g, 1), tpa = (g + kCT - 1) / kCT;
+    const int ntile = conv_tiles(g, 1, 1), tpa = (g + kCT - 1) / kCT;
     const int64_t G3 = (int64_t)g * g * g, items = (int64_t)B * ntile;
     float acc[28];
 #pragma unroll
@@ -379,10 +394,11 @@ __global__ void k_conv_wgrad_final(const float *part, int nblk, float *dw, float
 static cudaError_t conv_wgrad(const float *dout, const float *in, float *part, float *dw, float *db, int B, int Ci,
                               int Co, int g, cudaStream_t st) {
     const int pairs = Co * Ci, NQ = 256 / pairs;
-    const size_t smem = sizeof(float) * ((size_t)Co * kWgDoutPitch + (size_t)Ci * kWgHaloPitch + (size_t)NQ * pairs * 28);
+    const size_t smem = sizeof(float) * std::max((size_t)Co * kWgDoutPitch + (size_t)Ci * kWgHaloPitch,
+                                                 (size_t)NQ * pairs * 28);
     cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t items = (int64_t)B * conv_tiles(g, 1);
+    const int64_t items = (int64_t)B * conv_tiles(g, 1, 1);
     const int nblk = (int)std::min<int64_t>(kWgBlocks, items);
     k_conv_wgrad_part<<<nblk, 256, smem, st>>>(dout, in, part, B, Ci, Co, g);
     k_conv_wgrad_final<<<grid_for((int64_t)pairs * 28), 256, 0, st>>>(part, nblk, dw, db, Ci, Co);
