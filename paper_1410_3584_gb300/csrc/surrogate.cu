@@ -176,8 +176,10 @@ static dim3 grid_for(int64_t n) {
 // ---- 3^3 convolutions, zero padding 1, on tiles of 8 XB x 8 x 8 NZ output points of one
 // sample.  Tap d = 9 dz + 3 dy + dx (offsets -1..1).  A block stages the input halo of its tile
 // (every input channel, zero outside the grid) and the layer's weights in shared memory; thread
-// (x, y, z-slab, channel group) computes 8 z outputs at XB adjacent x of CO_T output channels,
-// each halo plane it loads feeding the three output planes it reaches.
+// (x, y, z-slab, output-channel group, input-channel group) computes 8 z outputs at XB adjacent
+// x of CO_T output channels over IC / CS input channels, each halo plane it loads feeding the
+// three output planes it reaches; with CS > 1 the input-channel groups' partial sums are added
+// through shared memory in group order.
 constexpr int kCT = 8;   // tile edge (x per XB, y; z per slab)
 
 __host__ __device__ inline int conv_tiles(int g, int xb, int nz) {
@@ -190,7 +192,7 @@ __host__ __device__ inline int conv_tiles(int g, int xb, int nz) {
 //   input gradient: IC = C_out, OC = C_in, W(oc, ic, d) = w[ic][oc][26 - d] (the flipped,
 //                   transposed stencil: d in[ci](p) = sum_co sum_d w[co][ci][d] dout[co](p - d + 1)),
 //                   no bias
-template <int CO_T, int XB, int NZ, bool BWD>
+template <int CO_T, int XB, int NZ, int CS, bool BWD>
 __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, const float *__restrict__ w,
                                                const float *__restrict__ bias, float *__restrict__ out, int IC,
                                                int OC, int g) {
@@ -220,8 +222,8 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, con
     __syncthreads();
     const int ng = OC / CO_T;
     const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, rest = threadIdx.x >> 6;
-    const int gq = rest % ng, zs = rest / ng;
-    if (zs >= NZ) return;
+    const int gq = rest % ng, zs = (rest / ng) % NZ, cs = rest / (ng * NZ);
+    if (cs >= CS) return;
     const int oc0 = gq * CO_T;
     float acc[CO_T][kCT][XB];
 #pragma unroll
@@ -230,7 +232,8 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, con
         for (int z = 0; z < kCT; ++z)
 #pragma unroll
             for (int u = 0; u < XB; ++u) acc[c][z][u] = BWD ? 0.f : bias[oc0 + c];
-    for (int ic = 0; ic < IC; ++ic) {
+    const int icn = IC / CS;
+    for (int ic = cs * icn; ic < (cs + 1) * icn; ++ic) {
         const float *hb = sh + (size_t)ic * HZ * HP + zs * kCT * HP + ly * HX + lx * XB;
         const float *wb = sw + ((size_t)oc0 * IC + ic) * 27;
 #pragma unroll
@@ -255,6 +258,32 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, con
             }
         }
     }
+    if constexpr (CS > 1) {
+        // partial sums of the input-channel groups 1.. through shared memory (the halo is free)
+        constexpr int PT = CO_T * kCT * XB;   // outputs per thread
+        float *red = csm;
+        const int slot = threadIdx.x % (64 * ng * NZ);
+        __syncthreads();
+        if (cs > 0) {
+#pragma unroll
+            for (int c = 0; c < CO_T; ++c)
+#pragma unroll
+                for (int z = 0; z < kCT; ++z)
+#pragma unroll
+                    for (int u = 0; u < XB; ++u)
+                        red[((size_t)(cs - 1) * PT + (c * kCT + z) * XB + u) * (64 * ng * NZ) + slot] = acc[c][z][u];
+        }
+        __syncthreads();
+        if (cs > 0) return;
+        for (int k = 1; k < CS; ++k)
+#pragma unroll
+            for (int c = 0; c < CO_T; ++c)
+#pragma unroll
+                for (int z = 0; z < kCT; ++z)
+#pragma unroll
+                    for (int u = 0; u < XB; ++u)
+                        acc[c][z][u] += red[((size_t)(k - 1) * PT + (c * kCT + z) * XB + u) * (64 * ng * NZ) + slot];
+    }
     const int y = ty * kCT + ly;
     if (y >= g) return;
 #pragma unroll
@@ -270,28 +299,31 @@ __global__ void __launch_bounds__(256) k_conv3(const float *__restrict__ in, con
         }
 }
 
-template <int CO_T, int XB, int NZ, bool BWD>
+template <int CO_T, int XB, int NZ, int CS, bool BWD>
 static cudaError_t launch_conv3(const float *in, const float *w, const float *bias, float *out, int B, int IC, int OC,
                                 int g, cudaStream_t st) {
-    const int threads = 64 * (OC / CO_T) * NZ;
-    const size_t smem =
-        sizeof(float) * ((size_t)IC * (kCT * NZ + 2) * (kCT + 2) * (kCT * XB + 2) + (size_t)OC * IC * 27);
-    cudaError_t e = cudaFuncSetAttribute(k_conv3<CO_T, XB, NZ, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (IC % CS) return cudaErrorInvalidValue;
+    const int threads = 64 * (OC / CO_T) * NZ * CS;
+    const size_t halo = (size_t)IC * (kCT * NZ + 2) * (kCT + 2) * (kCT * XB + 2) + (size_t)OC * IC * 27;
+    const size_t red = (size_t)(CS - 1) * CO_T * kCT * XB * 64 * (OC / CO_T) * NZ;
+    const size_t smem = sizeof(float) * std::max(halo, red);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3<CO_T, XB, NZ, CS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv3<CO_T, XB, NZ, BWD><<<(unsigned)(B * conv_tiles(g, XB, NZ)), threads, smem, st>>>(in, w, bias, out, IC,
-                                                                                             OC, g);
+    k_conv3<CO_T, XB, NZ, CS, BWD><<<(unsigned)(B * conv_tiles(g, XB, NZ)), threads, smem, st>>>(in, w, bias, out,
+                                                                                                 IC, OC, g);
     return cudaGetLastError();
 }
 
 // one layer's convolution (forward or input gradient) with the tile shape for its channel counts:
-// 8 output channels: 4 groups of 2 (256 threads, 8^3 tiles); 1 output channel: 2 x and 2 z-slabs
-// per thread group (128 threads, 16 x 8 x 16 tiles)
+// 8 output channels: 4 groups of 2 (256 threads, 8^3 tiles); 1 output channel: 2 x per thread
+// and 4 input-channel groups (256 threads, 16 x 8 x 8 tiles)
 template <bool BWD>
 static cudaError_t conv3(const float *in, const float *w, const float *bias, float *out, int B, int IC, int OC, int g,
                          cudaStream_t st) {
-    if (OC == 8) return launch_conv3<2, 1, 1, BWD>(in, w, bias, out, B, IC, OC, g, st);
-    if (OC == 1) return launch_conv3<1, 2, 2, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    if (OC == 8) return launch_conv3<2, 1, 1, 1, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    if (OC == 1 && IC % 4 == 0) return launch_conv3<1, 2, 1, 4, BWD>(in, w, bias, out, B, IC, OC, g, st);
+    if (OC == 1) return launch_conv3<1, 2, 1, 1, BWD>(in, w, bias, out, B, IC, OC, g, st);
     return cudaErrorInvalidValue;
 }
 
