@@ -45,7 +45,8 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     a1.os = (int64_t)D.nf[1] * nh;
     a1.outer_map_n = three ? D.n[0] : 0;
     a1.outer_map_N = D.nf[0];
-    NLP_CUDA_TRY(launch_fft_strided<T>(D.F, a1, D.len[1], -1, st));
+    if (!three && D.four) NLP_CUDA_TRY(launch_fft_four<T>(D.F, D.F, a1, D, -1, st));
+    else NLP_CUDA_TRY(launch_fft_strided<T>(D.F, a1, D.len[1], -1, st));
     mark(p, NLP_STAGE_FWD_MID);
     StridedDesc a0{};
     if (three) {
@@ -100,7 +101,8 @@ nlp_status eval_impl(nlp_plan_s *p, DevPlan<T> &D, const T *rho, T *phi) {
     b1.n_in = D.nf[1];
     b1.n_out = D.n[1];
     b1.out = R;
-    NLP_CUDA_TRY(launch_fft_strided<T>(three ? R : D.G, b1, D.len[1], +1, st));
+    if (!three && D.four) NLP_CUDA_TRY(launch_fft_four<T>(D.G, R, b1, D, +1, st));
+    else NLP_CUDA_TRY(launch_fft_strided<T>(three ? R : D.G, b1, D.len[1], +1, st));
     mark(p, NLP_STAGE_INV_MID);
     DevPlan<T> Dr = D;
     Dr.G = R;

@@ -71,6 +71,11 @@ template <typename T> struct DevPlan {
     T beta;             // ES shape
     int T_tile[3];      // tile edge per axis (2D: T_tile[2] = 1)
     FftLen<T> len[3];   // FFT lengths of the fine axes
+    // 2D, fine axis 1 too long for a register-engine block of enough columns: the four-step
+    // decomposition N = N1 N2 (len4[0]: N1, len4[1]: N2) through the scratch spectrum S4
+    int four;
+    FftLen<T> len4[2];
+    cpx<T> *S4;
     const T *deconv[3]; // 1/psi-hat(i 2pi/nf) per axis, i = 0..n-1 (grid index order)
     cpx<T> *F;          // forward spectrum, [nf0][nf1][nh] (3D) or [nf0][nh] (2D)
     cpx<T> *G;          // spread target, same layout

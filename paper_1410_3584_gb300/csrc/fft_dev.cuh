@@ -471,6 +471,60 @@ __global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedD
     fft_cols_block<T, SGN, NBC>(data, d, L, blockIdx.x, smraw);
 }
 
+// Long column passes (2D: fine axis 1 with N = N1 N2 points, too long for a register-engine
+// block of enough columns to coalesce): the four-step decomposition, two passes of short
+// transforms over the same columns.
+//   step 1: for every column and j2 < N2, the N1-point transform of positions j1 N2 + j2
+//           (input window applied), output k1 multiplied by w_N^{j2 k1} (w = e^{SGN 2 pi i / N})
+//           and written to position k1 N2 + j2 of out;
+//   step 2: for every column and k1 < N1, the N2-point transform of positions k1 N2 + j2 of
+//           in, output k2 written to position k1 + N1 k2 of out (output window applied);
+// so that X[k1 + N1 k2] = sum_j2 w_N2^{j2 k2} w_N^{j2 k1} sum_j1 x[j1 N2 + j2] w_N1^{j1 k1}.
+// Block: NBC of the (sub-line, column) pairs q = s ncol + c, 16 threads each; 2D descriptors
+// only (one outer line).
+template <typename T, int SGN, int NBC, int STEP>
+__device__ __forceinline__ void fft_four_block(const cpx<T> *in, cpx<T> *out, const StridedDesc &d,
+                                               const FftLen<T> &L, const FftLen<T> &Ls, int N1, int N2, int bid,
+                                               unsigned char *smraw) {
+    const int N = L.N;
+    cpx<T> *sA = (cpx<T> *)smraw;
+    cpx<T> *sB = sA + (size_t)Ls.N * NBC;
+    const int b = threadIdx.x % NBC, t = threadIdx.x / NBC;
+    const int nsub = STEP == 1 ? N2 : N1;
+    const int64_t q = (int64_t)bid * NBC + b;
+    const bool ok = q < (int64_t)nsub * d.ncol;
+    const int sl = ok ? (int)(q / d.ncol) : 0, c = ok ? (int)(q - (int64_t)sl * d.ncol) : 0;
+    const cpx<T> *ib = in + c;
+    cpx<T> *ob = out + c;
+    const int ilo = d.n_in < N ? d.n_in - d.n_in / 2 : N, ihi = d.n_in < N ? N - d.n_in / 2 : N;
+    const int olo = d.n_out < N ? d.n_out - d.n_out / 2 : N, ohi = d.n_out < N ? N - d.n_out / 2 : N;
+    auto gsrc = [&](int l) -> cpx<T> {
+        const int pos = STEP == 1 ? l * N2 + sl : sl * N2 + l;
+        const bool inw = STEP == 2 || pos < ilo || pos >= ihi;
+        return (ok && inw) ? ib[(int64_t)pos * d.es] : mk<T>(0, 0);
+    };
+    auto gdst = [&](int k, cpx<T> v) {
+        if (!ok) return;
+        if (STEP == 1) {
+            cpx<T> w = L.tw[(int)(((int64_t)sl * k) % N)];
+            if (SGN > 0) w = conj(w);
+            ob[(int64_t)(k * N2 + sl) * d.es] = v * w;
+        } else {
+            const int pos = sl + N1 * k;
+            if (pos < olo || pos >= ohi) ob[(int64_t)pos * d.es] = v;
+        }
+    };
+    auto idx = [](int l, int cc) { return l * NBC + cc; };
+    fft_reg_lines<T, SGN>(Ls, sA, sB, idx, b, t, 16, gsrc, gdst);
+}
+
+template <typename T, int SGN, int NBC, int STEP>
+__global__ void __launch_bounds__(NBC * 16, 4) k_fft_four(const cpx<T> *in, cpx<T> *out, StridedDesc d, FftLen<T> L,
+                                                        FftLen<T> Ls, int N1, int N2) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fft_four_block<T, SGN, NBC, STEP>(in, out, d, L, Ls, N1, N2, blockIdx.x, smraw);
+}
+
 // shared-memory bytes of the register-engine passes for line length N
 template <typename T> __host__ __device__ inline size_t cols_smem_bytes(const FftLen<T> &L, int nbc) {
     return sizeof(cpx<T>) * (size_t)L.N * nbc * (L.nrad_reg > 2 ? 2 : 1);

@@ -6,4 +6,6 @@ template cudaError_t launch_fft_contig<double>(cpx<double> *, int64_t, const Fft
 template cudaError_t launch_fwd_r2c<double>(const double *, const DevPlan<double> &, cudaStream_t);
 template cudaError_t launch_inv_c2r<double>(double *, const DevPlan<double> &, cudaStream_t);
 template cudaError_t launch_fft_strided<double>(cpx<double> *, const StridedDesc &, const FftLen<double> &, int, cudaStream_t);
+template cudaError_t launch_fft_four<double>(const cpx<double> *, cpx<double> *, const StridedDesc &, const DevPlan<double> &, int, cudaStream_t);
+template bool cols_on_reg_engine<double>(const FftLen<double> &);
 }  // namespace nlp

@@ -147,6 +147,36 @@ cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<
     return cudaGetLastError();
 }
 
+// The register engine takes a column pass when a block of at least kRegMinLines columns fits.
+template <typename T> bool cols_on_reg_engine(const FftLen<T> &L) {
+    return L.nrad_reg > 0 &&
+           pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)L.N * (L.nrad_reg > 2 ? 2 : 1)) >= kRegMinLines;
+}
+
+template <typename T, int SGN, int STEP>
+static cudaError_t four_step(const cpx<T> *in, cpx<T> *out, const StridedDesc &d, const DevPlan<T> &D,
+                             cudaStream_t st) {
+    constexpr int NBC = lines_max<T>();
+    const FftLen<T> &Ls = D.len4[STEP - 1];
+    const int N1 = D.len4[0].N, N2 = D.len4[1].N;
+    const int64_t cols = (int64_t)(STEP == 1 ? N2 : N1) * d.ncol;
+    const size_t sm = cols_smem_bytes<T>(Ls, NBC);
+    allow_smem<k_fft_four<T, SGN, NBC, STEP>>();
+    k_fft_four<T, SGN, NBC, STEP><<<(unsigned)((cols + NBC - 1) / NBC), NBC * 16, sm, st>>>(in, out, d, D.len[1], Ls,
+                                                                                          N1, N2);
+    return cudaGetLastError();
+}
+
+// the 2D axis-1 pass as the four-step decomposition: in -> S4 (step 1) -> out (step 2)
+template <typename T>
+cudaError_t launch_fft_four(const cpx<T> *in, cpx<T> *out, const StridedDesc &d, const DevPlan<T> &D, int sign,
+                            cudaStream_t st) {
+    if (!D.four || !D.S4 || d.nouter != 1) return cudaErrorInvalidValue;
+    cudaError_t e = sign < 0 ? four_step<T, -1, 1>(in, D.S4, d, D, st) : four_step<T, +1, 1>(in, D.S4, d, D, st);
+    if (e != cudaSuccess) return e;
+    return sign < 0 ? four_step<T, -1, 2>(D.S4, out, d, D, st) : four_step<T, +1, 2>(D.S4, out, d, D, st);
+}
+
 template <typename T>
 cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, int sign, T post, cudaStream_t st) {
     const int nb = lines_per_block<T>(L.N);

@@ -37,6 +37,10 @@ template <typename T> cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> 
 template <typename T> cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fft_strided(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fft_four(const cpx<T> *in, cpx<T> *out, const StridedDesc &d, const DevPlan<T> &D, int sign,
+                            cudaStream_t st);
+template <typename T> bool cols_on_reg_engine(const FftLen<T> &L);
 
 template <typename T>
 cudaError_t launch_fft_contig(cpx<T> *data, int64_t nlines, const FftLen<T> &L, int sign, T post, cudaStream_t st);

@@ -357,6 +357,27 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
         nlp_status s = make_fft_len<T>(p, D.nf[a], &D.len[a]);
         if (s) return s;
     }
+    // 2D: a fine axis 1 too long for the register engine's column blocks runs as two passes of
+    // short transforms (four-step, N = N1 N2 with N2 in {32, 16, 8, 4}) through a scratch spectrum
+    D.four = 0;
+    D.S4 = nullptr;
+    if (p->grid.dim == 2 && !cols_on_reg_engine<T>(D.len[1])) {
+        const int N = D.len[1].N;
+        for (int n2 : {32, 16, 8, 4}) {
+            if (N % n2 || N / n2 < 2) continue;
+            FftLen<T> a, b;
+            if (make_fft_len<T>(p, N / n2, &a) || make_fft_len<T>(p, n2, &b)) return NLP_ERR_OOM;
+            if (!cols_on_reg_engine<T>(a) || !cols_on_reg_engine<T>(b)) continue;
+            void *d4 = nullptr;
+            nlp_status s = alloc_dev(p, &d4, sizeof(cpx<T>) * (size_t)D.nf[0] * D.nf[1] * D.nh);
+            if (s) return s;
+            D.len4[0] = a;
+            D.len4[1] = b;
+            D.S4 = (cpx<T> *)d4;
+            D.four = 1;
+            break;
+        }
+    }
     // deconvolution tables 1/psi-hat(2 pi (i - n/2)/nf)
     for (int a = 0; a < 3; ++a) {
         std::vector<T> dc(D.n[a]);
