@@ -480,9 +480,10 @@ __global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedD
 //   step 2: for every column and k1 < N1, the N2-point transform of positions k1 N2 + j2 of
 //           in, output k2 written to position k1 + N1 k2 of out (output window applied);
 // so that X[k1 + N1 k2] = sum_j2 w_N2^{j2 k2} w_N^{j2 k1} sum_j1 x[j1 N2 + j2] w_N1^{j1 k1}.
-// Block: NBC of the (sub-line, column) pairs q = s ncol + c, 16 threads each; 2D descriptors
-// only (one outer line).
-template <typename T, int SGN, int NBC, int STEP>
+// Block: NBC of the (sub-line, column) pairs q = s ncol + c, TPC threads each (the sub-lines
+// are short: TPC ~ N_sub / 16 keeps the threads of a radix-16 pass busy and a block's
+// columns one long coalesced row); 2D descriptors only (one outer line).
+template <typename T, int SGN, int NBC, int TPC, int STEP>
 __device__ __forceinline__ void fft_four_block(const cpx<T> *in, cpx<T> *out, const StridedDesc &d,
                                                const FftLen<T> &L, const FftLen<T> &Ls, int N1, int N2, int bid,
                                                unsigned char *smraw) {
@@ -515,14 +516,14 @@ __device__ __forceinline__ void fft_four_block(const cpx<T> *in, cpx<T> *out, co
         }
     };
     auto idx = [](int l, int cc) { return l * NBC + cc; };
-    fft_reg_lines<T, SGN>(Ls, sA, sB, idx, b, t, 16, gsrc, gdst);
+    fft_reg_lines<T, SGN>(Ls, sA, sB, idx, b, t, TPC, gsrc, gdst);
 }
 
-template <typename T, int SGN, int NBC, int STEP>
-__global__ void __launch_bounds__(NBC * 16, 4) k_fft_four(const cpx<T> *in, cpx<T> *out, StridedDesc d, FftLen<T> L,
-                                                        FftLen<T> Ls, int N1, int N2) {
+template <typename T, int SGN, int NBC, int TPC, int STEP>
+__global__ void __launch_bounds__(NBC * TPC, 2) k_fft_four(const cpx<T> *in, cpx<T> *out, StridedDesc d, FftLen<T> L,
+                                                         FftLen<T> Ls, int N1, int N2) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fft_four_block<T, SGN, NBC, STEP>(in, out, d, L, Ls, N1, N2, blockIdx.x, smraw);
+    fft_four_block<T, SGN, NBC, TPC, STEP>(in, out, d, L, Ls, N1, N2, blockIdx.x, smraw);
 }
 
 // shared-memory bytes of the register-engine passes for line length N

@@ -153,18 +153,29 @@ template <typename T> bool cols_on_reg_engine(const FftLen<T> &L) {
            pick_lines(lines_max<T>(), sizeof(cpx<T>) * (size_t)L.N * (L.nrad_reg > 2 ? 2 : 1)) >= kRegMinLines;
 }
 
-template <typename T, int SGN, int STEP>
-static cudaError_t four_step(const cpx<T> *in, cpx<T> *out, const StridedDesc &d, const DevPlan<T> &D,
-                             cudaStream_t st) {
-    constexpr int NBC = lines_max<T>();
+template <typename T, int SGN, int STEP, int TPC>
+static cudaError_t four_step_tpc(const cpx<T> *in, cpx<T> *out, const StridedDesc &d, const DevPlan<T> &D,
+                                 cudaStream_t st) {
+    constexpr int NBC = 256 / TPC;
     const FftLen<T> &Ls = D.len4[STEP - 1];
     const int N1 = D.len4[0].N, N2 = D.len4[1].N;
     const int64_t cols = (int64_t)(STEP == 1 ? N2 : N1) * d.ncol;
     const size_t sm = cols_smem_bytes<T>(Ls, NBC);
-    allow_smem<k_fft_four<T, SGN, NBC, STEP>>();
-    k_fft_four<T, SGN, NBC, STEP><<<(unsigned)((cols + NBC - 1) / NBC), NBC * 16, sm, st>>>(in, out, d, D.len[1], Ls,
+    allow_smem<k_fft_four<T, SGN, NBC, TPC, STEP>>();
+    k_fft_four<T, SGN, NBC, TPC, STEP><<<(unsigned)((cols + NBC - 1) / NBC), 256, sm, st>>>(in, out, d, D.len[1], Ls,
                                                                                           N1, N2);
     return cudaGetLastError();
+}
+
+// threads per sub-line: the power of two nearest below N_sub / 16, 1..8
+template <typename T, int SGN, int STEP>
+static cudaError_t four_step(const cpx<T> *in, cpx<T> *out, const StridedDesc &d, const DevPlan<T> &D,
+                             cudaStream_t st) {
+    const int n = D.len4[STEP - 1].N / 16;
+    if (n >= 8) return four_step_tpc<T, SGN, STEP, 8>(in, out, d, D, st);
+    if (n >= 4) return four_step_tpc<T, SGN, STEP, 4>(in, out, d, D, st);
+    if (n >= 2) return four_step_tpc<T, SGN, STEP, 2>(in, out, d, D, st);
+    return four_step_tpc<T, SGN, STEP, 1>(in, out, d, D, st);
 }
 
 // the 2D axis-1 pass as the four-step decomposition: in -> S4 (step 1) -> out (step 2)

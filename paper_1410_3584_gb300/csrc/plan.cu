@@ -367,7 +367,7 @@ static nlp_status build_device(nlp_plan_s *p, const std::vector<HostNode> &nodes
             if (N % n2 || N / n2 < 2) continue;
             FftLen<T> a, b;
             if (make_fft_len<T>(p, N / n2, &a) || make_fft_len<T>(p, n2, &b)) return NLP_ERR_OOM;
-            if (!cols_on_reg_engine<T>(a) || !cols_on_reg_engine<T>(b)) continue;
+            if (a.nrad_reg == 0 || b.nrad_reg == 0 || N / n2 > 128) continue;   // sub-lines of <= 128 points
             void *d4 = nullptr;
             nlp_status s = alloc_dev(p, &d4, sizeof(cpx<T>) * (size_t)D.nf[0] * D.nf[1] * D.nh);
             if (s) return s;
