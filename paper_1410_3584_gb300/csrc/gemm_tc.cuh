@@ -3,7 +3,9 @@
 //
 //   C[M x N] (FP32) = A[M x K] * B[N x K]^T,  A and B BF16, row-major (K contiguous).
 //
-// One CTA (4 warps) computes a 128 x BN tile.  Per K chunk of 64 the CTA stages A and B in
+// One CTA (4 warps) computes a 128 x BN tile over the K range [z kper, (z + 1) kper) of its
+// grid z index (split K: each split writes its partial product to C + z M N; kper = K gives
+// the plain product).  Per K chunk of 64 the CTA stages A and B in
 // shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices;
 // core matrices adjacent in K are LBO bytes apart, adjacent 8-row groups SBO bytes apart),
 // one elected thread issues four 128 x BN x 16 MMAs accumulating in tensor memory and
@@ -66,7 +68,8 @@ constexpr int kGemmSmemBytes = 64 * 1024;
 template <int BN>
 __global__ void __launch_bounds__(128) k_gemm_bf16_tc(const __nv_bfloat16 *__restrict__ A,
                                                      const __nv_bfloat16 *__restrict__ B, float *__restrict__ C,
-                                                     int M, int N, int K, int *err, long long wait_limit) {
+                                                     int M, int N, int K, int kper, int *err,
+                                                     long long wait_limit) {
     constexpr int BM = 128;
     // A tile at 0, B tile at BM*128 bytes of one dynamic buffer of kGemmSmemBytes: larger than
     // the tiles so that every address an MMA can form from these descriptors stays inside it
@@ -75,6 +78,8 @@ __global__ void __launch_bounds__(128) k_gemm_bf16_tc(const __nv_bfloat16 *__res
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kper, ke = min(K, kb + kper);
+    C += (size_t)blockIdx.z * M * N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t mb = smem_u32(&mbar);
     if (warp == 0) {
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16_tc(const __nv_bfloat16 *__res
     constexpr uint32_t lboA = (BM / 8) * 128, lboB = (BN / 8) * 128, sbo = 128;
     uint32_t phase = 0;
     bool ok = true;
-    for (int k0 = 0; k0 < K && ok; k0 += 64) {
+    for (int k0 = kb; k0 < ke && ok; k0 += 64) {
         stage_tile<BM>(sA, A, K, m0, k0);
         stage_tile<BN>(sB, B, K, n0, k0);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16_tc(const __nv_bfloat16 *__res
             for (int ks = 0; ks < 4; ++ks) {   // K = 16 per MMA = two core matrices along K
                 const uint64_t ad = umma_desc(smem_u32(sA) + ks * 2 * lboA, lboA, sbo);
                 const uint64_t bd = umma_desc(smem_u32(sB) + ks * 2 * lboB, lboB, sbo);
-                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t acc = (k0 > kb || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -147,6 +152,15 @@ __global__ void __launch_bounds__(128) k_gemm_bf16_tc(const __nv_bfloat16 *__res
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+}
+
+// C = sum over the S split-K partials P[z] (M N floats each), added in z order
+__global__ void k_splitk_sum(const float *__restrict__ P, int S, int64_t MN, float *__restrict__ C) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+        float t = P[i];
+        for (int z = 1; z < S; ++z) t += P[(size_t)z * MN + i];
+        C[i] = t;
+    }
 }
 
 // FP32 CUDA-core GEMM with the same contract (inputs given in FP32), 16 x 16 tiles.

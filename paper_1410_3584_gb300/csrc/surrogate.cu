@@ -576,6 +576,7 @@ __global__ void k_base_cube(double Ls, const float *gamma, int B, float *out) {
 }
 
 constexpr int kRedBlocks = 512;
+constexpr size_t kGemmWorkFloats = (size_t)16 * kBP * kHeadPad;   // split-K partials: 16 x 128 x 1792
 
 }  // namespace nlp
 
@@ -599,6 +600,7 @@ struct nlp_surrogate_s {
     float *z0 = nullptr, *cin[kConv] = {}, *cpre[kConv] = {}, *cact[kConv] = {};
     float *dz0 = nullptr, *dcin[kConv] = {}, *dcpre[kConv] = {}, *dcact[kConv] = {};
     float *wpart = nullptr, *dout = nullptr, *feat1 = nullptr;
+    float *gemm_work = nullptr;   // split-K partials of the tensor-core GEMMs
     double *part = nullptr;
     int *err = nullptr;
     long long step = 0;
@@ -646,16 +648,38 @@ static nlp_status sg_alloc(nlp_surrogate_s *s, void **p, size_t bytes) {
     return NLP_OK;
 }
 
+// split-K factor: the largest divisor of the K chunks that keeps the grid near 128 CTAs and the
+// partials within `work_floats` (S = 1: no split)
+static int gemm_splits(int M, int N, int K, size_t work_floats) {
+    const int bn = N % 128 == 0 ? 128 : 64;
+    const int tiles = (N / bn) * (M / 128), kch = K / 64;
+    int best = 1;
+    for (int S = 2; S <= kch; ++S)
+        if (kch % S == 0 && tiles * S <= 128 && (size_t)S * M * N <= work_floats) best = S;
+    return best;
+}
+
+// C = A B^T on the tensor cores; with S > 1 the K range is split over grid z and the partials
+// (in work) are summed in order
 static cudaError_t launch_gemm_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K,
-                                  int *err, cudaStream_t st) {
+                                  int *err, cudaStream_t st, float *work = nullptr, size_t work_floats = 0) {
     if (M % 128 || K % 64 || N % 64) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem<k_gemm_bf16_tc<128>>();
     if (e == cudaSuccess) e = allow_smem<k_gemm_bf16_tc<64>>();
     if (e != cudaSuccess) return e;
+    const int S = work ? gemm_splits(M, N, K, work_floats) : 1;
+    const int kper = K / S;
+    float *out = S > 1 ? work : C;
     if (N % 128 == 0)
-        k_gemm_bf16_tc<128><<<dim3(N / 128, M / 128), 128, kGemmSmemBytes, st>>>(A, B, C, M, N, K, err, 1ll << 22);
+        k_gemm_bf16_tc<128><<<dim3(N / 128, M / 128, S), 128, kGemmSmemBytes, st>>>(A, B, out, M, N, K, kper, err,
+                                                                                    1ll << 22);
     else
-        k_gemm_bf16_tc<64><<<dim3(N / 64, M / 128), 128, kGemmSmemBytes, st>>>(A, B, C, M, N, K, err, 1ll << 22);
+        k_gemm_bf16_tc<64><<<dim3(N / 64, M / 128, S), 128, kGemmSmemBytes, st>>>(A, B, out, M, N, K, kper, err,
+                                                                                  1ll << 22);
+    if (S > 1) {
+        const int64_t MN = (int64_t)M * N;
+        k_splitk_sum<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 1024), 256, 0, st>>>(work, S, MN, C);
+    }
     return cudaGetLastError();
 }
 
@@ -667,7 +691,7 @@ static nlp_status gemm(nlp_surrogate_s *s, const __nv_bfloat16 *A, const __nv_bf
         mark(s, NLP_SK_GEMM);
         return cudaGetLastError() == cudaSuccess ? NLP_OK : NLP_ERR_CUDA;
     }
-    const bool ok = launch_gemm_tc(A, B, C, M, N, K, s->err, s->stream) == cudaSuccess;
+    const bool ok = launch_gemm_tc(A, B, C, M, N, K, s->err, s->stream, s->gemm_work, kGemmWorkFloats) == cudaSuccess;
     mark(s, NLP_SK_GEMM);
     return ok ? NLP_OK : NLP_ERR_CUDA;
 }
@@ -861,6 +885,7 @@ nlp_status nlp_surrogate_create(double box_L, unsigned long long seed, int mode,
     }
     s->dout = (float *)A(4 * (size_t)kBP * kOut);
     s->wpart = (float *)A(4 * (size_t)kWgBlocks * kC * kC * 28);
+    s->gemm_work = (float *)A(4 * kGemmWorkFloats);
     s->feat1 = (float *)A(4 * kFeat);
     s->part = (double *)A(8 * kRedBlocks);
     s->err = (int *)A(sizeof(int));
@@ -1037,13 +1062,21 @@ nlp_status nlp_gemm_bf16(const void *A, const void *B, float *C, int M, int N, i
     if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 64) return NLP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int *err = nullptr;
+    float *work = nullptr;
+    const size_t wf = (size_t)16 * M * N;   // split-K partials, as the network's GEMMs use them
     if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return NLP_ERR_OOM;
+    if (cudaMalloc(&work, sizeof(float) * wf) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(err);
+        return NLP_ERR_OOM;
+    }
     int h = 0;
     const bool ok = cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess &&
-                    launch_gemm_tc((const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, C, M, N, K, err, st) ==
-                        cudaSuccess &&
+                    launch_gemm_tc((const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, C, M, N, K, err, st, work,
+                                   wf) == cudaSuccess &&
                     cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
                     cudaStreamSynchronize(st) == cudaSuccess;
+    cudaFree(work);
     cudaFree(err);
     if (!ok) return NLP_ERR_CUDA;
     return h ? NLP_ERR_TIMEOUT : NLP_OK;
