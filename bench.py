@@ -529,7 +529,7 @@ def batch_arm(args):
         "ms_per_batch": 1e3 * tsum / args.steps, "steps": args.steps, "warmup": args.warmup,
         "items": len(items), "nodes_total": nodes, "tasks": info["tasks"], "grid_ctas": info["grid"],
         "smem_bytes": info["smem"], "tiles": tiles, "plan_s": t_plan, "tune_s": t_tune,
-        "batch_autotune": {"grid_default": grid0, "grid_best": grid_best, "ms_best": tune_ms, "tune_s": t_btune},
+        "batch_autotune": {"grid_default": grid0, "grid_best": grid_best, "order": info["order"], "ms_best": tune_ms, "tune_s": t_btune},
         "sequential_ms": sum(seq) / len(seq), "sequential_graph_ms": seq_graph,
         "speedup_vs_sequential": (sum(seq) / len(seq)) / (1e3 * tsum / args.steps),
         "max_rel_vs_single_plan": worst_single, "max_rel_vs_oracle_sampled": worst_oracle,

@@ -231,8 +231,10 @@ nlp_status nlp_ts_step(nlp_plan plan, void *psi_dev, const void *V_dev, double b
 /* ---------------------------------------------------------------- batched evaluation
  * Many FP32 plans (any mix of grids and of the NLP_COULOMB_3D / NLP_DIPOLE_3D /
  * NLP_COULOMB_2D kernels) evaluated by ONE persistent kernel launch, replayed from a CUDA
- * graph captured at creation.  Work items are (plan, stage, block) tasks taken in
- * stage-major order from a device ticket counter; a stage of one plan starts when the
+ * graph captured at creation.  Work items are (plan, stage, block) tasks taken in a fixed
+ * order from a device ticket counter, stage-major (every plan's stage k before any plan's
+ * stage k + 1; the default) or item-major (plan by plan; chosen by nlp_batch_autotune when it
+ * is faster); a stage of one plan starts when the
  * previous stage of the same plan has completed, which the device checks with a bounded
  * number of polls (NLP_ERR_TIMEOUT if a limit runs out; the batch stays usable).
  * The batch uses the plans' own workspaces: the plans must outlive the batch and must not
@@ -253,10 +255,14 @@ nlp_status nlp_batch_sync(nlp_batch batch);
 
 nlp_status nlp_batch_get_info(nlp_batch batch, int *tasks, int *grid_ctas, size_t *smem_bytes);
 
-/* Autotuner of the batch's own launch: times the graph (4 replays, the first a warm-up) with
- * the persistent grid at 1, 2, ... up to the occupancy limit of CTAs per SM on these inputs
- * and keeps the fastest (the graph is re-captured).  Outputs (may be NULL): *best_grid CTAs,
- * *best_ms per evaluation of the batch.  Synchronous; the outputs phi_dev are overwritten. */
+/* The task order in use: *item_major = 0 (stage-major) or 1 (item-major). */
+nlp_status nlp_batch_get_order(nlp_batch batch, int *item_major);
+
+/* Autotuner of the batch's own launch: times the graph (4 replays, the first a warm-up) for
+ * both task orders and the persistent grid at 1, 2, ... up to the occupancy limit of CTAs per
+ * SM on these inputs, and keeps the fastest (the graph is re-captured).  Outputs (may be
+ * NULL): *best_grid CTAs, *best_ms per evaluation of the batch; nlp_batch_get_order reports
+ * the order kept.  Synchronous; the outputs phi_dev are overwritten. */
 nlp_status nlp_batch_autotune(nlp_batch batch, const void *const *rho_dev, void *const *phi_dev,
                               int *best_grid, double *best_ms);
 

@@ -74,6 +74,7 @@ def _load():
         "nlp_batch_get_info": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t)], I),
         "nlp_batch_autotune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "nlp_batch_set_wait_limit": ([P, ctypes.c_longlong, I, I], I),
+        "nlp_batch_get_order": ([P, ctypes.POINTER(I)], I),
         "nlp_batch_destroy": ([P], None),
         "nlp_autotune_tile": ([ctypes.POINTER(nlp_grid), I, I, ctypes.POINTER(nlp_opts), P, ctypes.c_char_p,
                                ctypes.POINTER(I), ctypes.POINTER(D)], I),
@@ -313,11 +314,14 @@ def nlp_batch_sync(batch, raise_on_error: bool = True) -> int:
 def nlp_batch_get_info(batch) -> dict:
     t, g, sm = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
     _check(_lib.nlp_batch_get_info(batch, ctypes.byref(t), ctypes.byref(g), ctypes.byref(sm)), "nlp_batch_get_info")
-    return {"tasks": t.value, "grid": g.value, "smem": sm.value}
+    o = ctypes.c_int(0)
+    _check(_lib.nlp_batch_get_order(batch, ctypes.byref(o)), "nlp_batch_get_order")
+    return {"tasks": t.value, "grid": g.value, "smem": sm.value, "order": "item-major" if o.value else "stage-major"}
 
 
 def nlp_batch_autotune(batch, rhos, phis):
-    """Pick the persistent grid of the batch by timing it on these inputs: (grid, ms)."""
+    """Pick the task order and the persistent grid of the batch by timing it on these inputs:
+    (grid, ms); nlp_batch_get_info(batch)["order"] reports the order kept."""
     rp = (ctypes.c_void_p * len(rhos))(*[t.data_ptr() for t in rhos])
     pp = (ctypes.c_void_p * len(phis))(*[t.data_ptr() for t in phis])
     g, ms = ctypes.c_int(0), ctypes.c_double(0.0)

@@ -41,7 +41,8 @@ struct BatchItem {
 struct BatchArgs {
     const BatchItem *items;
     int nitems;
-    const int *off;          // kStages * nitems + 1 ticket offsets (stage-major)
+    const int *off;          // kStages * nitems + 1 ticket offsets (stage-major or item-major)
+    int item_major;          // 0: all items' stage k before any stage k + 1; 1: item by item
     int total;
     int *ticket;             // [0] ticket counter, [1] error word
     int *done;               // nitems * kStages completion counters
@@ -72,7 +73,8 @@ __global__ void __launch_bounds__(256, 2) k_batch_persistent(BatchArgs A) {
             if (A.off[mid] <= t) lo = mid;
             else hi = mid;
         }
-        const int k = lo / A.nitems, p = lo % A.nitems, i = t - A.off[lo];
+        const int k = A.item_major ? lo % kStages : lo / A.nitems;
+        const int p = A.item_major ? lo / kStages : lo % A.nitems, i = t - A.off[lo];
         const BatchItem &B = A.items[p];
         if (threadIdx.x == 0) {
             int ok = ld_acquire(A.ticket + 1) == 0;
@@ -179,6 +181,7 @@ struct nlp_batch_s {
     int *h_err = nullptr;                     // pinned copy of the error word
     size_t ctr_bytes = 0;
     int total = 0, grid = 0;
+    int item_major = 0;   // ticket order (see BatchArgs)
     size_t smem = 0;
     long long spin_limit = 1 << 24;
     std::vector<BatchItem> items;
@@ -189,6 +192,23 @@ struct nlp_batch_s {
     bool pending = false;
 };
 
+// Ticket offsets in the batch's order: stage-major (all items' stage k, then stage k + 1: every
+// stage has the whole batch's parallelism) or item-major (item p's stages in sequence, then item
+// p + 1: an item's spectra stay in L2 between its stages).
+static void batch_offsets(nlp_batch_s *b) {
+    const int count = b->count;
+    b->off.assign((size_t)kStages * count + 1, 0);
+    int t = 0;
+    for (int a = 0; a < (b->item_major ? count : kStages); ++a)
+        for (int c = 0; c < (b->item_major ? kStages : count); ++c) {
+            const int k = b->item_major ? c : a, p = b->item_major ? a : c;
+            b->off[b->item_major ? (size_t)p * kStages + k : (size_t)k * count + p] = t;
+            t += b->items[p].ntask[k];
+        }
+    b->off[(size_t)kStages * count] = t;
+    b->total = t;
+}
+
 static nlp_status batch_graph(nlp_batch_s *b) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -196,6 +216,7 @@ static nlp_status batch_graph(nlp_batch_s *b) {
     A.items = b->d_items;
     A.nitems = b->count;
     A.off = b->d_off;
+    A.item_major = b->item_major;
     A.total = b->total;
     A.ticket = b->d_ctr;
     A.done = b->d_ctr + 2;
@@ -323,15 +344,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
     b->smem = smem;
     // Stages run in this order per item, so the window slots and G are never rewritten while
     // an earlier stage of the same item still reads them.
-    b->off.assign((size_t)kStages * count + 1, 0);
-    int t = 0;
-    for (int k = 0; k < kStages; ++k)
-        for (int p = 0; p < count; ++p) {
-            b->off[(size_t)k * count + p] = t;
-            t += b->items[p].ntask[k];
-        }
-    b->off[(size_t)kStages * count] = t;
-    b->total = t;
+    batch_offsets(b);
     auto dalloc = [&](void **ptr, size_t bytes) -> nlp_status {
         if (cudaMalloc(ptr, bytes) != cudaSuccess) { cudaGetLastError(); return NLP_ERR_OOM; }
         b->allocs.push_back(*ptr);
@@ -357,7 +370,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
     memset(b->h_ptrs, 0, sizeof(void *) * 2 * count);
     *b->h_err = 0;
     cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice);
-    cudaMemcpy(b->d_off, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_off, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice);   // (item_major 0)
     if ((int)b->smem > max_dyn_smem() || allow_smem<k_batch_persistent>() != cudaSuccess) {
         nlp_batch_destroy(b);
         return NLP_ERR_UNSUPPORTED;
@@ -401,6 +414,12 @@ nlp_status nlp_batch_sync(nlp_batch b) {
     return *b->h_err ? NLP_ERR_TIMEOUT : NLP_OK;
 }
 
+nlp_status nlp_batch_get_order(nlp_batch b, int *item_major) {
+    if (!b || !item_major) return NLP_ERR_INVALID_ARG;
+    *item_major = b->item_major;
+    return NLP_OK;
+}
+
 nlp_status nlp_batch_get_info(nlp_batch b, int *tasks, int *grid, size_t *smem_bytes) {
     if (!b) return NLP_ERR_INVALID_ARG;
     if (tasks) *tasks = b->total;
@@ -419,11 +438,22 @@ nlp_status nlp_batch_autotune(nlp_batch b, const void *const *rho_dev, void *con
     per = std::max(1, per);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NLP_ERR_CUDA;
-    int best = 0;
+    int best = 0, best_order = 0;
     double bms = 1e300;
     nlp_status s = NLP_OK;
-    // resident persistent CTAs per SM: every count from one to the occupancy limit
-    for (int k = 1; k <= per && s == NLP_OK; ++k) {
+    // the ticket order, and resident persistent CTAs per SM: every count from one to the
+    // occupancy limit
+    for (int kk = 0; kk < 2 * per && s == NLP_OK; ++kk) {
+        const int order = kk / per, k = kk % per + 1;
+        if (order != b->item_major) {
+            b->item_major = order;
+            batch_offsets(b);
+            if (cudaMemcpy(b->d_off, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+                s = NLP_ERR_CUDA;
+                break;
+            }
+        }
         b->grid = sms * k;
         if ((s = batch_graph(b))) break;
         double tmin = 1e300;
@@ -439,12 +469,19 @@ nlp_status nlp_batch_autotune(nlp_batch b, const void *const *rho_dev, void *con
         if (tmin < bms) {
             bms = tmin;
             best = b->grid;
+            best_order = b->item_major;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s) return s;
     b->grid = best;
+    if (best_order != b->item_major) {
+        b->item_major = best_order;
+        batch_offsets(b);
+        if (cudaMemcpy(b->d_off, b->off.data(), sizeof(int) * b->off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return NLP_ERR_CUDA;
+    }
     if ((s = batch_graph(b))) return s;
     if (best_grid) *best_grid = best;
     if (best_ms) *best_ms = bms;
