@@ -541,14 +541,14 @@ __host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; 
 // line, so the global loads and stores are contiguous).  The first pass reads rho,
 // deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
 // where the spectra of the two real lines are separated and written as half spectra.
-template <typename T, int NBC, bool kInplace = true>
+template <typename T, int NBC, bool kInplace = true, int TPC = 16>
 __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
     cpx<T> *sB = sA + (size_t)NBC * LDL;
-    const int t = threadIdx.x & 15, b = threadIdx.x >> 4;
+    const int t = threadIdx.x % TPC, b = threadIdx.x / TPC;
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const int64_t p = (int64_t)bid * NBC + b;
     const bool ok = p < npairs;
@@ -564,7 +564,7 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
     cpx<T> *res;
-    if (kInplace && r2c_inplace(L)) {
+    if (kInplace && TPC == 16 && r2c_inplace(L)) {
         // 256 = 16 x 16: the first pass lands in sA, the second transforms sA in place
         res = sA;
         auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
@@ -576,13 +576,13 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     } else {
         res = ((L.nrad_reg - 1) & 1) ? sB : sA;
         auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
-        fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+        fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
     }
     if (!ok) return;
     const int l0a = wrapi(i0a - P.n[0] / 2, P.nf[0]), l1a = wrapi(i1a - P.n[1] / 2, P.nf[1]);
     const int l0b = wrapi(i0b - P.n[0] / 2, P.nf[0]), l1b = wrapi(i1b - P.n[1] / 2, P.nf[1]);
     cpx<T> *Fa = P.F + ((int64_t)l0a * P.nf[1] + l1a) * nh, *Fb = P.F + ((int64_t)l0b * P.nf[1] + l1b) * nh;
-    for (int k = t; k < nh; k += 16) {
+    for (int k = t; k < nh; k += TPC) {
         const cpx<T> z = res[idx(k, b)];
         const int kc = k == 0 ? 0 : N - k;
         const cpx<T> zc = conj(res[idx(kc, b)]);
@@ -591,24 +591,24 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     }
 }
 
-template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16, 4) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+template <typename T, int NBC, int TPC = 16>
+__global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fwd_r2c_reg_block<T, NBC>(rho, P, blockIdx.x, smraw);
+    fwd_r2c_reg_block<T, NBC, true, TPC>(rho, P, blockIdx.x, smraw);
 }
 
 // Inverse C2R along the last axis on the register engine: the same operation as
 // k_inv_c2r.  The first pass reads the half spectra of a line pair from HBM and forms
 // Z = X1 + i X2 on the fly (Z[N - k] = conj(X1[k]) + i conj(X2[k])); the last pass writes
 // the output window, deconvolved, straight to HBM.
-template <typename T, int NBC>
+template <typename T, int NBC, int TPC = 16>
 __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
     cpx<T> *sB = sA + (size_t)NBC * LDL;
-    const int t = threadIdx.x & 15, b = threadIdx.x >> 4;
+    const int t = threadIdx.x % TPC, b = threadIdx.x / TPC;
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const int64_t p = (int64_t)bid * NBC + b;
     const bool ok = p < npairs;
@@ -648,13 +648,13 @@ __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const Dev
         }
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
-    fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+    fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
 }
 
-template <typename T, int NBC>
-__global__ void __launch_bounds__(NBC * 16, 4) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
+template <typename T, int NBC, int TPC = 16>
+__global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    inv_c2r_reg_block<T, NBC>(phi, P, blockIdx.x, smraw);
+    inv_c2r_reg_block<T, NBC, TPC>(phi, P, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ contiguous C2C pass

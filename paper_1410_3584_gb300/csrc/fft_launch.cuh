@@ -44,6 +44,28 @@ static int pick_lines(int nmax, size_t bytes_per_line) {
     return nb;
 }
 
+// Last-axis lines too long for 16 threads a line pair (N >= 1024): 128 threads a pair (one
+// radix-16 butterfly each per pass), one (FP64) or two (FP32) pairs per block, two shared
+// buffers of a padded line each.
+template <typename T> static bool long_lines_reg(const FftLen<T> &L) { return L.N >= 1024 && L.N <= 4096; }
+template <typename T> constexpr int long_pairs() { return sizeof(T) == 4 ? 2 : 1; }
+template <typename T> static cudaError_t r2c_reg_long(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
+    constexpr int NBC = long_pairs<T>(), TPC = 128;
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+    allow_smem<k_fwd_r2c_reg<T, NBC, TPC>>();
+    k_fwd_r2c_reg<T, NBC, TPC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * TPC, sm, st>>>(rho, P);
+    return cudaGetLastError();
+}
+template <typename T> static cudaError_t c2r_reg_long(T *phi, const DevPlan<T> &P, cudaStream_t st) {
+    constexpr int NBC = long_pairs<T>(), TPC = 128;
+    const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
+    const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+    allow_smem<k_inv_c2r_reg<T, NBC, TPC>>();
+    k_inv_c2r_reg<T, NBC, TPC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * TPC, sm, st>>>(phi, P);
+    return cudaGetLastError();
+}
+
 template <typename T, int NBC> static cudaError_t r2c_reg(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (r2c_inplace(P.len[2]) ? 1 : 2);
@@ -92,6 +114,7 @@ cudaError_t launch_fwd_r2c(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
             NLP_LINES_SWITCH(T, nb, NLP_CALL)
 #undef NLP_CALL
         }
+        if (long_lines_reg(P.len[2])) return r2c_reg_long<T>(rho, P, st);
     }
     const int N = P.len[2].N;
     const int nb = lines_per_block<T>(N);
@@ -112,6 +135,7 @@ cudaError_t launch_inv_c2r(T *phi, const DevPlan<T> &P, cudaStream_t st) {
             NLP_LINES_SWITCH(T, nb, NLP_CALL)
 #undef NLP_CALL
         }
+        if (long_lines_reg(P.len[2])) return c2r_reg_long<T>(phi, P, st);
     }
     const int N = P.len[2].N;
     const int nb = lines_per_block<T>(N);
