@@ -250,6 +250,24 @@ def test_2d_full_size_vs_oracle_and_closed_form(nl, kernel, prec):
     assert err_cf < (1e-9 if prec == "fp64" else 1e-5)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
+def test_2d_long_lines_with_radix_3_and_5(nl, kernel, prec):
+    """2D grids whose fine lines are too long for 16 threads a line (the four-step column pass
+    and the 128-thread last-axis passes) with radix-3 and radix-5 factors: 640 x 768 (fine
+    1280 = 40 x 32 and 1536 points), against the oracle on the same nodes."""
+    g = W.Grid((640, 768), (15.0, 16.0))
+    cs, ws = W.three_gaussians_2d(23)
+    rho = W.gaussian_sum(g, cs, ws)
+    P = quadrature.density_P(min(ws), max(g.h))
+    counts = quadrature.default_counts(g.L, P)
+    phi, info = gpu_eval(nl, g, rho, kernel, prec, kmax=P, counts=counts)
+    ref = potential.eval_nufft(rho, g, kernel, P, counts, tol=1e-13)
+    err = cf.rel_linf(phi, ref)
+    print("640 x 768 %s %s: vs oracle %.3e" % (kernel, prec, err))
+    assert err < TOL[prec]
+
+
 SPLIT = {"fp64": dict(eps=1e-16, kappa=5.5), "fp32": dict(eps=1e-8, kappa=3.8)}
 
 
