@@ -409,8 +409,9 @@ def gpu_arm(args):
 
 def batch_arm(args):
     """Batched workload: 64 densities, grids from {64,96,128,160,192}^3, Coulomb or dipolar-z,
-    anisotropic Gaussians (axis ratios in [1,4]), L = 6 a_max, FP32 tol 1e-6, one persistent
-    launch per step replayed from a CUDA graph, spread tiles from the autotuner."""
+    anisotropic Gaussians (axis ratios in [1,4]), L = 6 a_max, FP32 tol 1e-6, one CUDA graph
+    replay per step in the form the batch autotuner keeps (one persistent launch, or the plans'
+    own launches on parallel branches), spread tiles from the autotuner."""
     import torch
     import paper_1410_3584_gb300 as nl
     torch.cuda.set_device(0)
@@ -451,10 +452,32 @@ def batch_arm(args):
     grid_best, tune_ms = nl.nlp_batch_autotune(b, rhos, phis)
     t_btune = time.perf_counter() - t0
     info = nl.nlp_batch_get_info(b)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def time_batch(steps):
+        out = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nl.nlp_batch_eval(b, rhos, phis)
+            e1.record(stream)
+            nl.nlp_batch_sync(b)
+            out.append(e0.elapsed_time(e1))
+        return sum(out) / len(out)
+
+    # each form on its own (the persistent form at the grid and order the autotuner kept)
+    forms = {}
+    for mode, br in (("persistent", 1), ("graph", 1), ("graph", 2), ("graph", 4), ("graph", 8)):
+        nl.nlp_batch_set_mode(b, mode, br)
+        nl.nlp_batch_eval(b, rhos, phis)   # captures the graph form for these pointers
+        nl.nlp_batch_sync(b)
+        forms[mode if mode == "persistent" else "graph_%d_branches" % br] = time_batch(3)
+    nl.nlp_batch_set_mode(b, info["mode"], info["branches"])
     for _ in range(args.warmup):
         nl.nlp_batch_eval(b, rhos, phis)
     nl.nlp_batch_sync(b)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
         with torch.cuda.stream(stream):
@@ -524,12 +547,14 @@ def batch_arm(args):
         p.close()
     tsum = sum(times) / 1e3
     print(json.dumps({
-        "metric": "batched phi=U*rho evals/s (64 mixed 3D densities, one persistent launch)",
+        "metric": "batched phi=U*rho evals/s (64 mixed 3D densities, one graph launch)",
         "value": len(items) * args.steps / tsum, "unit": "evals/s", "batches_per_s": args.steps / tsum,
         "ms_per_batch": 1e3 * tsum / args.steps, "steps": args.steps, "warmup": args.warmup,
         "items": len(items), "nodes_total": nodes, "tasks": info["tasks"], "grid_ctas": info["grid"],
         "smem_bytes": info["smem"], "tiles": tiles, "plan_s": t_plan, "tune_s": t_tune,
-        "batch_autotune": {"grid_default": grid0, "grid_best": grid_best, "order": info["order"], "ms_best": tune_ms, "tune_s": t_btune},
+        "batch_autotune": {"form": info["mode"], "branches": info["branches"], "grid_default": grid0,
+                           "grid_best": grid_best, "order": info["order"], "ms_best": tune_ms, "tune_s": t_btune},
+        "forms_ms": forms,
         "sequential_ms": sum(seq) / len(seq), "sequential_graph_ms": seq_graph,
         "speedup_vs_sequential": (sum(seq) / len(seq)) / (1e3 * tsum / args.steps),
         "max_rel_vs_single_plan": worst_single, "max_rel_vs_oracle_sampled": worst_oracle,

@@ -230,15 +230,26 @@ nlp_status nlp_ts_step(nlp_plan plan, void *psi_dev, const void *V_dev, double b
 
 /* ---------------------------------------------------------------- batched evaluation
  * Many FP32 plans (any mix of grids and of the NLP_COULOMB_3D / NLP_DIPOLE_3D /
- * NLP_COULOMB_2D kernels) evaluated by ONE persistent kernel launch, replayed from a CUDA
- * graph captured at creation.  Work items are (plan, stage, block) tasks taken in a fixed
- * order from a device ticket counter, stage-major (every plan's stage k before any plan's
- * stage k + 1; the default) or item-major (plan by plan; chosen by nlp_batch_autotune when it
- * is faster); a stage of one plan starts when the
- * previous stage of the same plan has completed, which the device checks with a bounded
- * number of polls (NLP_ERR_TIMEOUT if a limit runs out; the batch stays usable).
- * The batch uses the plans' own workspaces: the plans must outlive the batch and must not
- * be evaluated while a batch evaluation is in flight.  Not thread-safe. */
+ * NLP_COULOMB_2D kernels) evaluated by one replay of a CUDA graph, in one of two forms:
+ *
+ * NLP_BATCH_PERSISTENT (the default at creation): the graph holds ONE persistent kernel
+ * launch.  Work items are (plan, stage, block) tasks taken in a fixed order from a device
+ * ticket counter, stage-major (every plan's stage k before any plan's stage k + 1; the
+ * default) or item-major (plan by plan); a stage of one plan starts when the previous stage
+ * of the same plan has completed, which the device checks with a bounded number of polls
+ * (NLP_ERR_TIMEOUT if a limit runs out; the batch stays usable).  Every stage runs at the one
+ * CTA shape (256 threads, the largest stage's shared memory) of the persistent kernel.
+ *
+ * NLP_BATCH_GRAPH: the graph holds every plan's own stage launches (the kernels of
+ * nlp_eval_potential, each at its own CTA shape), the plans spread over B parallel branches
+ * (largest fine grid first, each to the branch with the least work so far); plans of one
+ * branch run one after another.  The launches carry the rho / phi pointers, so an evaluation
+ * with other pointers than the previous one captures the graph again first (the
+ * instantiated graph is updated in place; a few milliseconds for 64 plans).
+ *
+ * nlp_batch_autotune times both forms and keeps the faster.  The batch uses the plans' own
+ * workspaces: the plans must outlive the batch and must not be evaluated while a batch
+ * evaluation is in flight.  Not thread-safe. */
 typedef struct nlp_batch_s *nlp_batch;
 
 /* plans: count FP32 plans of method 0 (NLP_POISSON_2D or another method: NLP_ERR_UNSUPPORTED).  stream: cudaStream_t
@@ -253,23 +264,38 @@ nlp_status nlp_batch_eval(nlp_batch batch, const void *const *rho_dev, void *con
 /* Waits for the last nlp_batch_eval; NLP_ERR_TIMEOUT if a dependency poll ran out. */
 nlp_status nlp_batch_sync(nlp_batch batch);
 
+/* Persistent form: tasks, persistent CTAs and dynamic shared memory per CTA (any may be NULL). */
 nlp_status nlp_batch_get_info(nlp_batch batch, int *tasks, int *grid_ctas, size_t *smem_bytes);
+
+enum { NLP_BATCH_PERSISTENT = 0, NLP_BATCH_GRAPH = 1 };
+
+/* Selects the form of the next nlp_batch_eval: mode NLP_BATCH_PERSISTENT or NLP_BATCH_GRAPH,
+ * branches (1..64, graph form; capped at the number of plans; ignored for the persistent
+ * form).  Waits for an evaluation in flight.  NLP_ERR_INVALID_ARG for other values. */
+nlp_status nlp_batch_set_mode(nlp_batch batch, int mode, int branches);
+
+/* The form in use and the graph form's branch count (branches may be NULL). */
+nlp_status nlp_batch_get_mode(nlp_batch batch, int *mode, int *branches);
 
 /* The task order in use: *item_major = 0 (stage-major) or 1 (item-major). */
 nlp_status nlp_batch_get_order(nlp_batch batch, int *item_major);
 
-/* Autotuner of the batch's own launch: times the graph (4 replays, the first a warm-up) for
- * both task orders and the persistent grid at 1, 2, ... up to the occupancy limit of CTAs per
- * SM on these inputs, and keeps the fastest (the graph is re-captured).  Outputs (may be
- * NULL): *best_grid CTAs, *best_ms per evaluation of the batch; nlp_batch_get_order reports
- * the order kept.  Synchronous; the outputs phi_dev are overwritten. */
+/* Autotuner of the batch's own launch: times the graph (4 replays, the first a warm-up) of
+ * the persistent form for both task orders and the persistent grid at 1, 2, ... up to the
+ * occupancy limit of CTAs per SM, and of the graph form at 1, 2, 4 and 8 branches, on these
+ * inputs, and keeps the fastest form with its settings (the persistent form's best order and
+ * grid are kept as well).  Outputs (may be NULL): *best_grid = the persistent CTAs, or 0 when
+ * the graph form won; *best_ms per evaluation of the batch; nlp_batch_get_mode and
+ * nlp_batch_get_order report what was kept.  Synchronous; the outputs phi_dev are
+ * overwritten. */
 nlp_status nlp_batch_autotune(nlp_batch batch, const void *const *rho_dev, void *const *phi_dev,
                               int *best_grid, double *best_ms);
 
 /* Test hook: set the poll limit of the dependency waits and, if block_item and block_stage
  * are >= 0, make that stage of that item never count as complete, so the stages after it
  * run out of polls (failure injection on the host; the device only sees an unreachable
- * count).  Pass -1, -1 to restore normal operation.  Re-captures the graph. */
+ * count).  Pass -1, -1 to restore normal operation.  Re-captures the graph.  Persistent form
+ * only (the graph form has no polls). */
 nlp_status nlp_batch_set_wait_limit(nlp_batch batch, long long polls, int block_item, int block_stage);
 
 void nlp_batch_destroy(nlp_batch batch);

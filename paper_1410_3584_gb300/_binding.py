@@ -75,6 +75,8 @@ def _load():
         "nlp_batch_autotune": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "nlp_batch_set_wait_limit": ([P, ctypes.c_longlong, I, I], I),
         "nlp_batch_get_order": ([P, ctypes.POINTER(I)], I),
+        "nlp_batch_set_mode": ([P, I, I], I),
+        "nlp_batch_get_mode": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "nlp_batch_destroy": ([P], None),
         "nlp_autotune_tile": ([ctypes.POINTER(nlp_grid), I, I, ctypes.POINTER(nlp_opts), P, ctypes.c_char_p,
                                ctypes.POINTER(I), ctypes.POINTER(D)], I),
@@ -316,12 +318,26 @@ def nlp_batch_get_info(batch) -> dict:
     _check(_lib.nlp_batch_get_info(batch, ctypes.byref(t), ctypes.byref(g), ctypes.byref(sm)), "nlp_batch_get_info")
     o = ctypes.c_int(0)
     _check(_lib.nlp_batch_get_order(batch, ctypes.byref(o)), "nlp_batch_get_order")
-    return {"tasks": t.value, "grid": g.value, "smem": sm.value, "order": "item-major" if o.value else "stage-major"}
+    m, br = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.nlp_batch_get_mode(batch, ctypes.byref(m), ctypes.byref(br)), "nlp_batch_get_mode")
+    return {"tasks": t.value, "grid": g.value, "smem": sm.value, "order": "item-major" if o.value else "stage-major",
+            "mode": BATCH_MODES_BY_ID[m.value], "branches": br.value}
+
+
+BATCH_MODES = {"persistent": 0, "graph": 1}
+BATCH_MODES_BY_ID = {v: k for k, v in BATCH_MODES.items()}
+
+
+def nlp_batch_set_mode(batch, mode: str, branches: int = 1):
+    """'persistent': one persistent kernel launch over all plans' stages; 'graph': the plans'
+    own stage launches as one graph on `branches` parallel branches."""
+    _check(_lib.nlp_batch_set_mode(batch, BATCH_MODES[mode], int(branches)), "nlp_batch_set_mode")
 
 
 def nlp_batch_autotune(batch, rhos, phis):
-    """Pick the task order and the persistent grid of the batch by timing it on these inputs:
-    (grid, ms); nlp_batch_get_info(batch)["order"] reports the order kept."""
+    """Pick the batch's form (persistent kernel: task order and grid; graph of the plans' own
+    launches: branches) by timing it on these inputs: (grid, ms), grid 0 when the graph form
+    won; nlp_batch_get_info(batch) reports the mode, branches and order kept."""
     rp = (ctypes.c_void_p * len(rhos))(*[t.data_ptr() for t in rhos])
     pp = (ctypes.c_void_p * len(phis))(*[t.data_ptr() for t in phis])
     g, ms = ctypes.c_int(0), ctypes.c_double(0.0)

@@ -1,6 +1,13 @@
-// Batched evaluation of many FP32 plans (different grids and kernels) in one persistent
-// launch, replayed from a captured CUDA graph, and the spread-tile autotuner.
+// Batched evaluation of many FP32 plans (different grids and kernels), replayed from a
+// captured CUDA graph, in one of two forms, and the spread-tile autotuner.
 //
+// Persistent form: one launch of a persistent kernel over all plans' stages.
+// Graph form: the plans' own stage launches (the single-plan kernels, each at its own CTA
+// shape and occupancy) as the nodes of one graph, the plans spread over B parallel branches
+// (largest first, each to the branch with the least work so far), so that small plans run
+// side by side and the launch gaps between stages go away.
+//
+// Persistent form in detail:
 // Work is a list of tasks (plan p, stage k, block i) in stage-major order; each CTA of the
 // persistent grid takes the next ticket from a global counter.  Stage k of plan p may run
 // once the last non-empty earlier stage of p has completed all its blocks: the CTA's first
@@ -22,6 +29,8 @@
 #include "spread_dev.cuh"
 
 namespace nlp {
+
+nlp_status eval_any(nlp_plan_s *p, const void *rho, void *phi);
 
 enum { ST_R2C = 0, ST_A1, ST_A0, ST_INTERP, ST_SPREAD, ST_WSUM, ST_COMBINE, ST_B0, ST_B1, ST_C2R, kStages };
 constexpr int kRegLines = 16;          // lines (pairs) per register-engine FFT task: 16 x 16 threads
@@ -190,6 +199,14 @@ struct nlp_batch_s {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev = nullptr;
     bool pending = false;
+    // graph form: branches, their streams and fork/join events, and the graph of the plans'
+    // stage launches for the pointers it was captured with
+    int mode = NLP_BATCH_PERSISTENT, branches = 1;
+    std::vector<cudaStream_t> bstreams;
+    std::vector<cudaEvent_t> bevents;   // [0] fork, [1 + i] join of branch i
+    cudaGraph_t sgraph = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    std::vector<const void *> cap_ptrs;   // rho[count], phi[count] of the captured launches
 };
 
 // Ticket offsets in the batch's order: stage-major (all items' stage k, then stage k + 1: every
@@ -234,11 +251,105 @@ static nlp_status batch_graph(nlp_batch_s *b) {
     return NLP_OK;
 }
 
+// The graph form: the plans' single-plan evaluations captured from B forked streams.  The
+// launches take rho and phi as arguments, so the graph is captured again (and the
+// instantiated graph updated in place) when the pointers change.
+static nlp_status batch_stage_graph(nlp_batch_s *b, const void *const *rho, void *const *phi) {
+    const int B = std::max(1, std::min(b->branches, b->count));
+    while ((int)b->bstreams.size() < B) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return NLP_ERR_CUDA;
+        b->bstreams.push_back(s);
+    }
+    while ((int)b->bevents.size() < B + 1) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return NLP_ERR_CUDA;
+        b->bevents.push_back(e);
+    }
+    // plans to branches: largest fine grid first, each to the least loaded branch
+    std::vector<int> order(b->count), branch(b->count);
+    std::vector<double> load(B, 0.0), work(b->count);
+    for (int p = 0; p < b->count; ++p) {
+        const DevPlan<float> &D = b->plans[p]->pf;
+        work[p] = (double)D.nf[0] * D.nf[1] * D.nf[2];
+        order[p] = p;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    for (int p : order) {
+        const int br = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        branch[p] = br;
+        load[br] += work[p];
+    }
+    cudaStream_t st = b->stream;
+    // relaxed capture: the launchers may set kernel attributes on their first use
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return NLP_ERR_CUDA;
+    nlp_status s = NLP_OK;
+    if (cudaEventRecord(b->bevents[0], st) != cudaSuccess) s = NLP_ERR_CUDA;
+    for (int br = 0; br < B && !s; ++br)
+        if (cudaStreamWaitEvent(b->bstreams[br], b->bevents[0], 0) != cudaSuccess) s = NLP_ERR_CUDA;
+    for (int p : order) {
+        if (s) break;
+        nlp_plan_s *pl = b->plans[p];
+        const cudaStream_t keep = pl->stream;
+        const int keep_timing = pl->timing;
+        pl->stream = b->bstreams[branch[p]];
+        pl->timing = 0;
+        s = eval_any(pl, rho[p], phi[p]);
+        pl->stream = keep;
+        pl->timing = keep_timing;
+    }
+    for (int br = 0; br < B && !s; ++br)
+        if (cudaEventRecord(b->bevents[1 + br], b->bstreams[br]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, b->bevents[1 + br], 0) != cudaSuccess)
+            s = NLP_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (s || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s ? s : NLP_ERR_CUDA;
+    }
+    bool updated = false;
+    if (b->sexec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(b->sexec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->sexec);
+            b->sexec = nullptr;
+        }
+    }
+    if (!updated && cudaGraphInstantiate(&b->sexec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        b->sexec = nullptr;
+        return NLP_ERR_CUDA;
+    }
+    if (b->sgraph) cudaGraphDestroy(b->sgraph);
+    b->sgraph = g;
+    b->cap_ptrs.assign(2 * (size_t)b->count, nullptr);
+    for (int p = 0; p < b->count; ++p) {
+        b->cap_ptrs[p] = rho[p];
+        b->cap_ptrs[b->count + p] = phi[p];
+    }
+    return NLP_OK;
+}
+
+static void drop_stage_graph(nlp_batch_s *b) {
+    if (b->sexec) cudaGraphExecDestroy(b->sexec);
+    if (b->sgraph) cudaGraphDestroy(b->sgraph);
+    b->sexec = nullptr;
+    b->sgraph = nullptr;
+    b->cap_ptrs.clear();
+}
+
 extern "C" {
 
 void nlp_batch_destroy(nlp_batch b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_stage_graph(b);
+    for (cudaStream_t s : b->bstreams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->bevents) cudaEventDestroy(e);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->ev) cudaEventDestroy(b->ev);
@@ -393,6 +504,22 @@ nlp_status nlp_batch_eval(nlp_batch b, const void *const *rho_dev, void *const *
     if (!b || !rho_dev || !phi_dev) return NLP_ERR_INVALID_ARG;
     for (int p = 0; p < b->count; ++p)
         if (!rho_dev[p] || !phi_dev[p]) return NLP_ERR_INVALID_ARG;
+    if (b->mode == NLP_BATCH_GRAPH) {
+        bool same = b->sexec != nullptr;
+        for (int p = 0; p < b->count && same; ++p)
+            same = b->cap_ptrs[p] == rho_dev[p] && b->cap_ptrs[b->count + p] == phi_dev[p];
+        if (!same) {
+            // the instantiated graph is updated in place: no replay of it may be in flight
+            if (b->pending && cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;
+            b->pending = false;
+            nlp_status s = batch_stage_graph(b, rho_dev, phi_dev);
+            if (s) return s;
+        }
+        if (cudaGraphLaunch(b->sexec, b->stream) != cudaSuccess) return NLP_ERR_CUDA;
+        if (cudaEventRecord(b->ev, b->stream) != cudaSuccess) return NLP_ERR_CUDA;
+        b->pending = true;
+        return NLP_OK;
+    }
     if (b->pending) {   // the pinned pointer table may still be read by the previous replay
         if (cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;
         b->pending = false;
@@ -420,6 +547,27 @@ nlp_status nlp_batch_get_order(nlp_batch b, int *item_major) {
     return NLP_OK;
 }
 
+nlp_status nlp_batch_set_mode(nlp_batch b, int mode, int branches) {
+    if (!b || (mode != NLP_BATCH_PERSISTENT && mode != NLP_BATCH_GRAPH) || branches < 1 || branches > 64)
+        return NLP_ERR_INVALID_ARG;
+    if (b->pending && cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;
+    b->pending = false;
+    if (mode == NLP_BATCH_GRAPH && (mode != b->mode || branches != b->branches)) drop_stage_graph(b);
+    b->mode = mode;
+    if (mode == NLP_BATCH_GRAPH) {
+        b->branches = branches;
+        *b->h_err = 0;   // written only by the persistent form's replays
+    }
+    return NLP_OK;
+}
+
+nlp_status nlp_batch_get_mode(nlp_batch b, int *mode, int *branches) {
+    if (!b || !mode) return NLP_ERR_INVALID_ARG;
+    *mode = b->mode;
+    if (branches) *branches = b->branches;
+    return NLP_OK;
+}
+
 nlp_status nlp_batch_get_info(nlp_batch b, int *tasks, int *grid, size_t *smem_bytes) {
     if (!b) return NLP_ERR_INVALID_ARG;
     if (tasks) *tasks = b->total;
@@ -438,11 +586,23 @@ nlp_status nlp_batch_autotune(nlp_batch b, const void *const *rho_dev, void *con
     per = std::max(1, per);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NLP_ERR_CUDA;
-    int best = 0, best_order = 0;
+    int best = 0, best_order = 0, best_mode = NLP_BATCH_PERSISTENT, best_br = 1;
     double bms = 1e300;
     nlp_status s = NLP_OK;
-    // the ticket order, and resident persistent CTAs per SM: every count from one to the
-    // occupancy limit
+    auto time_it = [&](double &tmin) {
+        tmin = 1e300;
+        for (int rep = 0; rep < 4 && s == NLP_OK; ++rep) {
+            cudaEventRecord(e0, b->stream);
+            if ((s = nlp_batch_eval(b, rho_dev, phi_dev))) break;
+            cudaEventRecord(e1, b->stream);
+            if ((s = nlp_batch_sync(b))) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, (double)ms);   // the first replay warms up
+        }
+    };
+    // persistent form: the ticket order, and resident CTAs per SM from one to the occupancy limit
+    b->mode = NLP_BATCH_PERSISTENT;
     for (int kk = 0; kk < 2 * per && s == NLP_OK; ++kk) {
         const int order = kk / per, k = kk % per + 1;
         if (order != b->item_major) {
@@ -456,26 +616,31 @@ nlp_status nlp_batch_autotune(nlp_batch b, const void *const *rho_dev, void *con
         }
         b->grid = sms * k;
         if ((s = batch_graph(b))) break;
-        double tmin = 1e300;
-        for (int rep = 0; rep < 4 && s == NLP_OK; ++rep) {
-            cudaEventRecord(e0, b->stream);
-            if ((s = nlp_batch_eval(b, rho_dev, phi_dev))) break;
-            cudaEventRecord(e1, b->stream);
-            if ((s = nlp_batch_sync(b))) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tmin = std::min(tmin, (double)ms);   // the first replay warms up
-        }
-        if (tmin < bms) {
+        double tmin;
+        time_it(tmin);
+        if (s == NLP_OK && tmin < bms) {
             bms = tmin;
             best = b->grid;
             best_order = b->item_major;
         }
     }
+    // graph form: 1, 2, 4, 8 branches
+    for (int br = 1; br <= 8 && br <= b->count && s == NLP_OK; br *= 2) {
+        if ((s = nlp_batch_set_mode(b, NLP_BATCH_GRAPH, br))) break;
+        double tmin;
+        time_it(tmin);
+        if (s == NLP_OK && tmin < bms) {
+            bms = tmin;
+            best_mode = NLP_BATCH_GRAPH;
+            best_br = br;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s) return s;
-    b->grid = best;
+    // keep the persistent form's best settings (its graph is re-captured) and the best form
+    b->mode = NLP_BATCH_PERSISTENT;
+    b->grid = best ? best : b->grid;
     if (best_order != b->item_major) {
         b->item_major = best_order;
         batch_offsets(b);
@@ -483,7 +648,8 @@ nlp_status nlp_batch_autotune(nlp_batch b, const void *const *rho_dev, void *con
             return NLP_ERR_CUDA;
     }
     if ((s = batch_graph(b))) return s;
-    if (best_grid) *best_grid = best;
+    if (best_mode == NLP_BATCH_GRAPH && (s = nlp_batch_set_mode(b, NLP_BATCH_GRAPH, best_br))) return s;
+    if (best_grid) *best_grid = best_mode == NLP_BATCH_GRAPH ? 0 : best;
     if (best_ms) *best_ms = bms;
     return NLP_OK;
 }

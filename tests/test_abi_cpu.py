@@ -74,6 +74,8 @@ def test_null_handles_rejected(nl):
     assert lib.nlp_batch_sync(None) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_batch_autotune(None, None, None, None, None) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_batch_get_order(None, None) == nl.NLP_ERR_INVALID_ARG
+    assert lib.nlp_batch_set_mode(None, 1, 2) == nl.NLP_ERR_INVALID_ARG
+    assert lib.nlp_batch_get_mode(None, None, None) == nl.NLP_ERR_INVALID_ARG
     lib.nlp_batch_destroy(None)
     assert lib.nlp_surrogate_set_timing(None, 1) == nl.NLP_ERR_INVALID_ARG
     assert lib.nlp_surrogate_get_kernel_times(None, None, None) == nl.NLP_ERR_INVALID_ARG

@@ -90,14 +90,61 @@ def test_batch_autotune_keeps_results(nl):
     b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
     grid, ms = nl.nlp_batch_autotune(b, rhos, phis)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert grid % sms == 0 and grid >= sms and ms > 0
-    assert nl.nlp_batch_get_info(b)["grid"] == grid
+    info = nl.nlp_batch_get_info(b)
+    assert ms > 0
+    if info["mode"] == "graph":
+        assert grid == 0 and info["branches"] in (1, 2, 4)
+    else:
+        assert grid % sms == 0 and grid >= sms and info["grid"] == grid
     for ph in phis:
         ph.zero_()
     nl.nlp_batch_eval(b, rhos, phis)
     nl.nlp_batch_sync(b)
     for ph, ref in zip(phis, refs):
         assert np.max(np.abs(ph.double().cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
+    nl.nlp_batch_destroy(b)
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("branches", [1, 2, 3])
+def test_batch_graph_form_equals_single_plans(nl, branches):
+    """The graph form (the plans' own stage launches on parallel branches of one graph) gives
+    exactly the single-plan results; other rho / phi pointers capture the graph again; a
+    switch back to the persistent form keeps working."""
+    import torch
+    stream = torch.cuda.Stream()
+    plans, rhos, phis, refs, grids = _build(nl, torch, stream)
+    singles = [torch.from_numpy(r).to("cuda", torch.float32) for r in refs]
+    b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
+    nl.nlp_batch_set_mode(b, "graph", branches)
+    info = nl.nlp_batch_get_info(b)
+    assert info["mode"] == "graph" and info["branches"] == branches
+    for rep in range(2):   # capture, then a replay of the same graph
+        for ph in phis:
+            ph.zero_()
+        torch.cuda.synchronize()
+        nl.nlp_batch_eval(b, rhos, phis)
+        nl.nlp_batch_sync(b)
+        for ph, ref in zip(phis, singles):
+            assert torch.equal(ph, ref)
+    scaled = [2.5 * r for r in rhos]
+    out2 = [torch.zeros_like(r) for r in rhos]
+    torch.cuda.synchronize()
+    nl.nlp_batch_eval(b, scaled, out2)   # new pointers: captured again
+    nl.nlp_batch_sync(b)
+    for ph, ref in zip(out2, refs):
+        assert np.max(np.abs(ph.double().cpu().numpy() - 2.5 * ref)) <= 3e-6 * np.max(np.abs(2.5 * ref))
+    nl.nlp_batch_set_mode(b, "persistent")
+    for ph in phis:
+        ph.zero_()
+    torch.cuda.synchronize()
+    nl.nlp_batch_eval(b, rhos, phis)
+    nl.nlp_batch_sync(b)
+    for ph, ref in zip(phis, refs):
+        assert np.max(np.abs(ph.double().cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
+    with pytest.raises(nl.NlpError):
+        nl.nlp_batch_set_mode(b, "graph", 0)
     nl.nlp_batch_destroy(b)
     for p in plans:
         p.close()
@@ -168,14 +215,21 @@ def test_batch_largest_grids_vs_oracle(nl):
         phis.append(torch.zeros_like(r))
         refs.append(potential.eval_nufft(rho, g, it.kernel, P, counts, tol=1e-10))
     b = nl.nlp_batch_create([p.handle for p in plans], stream=stream)
-    nl.nlp_batch_eval(b, rhos, phis)
-    nl.nlp_batch_sync(b)
-    for it, ph, single, ref in zip(pick, phis, singles, refs):
-        out = ph.double().cpu().numpy()
-        e_single, e_batch = cf.rel_linf(single, ref), cf.rel_linf(out, ref)
-        print("%d^3 %s: single plan %.3e, batch %.3e vs oracle" % (it.n, it.kernel, e_single, e_batch))
-        assert e_single < 1e-5 and e_batch < 1e-5
-        assert np.max(np.abs(out - single)) <= 1e-6 * np.max(np.abs(single))
+    for mode in ("persistent", "graph"):
+        nl.nlp_batch_set_mode(b, mode, 2)
+        for ph in phis:
+            ph.zero_()
+        torch.cuda.synchronize()
+        nl.nlp_batch_eval(b, rhos, phis)
+        nl.nlp_batch_sync(b)
+        for it, ph, single, ref in zip(pick, phis, singles, refs):
+            out = ph.double().cpu().numpy()
+            e_single, e_batch = cf.rel_linf(single, ref), cf.rel_linf(out, ref)
+            print("%d^3 %s: single plan %.3e, batch (%s) %.3e vs oracle" % (it.n, it.kernel, e_single, mode, e_batch))
+            assert e_single < 1e-5 and e_batch < 1e-5
+            assert np.max(np.abs(out - single)) <= 1e-6 * np.max(np.abs(single))
+            if mode == "graph":
+                assert np.array_equal(out, single)
     nl.nlp_batch_destroy(b)
     for p in plans:
         p.close()
