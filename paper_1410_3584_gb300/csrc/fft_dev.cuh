@@ -428,6 +428,23 @@ __device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cp
     }
 }
 
+// Lines of 256 points (the 2x upsampled 128-point axes) as two radix-16 passes with the sizes
+// fixed at compile time: the same operations as fft_reg_lines for that factorisation (first
+// pass gsrc -> sA, second pass sA -> gdst), without the run-time radix dispatch.
+template <typename T> __host__ __device__ inline bool len_256(const FftLen<T> &L) {
+    return L.N == 256 && L.nrad_reg == 2 && L.rad_reg[0] == 16 && L.rad_reg[1] == 16;
+}
+template <typename T, int SGN, class GSrc, class GDst, class Idx>
+__device__ __forceinline__ void fft_lines_256(const FftLen<T> &L, cpx<T> *sA, const Idx &idx, int b, int t,
+                                              GSrc &gsrc, GDst &gdst) {
+    auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
+    auto ssrc = [&](int l) { return sA[idx(l, b)]; };
+    reg_pass<T, SGN, 16>(gsrc, sdst, 256, 1, L.tw, t, 16);
+    __syncthreads();
+    reg_pass<T, SGN, 16>(ssrc, gdst, 256, 16, L.tw, t, 16);
+    __syncthreads();
+}
+
 // Strided C2C pass on the register engine: the same operation as k_fft_strided, NBC
 // columns per block, 16 threads per column.  The columns of all outer indices are numbered
 // q = o ncol + c and block bid takes q = bid NBC .. bid NBC + NBC - 1 (a block may span two
@@ -439,7 +456,7 @@ __host__ __device__ inline int64_t cols_blocks(const StridedDesc &d) {
     return ((int64_t)d.nouter * d.ncol + NBC - 1) / NBC;
 }
 
-template <typename T, int SGN, int NBC>
+template <typename T, int SGN, int NBC, bool F256 = false>
 __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int bid,
                                                unsigned char *smraw) {
     const int N = L.N;
@@ -462,13 +479,17 @@ __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &
         if (colok && (l < olo || l >= ohi)) obase[(int64_t)l * d.es] = v;
     };
     auto idx = [](int l, int c) { return l * NBC + c; };
-    fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
+    if constexpr (F256) fft_lines_256<T, SGN>(L, sA, idx, b, t, gsrc, gdst);
+    else fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
 }
 
-template <typename T, int SGN, int NBC>
-__global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
+#ifndef NLP_F256_MINB
+#define NLP_F256_MINB 4
+#endif
+template <typename T, int SGN, int NBC, bool F256 = false>
+__global__ void __launch_bounds__(NBC * 16, F256 ? NLP_F256_MINB : 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fft_cols_block<T, SGN, NBC>(data, d, L, blockIdx.x, smraw);
+    fft_cols_block<T, SGN, NBC, F256>(data, d, L, blockIdx.x, smraw);
 }
 
 // Long column passes (2D: fine axis 1 with N = N1 N2 points, too long for a register-engine
@@ -541,9 +562,10 @@ __host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; 
 // line, so the global loads and stores are contiguous).  The first pass reads rho,
 // deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
 // where the spectra of the two real lines are separated and written as half spectra.
-template <typename T, int NBC, bool kInplace = true, int TPC = 16>
+template <typename T, int NBC, bool kInplace = true, int TPC = 16, bool F256 = false>
 __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
+    static_assert(!F256 || (kInplace && TPC == 16), "the fixed 256-point path transforms in place");
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -564,16 +586,16 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
     cpx<T> *res;
-    if (kInplace && TPC == 16 && r2c_inplace(L)) {
+    if (F256 || (kInplace && TPC == 16 && r2c_inplace(L))) {
         // 256 = 16 x 16: the first pass lands in sA, the second transforms sA in place
         res = sA;
         auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
         auto ssrc = [&](int l) { return sA[idx(l, b)]; };
-        reg_pass<T, -1, 16>(gsrc, sdst, N, 1, L.tw, t, 16);
+        reg_pass<T, -1, 16>(gsrc, sdst, F256 ? 256 : N, 1, L.tw, t, 16);
         __syncthreads();
-        reg_pass_inplace<T, -1, 16>(ssrc, sdst, N, 16, L.tw, t);
+        reg_pass_inplace<T, -1, 16>(ssrc, sdst, F256 ? 256 : N, 16, L.tw, t);
         __syncthreads();
-    } else {
+    } else if constexpr (!F256) {
         res = ((L.nrad_reg - 1) & 1) ? sB : sA;
         auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
         fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
@@ -591,19 +613,20 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     }
 }
 
-template <typename T, int NBC, int TPC = 16>
-__global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+template <typename T, int NBC, int TPC = 16, bool F256 = false>
+__global__ void __launch_bounds__(NBC * TPC, F256 ? NLP_F256_MINB : TPC == 16 ? 4 : 2) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fwd_r2c_reg_block<T, NBC, true, TPC>(rho, P, blockIdx.x, smraw);
+    fwd_r2c_reg_block<T, NBC, true, TPC, F256>(rho, P, blockIdx.x, smraw);
 }
 
 // Inverse C2R along the last axis on the register engine: the same operation as
 // k_inv_c2r.  The first pass reads the half spectra of a line pair from HBM and forms
 // Z = X1 + i X2 on the fly (Z[N - k] = conj(X1[k]) + i conj(X2[k])); the last pass writes
 // the output window, deconvolved, straight to HBM.
-template <typename T, int NBC, int TPC = 16>
+template <typename T, int NBC, int TPC = 16, bool F256 = false>
 __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
+    static_assert(!F256 || TPC == 16, "the fixed 256-point path runs 16 threads a line pair");
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -648,13 +671,14 @@ __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const Dev
         }
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
-    fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
+    if constexpr (F256) fft_lines_256<T, +1>(L, sA, idx, b, t, gsrc, gdst);
+    else fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
 }
 
-template <typename T, int NBC, int TPC = 16>
-__global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
+template <typename T, int NBC, int TPC = 16, bool F256 = false>
+__global__ void __launch_bounds__(NBC * TPC, F256 ? NLP_F256_MINB : TPC == 16 ? 4 : 2) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    inv_c2r_reg_block<T, NBC, TPC>(phi, P, blockIdx.x, smraw);
+    inv_c2r_reg_block<T, NBC, TPC, F256>(phi, P, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ contiguous C2C pass

@@ -69,6 +69,12 @@ template <typename T> static cudaError_t c2r_reg_long(T *phi, const DevPlan<T> &
 template <typename T, int NBC> static cudaError_t r2c_reg(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (r2c_inplace(P.len[2]) ? 1 : 2);
+    if constexpr (NBC == lines_max<T>())
+        if (len_256(P.len[2])) {   // sizes fixed at compile time
+            allow_smem<k_fwd_r2c_reg<T, NBC, 16, true>>();
+            k_fwd_r2c_reg<T, NBC, 16, true><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
+            return cudaGetLastError();
+        }
     allow_smem<k_fwd_r2c_reg<T, NBC>>();
     k_fwd_r2c_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
     return cudaGetLastError();
@@ -76,6 +82,12 @@ template <typename T, int NBC> static cudaError_t r2c_reg(const T *rho, const De
 template <typename T, int NBC> static cudaError_t c2r_reg(T *phi, const DevPlan<T> &P, cudaStream_t st) {
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (P.len[2].nrad_reg > 2 ? 2 : 1);
+    if constexpr (NBC == lines_max<T>())
+        if (len_256(P.len[2])) {
+            allow_smem<k_inv_c2r_reg<T, NBC, 16, true>>();
+            k_inv_c2r_reg<T, NBC, 16, true><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(phi, P);
+            return cudaGetLastError();
+        }
     allow_smem<k_inv_c2r_reg<T, NBC>>();
     k_inv_c2r_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(phi, P);
     return cudaGetLastError();
@@ -84,6 +96,17 @@ template <typename T, int NBC>
 static cudaError_t cols_reg(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign, cudaStream_t st) {
     const size_t sm = sizeof(cpx<T>) * (size_t)L.N * NBC * (L.nrad_reg > 2 ? 2 : 1);
     const unsigned grid = (unsigned)cols_blocks<T, NBC>(d);
+    if constexpr (NBC == lines_max<T>())
+        if (len_256(L)) {
+            if (sign < 0) {
+                allow_smem<k_fft_cols<T, -1, NBC, true>>();
+                k_fft_cols<T, -1, NBC, true><<<grid, NBC * 16, sm, st>>>(data, d, L);
+            } else {
+                allow_smem<k_fft_cols<T, +1, NBC, true>>();
+                k_fft_cols<T, +1, NBC, true><<<grid, NBC * 16, sm, st>>>(data, d, L);
+            }
+            return cudaGetLastError();
+        }
     if (sign < 0) {
         allow_smem<k_fft_cols<T, -1, NBC>>();
         k_fft_cols<T, -1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);
