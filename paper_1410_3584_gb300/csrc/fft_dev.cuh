@@ -2,6 +2,7 @@
 // kernel (batch.cu): small DFTs, the shared-memory Stockham engine and the per-block bodies
 // of the R2C / C2R / strided passes (block index passed explicitly).
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 #include "launch.h"
 
@@ -428,22 +429,58 @@ __device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cp
     }
 }
 
-// Lines of 256 points (the 2x upsampled 128-point axes) as two radix-16 passes with the sizes
-// fixed at compile time: the same operations as fft_reg_lines for that factorisation (first
-// pass gsrc -> sA, second pass sA -> gdst), without the run-time radix dispatch.
-template <typename T> __host__ __device__ inline bool len_256(const FftLen<T> &L) {
-    return L.N == 256 && L.nrad_reg == 2 && L.rad_reg[0] == 16 && L.rad_reg[1] == 16;
-}
-template <typename T, int SGN, class GSrc, class GDst, class Idx>
-__device__ __forceinline__ void fft_lines_256(const FftLen<T> &L, cpx<T> *sA, const Idx &idx, int b, int t,
-                                              GSrc &gsrc, GDst &gdst) {
-    auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
-    auto ssrc = [&](int l) { return sA[idx(l, b)]; };
-    reg_pass<T, SGN, 16>(gsrc, sdst, 256, 1, L.tw, t, 16);
-    __syncthreads();
-    reg_pass<T, SGN, 16>(ssrc, gdst, 256, 16, L.tw, t, 16);
-    __syncthreads();
-}
+// Lines whose register-engine factorisation is fixed at compile time (the upsampled lengths
+// of the common grids): the same passes as fft_reg_lines for that radix sequence (pass s
+// writes (s odd ? sB : sA), the last pass writes through gdst), without the run-time radix
+// dispatch, so the sizes, strides and twiddle steps are constants.  Radices<> is the run-time
+// engine.
+template <int... R> struct Radices {};
+
+template <typename T, int SGN, int N, int Ns, int S, int R, int... Rest> struct FixedPasses {
+    template <class Src, class GDst, class Idx>
+    static __device__ __forceinline__ void run(const cpx<T> *tw, cpx<T> *sA, cpx<T> *sB, const Idx &idx, int b,
+                                               int t, Src &src, GDst &gdst) {
+        if constexpr (sizeof...(Rest) == 0) {
+            reg_pass<T, SGN, R>(src, gdst, N, Ns, tw, t, 16);
+            __syncthreads();
+        } else {
+            cpx<T> *out = (S & 1) ? sB : sA;
+            auto sdst = [&](int l, cpx<T> v) { out[idx(l, b)] = v; };
+            reg_pass<T, SGN, R>(src, sdst, N, Ns, tw, t, 16);
+            __syncthreads();
+            auto ssrc = [&](int l) { return out[idx(l, b)]; };
+            FixedPasses<T, SGN, N, Ns * R, S + 1, Rest...>::run(tw, sA, sB, idx, b, t, ssrc, gdst);
+        }
+    }
+};
+
+template <class FL> struct FixedLen;
+template <int... R> struct FixedLen<Radices<R...>> {
+    static constexpr int npass = (int)sizeof...(R);
+    static constexpr bool on = npass > 0;
+    static constexpr int N = (1 * ... * R);
+    template <typename T> static __host__ __device__ bool match(const FftLen<T> &L) {
+        if constexpr (npass == 0) {
+            return false;
+        } else {
+            constexpr int r[] = {R...};
+            if (L.N != N || L.nrad_reg != npass) return false;
+            for (int i = 0; i < npass; ++i)
+                if (L.rad_reg[i] != r[i]) return false;
+            return true;
+        }
+    }
+    template <typename T, int SGN, class Src, class GDst, class Idx>
+    static __device__ __forceinline__ void lines(const FftLen<T> &L, cpx<T> *sA, cpx<T> *sB, const Idx &idx, int b,
+                                                 int t, Src &src, GDst &gdst) {
+        if constexpr (on) FixedPasses<T, SGN, N, 1, 0, R...>::run(L.tw, sA, sB, idx, b, t, src, gdst);
+    }
+};
+using Rad256 = Radices<16, 16>;
+using Rad128 = Radices<16, 8>;
+using Rad192 = Radices<16, 4, 3>;
+using Rad320 = Radices<16, 4, 5>;
+using Rad384 = Radices<16, 8, 3>;
 
 // Strided C2C pass on the register engine: the same operation as k_fft_strided, NBC
 // columns per block, 16 threads per column.  The columns of all outer indices are numbered
@@ -456,7 +493,7 @@ __host__ __device__ inline int64_t cols_blocks(const StridedDesc &d) {
     return ((int64_t)d.nouter * d.ncol + NBC - 1) / NBC;
 }
 
-template <typename T, int SGN, int NBC, bool F256 = false>
+template <typename T, int SGN, int NBC, class FL = Radices<>>
 __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int bid,
                                                unsigned char *smraw) {
     const int N = L.N;
@@ -479,17 +516,14 @@ __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &
         if (colok && (l < olo || l >= ohi)) obase[(int64_t)l * d.es] = v;
     };
     auto idx = [](int l, int c) { return l * NBC + c; };
-    if constexpr (F256) fft_lines_256<T, SGN>(L, sA, idx, b, t, gsrc, gdst);
+    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, SGN>(L, sA, sB, idx, b, t, gsrc, gdst);
     else fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
 }
 
-#ifndef NLP_F256_MINB
-#define NLP_F256_MINB 4
-#endif
-template <typename T, int SGN, int NBC, bool F256 = false>
-__global__ void __launch_bounds__(NBC * 16, F256 ? NLP_F256_MINB : 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
+template <typename T, int SGN, int NBC, class FL = Radices<>>
+__global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedDesc d, FftLen<T> L) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fft_cols_block<T, SGN, NBC, F256>(data, d, L, blockIdx.x, smraw);
+    fft_cols_block<T, SGN, NBC, FL>(data, d, L, blockIdx.x, smraw);
 }
 
 // Long column passes (2D: fine axis 1 with N = N1 N2 points, too long for a register-engine
@@ -562,10 +596,11 @@ __host__ __device__ __forceinline__ int line_ld(int N) { return N + N / 16 + 1; 
 // line, so the global loads and stores are contiguous).  The first pass reads rho,
 // deconvolved and zero-padded, straight from HBM; the last pass lands in shared memory,
 // where the spectra of the two real lines are separated and written as half spectra.
-template <typename T, int NBC, bool kInplace = true, int TPC = 16, bool F256 = false>
+template <typename T, int NBC, bool kInplace = true, int TPC = 16, class FL = Radices<>>
 __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
-    static_assert(!F256 || (kInplace && TPC == 16), "the fixed 256-point path transforms in place");
+    constexpr bool kFixed = FixedLen<FL>::on;
+    static_assert(!kFixed || (kInplace && TPC == 16), "fixed radix sequences: 16 threads a pair, single-plan kernels");
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -586,16 +621,26 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
     cpx<T> *res;
-    if (F256 || (kInplace && TPC == 16 && r2c_inplace(L))) {
-        // 256 = 16 x 16: the first pass lands in sA, the second transforms sA in place
-        res = sA;
+    // 256 = 16 x 16: the first pass lands in sA, the second transforms sA in place
+    auto inplace256 = [&](int Nn) {
         auto sdst = [&](int l, cpx<T> v) { sA[idx(l, b)] = v; };
         auto ssrc = [&](int l) { return sA[idx(l, b)]; };
-        reg_pass<T, -1, 16>(gsrc, sdst, F256 ? 256 : N, 1, L.tw, t, 16);
+        reg_pass<T, -1, 16>(gsrc, sdst, Nn, 1, L.tw, t, 16);
         __syncthreads();
-        reg_pass_inplace<T, -1, 16>(ssrc, sdst, F256 ? 256 : N, 16, L.tw, t);
+        reg_pass_inplace<T, -1, 16>(ssrc, sdst, Nn, 16, L.tw, t);
         __syncthreads();
-    } else if constexpr (!F256) {
+    };
+    if constexpr (std::is_same<FL, Rad256>::value) {
+        res = sA;
+        inplace256(256);
+    } else if constexpr (kFixed) {
+        res = ((FixedLen<FL>::npass - 1) & 1) ? sB : sA;
+        auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
+        FixedLen<FL>::template lines<T, -1>(L, sA, sB, idx, b, t, gsrc, gdst);
+    } else if (kInplace && TPC == 16 && r2c_inplace(L)) {
+        res = sA;
+        inplace256(N);
+    } else {
         res = ((L.nrad_reg - 1) & 1) ? sB : sA;
         auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
         fft_reg_lines<T, -1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
@@ -613,20 +658,20 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
     }
 }
 
-template <typename T, int NBC, int TPC = 16, bool F256 = false>
-__global__ void __launch_bounds__(NBC * TPC, F256 ? NLP_F256_MINB : TPC == 16 ? 4 : 2) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
+template <typename T, int NBC, int TPC = 16, class FL = Radices<>>
+__global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_fwd_r2c_reg(const T *__restrict__ rho, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fwd_r2c_reg_block<T, NBC, true, TPC, F256>(rho, P, blockIdx.x, smraw);
+    fwd_r2c_reg_block<T, NBC, true, TPC, FL>(rho, P, blockIdx.x, smraw);
 }
 
 // Inverse C2R along the last axis on the register engine: the same operation as
 // k_inv_c2r.  The first pass reads the half spectra of a line pair from HBM and forms
 // Z = X1 + i X2 on the fly (Z[N - k] = conj(X1[k]) + i conj(X2[k])); the last pass writes
 // the output window, deconvolved, straight to HBM.
-template <typename T, int NBC, int TPC = 16, bool F256 = false>
+template <typename T, int NBC, int TPC = 16, class FL = Radices<>>
 __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
-    static_assert(!F256 || TPC == 16, "the fixed 256-point path runs 16 threads a line pair");
+    static_assert(!FixedLen<FL>::on || TPC == 16, "fixed radix sequences run 16 threads a line pair");
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -671,14 +716,14 @@ __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const Dev
         }
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
-    if constexpr (F256) fft_lines_256<T, +1>(L, sA, idx, b, t, gsrc, gdst);
+    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, +1>(L, sA, sB, idx, b, t, gsrc, gdst);
     else fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
 }
 
-template <typename T, int NBC, int TPC = 16, bool F256 = false>
-__global__ void __launch_bounds__(NBC * TPC, F256 ? NLP_F256_MINB : TPC == 16 ? 4 : 2) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
+template <typename T, int NBC, int TPC = 16, class FL = Radices<>>
+__global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_inv_c2r_reg(T *__restrict__ phi, DevPlan<T> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    inv_c2r_reg_block<T, NBC, TPC, F256>(phi, P, blockIdx.x, smraw);
+    inv_c2r_reg_block<T, NBC, TPC, FL>(phi, P, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ contiguous C2C pass

@@ -66,47 +66,75 @@ template <typename T> static cudaError_t c2r_reg_long(T *phi, const DevPlan<T> &
     return cudaGetLastError();
 }
 
+// Calls fn(FL{}) with the radix sequence of L when it has compile-time kernels (FP32: the
+// upsampled lengths 128, 192, 256, 320, 384 of 64^3 ... 192^3 grids; FP64: 256) and returns
+// true; false otherwise.
+template <typename T, class Fn> static bool with_fixed_len(const FftLen<T> &L, Fn &&fn) {
+    if (FixedLen<Rad256>::match(L)) { fn(Rad256{}); return true; }
+    if constexpr (sizeof(T) == 4) {
+        if (FixedLen<Rad128>::match(L)) { fn(Rad128{}); return true; }
+        if (FixedLen<Rad192>::match(L)) { fn(Rad192{}); return true; }
+        if (FixedLen<Rad320>::match(L)) { fn(Rad320{}); return true; }
+        if (FixedLen<Rad384>::match(L)) { fn(Rad384{}); return true; }
+    }
+    return false;
+}
+
 template <typename T, int NBC> static cudaError_t r2c_reg(const T *rho, const DevPlan<T> &P, cudaStream_t st) {
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (r2c_inplace(P.len[2]) ? 1 : 2);
-    if constexpr (NBC == lines_max<T>())
-        if (len_256(P.len[2])) {   // sizes fixed at compile time
-            allow_smem<k_fwd_r2c_reg<T, NBC, 16, true>>();
-            k_fwd_r2c_reg<T, NBC, 16, true><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
-            return cudaGetLastError();
-        }
+    const unsigned grid = (unsigned)((npairs + NBC - 1) / NBC);
+    if constexpr (NBC == lines_max<T>()) {   // sizes fixed at compile time
+        cudaError_t e = cudaSuccess;
+        if (with_fixed_len(P.len[2], [&](auto fl) {
+                using FL = decltype(fl);
+                allow_smem<k_fwd_r2c_reg<T, NBC, 16, FL>>();
+                k_fwd_r2c_reg<T, NBC, 16, FL><<<grid, NBC * 16, sm, st>>>(rho, P);
+                e = cudaGetLastError();
+            }))
+            return e;
+    }
     allow_smem<k_fwd_r2c_reg<T, NBC>>();
-    k_fwd_r2c_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(rho, P);
+    k_fwd_r2c_reg<T, NBC><<<grid, NBC * 16, sm, st>>>(rho, P);
     return cudaGetLastError();
 }
 template <typename T, int NBC> static cudaError_t c2r_reg(T *phi, const DevPlan<T> &P, cudaStream_t st) {
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * (P.len[2].nrad_reg > 2 ? 2 : 1);
-    if constexpr (NBC == lines_max<T>())
-        if (len_256(P.len[2])) {
-            allow_smem<k_inv_c2r_reg<T, NBC, 16, true>>();
-            k_inv_c2r_reg<T, NBC, 16, true><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(phi, P);
-            return cudaGetLastError();
-        }
+    const unsigned grid = (unsigned)((npairs + NBC - 1) / NBC);
+    if constexpr (NBC == lines_max<T>()) {
+        cudaError_t e = cudaSuccess;
+        if (with_fixed_len(P.len[2], [&](auto fl) {
+                using FL = decltype(fl);
+                allow_smem<k_inv_c2r_reg<T, NBC, 16, FL>>();
+                k_inv_c2r_reg<T, NBC, 16, FL><<<grid, NBC * 16, sm, st>>>(phi, P);
+                e = cudaGetLastError();
+            }))
+            return e;
+    }
     allow_smem<k_inv_c2r_reg<T, NBC>>();
-    k_inv_c2r_reg<T, NBC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * 16, sm, st>>>(phi, P);
+    k_inv_c2r_reg<T, NBC><<<grid, NBC * 16, sm, st>>>(phi, P);
     return cudaGetLastError();
 }
 template <typename T, int NBC>
 static cudaError_t cols_reg(cpx<T> *data, const StridedDesc &d, const FftLen<T> &L, int sign, cudaStream_t st) {
     const size_t sm = sizeof(cpx<T>) * (size_t)L.N * NBC * (L.nrad_reg > 2 ? 2 : 1);
     const unsigned grid = (unsigned)cols_blocks<T, NBC>(d);
-    if constexpr (NBC == lines_max<T>())
-        if (len_256(L)) {
-            if (sign < 0) {
-                allow_smem<k_fft_cols<T, -1, NBC, true>>();
-                k_fft_cols<T, -1, NBC, true><<<grid, NBC * 16, sm, st>>>(data, d, L);
-            } else {
-                allow_smem<k_fft_cols<T, +1, NBC, true>>();
-                k_fft_cols<T, +1, NBC, true><<<grid, NBC * 16, sm, st>>>(data, d, L);
-            }
-            return cudaGetLastError();
-        }
+    if constexpr (NBC == lines_max<T>()) {
+        cudaError_t e = cudaSuccess;
+        if (with_fixed_len(L, [&](auto fl) {
+                using FL = decltype(fl);
+                if (sign < 0) {
+                    allow_smem<k_fft_cols<T, -1, NBC, FL>>();
+                    k_fft_cols<T, -1, NBC, FL><<<grid, NBC * 16, sm, st>>>(data, d, L);
+                } else {
+                    allow_smem<k_fft_cols<T, +1, NBC, FL>>();
+                    k_fft_cols<T, +1, NBC, FL><<<grid, NBC * 16, sm, st>>>(data, d, L);
+                }
+                e = cudaGetLastError();
+            }))
+            return e;
+    }
     if (sign < 0) {
         allow_smem<k_fft_cols<T, -1, NBC>>();
         k_fft_cols<T, -1, NBC><<<grid, NBC * 16, sm, st>>>(data, d, L);
