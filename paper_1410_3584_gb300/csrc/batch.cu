@@ -451,6 +451,7 @@ nlp_status nlp_batch_create(const nlp_plan *plans, int count, void *stream, nlp_
             if (three) smem = std::max(smem, fft_bytes(D.len[0].N, B.nb_a0));
         }
         smem = std::max(smem, B.spread_warp ? interp_spread_reg_smem<float>(D, 8) : interp_spread_smem<float>(D, 8));
+        smem = std::max(smem, window_sum_smem<float>());
     }
     b->smem = smem;
     // Stages run in this order per item, so the window slots and G are never rewritten while

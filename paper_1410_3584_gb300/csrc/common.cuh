@@ -9,6 +9,11 @@
 
 namespace nlp {
 
+// window cells per 256-thread block of the window-sum pass (spread_common.cuh): FP32 64 cells
+// with the members in 4 subsets (chunks of 2048 nodes: few, long member lists), FP64 256 cells
+// read in member order (chunks of 256 nodes: many short lists)
+template <typename T> constexpr int wsum_cells() { return sizeof(T) == 4 ? 64 : 256; }
+
 // ---------------------------------------------------------------- complex arithmetic
 template <typename T> struct cpx;
 template <> struct __align__(8) cpx<float> { float x, y; };
@@ -111,7 +116,7 @@ template <typename T> struct DevPlan {
     const int *grp;         // tiles split into several chunks: {first, count} into grp_list, per group
     const int *grp_list;    // slots of each such tile, ascending; the first one receives their sum
     int64_t ngroups;
-    int grp_parts;          // window-sum tasks per group (256-cell parts of the window)
+    int grp_parts;          // window-sum tasks per group (wsum_cells<T>() cells of the window each)
     const int *cmb_off;     // per combine tile: its entries are cmb[cmb_off[t] .. cmb_off[t+1])
     const CombEntry *cmb;
     int cmb_t[3];       // combine tile edge per axis

@@ -233,7 +233,7 @@ static nlp_status build_combine(nlp_plan_s *p, DevPlan<T> &D, const std::vector<
         i = k;
     }
     D.ngroups = (int64_t)grp.size() / 2;
-    D.grp_parts = (int)((D.win_cells + 255) / 256);
+    D.grp_parts = (int)((D.win_cells + wsum_cells<T>() - 1) / wsum_cells<T>());
     D.grp = nullptr;
     D.grp_list = nullptr;
     if (D.ngroups > 0) {

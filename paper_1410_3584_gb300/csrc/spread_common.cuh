@@ -88,26 +88,36 @@ __device__ __forceinline__ T window_fill(const DevPlan<T> &P, const WinCol &k, c
 // ------------------------------------------------------------------ combine
 // Tiles with many nodes are split into several chunks, whose windows share the tile's origin.
 // First pass (window_sum_block): per such tile, the windows of its chunks are added cell by
-// cell, in slot order, into its first slot.  Part p of group g covers window cells
-// [256 p, 256 p + 256).
+// cell into its first slot.  Part p of group g covers window cells [C p, C p + C),
+// C = wsum_cells<T>(); of the 256 threads of a block, thread (s, c) takes cell C p + c and the
+// members of subset s (members s, s + S, s + 2S, ... in order, S = 256 / C), so that a heavy
+// group (the FP32 tile at k = 0 holds up to ~150 chunks) is read with S times the loads in
+// flight; the S partial sums of a cell are then added in subset order (S = 1: one sum in
+// member order).  Shared memory: 256 member offsets, then (S - 1) C partial sums.
+template <typename T> constexpr size_t window_sum_smem() {
+    return 256 * sizeof(long long) + (size_t)(256 / wsum_cells<T>() - 1) * wsum_cells<T>() * sizeof(cpx<T>);
+}
+
 template <typename T>
 __device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t task, long long *sb) {
+    constexpr int C = wsum_cells<T>(), S = 256 / C;
     const int64_t g = task / P.grp_parts;
-    const int64_t q = (task % P.grp_parts) * 256 + threadIdx.x;
+    const int c = threadIdx.x % C, sub = threadIdx.x / C;
+    const int64_t q = (task % P.grp_parts) * C + c;
     const bool act = q < P.win_cells && threadIdx.x < 256;
     const int first = P.grp[2 * g], count = P.grp[2 * g + 1];
     T sx = (T)0, sy = (T)0;
-    // the members' slot offsets, staged 256 at a time
+    // the members' slot offsets, staged 256 at a time (a multiple of S: subsets stay aligned)
     for (int m0 = 0; m0 < count; m0 += 256) {
         const int mc = min(256, count - m0);
         __syncthreads();
         for (int i = threadIdx.x; i < mc; i += blockDim.x) sb[i] = (long long)P.grp_list[first + m0 + i] * P.win_cells;
         __syncthreads();
         if (!act) continue;
-        for (int i = 0; i < mc; i += 16) {
+        for (int i = sub; i < mc; i += 16 * S) {
             cpx<T> v[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) v[u] = (i + u < mc) ? P.win[sb[i + u] + q] : mk<T>(0, 0);
+            for (int u = 0; u < 16; ++u) v[u] = (i + S * u < mc) ? P.win[sb[i + S * u] + q] : mk<T>(0, 0);
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 sx += v[u].x;
@@ -115,7 +125,21 @@ __device__ __forceinline__ void window_sum_block(const DevPlan<T> &P, int64_t ta
             }
         }
     }
-    if (act) P.win[(long long)P.grp_list[first] * P.win_cells + q] = mk<T>(sx, sy);
+    if constexpr (S > 1) {
+        cpx<T> *red = reinterpret_cast<cpx<T> *>(sb + 256);
+        __syncthreads();
+        if (act && sub > 0) red[(sub - 1) * C + c] = mk<T>(sx, sy);
+        __syncthreads();
+        if (act && sub == 0) {
+#pragma unroll
+            for (int k = 0; k < S - 1; ++k) {
+                const cpx<T> r = red[k * C + c];
+                sx += r.x;
+                sy += r.y;
+            }
+        }
+    }
+    if (act && sub == 0) P.win[(long long)P.grp_list[first] * P.win_cells + q] = mk<T>(sx, sy);
 }
 
 // Second pass: output tile t = (t0, t1, t2) covers cells [t_d T_d, min((t_d + 1) T_d, N_d)) of G

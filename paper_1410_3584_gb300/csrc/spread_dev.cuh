@@ -270,6 +270,23 @@ __device__ __forceinline__ float es_fast(float i_f, float d, float c2w, float nb
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// es_fast for two values at once: the same operations, the FP32 ones as packed FP32x2 (each
+// lane of a packed operation rounds as the scalar one), the approximations per value.
+__device__ __forceinline__ float2 es_fast2(float2 i_f, float2 d, float c2w, float nbl2) {
+    const float2 x = __fmul2_rn(__fadd2_rn(i_f, f2(-d.x, -d.y)), f2(c2w, c2w));
+    const float2 s = __ffma2_rn(f2(-x.x, -x.y), x, f2(1.0f, 1.0f));
+    float2 rs, rd, e;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.x) : "f"(s.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.y) : "f"(s.y));
+    const float2 den = __ffma2_rn(s, rs, f2(1.0f, 1.0f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd.x) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd.y) : "f"(den.y));
+    const float2 arg = __fmul2_rn(__fmul2_rn(x, __fmul2_rn(x, f2(nbl2, nbl2))), rd);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(arg.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(arg.y));
+    return f2(s.x > 0.0f ? e.x : 0.0f, s.y > 0.0f ? e.y : 0.0f);
+}
+
 // power-of-two quantum q = 2^(e - 30) for a bound B (1.01 B < 2^e); 2^-126 floor; NaN bound -> NaN
 __device__ __forceinline__ void fixed_quantum(float B, float &q, float &qinv) {
     B *= 1.01f;
@@ -337,10 +354,16 @@ template <int W, int NB> struct WarpLane {
         for (int u = 0; u < KR; ++u) pd[u] = base[kv_fo[u]];
     }
     __device__ __forceinline__ void evaluate(const float (&pd)[KR], float *stage) const {
+        // rounds in pairs (packed arithmetic), an odd last round alone
 #pragma unroll
-        for (int u = 0; u < KR; ++u) {
-            const float e = es_fast(kv_t[u], pd[u], c2w, nbl2);
-            *reinterpret_cast<float2 *>(stage + kv_st[u]) = f2(e, e);
+        for (int u = 0; u + 1 < KR; u += 2) {
+            const float2 e = es_fast2(f2(kv_t[u], kv_t[u + 1]), f2(pd[u], pd[u + 1]), c2w, nbl2);
+            *reinterpret_cast<float2 *>(stage + kv_st[u]) = f2(e.x, e.x);
+            *reinterpret_cast<float2 *>(stage + kv_st[u + 1]) = f2(e.y, e.y);
+        }
+        if constexpr (KR % 2) {
+            const float e = es_fast(kv_t[KR - 1], pd[KR - 1], c2w, nbl2);
+            *reinterpret_cast<float2 *>(stage + kv_st[KR - 1]) = f2(e, e);
         }
     }
     // x/y weights (w, w) of the lane's two columns for node k of the stage
@@ -649,15 +672,18 @@ __device__ __forceinline__ void spread_warp_block(const DevPlan<float> &P, int b
         const int ga0 = (so0 + ln.xa) * L.SG + (so1 + ln.ya) * L.RG + so2;
         const int gb0 = (so0 + ln.xb) * L.SG + (so1 + ln.yb) * L.RG + so2;
         int *pa = &sG[ga0].x + sw, *pb = &sG[gb0].x + sw;
+        const float2 qi2 = f2(q2inv, q2inv);
 #pragma unroll
         for (int z = 0; z < W; ++z) {
             if (ln.act_a) {
-                const int re = __float2int_rn(ga[z].x * q2inv), im = __float2int_rn(ga[z].y * q2inv);
+                const float2 u = __fmul2_rn(ga[z], qi2);
+                const int re = __float2int_rn(u.x), im = __float2int_rn(u.y);
                 atomicAdd(pa + 2 * z, sw ? im : re);
                 atomicAdd(pa + 2 * z + 1 - 2 * sw, sw ? re : im);
             }
             if (ln.act_b) {
-                const int re = __float2int_rn(gb[z].x * q2inv), im = __float2int_rn(gb[z].y * q2inv);
+                const float2 u = __fmul2_rn(gb[z], qi2);
+                const int re = __float2int_rn(u.x), im = __float2int_rn(u.y);
                 atomicAdd(pb + 2 * z, sw ? im : re);
                 atomicAdd(pb + 2 * z + 1 - 2 * sw, sw ? re : im);
             }

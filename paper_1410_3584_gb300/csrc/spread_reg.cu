@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kWarpBlock, NLP_WARP_MINB) k_spread_warp(DevPl
 }
 
 template <typename T> __global__ void __launch_bounds__(256) k_window_sum(DevPlan<T> P) {
-    __shared__ long long sb[256];
+    __shared__ __align__(16) long long sb[window_sum_smem<T>() / sizeof(long long)];
     window_sum_block<T>(P, blockIdx.x, sb);
 }
 
