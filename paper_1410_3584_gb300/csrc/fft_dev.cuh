@@ -436,20 +436,20 @@ __device__ __forceinline__ void fft_reg_lines(const FftLen<T> &L, cpx<T> *sA, cp
 // engine.
 template <int... R> struct Radices {};
 
-template <typename T, int SGN, int N, int Ns, int S, int R, int... Rest> struct FixedPasses {
+template <typename T, int SGN, int TPC, int N, int Ns, int S, int R, int... Rest> struct FixedPasses {
     template <class Src, class GDst, class Idx>
     static __device__ __forceinline__ void run(const cpx<T> *tw, cpx<T> *sA, cpx<T> *sB, const Idx &idx, int b,
                                                int t, Src &src, GDst &gdst) {
         if constexpr (sizeof...(Rest) == 0) {
-            reg_pass<T, SGN, R>(src, gdst, N, Ns, tw, t, 16);
+            reg_pass<T, SGN, R>(src, gdst, N, Ns, tw, t, TPC);
             __syncthreads();
         } else {
             cpx<T> *out = (S & 1) ? sB : sA;
             auto sdst = [&](int l, cpx<T> v) { out[idx(l, b)] = v; };
-            reg_pass<T, SGN, R>(src, sdst, N, Ns, tw, t, 16);
+            reg_pass<T, SGN, R>(src, sdst, N, Ns, tw, t, TPC);
             __syncthreads();
             auto ssrc = [&](int l) { return out[idx(l, b)]; };
-            FixedPasses<T, SGN, N, Ns * R, S + 1, Rest...>::run(tw, sA, sB, idx, b, t, ssrc, gdst);
+            FixedPasses<T, SGN, TPC, N, Ns * R, S + 1, Rest...>::run(tw, sA, sB, idx, b, t, ssrc, gdst);
         }
     }
 };
@@ -470,10 +470,11 @@ template <int... R> struct FixedLen<Radices<R...>> {
             return true;
         }
     }
-    template <typename T, int SGN, class Src, class GDst, class Idx>
+    // TPC threads a line (the thread index t < TPC)
+    template <typename T, int SGN, int TPC, class Src, class GDst, class Idx>
     static __device__ __forceinline__ void lines(const FftLen<T> &L, cpx<T> *sA, cpx<T> *sB, const Idx &idx, int b,
                                                  int t, Src &src, GDst &gdst) {
-        if constexpr (on) FixedPasses<T, SGN, N, 1, 0, R...>::run(L.tw, sA, sB, idx, b, t, src, gdst);
+        if constexpr (on) FixedPasses<T, SGN, TPC, N, 1, 0, R...>::run(L.tw, sA, sB, idx, b, t, src, gdst);
     }
 };
 using Rad256 = Radices<16, 16>;
@@ -481,6 +482,9 @@ using Rad128 = Radices<16, 8>;
 using Rad192 = Radices<16, 4, 3>;
 using Rad320 = Radices<16, 4, 5>;
 using Rad384 = Radices<16, 8, 3>;
+using Rad2048 = Radices<16, 16, 8>;   // 2D 1024^2: last axis (128 threads a line pair)
+using Rad64 = Radices<16, 4>;         // 2D four-step sub-lines
+using Rad32 = Radices<16, 2>;
 
 // Strided C2C pass on the register engine: the same operation as k_fft_strided, NBC
 // columns per block, 16 threads per column.  The columns of all outer indices are numbered
@@ -516,7 +520,7 @@ __device__ __forceinline__ void fft_cols_block(cpx<T> *data, const StridedDesc &
         if (colok && (l < olo || l >= ohi)) obase[(int64_t)l * d.es] = v;
     };
     auto idx = [](int l, int c) { return l * NBC + c; };
-    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, SGN>(L, sA, sB, idx, b, t, gsrc, gdst);
+    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, SGN, 16>(L, sA, sB, idx, b, t, gsrc, gdst);
     else fft_reg_lines<T, SGN>(L, sA, sB, idx, b, t, 16, gsrc, gdst);
 }
 
@@ -538,7 +542,7 @@ __global__ void __launch_bounds__(NBC * 16, 4) k_fft_cols(cpx<T> *data, StridedD
 // Block: NBC of the (sub-line, column) pairs q = s ncol + c, TPC threads each (the sub-lines
 // are short: TPC ~ N_sub / 16 keeps the threads of a radix-16 pass busy and a block's
 // columns one long coalesced row); 2D descriptors only (one outer line).
-template <typename T, int SGN, int NBC, int TPC, int STEP>
+template <typename T, int SGN, int NBC, int TPC, int STEP, class FL = Radices<>>
 __device__ __forceinline__ void fft_four_block(const cpx<T> *in, cpx<T> *out, const StridedDesc &d,
                                                const FftLen<T> &L, const FftLen<T> &Ls, int N1, int N2, int bid,
                                                unsigned char *smraw) {
@@ -571,14 +575,16 @@ __device__ __forceinline__ void fft_four_block(const cpx<T> *in, cpx<T> *out, co
         }
     };
     auto idx = [](int l, int cc) { return l * NBC + cc; };
-    fft_reg_lines<T, SGN>(Ls, sA, sB, idx, b, t, TPC, gsrc, gdst);
+    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, SGN, TPC>(Ls, sA, sB, idx, b, t, gsrc, gdst);
+    else fft_reg_lines<T, SGN>(Ls, sA, sB, idx, b, t, TPC, gsrc, gdst);
 }
 
-template <typename T, int SGN, int NBC, int TPC, int STEP>
-__global__ void __launch_bounds__(NBC * TPC, 2) k_fft_four(const cpx<T> *in, cpx<T> *out, StridedDesc d, FftLen<T> L,
-                                                         FftLen<T> Ls, int N1, int N2) {
+template <typename T, int SGN, int NBC, int TPC, int STEP, class FL = Radices<>>
+__global__ void __launch_bounds__(NBC * TPC, FixedLen<FL>::on ? 4 : 2) k_fft_four(const cpx<T> *in, cpx<T> *out,
+                                                                                 StridedDesc d, FftLen<T> L,
+                                                                                 FftLen<T> Ls, int N1, int N2) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fft_four_block<T, SGN, NBC, TPC, STEP>(in, out, d, L, Ls, N1, N2, blockIdx.x, smraw);
+    fft_four_block<T, SGN, NBC, TPC, STEP, FL>(in, out, d, L, Ls, N1, N2, blockIdx.x, smraw);
 }
 
 // shared-memory bytes of the register-engine passes for line length N
@@ -600,7 +606,7 @@ template <typename T, int NBC, bool kInplace = true, int TPC = 16, class FL = Ra
 __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
     constexpr bool kFixed = FixedLen<FL>::on;
-    static_assert(!kFixed || (kInplace && TPC == 16), "fixed radix sequences: 16 threads a pair, single-plan kernels");
+    static_assert(!kFixed || kInplace, "fixed radix sequences: single-plan kernels");
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -630,13 +636,13 @@ __device__ __forceinline__ void fwd_r2c_reg_block(const T *__restrict__ rho, con
         reg_pass_inplace<T, -1, 16>(ssrc, sdst, Nn, 16, L.tw, t);
         __syncthreads();
     };
-    if constexpr (std::is_same<FL, Rad256>::value) {
+    if constexpr (std::is_same<FL, Rad256>::value && TPC == 16) {
         res = sA;
         inplace256(256);
     } else if constexpr (kFixed) {
         res = ((FixedLen<FL>::npass - 1) & 1) ? sB : sA;
         auto gdst = [&](int l, cpx<T> v) { res[idx(l, b)] = v; };
-        FixedLen<FL>::template lines<T, -1>(L, sA, sB, idx, b, t, gsrc, gdst);
+        FixedLen<FL>::template lines<T, -1, TPC>(L, sA, sB, idx, b, t, gsrc, gdst);
     } else if (kInplace && TPC == 16 && r2c_inplace(L)) {
         res = sA;
         inplace256(N);
@@ -671,7 +677,7 @@ __global__ void __launch_bounds__(NBC * TPC, TPC == 16 ? 4 : 2) k_fwd_r2c_reg(co
 template <typename T, int NBC, int TPC = 16, class FL = Radices<>>
 __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const DevPlan<T> &P, int bid,
                                                   unsigned char *smraw) {
-    static_assert(!FixedLen<FL>::on || TPC == 16, "fixed radix sequences run 16 threads a line pair");
+
     const FftLen<T> &L = P.len[2];
     const int N = L.N, n2 = P.n[2], nh = P.nh, LDL = line_ld(N);
     cpx<T> *sA = (cpx<T> *)smraw;
@@ -716,7 +722,7 @@ __device__ __forceinline__ void inv_c2r_reg_block(T *__restrict__ phi, const Dev
         }
     };
     auto idx = [LDL](int l, int c) { return c * LDL + l + (l >> 4); };
-    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, +1>(L, sA, sB, idx, b, t, gsrc, gdst);
+    if constexpr (FixedLen<FL>::on) FixedLen<FL>::template lines<T, +1, TPC>(L, sA, sB, idx, b, t, gsrc, gdst);
     else fft_reg_lines<T, +1>(L, sA, sB, idx, b, t, TPC, gsrc, gdst);
 }
 

@@ -53,6 +53,11 @@ template <typename T> static cudaError_t r2c_reg_long(const T *rho, const DevPla
     constexpr int NBC = long_pairs<T>(), TPC = 128;
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+    if (FixedLen<Rad2048>::match(P.len[2])) {   // radix sequence fixed at compile time
+        allow_smem<k_fwd_r2c_reg<T, NBC, TPC, Rad2048>>();
+        k_fwd_r2c_reg<T, NBC, TPC, Rad2048><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * TPC, sm, st>>>(rho, P);
+        return cudaGetLastError();
+    }
     allow_smem<k_fwd_r2c_reg<T, NBC, TPC>>();
     k_fwd_r2c_reg<T, NBC, TPC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * TPC, sm, st>>>(rho, P);
     return cudaGetLastError();
@@ -61,6 +66,11 @@ template <typename T> static cudaError_t c2r_reg_long(T *phi, const DevPlan<T> &
     constexpr int NBC = long_pairs<T>(), TPC = 128;
     const int64_t npairs = (int64_t)P.n[0] * P.n[1] / 2;
     const size_t sm = sizeof(cpx<T>) * (size_t)NBC * line_ld(P.len[2].N) * 2;
+    if (FixedLen<Rad2048>::match(P.len[2])) {
+        allow_smem<k_inv_c2r_reg<T, NBC, TPC, Rad2048>>();
+        k_inv_c2r_reg<T, NBC, TPC, Rad2048><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * TPC, sm, st>>>(phi, P);
+        return cudaGetLastError();
+    }
     allow_smem<k_inv_c2r_reg<T, NBC, TPC>>();
     k_inv_c2r_reg<T, NBC, TPC><<<(unsigned)((npairs + NBC - 1) / NBC), NBC * TPC, sm, st>>>(phi, P);
     return cudaGetLastError();
@@ -236,6 +246,20 @@ static cudaError_t four_step_tpc(const cpx<T> *in, cpx<T> *out, const StridedDes
     const int N1 = D.len4[0].N, N2 = D.len4[1].N;
     const int64_t cols = (int64_t)(STEP == 1 ? N2 : N1) * d.ncol;
     const size_t sm = cols_smem_bytes<T>(Ls, NBC);
+    const unsigned grid = (unsigned)((cols + NBC - 1) / NBC);
+    // sub-lines with a compile-time radix sequence: 64 points (step 1) and 32 points (either step)
+    if constexpr (TPC == 4 && STEP == 1)
+        if (FixedLen<Rad64>::match(Ls)) {
+            allow_smem<k_fft_four<T, SGN, NBC, TPC, STEP, Rad64>>();
+            k_fft_four<T, SGN, NBC, TPC, STEP, Rad64><<<grid, 256, sm, st>>>(in, out, d, D.len[1], Ls, N1, N2);
+            return cudaGetLastError();
+        }
+    if constexpr (TPC == 2)
+        if (FixedLen<Rad32>::match(Ls)) {
+            allow_smem<k_fft_four<T, SGN, NBC, TPC, STEP, Rad32>>();
+            k_fft_four<T, SGN, NBC, TPC, STEP, Rad32><<<grid, 256, sm, st>>>(in, out, d, D.len[1], Ls, N1, N2);
+            return cudaGetLastError();
+        }
     allow_smem<k_fft_four<T, SGN, NBC, TPC, STEP>>();
     k_fft_four<T, SGN, NBC, TPC, STEP><<<(unsigned)((cols + NBC - 1) / NBC), 256, sm, st>>>(in, out, d, D.len[1], Ls,
                                                                                           N1, N2);
