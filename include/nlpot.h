@@ -270,8 +270,9 @@ nlp_status nlp_batch_get_info(nlp_batch batch, int *tasks, int *grid_ctas, size_
 enum { NLP_BATCH_PERSISTENT = 0, NLP_BATCH_GRAPH = 1 };
 
 /* Selects the form of the next nlp_batch_eval: mode NLP_BATCH_PERSISTENT or NLP_BATCH_GRAPH,
- * branches (1..64, graph form; capped at the number of plans; ignored for the persistent
- * form).  Waits for an evaluation in flight.  NLP_ERR_INVALID_ARG for other values. */
+ * branches (graph form: 1..64, capped at the number of plans; ignored for the persistent
+ * form).  Waits for an evaluation in flight.  NLP_ERR_INVALID_ARG for another mode or, in the
+ * graph form, another branch count. */
 nlp_status nlp_batch_set_mode(nlp_batch batch, int mode, int branches);
 
 /* The form in use and the graph form's branch count (branches may be NULL). */

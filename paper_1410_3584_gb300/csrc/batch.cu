@@ -549,7 +549,8 @@ nlp_status nlp_batch_get_order(nlp_batch b, int *item_major) {
 }
 
 nlp_status nlp_batch_set_mode(nlp_batch b, int mode, int branches) {
-    if (!b || (mode != NLP_BATCH_PERSISTENT && mode != NLP_BATCH_GRAPH) || branches < 1 || branches > 64)
+    if (!b || (mode != NLP_BATCH_PERSISTENT && mode != NLP_BATCH_GRAPH) ||
+        (mode == NLP_BATCH_GRAPH && (branches < 1 || branches > 64)))
         return NLP_ERR_INVALID_ARG;
     if (b->pending && cudaEventSynchronize(b->ev) != cudaSuccess) return NLP_ERR_CUDA;
     b->pending = false;
